@@ -1,0 +1,373 @@
+"""FP64 oracle: joint time-frequency scattering, JTFS loss and its gradient.
+
+TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.  The product path
+never imports this module.
+
+What it computes (Lostanlen & Han, "Musical Metamerism with Time-Frequency
+Scattering"):
+
+* Filterbanks: the generator of §3.1 (constant-Q progression down to an
+  elbow, then Q-1 constant-bandwidth filters), used for the first-order time
+  filters (J, Q), the second-order time filters (J, Q2) and the frequential
+  filters (J_fr, Q_fr), the latter spun to +xi and -xi (§3.4).
+* Morlet wavelets of Eq. (1) in the Fourier domain, with the corrective term
+  kappa giving a null average; Gaussian low-pass phi_T, phi_F (§2.1, §2.2).
+* The multirate schedule of §3.2-§3.5: first layer U1 = |x * psi| at stride
+  2^k1 (§3.2), width-first second layer over n2 then n1 (§3.3), frequential
+  scattering along n1 with zero padding to N_fr (§3.4), the order of yielded
+  paths of the main algorithm (§3.5), and Gaussian averaging in time and
+  log-frequency after the modulus, Eqs. (4)-(5).
+* Loss E = ||Phi(y) - Phi(x)||^2 (§1.2, §2.3) and its gradient by
+  reverse-mode automatic differentiation, the route §2.3 describes
+  (Eqs. (6)-(8) are the structure autograd realises).
+
+Route: every filtering step is a circular convolution evaluated as
+ifft(fft(z) * h_hat) (a library FFT as a step) followed by time-domain
+decimation z[::2^k].  The CUDA path instead decimates in the Fourier domain
+(periodisation) with band-limited alias sums; the two agree because
+periodising a spectrum by 2^k is exactly decimating the signal by 2^k.
+
+Readings of passages that are silent or ambiguous (each is listed with its
+reason in the repository's design notes):
+  R1  listing §3.1 uses an undefined ``r``: read as r_psi = sqrt(1/2).
+  R2  filter field 'j' (§3.2-§3.4) is undefined: j = max(0, floor(log2(
+      0.5 / (xi + 3 sigma)))), the largest dyadic subsampling that keeps
+      xi + 3 sigma below the new Nyquist frequency.
+  R3  phi_T has sigma = sigma0 / T cycles/sample and phi_F has
+      sigma = sigma0 / F cycles/bin; output strides are T in time and
+      2^floor(log2 F) along n1.
+  R4  Filters are sampled in the Fourier domain at omega_m = m/n for
+      m < n/2 and (m - n)/n otherwise (the Nyquist bin is -1/2); peak value
+      1 before the kappa correction; no periodisation at full rate.
+  R5  levels[k] of a filter = its full-rate spectrum periodised onto n/2^k
+      bins (sum of the 2^k aliases).
+  R6  subsample_fourier = exact time-domain decimation (keep every 2^k-th
+      sample, starting at sample 0).
+  R7  k1 = min(j1, log2 T); second order keeps rows with j1 < j2 at total
+      stride s2 = min(j2, log2 T), i.e. k2 = s2 - k1; frequential stride
+      k_fr = min(j_fr, floor(log2 F)).
+  R8  N_fr = next power of two >= N1 + 2^(J_fr + 1); rows zero-padded on the
+      right; all N_fr / 2^floor(log2 F) pooled rows are kept.
+  R9  Time boundary: periodic (power-of-two N, no padding).
+  R10 Frequential filter set: first order {phi_F} + {+xi_n}; second order
+      {phi_F} + {+xi_n} + {-xi_n}; phi_F is the beta = 0 member.
+  R11 First-order frequential paths: |S1 *_n1 psi_beta| *_n1 phi_F
+      (S1 = U1 *_t phi_T already at stride T).  Second-order paths:
+      |U1 *_t psi_alpha *_n1 psi_beta| *_t phi_T *_n1 phi_F.
+  R12 Phi layout per clip: S0 [N/T]; first order [1+K][R_out][N/T];
+      second order per active n2 ascending [1+2K][R_out][N/T].
+  R13 E = sum over all Phi entries of (Phi(y) - Phi(x))^2; modulus
+      derivative at 0 is 0 (torch's convention for |z|).
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Dict, List, Tuple
+
+import torch
+
+SIGMA0 = 0.1                 # §3.1 listing: sigma0
+R_PSI = math.sqrt(0.5)       # §3.1 listing: r_psi (reading R1)
+F64 = torch.float64
+C128 = torch.complex128
+
+
+# ---------------------------------------------------------------------------
+# Filterbank design (§3.1)
+# ---------------------------------------------------------------------------
+
+def morlet_filterbank(J: int, Q: int) -> List[Tuple[float, float]]:
+    """(xi, sigma) pairs of the §3.1 generator, in the order it yields them.
+
+    Start at xi = max(1/(1 + 2^(3/Q)), 0.35) with the bandwidth that keeps
+    quality factor Q at an overlap of r_psi between neighbours; divide xi and
+    sigma by 2^(1/Q) while sigma stays above sigma_min * 2^(1/Q), where
+    sigma_min = sigma0 / 2^J (the "elbow"); then emit Q-1 constant-bandwidth
+    filters whose xi decreases arithmetically by elbow_xi / Q.
+    """
+    xi = max(1.0 / (1.0 + math.pow(2.0, 3.0 / Q)), 0.35)
+    factor = 1.0 / math.pow(2.0, 1.0 / Q)
+    sigma = (1.0 - factor) / (1.0 + factor) * xi / math.sqrt(2.0 * math.log(1.0 / R_PSI))
+    sigma_min = SIGMA0 / 2 ** J
+    out: List[Tuple[float, float]] = []
+    if sigma <= sigma_min:
+        xi = sigma
+    else:
+        out.append((xi, sigma))
+        while sigma > sigma_min * math.pow(2.0, 1.0 / Q):
+            xi /= math.pow(2.0, 1.0 / Q)
+            sigma /= math.pow(2.0, 1.0 / Q)
+            out.append((xi, sigma))
+    elbow_xi = xi
+    for _ in range(Q - 1):
+        xi -= 1.0 / Q * elbow_xi
+        out.append((xi, sigma_min))
+    return out
+
+
+def max_subsampling(xi: float, sigma: float) -> int:
+    """Filter field 'j' (reading R2): largest k with 2^k (xi + 3 sigma) <= 1/2."""
+    return max(0, int(math.floor(math.log2(0.5 / (xi + 3.0 * sigma)))))
+
+
+def _next_pow2(n: int) -> int:
+    return 1 << (int(n) - 1).bit_length()
+
+
+@dataclass
+class Filter:
+    xi: float
+    sigma: float
+    j: int
+
+
+@dataclass
+class Plan:
+    """Filterbanks and multirate schedule of one JTFS configuration."""
+
+    N: int
+    J: int
+    Q: int
+    Q2: int
+    J_fr: int
+    Q_fr: int
+    T: int
+    F: int
+    psi1: List[Filter] = field(init=False)
+    psi2: List[Filter] = field(init=False)
+    psi_fr: List[Filter] = field(init=False)
+
+    def __post_init__(self) -> None:
+        if self.N <= 0 or self.N & (self.N - 1):
+            raise ValueError("N must be a power of two")
+        if self.T <= 0 or self.T & (self.T - 1) or self.T > self.N:
+            raise ValueError("T must be a power of two <= N")
+        if self.F < 1:
+            raise ValueError("F must be >= 1")
+        self.lT = self.T.bit_length() - 1
+        self.lF = int(math.floor(math.log2(self.F)))
+        self.psi1 = [Filter(x, s, max_subsampling(x, s)) for x, s in morlet_filterbank(self.J, self.Q)]
+        self.psi2 = [Filter(x, s, max_subsampling(x, s)) for x, s in morlet_filterbank(self.J, self.Q2)]
+        self.psi_fr = [Filter(x, s, max_subsampling(x, s)) for x, s in morlet_filterbank(self.J_fr, self.Q_fr)]
+        self.sigma_phiT = SIGMA0 / self.T
+        self.sigma_phiF = SIGMA0 / self.F
+        self.j_phiF = max_subsampling(0.0, self.sigma_phiF)
+        self.N1 = len(self.psi1)
+        self.K = len(self.psi_fr)
+        self.N_fr = _next_pow2(self.N1 + 2 ** (self.J_fr + 1))
+        if (1 << self.lF) > self.N_fr:
+            raise ValueError("2^floor(log2 F) exceeds the frequential length")
+        self.k1 = [min(f.j, self.lT) for f in self.psi1]
+        self.n1_max = [sum(1 for f1 in self.psi1 if f1.j < f2.j) for f2 in self.psi2]
+        self.active = [n2 for n2 in range(len(self.psi2)) if self.n1_max[n2] > 0]
+        # Frequential filter sets (reading R10): (xi, sigma, k_fr); xi = 0 is phi_F.
+        phi = (0.0, self.sigma_phiF, min(self.j_phiF, self.lF))
+        plus = [(f.xi, f.sigma, min(f.j, self.lF)) for f in self.psi_fr]
+        minus = [(-f.xi, f.sigma, min(f.j, self.lF)) for f in self.psi_fr]
+        self.beta_first = [phi] + plus
+        self.beta_second = [phi] + plus + minus
+        self.R_out = self.N_fr >> self.lF
+        self.n_frames = self.N >> self.lT
+
+    @property
+    def phi_size(self) -> int:
+        """Floats per clip in the flat Phi vector (reading R12)."""
+        per_path = self.R_out * self.n_frames
+        return (self.n_frames + len(self.beta_first) * per_path
+                + len(self.active) * len(self.beta_second) * per_path)
+
+
+# ---------------------------------------------------------------------------
+# Fourier-domain filters (Eq. (1); §2.1-§2.2)
+# ---------------------------------------------------------------------------
+
+def fourier_grid(n: int) -> torch.Tensor:
+    """omega_m in cycles per sample on [-1/2, 1/2) (reading R4)."""
+    m = torch.arange(n, dtype=F64)
+    return torch.where(m < n / 2, m, m - n) / n
+
+
+def morlet_hat(n: int, xi: float, sigma: float) -> torch.Tensor:
+    """Morlet wavelet of Eq. (1) in the Fourier domain, sampled on n bins.
+
+    psi_hat(w) = exp(-(w - xi)^2 / 2 sigma^2) - kappa exp(-w^2 / 2 sigma^2),
+    kappa = exp(-xi^2 / 2 sigma^2), so psi_hat(0) = 0 (one vanishing moment).
+    """
+    w = fourier_grid(n)
+    kappa = math.exp(-xi * xi / (2.0 * sigma * sigma))
+    return torch.exp(-(w - xi) ** 2 / (2.0 * sigma * sigma)) - kappa * torch.exp(-w * w / (2.0 * sigma * sigma))
+
+
+def gauss_hat(n: int, sigma: float) -> torch.Tensor:
+    """Gaussian low-pass phi_hat(w) = exp(-w^2 / 2 sigma^2) on n bins."""
+    w = fourier_grid(n)
+    return torch.exp(-w * w / (2.0 * sigma * sigma))
+
+
+def freq_filter_hat(n: int, xi: float, sigma: float) -> torch.Tensor:
+    """Frequential filter: phi_F when xi == 0, else the (spun) Morlet."""
+    return gauss_hat(n, sigma) if xi == 0.0 else morlet_hat(n, xi, sigma)
+
+
+def periodise(h_hat: torch.Tensor, k: int) -> torch.Tensor:
+    """levels[k] (reading R5): sum of the 2^k aliases onto n / 2^k bins."""
+    n = h_hat.shape[-1]
+    return h_hat.reshape(2 ** k, n >> k).sum(0)
+
+
+# ---------------------------------------------------------------------------
+# Multirate primitives
+# ---------------------------------------------------------------------------
+
+def decimate(z: torch.Tensor, k: int, dim: int) -> torch.Tensor:
+    """Keep every 2^k-th sample along ``dim``, starting at 0 (reading R6)."""
+    if k == 0:
+        return z
+    idx = torch.arange(0, z.shape[dim], 2 ** k)
+    return z.index_select(dim, idx)
+
+
+def conv_circ(z: torch.Tensor, h_hat: torch.Tensor, dim: int) -> torch.Tensor:
+    """Circular convolution along ``dim`` with the filter whose DFT is h_hat."""
+    shape = [1] * z.dim()
+    shape[dim] = h_hat.shape[0]
+    return torch.fft.ifft(torch.fft.fft(z, dim=dim) * h_hat.reshape(shape), dim=dim)
+
+
+def pad_rows(z: torch.Tensor, n: int, dim: int) -> torch.Tensor:
+    """Zero-pad ``dim`` on the right to length n (§3.4 listing, pad_frequency)."""
+    extra = n - z.shape[dim]
+    if extra <= 0:
+        return z
+    shape = list(z.shape)
+    shape[dim] = extra
+    return torch.cat([z, torch.zeros(shape, dtype=z.dtype)], dim=dim)
+
+
+# ---------------------------------------------------------------------------
+# The transform
+# ---------------------------------------------------------------------------
+
+def jtfs(x: torch.Tensor, plan: Plan, keep: bool = False,
+         checkpoint_blocks: bool = False) -> Dict[str, torch.Tensor]:
+    """JTFS of x [B, N] (float64).  Returns {'phi': [B, phi_size], ...}.
+
+    With ``keep`` the intermediates U1 (list over n1), S1 and Y2 (list over
+    active n2) are returned too.  ``checkpoint_blocks`` recomputes each
+    second-order block in the backward pass instead of storing it (same
+    arithmetic; only bounds autograd memory for long signals).
+    """
+    if x.dim() == 1:
+        x = x[None]
+    B, N = x.shape
+    assert N == plan.N
+    lT, lF = plan.lT, plan.lF
+    X = torch.fft.fft(x.to(C128), dim=-1)
+    phiT = gauss_hat(N, plan.sigma_phiT)
+    phiF = gauss_hat(plan.N_fr, plan.sigma_phiF)
+
+    # Zeroth order: x * phi_T at stride T (first yield of the main algorithm).
+    S0 = decimate(torch.fft.ifft(X * phiT, dim=-1).real, lT, -1)
+
+    # First layer (§3.2): U1 = |x * psi_n1| at stride 2^k1.
+    U1 = []
+    for f, k1 in zip(plan.psi1, plan.k1):
+        z = torch.fft.ifft(X * morlet_hat(N, f.xi, f.sigma), dim=-1)
+        U1.append(decimate(z, k1, -1).abs())
+
+    # First-order time averaging, S_1 of the main algorithm (§3.5), Eq. (4)'s phi_T.
+    S1 = torch.stack([
+        decimate(conv_circ(U1[n1], periodise(phiT, k1), -1), lT - k1, -1).real
+        for n1, k1 in enumerate(plan.k1)], dim=1)                         # [B, N1, N/T]
+
+    # First-order frequential scattering (spinned=False, §3.4) then phi_F averaging.
+    S1p = pad_rows(S1, plan.N_fr, 1)
+    phi1 = []
+    for xi_b, sig_b, k_b in plan.beta_first:
+        yfr = decimate(conv_circ(S1p, freq_filter_hat(plan.N_fr, xi_b, sig_b), 1), k_b, 1)
+        v = decimate(conv_circ(yfr.abs(), periodise(phiF, k_b), 1), lF - k_b, 1).real
+        phi1.append(v)
+    Phi1 = torch.stack(phi1, 1)                                          # [B, 1+K, R_out, N/T]
+
+    def second_order_block(U1_rows: List[torch.Tensor], n2: int) -> Tuple[torch.Tensor, torch.Tensor]:
+        f2 = plan.psi2[n2]
+        s2 = min(f2.j, lT)
+        psi2 = morlet_hat(N, f2.xi, f2.sigma)
+        # Second layer, time variable (§3.3): rows n1 with j1 < j2, stacked.
+        rows = []
+        for n1 in range(plan.n1_max[n2]):
+            k1 = plan.k1[n1]
+            rows.append(decimate(conv_circ(U1_rows[n1], periodise(psi2, k1), -1), s2 - k1, -1))
+        Y2 = torch.stack(rows, 1)                                        # [B, n1_max, N/2^s2]
+        # Second layer, frequency variable (§3.4, spinned=True), modulus, Eq. (5).
+        Y2p = pad_rows(Y2, plan.N_fr, 1)
+        blocks = []
+        for xi_b, sig_b, k_b in plan.beta_second:
+            yfr = decimate(conv_circ(Y2p, freq_filter_hat(plan.N_fr, xi_b, sig_b), 1), k_b, 1)
+            u2 = yfr.abs()
+            a = decimate(conv_circ(u2, periodise(phiT, s2), 2), lT - s2, 2).real      # *_t phi_T
+            v = decimate(conv_circ(a, periodise(phiF, k_b), 1), lF - k_b, 1).real     # *_n1 phi_F
+            blocks.append(v)
+        return torch.stack(blocks, 1), Y2                                # [B, 1+2K, R_out, N/T]
+
+    phi2, Y2s = [], []
+    for n2 in plan.active:
+        if checkpoint_blocks and torch.is_grad_enabled():
+            from torch.utils.checkpoint import checkpoint
+            blk = checkpoint(lambda *rows, _n2=n2: second_order_block(list(rows), _n2)[0],
+                             *U1[:plan.n1_max[n2]], use_reentrant=False)
+        else:
+            blk, Y2 = second_order_block(U1, n2)
+            if keep:
+                Y2s.append(Y2)
+        phi2.append(blk)
+
+    parts = [S0, Phi1.reshape(B, -1)]
+    if phi2:
+        parts.append(torch.stack(phi2, 1).reshape(B, -1))
+    out = {"phi": torch.cat(parts, 1)}
+    if keep:
+        out.update(S0=S0, U1=U1, S1=S1, Phi1=Phi1, Y2=Y2s,
+                   Phi2=torch.stack(phi2, 1) if phi2 else None)
+    return out
+
+
+def phi_blocks(phi: torch.Tensor, plan: Plan) -> Dict[str, torch.Tensor]:
+    """Split a flat [B, phi_size] Phi into S0, first-order and per-n2 blocks."""
+    B = phi.shape[0]
+    nf = plan.n_frames
+    per_path = plan.R_out * nf
+    o = 0
+    out = {"S0": phi[:, o:o + nf]}
+    o += nf
+    n = len(plan.beta_first) * per_path
+    out["first"] = phi[:, o:o + n]
+    o += n
+    for n2 in plan.active:
+        n = len(plan.beta_second) * per_path
+        out[f"n2={n2}"] = phi[:, o:o + n]
+        o += n
+    assert o == phi.shape[1] == plan.phi_size and B == phi.shape[0]
+    return out
+
+
+def loss(y: torch.Tensor, phi_target: torch.Tensor, plan: Plan) -> torch.Tensor:
+    """Per-clip E(y) = ||Phi(y) - Phi_target||^2 (§1.2; reading R13)."""
+    phi = jtfs(y, plan)["phi"]
+    return ((phi - phi_target) ** 2).sum(-1)
+
+
+def loss_and_grad(y: torch.Tensor, phi_target: torch.Tensor, plan: Plan,
+                  checkpoint_blocks: bool = False) -> Tuple[torch.Tensor, torch.Tensor]:
+    """(E [B], dE/dy [B, N]) by reverse-mode autodiff (§2.3)."""
+    y = y.detach().to(F64)
+    if y.dim() == 1:
+        y = y[None]
+    y = y.clone().requires_grad_(True)
+    with torch.enable_grad():
+        phi = jtfs(y, plan, checkpoint_blocks=checkpoint_blocks)["phi"]
+        E = ((phi - phi_target.to(F64)) ** 2).sum(-1)
+        (g,) = torch.autograd.grad(E.sum(), y)
+    return E.detach(), g.detach()
