@@ -1,0 +1,360 @@
+"""Benchmark: JTFS metamer step throughput (audio samples/s) on GB300.
+
+One step = metamer_step on the batch-8, 2^16-sample chirp workload (J=12,
+Q=12, Q2=1, J_fr=5, Q_fr=2, T=2^11, F=12): JTFS forward, loss against the
+target Phi, hand-written adjoint, Adam update, all in the library's CUDA
+kernels.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank solves its own batch of
+clips (independent metamers, no data-path collective; weak scaling).
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import get_workload  # noqa: E402
+
+WORKLOAD = "chirps22k_b8_n65536"
+METRIC = "JTFS fwd+bwd audio-samples/s"
+UNIT = "audio-samples/s"
+L2_FLUSH_BYTES = 256 << 20
+# FP32 ALU peak of a GB300 from unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic FLOP model (5 n log2 n per complex FFT, 2.5 n log2 n per real
+# FFT, 2 per real-filter product, 3 per modulus, 6 per modulus adjoint).
+# ---------------------------------------------------------------------------
+def _lg(n):
+    return math.log2(n) if n > 1 else 0.0
+
+
+def freq_flops_per_column(plan, adjoint: bool) -> float:
+    info = plan.info
+    Nfr, Rout, lF = info["N_fr"], info["R_out"], info["log2_F"]
+    _, _, jf = plan.filters(2)
+    _, _, jl = plan.filters(3)
+    ks = [min(int(jl[1]), lF)] + [min(int(j), lF) for j in jf] * 2
+    f = 5 * Nfr * _lg(Nfr)
+    for k in ks:
+        R = Nfr >> k
+        if not adjoint:
+            f += 2 * Nfr + 5 * R * _lg(R) + 3 * R + 2.5 * R * _lg(R) + 2 * R + 2.5 * Rout * _lg(Rout)
+        else:
+            f += (2 * Nfr + 5 * R * _lg(R) + 2.5 * Rout * _lg(Rout) + 2 * R + 2.5 * R * _lg(R)
+                  + 6 * R + 5 * R * _lg(R) + 2 * Nfr)
+    if adjoint:
+        f += 5 * Nfr * _lg(Nfr)
+    return f
+
+
+def columns_per_launch(plan) -> int:
+    """Time columns the second-order frequential kernels process per launch."""
+    info = plan.info
+    _, _, j2 = plan.filters(1)
+    _, _, j1 = plan.filters(0)
+    lT = info["log2_T"]
+    cols = 0
+    for jj in j2:
+        if (j1 < jj).sum() > 0:
+            cols += info["N"] >> min(int(jj), lT)
+    return cols * info["batch"]
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region.
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        self.proc = subprocess.Popen([exe, f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits", "-lms", "200"],
+                                     stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the FP64 oracle on the host cores.
+# ---------------------------------------------------------------------------
+def oracle_clip_seconds(wl, clip: int):
+    from oracle import jtfs_oracle as O
+    ref = O.Plan(**wl.params)
+    y = torch.tensor(wl.inits()[clip:clip + 1], dtype=torch.float64)
+    tgt = O.jtfs(torch.tensor(wl.targets()[clip:clip + 1], dtype=torch.float64), ref)["phi"]
+    t0 = time.perf_counter()
+    O.loss_and_grad(y, tgt, ref, checkpoint_blocks=True)
+    return time.perf_counter() - t0
+
+
+def run_reference(args, wl):
+    from oracle import jtfs_oracle as O
+    small = get_workload("tones8k_n8192")
+    sp = O.Plan(**small.params)
+    ys = torch.tensor(small.inits(), dtype=torch.float64)
+    ts = O.jtfs(torch.tensor(small.targets(), dtype=torch.float64), sp)["phi"]
+    for _ in range(args.warmup):
+        O.loss_and_grad(ys, ts, sp)
+    steps = max(1, min(args.steps, 3))
+    total = 0.0
+    for k in range(steps):
+        total += oracle_clip_seconds(wl, k % wl.batch)
+    value = steps * wl.N / total
+    cores = torch.get_num_threads()
+    sample = (f"{steps} step(s), each the oracle's FP64 forward+loss+adjoint (autograd) of one "
+              f"{wl.N}-sample clip of the {wl.name} workload; warm-up on 8192-sample clips")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(wl):
+    return {"workload": wl.name, "batch": wl.batch, "N": wl.N, "J": wl.J, "Q": wl.Q, "Q2": wl.Q2,
+            "J_fr": wl.J_fr, "Q_fr": wl.Q_fr, "T": wl.T, "F": wl.F, "sample_rate_hz": wl.sr,
+            "step": "metamer_step: JTFS forward + loss + hand-written adjoint + Adam (lr 0.1)",
+            "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written between timed steps (outside the events)",
+            "parallelism": "replicas (independent clips per GPU)"}
+
+
+# ---------------------------------------------------------------------------
+# Native arm.
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    wl = get_workload(WORKLOAD)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, wl)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    from paper_2602_11896_gb300 import JTFSPlan, _native
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    plan = JTFSPlan(**wl.params, batch=wl.batch)
+    seed_off = 1000 * rank
+    targets = np.stack([get_workload(WORKLOAD).targets()[b] for b in range(wl.batch)]) if rank == 0 else None
+    if rank != 0:
+        from workloads import signals
+        targets = np.stack([signals.chirp_am_mix(wl.N, wl.sr, s + seed_off) for s in wl.target_seeds])
+        inits = np.stack([signals.white_noise(wl.N, s + seed_off) for s in wl.init_seeds])
+    else:
+        inits = wl.inits()
+    x = torch.tensor(targets, device=dev)
+    y0 = torch.tensor(inits, device=dev)
+    phi_t = plan.forward(x)
+    y = y0.clone()
+    m = torch.zeros_like(y)
+    v = torch.zeros_like(y)
+    loss = torch.empty(wl.batch, device=dev)
+    ws = plan.workspace(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    step_no = [0]
+
+    def step():
+        step_no[0] += 1
+        plan.metamer_step(y, phi_t, m, v, step_no[0], 0.1, loss_out=loss, workspace=ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    lib = _native.load()
+    stage_events = {}
+    for st in range(4):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
+        for e in evs:           # torch creates the CUDA event on its first record
+            e.record()
+        arr = (ctypes_void_p * (2 * K))(*[ctypes_void_p(e.cuda_event) for e in evs])
+        _native.check(lib.jtfs_profile_stage(plan._h, st, arr, 2 * K), "jtfs_profile_stage")
+        stage_events[st] = (evs, arr)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for k in range(K):
+        flush.fill_(float(k))
+        starts[k].record()
+        step()
+        ends[k].record()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    for st in range(4):
+        lib.jtfs_profile_stage(plan._h, st, None, 0)
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / K
+    value = world * wl.batch * wl.N * K / (ms / 1e3)
+
+    # Per-stage average launch duration (CUDA events on the library's stream).
+    stage_ms = {}
+    for st, (evs, _) in stage_events.items():
+        d = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(K)]
+        stage_ms[st] = float(np.mean(d))
+    names = {0: "k_freq_fwd<2> (second-order frequential scattering + modulus + phi_F)",
+             1: "k_freq_adj<2> (adjoint of the second-order frequential scattering)",
+             2: "k_pool_fwd (phi_T averaging FIR)", 3: "k_pool_adj (adjoint phi_T FIR)"}
+    dom = max(stage_ms, key=stage_ms.get)
+    cols = columns_per_launch(plan)
+    flops = None
+    if dom in (0, 1):
+        flops = freq_flops_per_column(plan, adjoint=(dom == 1)) * cols
+    else:
+        info = plan.info
+        flops = None
+    roofline = None
+    if flops is not None:
+        ach = flops / (stage_ms[dom] / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": names[dom], "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                    "flops_per_launch": flops, "launch_ms": stage_ms[dom],
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (no measured FP32 peak)",
+                    "stage_ms": {names[s].split(" ")[0]: round(t, 4) for s, t in stage_ms.items()},
+                    "step_share": stage_ms[dom] / ms_per_step}
+
+    # End to end through the public API from pinned host memory.
+    y_host = torch.tensor(inits, dtype=torch.float32).pin_memory()
+    t_host = phi_t.cpu().pin_memory()
+    l_host = torch.empty(wl.batch, dtype=torch.float32).pin_memory()
+    yo_host = torch.empty_like(y_host).pin_memory()
+    y_dev = torch.empty_like(y)
+    t_dev = torch.empty_like(phi_t)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    Ke = max(1, min(K, 50))
+    m.zero_()
+    v.zero_()
+    e0.record()
+    for k in range(Ke):
+        y_dev.copy_(y_host, non_blocking=True)
+        t_dev.copy_(t_host, non_blocking=True)
+        plan.metamer_step(y_dev, t_dev, m, v, k + 1, 0.1, loss_out=loss, workspace=ws)
+        l_host.copy_(loss, non_blocking=True)
+        yo_host.copy_(y_dev, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / Ke
+    e2e = {"value": world * wl.batch * wl.N / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(y_host.numel() * 4 + t_host.numel() * 4),
+           "d2h_bytes_per_step": int(l_host.numel() * 4 + yo_host.numel() * 4), "ms_per_step": e2e_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs = oracle_clip_seconds(wl, 0)
+        cpu = {"value": wl.N / secs, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+               "sample": f"one {wl.N}-sample clip of {wl.name}: FP64 forward + loss + autograd adjoint, "
+                         f"{secs:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(wl), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(lib.jtfs_launch_count(plan._h, 3)) * K,
+                "clocks": clk, "wall_s_timed": t_wall,
+                "final_loss_mean": float(loss.mean().item())}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+from ctypes import c_void_p as ctypes_void_p  # noqa: E402
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * jtfs.h -- C ABI of the GB300 (sm_103a) joint time-frequency scattering
+ * library: the JTFS transform Phi(x), its adjoint, the metamer loss
+ * E(y) = ||Phi(y) - Phi_target||^2 with its gradient, and an Adam metamer step.
+ *
+ * Method: Lostanlen & Han, "Musical Metamerism with Time-Frequency
+ * Scattering".  Section, equation and listing references below are to that
+ * paper.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: 0 on success, a negative JTFS_ERR_* code otherwise; no C++
+ *   exception crosses this boundary.  jtfs_error_string() names a code.
+ * - Device pointers: every float* / void* data argument of the compute calls
+ *   (x, phi, dphi, dx, y, phi_target, loss, dy, adam_m, adam_v, workspace) is a
+ *   pointer to GPU global memory owned by the caller.  Arrays are dense and
+ *   row-major; pointers to float data must be 16-byte aligned.  The library
+ *   never frees or retains them beyond the call.
+ * - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Every compute call only enqueues work on that stream and returns
+ *   without synchronising; errors that only a finished kernel can reveal are
+ *   not reported by the call.
+ * - Workspace: compute calls need a caller-allocated device scratch buffer of
+ *   at least jtfs_workspace_bytes(plan) bytes (256-byte aligned).  Its content
+ *   on entry is ignored; calls sharing one workspace must not overlap in time.
+ * - A plan is immutable after creation and may be shared by several streams
+ *   provided each uses its own workspace.
+ */
+#ifndef JTFS_H
+#define JTFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define JTFS_OK             0
+#define JTFS_ERR_ARG       -1  /* invalid argument (NULL pointer, bad value) */
+#define JTFS_ERR_SHAPE     -2  /* unsupported sizes (N, T, F, filterbank)   */
+#define JTFS_ERR_WORKSPACE -3  /* workspace NULL or misaligned              */
+#define JTFS_ERR_CUDA      -4  /* a CUDA runtime call failed                */
+#define JTFS_ERR_NOMEM     -5  /* host or device allocation failed          */
+#define JTFS_ERR_NODEVICE  -6  /* plan was created host-only                */
+
+/* Plan flags. */
+#define JTFS_PLAN_HOST_ONLY 1u /* build the tables on the host only; compute
+                                  calls then fail with JTFS_ERR_NODEVICE.   */
+
+typedef struct jtfs_plan_s* jtfs_plan_t;
+
+/*
+ * Create a plan: filterbanks and the multirate schedule of one JTFS
+ * configuration, plus (unless JTFS_PLAN_HOST_ONLY) their device tables on the
+ * current CUDA device.
+ *
+ *   N      samples per clip, a power of two, 16 <= N <= 2^20; periodic boundary.
+ *   J, Q   first-order filterbank (§3.1 generator): octaves and filters per
+ *          octave (constant-Q part), Q-1 constant-bandwidth filters below.
+ *   Q2     filters per octave of the second-order time filterbank (same J).
+ *   J_fr, Q_fr  frequential filterbank along the n1 axis (§3.4), spun to +/-.
+ *   T      time averaging scale and output stride (power of two, <= N);
+ *          phi_T has sigma = 0.1/T cycles/sample (§2.2).
+ *   F      frequency averaging scale (>= 1); phi_F has sigma = 0.1/F
+ *          cycles/bin, output stride 2^floor(log2 F) along n1.
+ *   batch  clips per call (>= 1).
+ *
+ * Derived quantities (per clip): N1 first-order filters; N_fr = next power
+ * of two >= N1 + 2^(J_fr+1) (frequential FFT length, rows zero-padded on the
+ * right, §3.4 listing); R_out = N_fr / 2^floor(log2 F) pooled rows;
+ * n_frames = N / T.
+ *
+ * On success *out owns host memory and, unless host-only, device memory;
+ * release it with jtfs_plan_destroy.  Errors: JTFS_ERR_ARG (out NULL),
+ * JTFS_ERR_SHAPE (sizes outside the ranges above or an empty filterbank),
+ * JTFS_ERR_CUDA / JTFS_ERR_NOMEM (device table upload failed).
+ */
+int jtfs_plan(jtfs_plan_t* out, int64_t N, int J, int Q, int Q2, int J_fr,
+              int Q_fr, int64_t T, int F, int batch, uint32_t flags);
+
+/* Release a plan (NULL is accepted).  Device memory is freed synchronously. */
+int jtfs_plan_destroy(jtfs_plan_t plan);
+
+/*
+ * Phi layout (main algorithm, §3.5): per clip a flat float vector of
+ * jtfs_phi_size(plan) entries,
+ *   [ S0 : n_frames ]
+ *   [ first order : (1+K) paths x R_out rows x n_frames ]
+ *   [ second order: for each active n2 ascending, (1+2K) paths x R_out x n_frames ]
+ * where K is the number of frequential wavelets before spinning, the first
+ * path of each group is the beta = 0 (phi_F) path, then +xi_n (n ascending),
+ * then (second order only) -xi_n.  An n2 is active when some first-order
+ * filter has j1 < j2.  Batched arrays are [batch][phi_size].
+ * Returns the size, or a negative error code if plan is NULL.
+ */
+int64_t jtfs_phi_size(jtfs_plan_t plan);
+
+/* Bytes of device workspace one compute call needs (0 if plan is NULL). */
+size_t jtfs_workspace_bytes(jtfs_plan_t plan);
+
+/*
+ * Plan inspection (host memory, no device access).
+ * jtfs_plan_info fills info[0..count) with, in order:
+ *   N, J, Q, Q2, J_fr, Q_fr, T, F, batch, N1, N2, K, N_fr, log2 T,
+ *   floor(log2 F), R_out, n_frames, n_active, phi_size
+ * and returns the number of values available (19), or JTFS_ERR_ARG.
+ */
+int jtfs_plan_info(jtfs_plan_t plan, int64_t* info, int count);
+
+/*
+ * jtfs_plan_filters copies one filterbank: which = 0 first-order time
+ * (psi^{tm,1}), 1 second-order time (psi^{tm,2}), 2 frequential (psi^{fr,1},
+ * positive spin), 3 the two low-pass filters (phi_T then phi_F, xi = 0).
+ * xi and sigma are in cycles per sample (per bin for the frequential axis);
+ * j is the largest dyadic subsampling with 2^j (xi + 3 sigma) <= 1/2.
+ * Writes min(count, size) entries to each non-NULL array and returns the
+ * filterbank size, or JTFS_ERR_ARG.
+ */
+int jtfs_plan_filters(jtfs_plan_t plan, int which, double* xi, double* sigma,
+                      int32_t* j, int count);
+
+/*
+ * Forward transform, Eqs. (1)-(5) with the multirate schedule of §3.2-§3.5:
+ *   x   [batch][N] float32 (device), real audio clips.
+ *   phi [batch][phi_size] float32 (device), output, layout as above.
+ * Errors: JTFS_ERR_ARG (NULL pointer), JTFS_ERR_NODEVICE, JTFS_ERR_WORKSPACE,
+ * JTFS_ERR_CUDA (launch failure).
+ */
+int jtfs_forward(jtfs_plan_t plan, const float* x, float* phi, void* workspace,
+                 void* stream);
+
+/*
+ * Adjoint (vector-Jacobian product) of jtfs_forward at x, §2.3 Eqs. (6)-(8):
+ *   dx = J_Phi(x)^T dphi.  Recomputes every intermediate from x.
+ *   x    [batch][N] float32 (device); dphi [batch][phi_size] float32 (device);
+ *   dx   [batch][N] float32 (device), output (overwritten).
+ * The modulus derivative at 0 is taken as 0.  Errors as jtfs_forward.
+ */
+int jtfs_backward(jtfs_plan_t plan, const float* x, const float* dphi,
+                  float* dx, void* workspace, void* stream);
+
+/*
+ * Metamer loss and gradient (§1.2, §2.3):
+ *   loss[b] = sum_i (Phi(y)[b][i] - phi_target[b][i])^2   (float32 [batch])
+ *   dy[b]   = d loss[b] / d y[b]                            ([batch][N])
+ * y and phi_target as for jtfs_forward; loss and dy are device outputs.
+ * dy may be NULL (loss only).  Errors as jtfs_forward.
+ */
+int jtfs_loss_grad(jtfs_plan_t plan, const float* y, const float* phi_target,
+                   float* loss, float* dy, void* workspace, void* stream);
+
+/*
+ * One metamer descent step with Adam (beta1 = 0.9, beta2 = 0.999,
+ * eps = 1e-8, bias-corrected with the 1-based step index `step`) on y, in
+ * place.  The paper refines y by additive gradient steps (§2.3); Adam is the
+ * optimiser this library's workloads use.
+ *   y, adam_m, adam_v  [batch][N] float32 (device), updated in place;
+ *                      m and v must start at zero before step 1.
+ *   phi_target         [batch][phi_size] float32 (device).
+ *   loss_out           [batch] float32 (device): loss at the y given on entry.
+ * Errors as jtfs_forward, plus JTFS_ERR_ARG for step < 1 or lr <= 0.
+ */
+int metamer_step(jtfs_plan_t plan, float* y, const float* phi_target,
+                 float* adam_m, float* adam_v, int step, float lr,
+                 float* loss_out, void* workspace, void* stream);
+
+/*
+ * Measurement hooks (host-side bookkeeping; not thread-safe).
+ *
+ * jtfs_profile_stage registers `count` CUDA events (cudaEvent_t passed as
+ * void*, created by the caller) for one stage: every later launch of that
+ * stage's kernel records events[2i] just before and events[2i+1] just after
+ * it on the stream of the call, for i = 0, 1, ... until count/2 launches are
+ * recorded.  events = NULL or count = 0 clears the registration.  Stages:
+ */
+#define JTFS_STAGE_FREQ2_FWD 0 /* second-order frequential scattering, modulus,
+                                  phi_F averaging (§3.4, Eq. (5))           */
+#define JTFS_STAGE_FREQ2_ADJ 1 /* its adjoint (§2.3, Eq. (7))                */
+#define JTFS_STAGE_POOL_FWD  2 /* second-order phi_T averaging (Eq. (5))     */
+#define JTFS_STAGE_POOL_ADJ  3 /* its adjoint (Eq. (6))                      */
+#define JTFS_STAGE_COUNT     4
+int jtfs_profile_stage(jtfs_plan_t plan, int stage, void** events, int count);
+
+/*
+ * Number of kernel launches one call makes: call = 0 jtfs_forward,
+ * 1 jtfs_backward, 2 jtfs_loss_grad (with gradient), 3 metamer_step.
+ * Returns the count or JTFS_ERR_ARG.
+ */
+int64_t jtfs_launch_count(jtfs_plan_t plan, int call);
+
+/* Static description of an error code (never NULL). */
+const char* jtfs_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JTFS_H */

@@ -1,0 +1,64 @@
+"""ctypes binding of the C ABI declared in include/jtfs.h (argument marshalling only).
+
+The library is the in-tree ``libjtfs.so`` built by ``paper_2602_11896_gb300.build``.
+There is no fallback: if it is missing, importing the compute API raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_int32, c_int64, c_size_t, c_uint32, c_void_p
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libjtfs.so")
+
+# Every symbol include/jtfs.h declares, with (restype, argtypes).
+SIGNATURES = {
+    "jtfs_plan": (c_int, [POINTER(c_void_p), c_int64, c_int, c_int, c_int, c_int, c_int,
+                          c_int64, c_int, c_int, c_uint32]),
+    "jtfs_plan_destroy": (c_int, [c_void_p]),
+    "jtfs_phi_size": (c_int64, [c_void_p]),
+    "jtfs_workspace_bytes": (c_size_t, [c_void_p]),
+    "jtfs_plan_info": (c_int, [c_void_p, POINTER(c_int64), c_int]),
+    "jtfs_plan_filters": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_double),
+                                  POINTER(c_int32), c_int]),
+    "jtfs_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "jtfs_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "jtfs_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                               c_void_p]),
+    "metamer_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_float,
+                             c_void_p, c_void_p, c_void_p]),
+    "jtfs_profile_stage": (c_int, [c_void_p, c_int, POINTER(c_void_p), c_int]),
+    "jtfs_launch_count": (c_int64, [c_void_p, c_int]),
+    "jtfs_error_string": (c_char_p, [c_int]),
+}
+
+PLAN_HOST_ONLY = 1
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libjtfs.so once; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing; build it with "
+                "`python -m paper_2602_11896_gb300.build` (needs nvcc)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return load().jtfs_error_string(code).decode()
+
+
+def check(code: int, what: str) -> None:
+    if code != 0:
+        raise RuntimeError(f"{what} failed: {error_string(code)} ({code})")

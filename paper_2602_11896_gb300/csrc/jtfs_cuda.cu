@@ -1,0 +1,1030 @@
+// CUDA kernels (sm_103a) and the compute entry points of the JTFS C ABI.
+//
+// Every filtering step of the method (Eqs. (1)-(5); §3.2-§3.5) is done in
+// the Fourier domain: a loader evaluates the analytic filter on the bins
+// where it is not negligible and folds them onto the decimated grid
+// ("subsample_fourier", §3.2: periodisation of the spectrum, which equals
+// time-domain decimation), a shared-memory Stockham FFT transforms, and a
+// storer writes.  The frequential scattering (§3.4) with its modulus and
+// phi_F averaging runs fused per tile of time columns; phi_T averaging of the
+// second order is a decimating FIR.  The adjoint chain (§2.3, Eqs. (6)-(8))
+// transposes each step: periodisation becomes tiling, filters multiply again
+// (they are real in the Fourier domain), the modulus becomes z/|z|.
+//
+// FFT convention: F (sign -1) and F^H (sign +1), both unnormalised; every
+// 1/n factor is applied by a loader.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "jtfs.h"
+#include "jtfs_internal.h"
+
+namespace jtfs {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxSmem = 227 * 1024;
+
+// ---------------------------------------------------------------------------
+// Complex helpers and filters
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// Filter value at signed bin s of its grid (see FiltD).
+__device__ __forceinline__ float fval(const FiltD& f, int s) {
+  const float d = static_cast<float>(s) - f.c0;
+  float v = expf(-d * d * f.a);
+  if (f.kappa != 0.f) {
+    const float sf = static_cast<float>(s);
+    v -= f.kappa * expf(-sf * sf * f.a);
+  }
+  return v;
+}
+
+// sum over signed bins s in [f.lo, f.hi] with s = m (mod Ld) of
+// src[s mod Ls] * value(s): a filter product folded onto Ld bins.
+__device__ __forceinline__ float2 band_gather(const float2* __restrict__ src, int Ls, int Ld, int m,
+                                              const FiltD& f) {
+  float2 acc = make_float2(0.f, 0.f);
+  for (int s = f.lo + ((m - f.lo) & (Ld - 1)); s <= f.hi; s += Ld) {
+    const float g = fval(f, s);
+    const float2 v = src[s & (Ls - 1)];
+    acc.x += g * v.x;
+    acc.y += g * v.y;
+  }
+  return acc;
+}
+
+// sum over signed bins s in [f.lo, f.hi] with s = m (mod L) of value(s):
+// the filter periodised onto L bins ("levels", read as a sum of aliases).
+__device__ __forceinline__ float band_lev(int m, int L, const FiltD& f) {
+  float acc = 0.f;
+  for (int s = f.lo + ((m - f.lo) & (L - 1)); s <= f.hi; s += L) acc += fval(f, s);
+  return acc;
+}
+
+template <bool INV>
+__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int e) {
+  float2 w = __ldg(tw + e);
+  if (INV) w.y = -w.y;
+  return w;
+}
+
+// ---------------------------------------------------------------------------
+// CTA-wide batched Stockham FFT in shared memory.
+// `count` transforms of size 2^logn; transform f lives at a + f*bstride.
+// Mixed radix: one radix-2 pass when logn is odd, then radix-4 passes.
+// Returns the buffer (a or b) holding the natural-order result.  Must be
+// called by every thread of the block.
+// ---------------------------------------------------------------------------
+template <bool INV>
+__device__ float2* cta_fft(float2* a, float2* b, int logn, int count, int bstride,
+                           const float2* __restrict__ tw, int twlog) {
+  const int n = 1 << logn;
+  int lNs = 0;
+  if (logn & 1) {
+    const int lq = logn - 1, q = n >> 1;
+    const int total = count << lq;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+      const int f = i >> lq, j = i & (q - 1);
+      const float2* src = a + f * bstride;
+      float2* dst = b + f * bstride;
+      const float2 v0 = src[j], v1 = src[j + q];
+      dst[2 * j] = make_float2(v0.x + v1.x, v0.y + v1.y);
+      dst[2 * j + 1] = make_float2(v0.x - v1.x, v0.y - v1.y);
+    }
+    __syncthreads();
+    float2* t = a; a = b; b = t;
+    lNs = 1;
+  }
+  while (lNs < logn) {
+    const int lq = logn - 2, q = n >> 2;
+    const int total = count << lq;
+    const int Ns = 1 << lNs;
+    const int shift = twlog - (lNs + 2);
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+      const int f = i >> lq, j = i & (q - 1);
+      const float2* src = a + f * bstride;
+      float2* dst = b + f * bstride;
+      const int k = j & (Ns - 1);
+      float2 v0 = src[j], v1 = src[j + q], v2 = src[j + 2 * q], v3 = src[j + 3 * q];
+      if (lNs > 0) {
+        v1 = cmul(v1, twiddle<INV>(tw, k << shift));
+        v2 = cmul(v2, twiddle<INV>(tw, (2 * k) << shift));
+        v3 = cmul(v3, twiddle<INV>(tw, (3 * k) << shift));
+      }
+      const float2 s02 = make_float2(v0.x + v2.x, v0.y + v2.y);
+      const float2 d02 = make_float2(v0.x - v2.x, v0.y - v2.y);
+      const float2 s13 = make_float2(v1.x + v3.x, v1.y + v3.y);
+      const float2 d13 = make_float2(v1.x - v3.x, v1.y - v3.y);
+      float2 y1, y3;
+      if (!INV) {  // W_4 = -i
+        y1 = make_float2(d02.x + d13.y, d02.y - d13.x);
+        y3 = make_float2(d02.x - d13.y, d02.y + d13.x);
+      } else {
+        y1 = make_float2(d02.x - d13.y, d02.y + d13.x);
+        y3 = make_float2(d02.x + d13.y, d02.y - d13.x);
+      }
+      const int d = ((j - k) << 2) + k;
+      dst[d] = make_float2(s02.x + s13.x, s02.y + s13.y);
+      dst[d + Ns] = y1;
+      dst[d + 2 * Ns] = make_float2(s02.x - s13.x, s02.y - s13.y);
+      dst[d + 3 * Ns] = y3;
+    }
+    __syncthreads();
+    float2* t = a; a = b; b = t;
+    lNs += 2;
+  }
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// Loaders: element idx of the input of the FFT described by a job.
+// ---------------------------------------------------------------------------
+struct LdReal {  // real row -> complex
+  const float* s;
+  __device__ float2 operator()(const Job& jb, int idx, int) const {
+    return make_float2(s[jb.src + idx], 0.f);
+  }
+};
+struct LdC {  // complex row
+  const float2* s;
+  __device__ float2 operator()(const Job& jb, int idx, int) const { return s[jb.src + idx]; }
+};
+struct LdMod {  // |z| of a complex row (the modulus of §2.1)
+  const float2* s;
+  __device__ float2 operator()(const Job& jb, int idx, int) const {
+    const float2 v = s[jb.src + idx];
+    return make_float2(sqrtf(v.x * v.x + v.y * v.y), 0.f);
+  }
+};
+// Filter product folded onto 2^logn bins, scaled by 1/Ls (Ls = source row
+// length): with an unnormalised inverse FFT this yields the decimated
+// filtered signal (§3.2 cdgmm + subsample_fourier + ifft).
+struct LdBand {
+  const float2* s;
+  const FiltD* table;  // per-job filter table[jb.filt], or NULL: `fixed`
+  FiltD fixed;
+  __device__ float2 operator()(const Job& jb, int idx, int logn) const {
+    const FiltD f = table ? table[jb.filt] : fixed;
+    const int Ls = 1 << jb.lslog;
+    return cscale(band_gather(s + jb.src, Ls, 1 << logn, idx, f), 1.f / static_cast<float>(Ls));
+  }
+};
+// Adjoint of the modulus: dz = du * z / |z| (0 where z = 0); du is the real
+// part of a complex row.
+struct LdDz {
+  const float2* du;
+  const float2* z;
+  __device__ float2 operator()(const Job& jb, int idx, int) const {
+    const float g = du[jb.src + idx].x;
+    const float2 v = z[jb.src + idx];
+    const float m = sqrtf(v.x * v.x + v.y * v.y);
+    return m > 0.f ? make_float2(g * v.x / m, g * v.y / m) : make_float2(0.f, 0.f);
+  }
+};
+
+struct StC {
+  float2* d;
+  __device__ void operator()(const Job& jb, int idx, float2 v) const { d[jb.dst + idx] = v; }
+};
+struct StR {  // real part
+  float* d;
+  __device__ void operator()(const Job& jb, int idx, float2 v) const { d[jb.dst + idx] = v.x; }
+};
+
+// ---------------------------------------------------------------------------
+// Batched FFT kernels.
+// ---------------------------------------------------------------------------
+template <bool INV, class Ld, class St>
+__global__ void __launch_bounds__(kThreads)
+k_fft_small(Ld ld, St st, const Job* __restrict__ jobs, int njobs, int logn, int per_cta,
+            const float2* __restrict__ tw, int twlog) {
+  extern __shared__ float2 sm[];
+  const int n = 1 << logn;
+  const int j0 = blockIdx.x * per_cta;
+  const int nj = min(per_cta, njobs - j0);
+  float2* a = sm;
+  float2* b = sm + per_cta * n;
+  for (int i = threadIdx.x; i < nj * n; i += blockDim.x) a[i] = ld(jobs[j0 + (i >> logn)], i & (n - 1), logn);
+  __syncthreads();
+  float2* r = cta_fft<INV>(a, b, logn, nj, n, tw, twlog);
+  for (int i = threadIdx.x; i < nj * n; i += blockDim.x) st(jobs[j0 + (i >> logn)], i & (n - 1), r[i]);
+}
+
+// Four-step FFT for 2^logn > 2^kSmallLogMax: n = na * nb, na = 2^la.
+// Pass 1: for each column c < nb, FFT of size na over x[c + nb*i], times
+// W_n^{c k}, into scratch row-major [k][c].  Pass 2: for each row k, FFT of
+// size nb over c; output index k + na*q.  CB columns / rows per CTA.
+template <bool INV, int CB, class Ld>
+__global__ void __launch_bounds__(kThreads)
+k_fft4_pass1(Ld ld, const Job* __restrict__ jobs, int logn, int la, float2* __restrict__ scr,
+             const float2* __restrict__ tw, int twlog) {
+  extern __shared__ float2 sm[];
+  const int lb = logn - la, na = 1 << la, nb = 1 << lb;
+  const int groups = nb / CB;
+  const int jl = blockIdx.x / groups;
+  const int c0 = (blockIdx.x % groups) * CB;
+  const Job jb = jobs[jl];
+  const int bs = na + 1;
+  float2* a = sm;
+  float2* b = sm + CB * bs;
+  for (int i = threadIdx.x; i < CB * na; i += blockDim.x) {
+    const int cc = i % CB, ii = i / CB;
+    a[cc * bs + ii] = ld(jb, (c0 + cc) + (ii << lb), logn);
+  }
+  __syncthreads();
+  float2* r = cta_fft<INV>(a, b, la, CB, bs, tw, twlog);
+  const int tshift = twlog - logn;
+  float2* out = scr + (static_cast<int64_t>(jl) << logn);
+  for (int i = threadIdx.x; i < CB * na; i += blockDim.x) {
+    const int cc = i % CB, k = i / CB;
+    const float2 v = cmul(r[cc * bs + k], twiddle<INV>(tw, ((c0 + cc) * k) << tshift));
+    out[(static_cast<int64_t>(k) << lb) + c0 + cc] = v;
+  }
+}
+
+template <bool INV, int CB, class St>
+__global__ void __launch_bounds__(kThreads)
+k_fft4_pass2(St st, const Job* __restrict__ jobs, int logn, int la, const float2* __restrict__ scr,
+             const float2* __restrict__ tw, int twlog) {
+  extern __shared__ float2 sm[];
+  const int lb = logn - la, na = 1 << la, nb = 1 << lb;
+  const int groups = na / CB;
+  const int jl = blockIdx.x / groups;
+  const int k0 = (blockIdx.x % groups) * CB;
+  const Job jb = jobs[jl];
+  const int bs = nb + 1;
+  float2* a = sm;
+  float2* b = sm + CB * bs;
+  const float2* in = scr + (static_cast<int64_t>(jl) << logn);
+  for (int i = threadIdx.x; i < CB * nb; i += blockDim.x) {
+    const int kk = i >> lb, c = i & (nb - 1);
+    a[kk * bs + c] = in[(static_cast<int64_t>(k0 + kk) << lb) + c];
+  }
+  __syncthreads();
+  float2* r = cta_fft<INV>(a, b, lb, CB, bs, tw, twlog);
+  for (int i = threadIdx.x; i < CB * nb; i += blockDim.x) {
+    const int kk = i % CB, q = i / CB;
+    st(jb, (k0 + kk) + (q << la), r[kk * bs + q]);
+  }
+}
+
+// Opt in to large dynamic shared memory once per kernel (keyed on the kernel
+// itself: instantiations that differ only in INV or MODE share a type).
+template <auto Kernel>
+void allow_big_smem() {
+  static const cudaError_t once = [] {
+    const cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaGetLastError();  // do not leave a sticky error for the next launch check
+    return e;
+  }();
+  (void)once;
+}
+
+template <bool INV, class Ld, class St>
+int run_fft(const Plan& p, const std::vector<FftLaunch>& L, const Ld& ld, const St& st, float2* scr,
+            cudaStream_t s) {
+  for (const FftLaunch& l : L) {
+    const Job* jobs = p.d_jobs + l.job0;
+    if (l.logn <= kSmallLogMax) {
+      const int n = 1 << l.logn;
+      const int per = std::max(1, (1 << 12) >> l.logn);
+      const int grid = (l.njobs + per - 1) / per;
+      const size_t smem = 2 * size_t(per) * n * sizeof(float2);
+      allow_big_smem<k_fft_small<INV, Ld, St>>();
+      k_fft_small<INV, Ld, St><<<grid, kThreads, smem, s>>>(ld, st, jobs, l.njobs, l.logn, per, p.d_tw,
+                                                             p.twlog);
+    } else {
+      const int la = l.logn / 2, lb = l.logn - la;
+      if (la <= 9 && lb <= 9) {
+        constexpr int CB = 16;
+        const size_t sm1 = 2 * size_t(CB) * ((1 << la) + 1) * sizeof(float2);
+        const size_t sm2 = 2 * size_t(CB) * ((1 << lb) + 1) * sizeof(float2);
+        allow_big_smem<k_fft4_pass1<INV, CB, Ld>>();
+        allow_big_smem<k_fft4_pass2<INV, CB, St>>();
+        k_fft4_pass1<INV, CB, Ld><<<l.njobs * ((1 << lb) / CB), kThreads, sm1, s>>>(ld, jobs, l.logn, la, scr,
+                                                                                  p.d_tw, p.twlog);
+        k_fft4_pass2<INV, CB, St><<<l.njobs * ((1 << la) / CB), kThreads, sm2, s>>>(st, jobs, l.logn, la, scr,
+                                                                                  p.d_tw, p.twlog);
+      } else {
+        constexpr int CB = 8;
+        const size_t sm1 = 2 * size_t(CB) * ((1 << la) + 1) * sizeof(float2);
+        const size_t sm2 = 2 * size_t(CB) * ((1 << lb) + 1) * sizeof(float2);
+        allow_big_smem<k_fft4_pass1<INV, CB, Ld>>();
+        allow_big_smem<k_fft4_pass2<INV, CB, St>>();
+        k_fft4_pass1<INV, CB, Ld><<<l.njobs * ((1 << lb) / CB), kThreads, sm1, s>>>(ld, jobs, l.logn, la, scr,
+                                                                                  p.d_tw, p.twlog);
+        k_fft4_pass2<INV, CB, St><<<l.njobs * ((1 << la) / CB), kThreads, sm2, s>>>(st, jobs, l.logn, la, scr,
+                                                                                  p.d_tw, p.twlog);
+      }
+    }
+    if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
+  }
+  return JTFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Frequential scattering (§3.4) fused with modulus and phi_F averaging.
+// One CTA per tile of W time columns; every column is zero-padded to N_fr
+// rows, transformed once, then for each frequential filter beta:
+// product + fold to R = N_fr/2^k bins, inverse FFT, modulus, FFT, phi_F
+// product + fold to R_out bins, inverse FFT, real part.
+// MODE 1: first order, input S1 (real), betas {phi_F, +xi}, output Phi.
+// MODE 2: second order, input Y2 (complex), all betas, output V2.
+// ---------------------------------------------------------------------------
+struct FreqArgs {
+  int N1, N_fr, logNfr, R_out, logRout, n_frames, logN, W, logW, n_beta1, n_beta2;
+  int64_t phi_size, phi1_off, y2_tot, v2_tot;
+  const FiltD* beta;
+  FiltD phiF;
+  const int* s2;
+  const int* n1max_act;
+  const int64_t* y2_off;
+  const int64_t* v2_off;
+  const float2* tw;
+  int twlog;
+};
+
+template <int MODE>
+__device__ __forceinline__ void freq_load_columns(const FreqArgs& A, const Tile& tl, const float* S1,
+                                                  const float2* Y2, float2* dst, int& stride) {
+  int n1m;
+  const float2* ysrc = nullptr;
+  const float* ssrc = nullptr;
+  if (MODE == 1) {
+    n1m = A.N1;
+    stride = A.n_frames;
+    ssrc = S1 + static_cast<int64_t>(tl.b) * A.N1 * A.n_frames + tl.t0;
+  } else {
+    n1m = A.n1max_act[tl.a];
+    stride = 1 << (A.logN - A.s2[tl.a]);
+    ysrc = Y2 + static_cast<int64_t>(tl.b) * A.y2_tot + A.y2_off[tl.a] + tl.t0;
+  }
+  const int W = A.W;
+  for (int i = threadIdx.x; i < W * A.N_fr; i += blockDim.x) {
+    const int r = i >> A.logW, w = i & (W - 1);
+    float2 v = make_float2(0.f, 0.f);
+    if (r < n1m && w < tl.ncols) {
+      if (MODE == 1) v = make_float2(ssrc[static_cast<int64_t>(r) * stride + w], 0.f);
+      else v = ysrc[static_cast<int64_t>(r) * stride + w];
+    }
+    dst[w * A.N_fr + r] = v;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_freq_fwd(FreqArgs A, const Tile* __restrict__ tiles, const float* __restrict__ S1,
+           const float2* __restrict__ Y2, float* __restrict__ out) {
+  extern __shared__ float2 sm[];
+  const Tile tl = tiles[blockIdx.x];
+  const int W = A.W, Nfr = A.N_fr;
+  float2* buf0 = sm;
+  float2* buf1 = sm + W * Nfr;
+  float2* buf2 = sm + 2 * W * Nfr;
+  int stride;
+  freq_load_columns<MODE>(A, tl, S1, Y2, buf0, stride);
+  __syncthreads();
+  float2* yh = cta_fft<false>(buf0, buf1, A.logNfr, W, Nfr, A.tw, A.twlog);
+  float2* f1 = (yh == buf0) ? buf1 : buf0;
+  float2* f2 = buf2;
+  const int nb = (MODE == 1) ? A.n_beta1 : A.n_beta2;
+  const float invNfr = 1.f / static_cast<float>(Nfr);
+  for (int bi = 0; bi < nb; ++bi) {
+    const FiltD fb = A.beta[bi];
+    const int lR = A.logNfr - fb.k, R = 1 << lR;
+    for (int i = threadIdx.x; i < W * R; i += blockDim.x) {
+      const int w = i >> lR, m = i & (R - 1);
+      f1[i] = cscale(band_gather(yh + w * Nfr, Nfr, R, m, fb), invNfr);
+    }
+    __syncthreads();
+    float2* z = cta_fft<true>(f1, f2, lR, W, R, A.tw, A.twlog);
+    for (int i = threadIdx.x; i < W * R; i += blockDim.x) {
+      const float2 v = z[i];
+      z[i] = make_float2(sqrtf(v.x * v.x + v.y * v.y), 0.f);
+    }
+    __syncthreads();
+    float2* zo = (z == f1) ? f2 : f1;
+    float2* uh = cta_fft<false>(z, zo, lR, W, R, A.tw, A.twlog);
+    float2* g = (uh == f1) ? f2 : f1;
+    const float invR = 1.f / static_cast<float>(R);
+    for (int i = threadIdx.x; i < W * A.R_out; i += blockDim.x) {
+      const int w = i >> A.logRout, m = i & (A.R_out - 1);
+      g[i] = cscale(band_gather(uh + w * R, R, A.R_out, m, A.phiF), invR);
+    }
+    __syncthreads();
+    float2* pr = cta_fft<true>(g, uh, A.logRout, W, A.R_out, A.tw, A.twlog);
+    for (int i = threadIdx.x; i < A.R_out * W; i += blockDim.x) {
+      const int row = i >> A.logW, w = i & (W - 1);
+      if (w < tl.ncols) {
+        const float v = pr[w * A.R_out + row].x;
+        if (MODE == 1)
+          out[static_cast<int64_t>(tl.b) * A.phi_size + A.phi1_off +
+              (static_cast<int64_t>(bi) * A.R_out + row) * A.n_frames + tl.t0 + w] = v;
+        else
+          out[static_cast<int64_t>(tl.b) * A.v2_tot + A.v2_off[tl.a] +
+              (static_cast<int64_t>(bi) * A.R_out + row) * stride + tl.t0 + w] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Adjoint of k_freq_fwd at the same input (recomputed): given the gradient
+// of its outputs (dPhi first-order block for MODE 1, dV2 for MODE 2), writes
+// the gradient of its input columns (dS1 real for MODE 1, dY2 for MODE 2).
+template <int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_freq_adj(FreqArgs A, const Tile* __restrict__ tiles, const float* S1, const float2* __restrict__ Y2,
+           const float* __restrict__ dout, float* dS1, float2* __restrict__ dY2) {
+  extern __shared__ float2 sm[];
+  const Tile tl = tiles[blockIdx.x];
+  const int W = A.W, Nfr = A.N_fr, WN = W * Nfr;
+  float2* buf0 = sm;
+  float2* buf1 = sm + WN;
+  float2* zb = sm + 2 * WN;
+  float2* f1 = sm + 3 * WN;
+  float2* f2 = sm + 4 * WN;
+  int stride;
+  freq_load_columns<MODE>(A, tl, S1, Y2, buf0, stride);
+  __syncthreads();
+  float2* yh = cta_fft<false>(buf0, buf1, A.logNfr, W, Nfr, A.tw, A.twlog);
+  float2* D = (yh == buf0) ? buf1 : buf0;
+  for (int i = threadIdx.x; i < WN; i += blockDim.x) D[i] = make_float2(0.f, 0.f);
+  const int nb = (MODE == 1) ? A.n_beta1 : A.n_beta2;
+  const float invNfr = 1.f / static_cast<float>(Nfr);
+  const int Rout = A.R_out, lRo = A.logRout;
+  for (int bi = 0; bi < nb; ++bi) {
+    const FiltD fb = A.beta[bi];
+    const int lR = A.logNfr - fb.k, R = 1 << lR;
+    const float invR = 1.f / static_cast<float>(R);
+    // Recompute z = F^H(fold(psi_beta * yhat)) / N_fr and keep it in zb.
+    for (int i = threadIdx.x; i < W * R; i += blockDim.x) {
+      const int w = i >> lR, m = i & (R - 1);
+      f1[i] = cscale(band_gather(yh + w * Nfr, Nfr, R, m, fb), invNfr);
+    }
+    __syncthreads();
+    float2* z = cta_fft<true>(f1, f2, lR, W, R, A.tw, A.twlog);
+    for (int i = threadIdx.x; i < W * R; i += blockDim.x) zb[i] = z[i];
+    // dW = F(dw), dw the output gradient of this beta's R_out rows.
+    for (int i = threadIdx.x; i < W * Rout; i += blockDim.x) {
+      const int w = i >> lRo, row = i & (Rout - 1);
+      float v = 0.f;
+      if (w < tl.ncols) {
+        if (MODE == 1)
+          v = dout[static_cast<int64_t>(tl.b) * A.phi_size + A.phi1_off +
+                   (static_cast<int64_t>(bi) * Rout + row) * A.n_frames + tl.t0 + w];
+        else
+          v = dout[static_cast<int64_t>(tl.b) * A.v2_tot + A.v2_off[tl.a] +
+                   (static_cast<int64_t>(bi) * Rout + row) * stride + tl.t0 + w];
+      }
+      f1[i] = make_float2(v, 0.f);
+    }
+    __syncthreads();
+    float2* dW = cta_fft<false>(f1, f2, lRo, W, Rout, A.tw, A.twlog);
+    float2* X = (dW == f1) ? f2 : f1;
+    // du_hat[m] = (1/R) phi_F-level(m) dW[m mod R_out]  (adjoint of the fold)
+    for (int i = threadIdx.x; i < W * R; i += blockDim.x) {
+      const int w = i >> lR, m = i & (R - 1);
+      X[i] = cscale(dW[w * Rout + (m & (Rout - 1))], band_lev(m, R, A.phiF) * invR);
+    }
+    __syncthreads();
+    float2* du = cta_fft<true>(X, dW, lR, W, R, A.tw, A.twlog);
+    // dz = Re(du) z / |z|
+    for (int i = threadIdx.x; i < W * R; i += blockDim.x) {
+      const float g = du[i].x;
+      const float2 v = zb[i];
+      const float mg = sqrtf(v.x * v.x + v.y * v.y);
+      du[i] = mg > 0.f ? make_float2(g * v.x / mg, g * v.y / mg) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* other = (du == f1) ? f2 : f1;
+    float2* dZ = cta_fft<false>(du, other, lR, W, R, A.tw, A.twlog);
+    // D[m] += (1/N_fr) psi_beta(s(m)) dZ[m mod R]
+    for (int i = threadIdx.x; i < WN; i += blockDim.x) {
+      const int w = i >> A.logNfr, m = i & (Nfr - 1);
+      const int s = m < (Nfr >> 1) ? m : m - Nfr;
+      if (s >= fb.lo && s <= fb.hi) {
+        const float g = fval(fb, s) * invNfr;
+        const float2 v = dZ[w * R + (m & (R - 1))];
+        D[i].x += g * v.x;
+        D[i].y += g * v.y;
+      }
+    }
+    __syncthreads();
+  }
+  float2* dy = cta_fft<true>(D, f1, A.logNfr, W, Nfr, A.tw, A.twlog);
+  int n1m;
+  if (MODE == 1) n1m = A.N1;
+  else n1m = A.n1max_act[tl.a];
+  for (int i = threadIdx.x; i < n1m * W; i += blockDim.x) {
+    const int r = i >> A.logW, w = i & (W - 1);
+    if (w < tl.ncols) {
+      const float2 v = dy[w * Nfr + r];
+      if (MODE == 1)
+        dS1[(static_cast<int64_t>(tl.b) * A.N1 + r) * A.n_frames + tl.t0 + w] = v.x;
+      else
+        dY2[static_cast<int64_t>(tl.b) * A.y2_tot + A.y2_off[tl.a] + static_cast<int64_t>(r) * stride + tl.t0 + w] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// phi_T averaging of the second order (Eq. (5)) as a decimating FIR and its
+// adjoint.  out[f] = sum_t v[t] g_s[(f D - t) mod L], L = N/2^s, D = T/2^s.
+// ---------------------------------------------------------------------------
+struct PoolArgs {
+  int logN, lT, n_frames, R_out, n_beta2, n_active, half;  // half = kPoolHalfT * T
+  int64_t phi_size, v2_tot;
+  const int* s2;
+  const int64_t* v2_off;
+  const int64_t* phi2_off;
+  const float* taps;
+  const int64_t* tap_off;
+};
+
+__global__ void __launch_bounds__(kThreads)
+k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ phi, int64_t nwarps) {
+  const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= nwarps) return;
+  const int64_t per_a = static_cast<int64_t>(A.n_beta2) * A.R_out * A.n_frames;
+  const int64_t per_b = per_a * A.n_active;
+  const int b = static_cast<int>(gw / per_b);
+  int64_t r = gw % per_b;
+  const int a = static_cast<int>(r / per_a);
+  r %= per_a;
+  const int64_t rowid = r / A.n_frames;
+  const int f = static_cast<int>(r % A.n_frames);
+  const int s = A.s2[a];
+  const int L = 1 << (A.logN - s);
+  const int D = 1 << (A.lT - s);
+  const float* v = V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a] + rowid * L;
+  const float* g = A.taps + A.tap_off[s];
+  const int H = A.half >> s;
+  const int c = f * D;
+  float acc = 0.f;
+  if (2 * H + 1 >= L) {
+    for (int t = lane; t < L; t += 32) acc += v[t] * g[(c - t) & (L - 1)];
+  } else {
+    for (int d = -H + lane; d <= H; d += 32) acc += v[(c - d) & (L - 1)] * g[d & (L - 1)];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) phi[static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a] + rowid * A.n_frames + f] = acc;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_pool_adj(PoolArgs A, const float* __restrict__ dphi, float* __restrict__ dV2, int64_t total) {
+  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int b = static_cast<int>(idx / A.v2_tot);
+  const int64_t loc = idx % A.v2_tot;
+  int a = A.n_active - 1;
+  while (a > 0 && A.v2_off[a] > loc) --a;
+  const int s = A.s2[a];
+  const int lL = A.logN - s, L = 1 << lL;
+  const int D = 1 << (A.lT - s);
+  const int64_t within = loc - A.v2_off[a];
+  const int64_t rowid = within >> lL;
+  const int t = static_cast<int>(within & (L - 1));
+  const float* g = A.taps + A.tap_off[s];
+  const float* dp = dphi + static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a] + rowid * A.n_frames;
+  float acc = 0.f;
+  for (int f = 0; f < A.n_frames; ++f) acc += dp[f] * g[(f * D - t) & (L - 1)];
+  dV2[idx] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint gathers of the time-axis filterings.
+// ---------------------------------------------------------------------------
+struct GradArgs {
+  int logN, N1, n_frames, n_active;
+  int64_t u1_tot, y2_tot;
+  const FiltD* psi1;
+  const FiltD* psi2;
+  FiltD phiT;
+  const int* s2;
+  const int* n1max_act;
+  const int* act_n2;
+  const int64_t* y2_off;
+  const int64_t* u1_off;
+};
+
+// dU1hat[b][n1][m] = (1/L1) [ sum_{n2: n1 < n1max} lev_{psi_n2}(m) dZ2[n2][n1][m mod L2]
+//                             + lev_{phi_T}(m) dS1hat[n1][m mod N/T] ]
+__global__ void __launch_bounds__(kThreads)
+k_dU1(GradArgs A, const Job* __restrict__ jobs, const float2* __restrict__ dZ2,
+      const float2* __restrict__ dS1h, float2* __restrict__ dU1h) {
+  const Job jb = jobs[blockIdx.y];
+  const int lL1 = jb.lslog, L1 = 1 << lL1;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= L1) return;
+  const int n1 = jb.filt, b = jb.b;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int a = 0; a < A.n_active; ++a) {
+    if (n1 >= A.n1max_act[a]) continue;
+    const int L2 = 1 << (A.logN - A.s2[a]);
+    const float lev = band_lev(m, L1, A.psi2[A.act_n2[a]]);
+    if (lev != 0.f) {
+      const float2 v = dZ2[static_cast<int64_t>(b) * A.y2_tot + A.y2_off[a] + static_cast<int64_t>(n1) * L2 +
+                           (m & (L2 - 1))];
+      acc.x += lev * v.x;
+      acc.y += lev * v.y;
+    }
+  }
+  {
+    const float lev = band_lev(m, L1, A.phiT);
+    if (lev != 0.f) {
+      const float2 v = dS1h[(static_cast<int64_t>(b) * A.N1 + n1) * A.n_frames + (m & (A.n_frames - 1))];
+      acc.x += lev * v.x;
+      acc.y += lev * v.y;
+    }
+  }
+  dU1h[jb.dst + m] = cscale(acc, 1.f / static_cast<float>(L1));
+}
+
+// dXhat[b][m] = (1/N) [ sum_n1 psi_n1(s) dZ1[n1][m mod L1] + phi_T(s) dS0hat[m mod N/T] ]
+__global__ void __launch_bounds__(kThreads)
+k_dX(GradArgs A, int64_t total, const float2* __restrict__ dZ1, const float2* __restrict__ dS0h,
+     float2* __restrict__ dXh) {
+  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int N = 1 << A.logN;
+  const int b = static_cast<int>(idx >> A.logN);
+  const int m = static_cast<int>(idx & (N - 1));
+  const int s = m < (N >> 1) ? m : m - N;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int n1 = 0; n1 < A.N1; ++n1) {
+    const FiltD f = A.psi1[n1];
+    if (s < f.lo || s > f.hi) continue;
+    const int L1 = 1 << (A.logN - f.k);
+    const float g = fval(f, s);
+    const float2 v = dZ1[static_cast<int64_t>(b) * A.u1_tot + A.u1_off[n1] + (m & (L1 - 1))];
+    acc.x += g * v.x;
+    acc.y += g * v.y;
+  }
+  if (s >= A.phiT.lo && s <= A.phiT.hi) {
+    const float g = fval(A.phiT, s);
+    const float2 v = dS0h[static_cast<int64_t>(b) * A.n_frames + (m & (A.n_frames - 1))];
+    acc.x += g * v.x;
+    acc.y += g * v.y;
+  }
+  dXh[idx] = cscale(acc, 1.f / static_cast<float>(N));
+}
+
+// ---------------------------------------------------------------------------
+// Loss E_b = sum (phi - target)^2 and dphi = 2 (phi - target); fixed-order
+// block reduction (deterministic).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512)
+k_loss(const float* __restrict__ phi, const float* __restrict__ tgt, float* __restrict__ dphi,
+       float* __restrict__ loss, int64_t size) {
+  __shared__ double red[512];
+  const int b = blockIdx.x;
+  const float* p = phi + static_cast<int64_t>(b) * size;
+  const float* t = tgt + static_cast<int64_t>(b) * size;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < size; i += blockDim.x) {
+    const float d = p[i] - t[i];
+    if (dphi) dphi[static_cast<int64_t>(b) * size + i] = 2.f * d;
+    acc += static_cast<double>(d) * d;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[b] = static_cast<float>(red[0]);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_adam(float* __restrict__ y, float* __restrict__ m, float* __restrict__ v, const float* __restrict__ g,
+       int64_t n, float lr, float c1, float c2) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = 0.9f * m[i] + 0.1f * gi;
+  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  y[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+}
+
+// ---------------------------------------------------------------------------
+// Orchestration.
+// ---------------------------------------------------------------------------
+struct Bufs {
+  float2 *Xh, *U1h, *Zs, *dS1h, *Y2, *dY2, *dXh, *dS0h, *scr;
+  float *S1, *V2, *phi, *dphi, *dy;
+};
+
+Bufs bufs(const Plan& p, void* ws) {
+  auto* c = static_cast<unsigned char*>(ws);
+  Bufs w;
+  w.Xh = reinterpret_cast<float2*>(c + p.ws_Xh);
+  w.U1h = reinterpret_cast<float2*>(c + p.ws_U1h);
+  w.Zs = reinterpret_cast<float2*>(c + p.ws_Zs);
+  w.S1 = reinterpret_cast<float*>(c + p.ws_S1);
+  w.dS1h = reinterpret_cast<float2*>(c + p.ws_dS1h);
+  w.Y2 = reinterpret_cast<float2*>(c + p.ws_Y2);
+  w.dY2 = reinterpret_cast<float2*>(c + p.ws_dY2);
+  w.V2 = reinterpret_cast<float*>(c + p.ws_V2);
+  w.phi = reinterpret_cast<float*>(c + p.ws_phi);
+  w.dphi = reinterpret_cast<float*>(c + p.ws_dphi);
+  w.dXh = reinterpret_cast<float2*>(c + p.ws_dXh);
+  w.dS0h = reinterpret_cast<float2*>(c + p.ws_dS0h);
+  w.dy = reinterpret_cast<float*>(c + p.ws_dy);
+  w.scr = reinterpret_cast<float2*>(c + p.ws_scr);
+  return w;
+}
+
+FreqArgs freq_args(const Plan& p) {
+  FreqArgs A{};
+  A.N1 = p.N1;
+  A.N_fr = p.N_fr;
+  A.logNfr = p.logNfr;
+  A.R_out = p.R_out;
+  A.logRout = p.logNfr - p.lF;
+  A.n_frames = p.n_frames;
+  A.logN = p.logN;
+  A.W = p.freq_cols;
+  int lw = 0;
+  while ((1 << lw) < A.W) ++lw;
+  A.logW = lw;
+  A.n_beta1 = p.n_beta1;
+  A.n_beta2 = p.n_beta2;
+  A.phi_size = p.phi_size;
+  A.phi1_off = p.phi1_off;
+  A.y2_tot = p.y2_tot;
+  A.v2_tot = p.v2_tot;
+  A.beta = p.d_beta;
+  A.phiF = p.h_phiF;
+  A.s2 = p.d_s2;
+  A.n1max_act = p.d_n1max_act;
+  A.y2_off = p.d_y2_off;
+  A.v2_off = p.d_v2_off;
+  A.tw = p.d_tw;
+  A.twlog = p.twlog;
+  return A;
+}
+
+PoolArgs pool_args(const Plan& p) {
+  PoolArgs A{};
+  A.logN = p.logN;
+  A.lT = p.lT;
+  A.n_frames = p.n_frames;
+  A.R_out = p.R_out;
+  A.n_beta2 = p.n_beta2;
+  A.n_active = p.n_active;
+  A.half = static_cast<int>(std::min<int64_t>(int64_t(kPoolHalfT) * p.T, p.N));
+  A.phi_size = p.phi_size;
+  A.v2_tot = p.v2_tot;
+  A.s2 = p.d_s2;
+  A.v2_off = p.d_v2_off;
+  A.phi2_off = p.d_phi2_off;
+  A.taps = p.d_taps;
+  A.tap_off = p.d_tap_off;
+  return A;
+}
+
+GradArgs grad_args(const Plan& p) {
+  GradArgs A{};
+  A.logN = p.logN;
+  A.N1 = p.N1;
+  A.n_frames = p.n_frames;
+  A.n_active = p.n_active;
+  A.u1_tot = p.u1_tot;
+  A.y2_tot = p.y2_tot;
+  A.psi1 = p.d_psi1;
+  A.psi2 = p.d_psi2;
+  A.phiT = p.h_phiT;
+  A.s2 = p.d_s2;
+  A.n1max_act = p.d_n1max_act;
+  A.act_n2 = p.d_act_n2;
+  A.y2_off = p.d_y2_off;
+  A.u1_off = p.d_u1_off;
+  return A;
+}
+
+#define JTFS_TRY(expr)            \
+  do {                            \
+    const int rc_ = (expr);       \
+    if (rc_ != JTFS_OK) return rc_; \
+  } while (0)
+
+int check_launch() { return cudaGetLastError() == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA; }
+
+// Bracket one launch of `stage` with the caller's events, if registered.
+void prof_begin(const Plan& p, int stage, cudaStream_t s) {
+  const auto& ev = p.prof_events[stage];
+  const int i = p.prof_next[stage];
+  if (2 * i + 1 < static_cast<int>(ev.size())) cudaEventRecord(static_cast<cudaEvent_t>(ev[2 * i]), s);
+}
+void prof_end(const Plan& p, int stage, cudaStream_t s) {
+  const auto& ev = p.prof_events[stage];
+  const int i = p.prof_next[stage];
+  if (2 * i + 1 < static_cast<int>(ev.size())) {
+    cudaEventRecord(static_cast<cudaEvent_t>(ev[2 * i + 1]), s);
+    p.prof_next[stage] = i + 1;
+  }
+}
+
+int64_t fft_launches(const std::vector<FftLaunch>& L) {
+  int64_t n = 0;
+  for (const FftLaunch& l : L) n += l.logn <= kSmallLogMax ? 1 : 2;
+  return n;
+}
+
+int64_t forward_launches(const Plan& p, bool full) {
+  int64_t n = fft_launches(p.L_x) + fft_launches(p.L_u1) + fft_launches(p.L_u1inplace) + fft_launches(p.L_s1);
+  if (full) n += fft_launches(p.L_s0) + 1;
+  if (p.n_active > 0) n += fft_launches(p.L_y2) + (full ? 2 : 0);
+  return n;
+}
+
+int64_t backward_launches(const Plan& p) {
+  int64_t n = 1 + fft_launches(p.L_ds1) + static_cast<int64_t>(p.L_u1inplace.size()) +
+              2 * fft_launches(p.L_u1inplace) + fft_launches(p.L_u1) + fft_launches(p.L_ds0) + 1 +
+              fft_launches(p.L_x);
+  if (p.n_active > 0) n += 2 + fft_launches(p.L_y2inplace);
+  return n;
+}
+
+size_t freq_smem(const Plan& p, int nbuf) { return size_t(nbuf) * p.freq_cols * p.N_fr * sizeof(float2); }
+
+// Forward stages.  `full` = false stops after what the adjoint needs
+// (Xhat, U1hat, S1, Y2) and skips writing Phi.
+int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, bool full, cudaStream_t s) {
+  JTFS_TRY((run_fft<false>(p, p.L_x, LdReal{x}, StC{w.Xh}, w.scr, s)));
+  JTFS_TRY((run_fft<true>(p, p.L_u1, LdBand{w.Xh, p.d_psi1, FiltD{}}, StC{w.U1h}, w.scr, s)));
+  JTFS_TRY((run_fft<false>(p, p.L_u1inplace, LdMod{w.U1h}, StC{w.U1h}, w.scr, s)));
+  if (full) JTFS_TRY((run_fft<true>(p, p.L_s0, LdBand{w.Xh, nullptr, p.h_phiT}, StR{phi}, w.scr, s)));
+  JTFS_TRY((run_fft<true>(p, p.L_s1, LdBand{w.U1h, nullptr, p.h_phiT}, StR{w.S1}, w.scr, s)));
+  const FreqArgs FA = freq_args(p);
+  if (full) {
+    allow_big_smem<k_freq_fwd<1>>();
+    k_freq_fwd<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 3), s>>>(
+        FA, p.d_tiles1, w.S1, nullptr, phi);
+    JTFS_TRY(check_launch());
+  }
+  if (p.n_active > 0) {
+    JTFS_TRY((run_fft<true>(p, p.L_y2, LdBand{w.U1h, p.d_psi2, FiltD{}}, StC{w.Y2}, w.scr, s)));
+    if (full) {
+      allow_big_smem<k_freq_fwd<2>>();
+      prof_begin(p, JTFS_STAGE_FREQ2_FWD, s);
+      k_freq_fwd<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 3), s>>>(
+          FA, p.d_tiles2, nullptr, w.Y2, w.V2);
+      prof_end(p, JTFS_STAGE_FREQ2_FWD, s);
+      JTFS_TRY(check_launch());
+      const PoolArgs PA = pool_args(p);
+      const int64_t nwarps = int64_t(p.batch) * p.n_active * p.n_beta2 * p.R_out * p.n_frames;
+      const int64_t blocks = (nwarps * 32 + kThreads - 1) / kThreads;
+      prof_begin(p, JTFS_STAGE_POOL_FWD, s);
+      k_pool_fwd<<<static_cast<unsigned>(blocks), kThreads, 0, s>>>(PA, w.V2, phi, nwarps);
+      prof_end(p, JTFS_STAGE_POOL_FWD, s);
+      JTFS_TRY(check_launch());
+    }
+  }
+  return JTFS_OK;
+}
+
+// Backward stages from dphi (device, [batch][phi_size]) to dx.  Requires
+// forward_stages(full or not) to have filled Xh, U1h, S1 and Y2.
+int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, cudaStream_t s) {
+  const FreqArgs FA = freq_args(p);
+  const GradArgs GA = grad_args(p);
+  if (p.n_active > 0) {
+    const PoolArgs PA = pool_args(p);
+    const int64_t total = int64_t(p.batch) * p.v2_tot;
+    prof_begin(p, JTFS_STAGE_POOL_ADJ, s);
+    k_pool_adj<<<static_cast<unsigned>((total + kThreads - 1) / kThreads), kThreads, 0, s>>>(PA, dphi, w.V2,
+                                                                                             total);
+    prof_end(p, JTFS_STAGE_POOL_ADJ, s);
+    JTFS_TRY(check_launch());
+    allow_big_smem<k_freq_adj<2>>();
+    prof_begin(p, JTFS_STAGE_FREQ2_ADJ, s);
+    k_freq_adj<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 5), s>>>(
+        FA, p.d_tiles2, nullptr, w.Y2, w.V2, nullptr, w.dY2);
+    prof_end(p, JTFS_STAGE_FREQ2_ADJ, s);
+    JTFS_TRY(check_launch());
+  }
+  allow_big_smem<k_freq_adj<1>>();
+  k_freq_adj<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 5), s>>>(
+      FA, p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr);
+  JTFS_TRY(check_launch());
+  if (p.n_active > 0) JTFS_TRY((run_fft<false>(p, p.L_y2inplace, LdC{w.dY2}, StC{w.dY2}, w.scr, s)));
+  JTFS_TRY((run_fft<false>(p, p.L_ds1, LdReal{w.S1}, StC{w.dS1h}, w.scr, s)));
+  for (const FftLaunch& l : p.L_u1inplace) {
+    dim3 grid((1u << l.logn) / kThreads + 1, l.njobs);
+    k_dU1<<<grid, kThreads, 0, s>>>(GA, p.d_jobs + l.job0, w.dY2, w.dS1h, w.U1h);
+    JTFS_TRY(check_launch());
+  }
+  JTFS_TRY((run_fft<true>(p, p.L_u1inplace, LdC{w.U1h}, StC{w.U1h}, w.scr, s)));
+  JTFS_TRY((run_fft<true>(p, p.L_u1, LdBand{w.Xh, p.d_psi1, FiltD{}}, StC{w.Zs}, w.scr, s)));
+  JTFS_TRY((run_fft<false>(p, p.L_u1inplace, LdDz{w.U1h, w.Zs}, StC{w.Zs}, w.scr, s)));
+  JTFS_TRY((run_fft<false>(p, p.L_ds0, LdReal{dphi}, StC{w.dS0h}, w.scr, s)));
+  {
+    const int64_t total = int64_t(p.batch) * p.N;
+    k_dX<<<static_cast<unsigned>((total + kThreads - 1) / kThreads), kThreads, 0, s>>>(GA, total, w.Zs, w.dS0h,
+                                                                                       w.dXh);
+    JTFS_TRY(check_launch());
+  }
+  JTFS_TRY((run_fft<true>(p, p.L_x, LdC{w.dXh}, StR{dx}, w.scr, s)));
+  return JTFS_OK;
+}
+
+int check_call(const Plan& p, void* ws) {
+  if (!p.on_device) return JTFS_ERR_NODEVICE;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return JTFS_ERR_WORKSPACE;
+  return JTFS_OK;
+}
+
+bool misaligned(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15) != 0; }
+
+}  // namespace
+}  // namespace jtfs
+
+
+using jtfs::Bufs;
+
+extern "C" int jtfs_forward(jtfs_plan_t plan, const float* x, float* phi, void* workspace, void* stream) {
+  if (!plan || !x || !phi || jtfs::misaligned(x) || jtfs::misaligned(phi)) return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  JTFS_TRY(jtfs::check_call(p, workspace));
+  const Bufs w = jtfs::bufs(p, workspace);
+  return jtfs::forward_stages(p, x, phi, w, true, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int jtfs_backward(jtfs_plan_t plan, const float* x, const float* dphi, float* dx, void* workspace,
+                             void* stream) {
+  if (!plan || !x || !dphi || !dx || jtfs::misaligned(x) || jtfs::misaligned(dphi) || jtfs::misaligned(dx))
+    return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  JTFS_TRY(jtfs::check_call(p, workspace));
+  const Bufs w = jtfs::bufs(p, workspace);
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  JTFS_TRY(jtfs::forward_stages(p, x, nullptr, w, false, s));
+  return jtfs::backward_stages(p, dphi, dx, w, s);
+}
+
+extern "C" int jtfs_loss_grad(jtfs_plan_t plan, const float* y, const float* phi_target, float* loss, float* dy,
+                              void* workspace, void* stream) {
+  if (!plan || !y || !phi_target || !loss || jtfs::misaligned(y) || jtfs::misaligned(phi_target) ||
+      (dy && jtfs::misaligned(dy)))
+    return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  JTFS_TRY(jtfs::check_call(p, workspace));
+  const Bufs w = jtfs::bufs(p, workspace);
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  JTFS_TRY(jtfs::forward_stages(p, y, w.phi, w, true, s));
+  jtfs::k_loss<<<p.batch, 512, 0, s>>>(w.phi, phi_target, dy ? w.dphi : nullptr, loss, p.phi_size);
+  JTFS_TRY(jtfs::check_launch());
+  if (!dy) return JTFS_OK;
+  return jtfs::backward_stages(p, w.dphi, dy, w, s);
+}
+
+extern "C" int metamer_step(jtfs_plan_t plan, float* y, const float* phi_target, float* adam_m, float* adam_v,
+                            int step, float lr, float* loss_out, void* workspace, void* stream) {
+  if (!plan || !y || !phi_target || !adam_m || !adam_v || !loss_out || step < 1 || !(lr > 0.f) ||
+      jtfs::misaligned(adam_m) || jtfs::misaligned(adam_v))
+    return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  JTFS_TRY(jtfs::check_call(p, workspace));
+  const Bufs w = jtfs::bufs(p, workspace);
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  JTFS_TRY(jtfs_loss_grad(plan, y, phi_target, loss_out, w.dy, workspace, stream));
+  const int64_t n = int64_t(p.batch) * p.N;
+  const float c1 = static_cast<float>(1.0 / (1.0 - std::pow(0.9, step)));
+  const float c2 = static_cast<float>(1.0 / (1.0 - std::pow(0.999, step)));
+  jtfs::k_adam<<<static_cast<unsigned>((n + jtfs::kThreads - 1) / jtfs::kThreads), jtfs::kThreads, 0, s>>>(
+      y, adam_m, adam_v, w.dy, n, lr, c1, c2);
+  return jtfs::check_launch();
+}
+
+extern "C" int jtfs_profile_stage(jtfs_plan_t plan, int stage, void** events, int count) {
+  if (!plan || stage < 0 || stage >= JTFS_STAGE_COUNT || count < 0 || (count > 0 && !events)) return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  p.prof_events[stage].assign(events ? events : nullptr, events ? events + count : nullptr);
+  p.prof_next[stage] = 0;
+  return JTFS_OK;
+}
+
+extern "C" int64_t jtfs_launch_count(jtfs_plan_t plan, int call) {
+  if (!plan) return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  switch (call) {
+    case 0: return jtfs::forward_launches(p, true);
+    case 1: return jtfs::forward_launches(p, false) + jtfs::backward_launches(p);
+    case 2: return jtfs::forward_launches(p, true) + 1 + jtfs::backward_launches(p);
+    case 3: return jtfs::forward_launches(p, true) + 2 + jtfs::backward_launches(p);
+    default: return JTFS_ERR_ARG;
+  }
+}

@@ -1,0 +1,176 @@
+// Internal definitions shared by the host plan (jtfs_plan.cpp) and the CUDA
+// kernels (jtfs_cuda.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace jtfs {
+
+// A filter as the kernels evaluate it on a grid of n bins (signed bin s,
+// frequency s/n): value(s) = exp(-(s - c0)^2 * a) - kappa * exp(-s^2 * a),
+// with c0 = xi * n and a = 1 / (2 (sigma n)^2); kappa = 0 for low-pass
+// filters.  Outside the band [lo, hi] (signed bins, clipped to
+// [-n/2, n/2 - 1]) the value is below exp(-72) and treated as 0.
+struct FiltD {
+  float c0;
+  float a;
+  float kappa;
+  int lo;
+  int hi;
+  int k;   // dyadic subsampling applied after this filter (stride level)
+  int j;
+  int pad;
+};
+
+// One FFT of a batched launch: where its input row and output row start
+// (element offsets into the launch's source / destination buffers), which
+// filter its loader applies and log2 of the source row length.
+struct Job {
+  int64_t src;
+  int64_t dst;
+  int32_t filt;
+  int32_t lslog;
+  int32_t b;
+  int32_t pad;
+};
+
+// A tile of columns for the frequential kernels.
+struct Tile {
+  int b;      // clip
+  int a;      // active second-order index (-1: first order)
+  int t0;     // first column
+  int ncols;  // columns in this tile
+};
+
+// A batched FFT launch: `njobs` transforms of size 2^logn described by
+// jobs[job0 .. job0 + njobs).
+struct FftLaunch {
+  int logn;
+  int njobs;
+  int job0;
+};
+
+struct FilterH {
+  double xi;
+  double sigma;
+  int j;
+};
+
+// Number of sigmas beyond which a Gaussian term is dropped (exp(-72)).
+constexpr double kBandSigmas = 12.0;
+// Time-pooling taps: half window in units of T (exp(-28) relative).
+constexpr int kPoolHalfT = 12;
+// Largest FFT done by one CTA in shared memory (2^13 complex, ping-pong).
+constexpr int kSmallLogMax = 13;
+// Columns per CTA in the frequential kernels.
+constexpr int kFreqCols = 16;
+
+struct Plan {
+  // Parameters.
+  int64_t N = 0;
+  int J = 0, Q = 0, Q2 = 0, J_fr = 0, Q_fr = 0;
+  int64_t T = 0;
+  int F = 0;
+  int batch = 0;
+  uint32_t flags = 0;
+
+  // Derived sizes.
+  int logN = 0, lT = 0, lF = 0;
+  int N1 = 0, N2 = 0, K = 0;
+  int N_fr = 0, logNfr = 0, R_out = 0;
+  int n_frames = 0, log_frames = 0;
+  int n_active = 0;
+  int n_beta1 = 0, n_beta2 = 0;
+  int64_t phi_size = 0;
+
+  // Filterbanks.
+  std::vector<FilterH> psi1, psi2, psifr;
+  FilterH phiT{}, phiF{};
+  std::vector<int> k1;        // per n1: min(j1, log2 T)
+  std::vector<int> n1max;     // per n2
+  std::vector<int> active;    // active n2 indices
+  std::vector<int> s2;        // per active index: min(j2, log2 T)
+  std::vector<int> beta_k;    // per second-order beta: frequential stride level
+
+  // Per-clip layouts (element counts).
+  std::vector<int64_t> u1_off;  // per n1, in complex elements
+  int64_t u1_tot = 0;
+  std::vector<int64_t> y2_off;  // per active index, start of its [n1max][L2] block
+  int64_t y2_tot = 0;
+  std::vector<int64_t> v2_off;  // per active index, start of [n_beta2][R_out][L2]
+  int64_t v2_tot = 0;
+  std::vector<int64_t> phi2_off;  // per active index, offset inside Phi
+  int64_t phi1_off = 0;
+  std::vector<int64_t> tap_off;   // per level s in [0, lT]: time-pooling taps
+  int64_t tap_tot = 0;
+
+  // Workspace layout (byte offsets).
+  size_t ws_Xh = 0, ws_U1h = 0, ws_Zs = 0, ws_S1 = 0, ws_dS1h = 0, ws_Y2 = 0,
+         ws_dY2 = 0, ws_V2 = 0, ws_phi = 0, ws_dphi = 0, ws_scr = 0,
+         ws_dXh = 0, ws_dS0h = 0, ws_dy = 0, ws_bytes = 0;
+  int64_t scr_elems = 0;  // four-step scratch, complex elements
+
+  // Launch descriptions.
+  std::vector<Job> jobs;
+  std::vector<FftLaunch> L_x;        // F0: FFT of x
+  std::vector<FftLaunch> L_u1;       // F1: per k1 level
+  std::vector<FftLaunch> L_s0;       // F2
+  std::vector<FftLaunch> L_s1;       // F3
+  std::vector<FftLaunch> L_y2;       // F5: per s2 level
+  std::vector<FftLaunch> L_u1inplace;// B6a/B6c: rows of U1h / Zs in place (per k1 level)
+  std::vector<FftLaunch> L_y2inplace;// B4: rows of dY2 in place (per s2 level)
+  std::vector<FftLaunch> L_ds1;      // B4b: FFT of dS1 rows
+  std::vector<FftLaunch> L_ds0;      // B7a: FFT of dS0
+  std::vector<Tile> tiles1, tiles2;
+  int freq_cols = kFreqCols;
+
+  // Host copies of the device tables.
+  std::vector<FiltD> h_psi1, h_psi2, h_beta;  // psi1/psi2 on grid N; beta on N_fr
+  FiltD h_phiT{}, h_phiF{};                   // phi_T on grid N, phi_F on grid N_fr
+  std::vector<float> h_taps;
+
+  // Device side.
+  bool on_device = false;
+  int device = -1;
+  void* d_blob = nullptr;
+  const float2* d_tw = nullptr;
+  int twlog = 0;
+  const FiltD* d_psi1 = nullptr;
+  const FiltD* d_psi2 = nullptr;
+  const FiltD* d_beta = nullptr;
+  const float* d_taps = nullptr;
+  const Job* d_jobs = nullptr;
+  const Tile* d_tiles1 = nullptr;
+  const Tile* d_tiles2 = nullptr;
+  const int* d_s2 = nullptr;          // per active index
+  const int* d_n1max_act = nullptr;   // per active index
+  const int64_t* d_y2_off = nullptr;  // per active index
+  const int64_t* d_v2_off = nullptr;
+  const int64_t* d_phi2_off = nullptr;
+  const int64_t* d_u1_off = nullptr;  // per n1
+  const int* d_k1 = nullptr;          // per n1
+  const int* d_act_n2 = nullptr;      // per active index: n2
+  const int64_t* d_tap_off = nullptr; // per level s
+
+  // Measurement hook (jtfs_profile_stage): events per stage and next index.
+  mutable std::vector<void*> prof_events[4];
+  mutable int prof_next[4] = {0, 0, 0, 0};
+};
+
+// Host plan construction (jtfs_plan.cpp).  Returns 0 or a JTFS_ERR_* code.
+int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
+               int64_t T, int F, int batch, uint32_t flags);
+int upload_plan(Plan& p);
+void release_plan(Plan& p);
+
+}  // namespace jtfs
+
+// Opaque handle of the C ABI.
+struct jtfs_plan_s {
+  jtfs::Plan p;
+};

@@ -1,0 +1,499 @@
+// Host side of a JTFS plan: filterbank design (§3.1), the multirate schedule
+// of §3.2-§3.5, per-clip layouts, workspace layout, the job tables of every
+// batched FFT launch, and the upload of the small device tables.
+//
+// Readings of passages the paper leaves open (shared with nothing else in
+// this library; the CUDA kernels only consume the tables built here):
+//  - §3.1 listing uses an undefined `r`: taken as r_psi = sqrt(1/2).
+//  - filter field 'j': the largest k with 2^k (xi + 3 sigma) <= 1/2 (>= 0).
+//  - phi_T has sigma = 0.1/T cycles/sample, phi_F sigma = 0.1/F cycles/bin;
+//    output strides are T in time and 2^floor(log2 F) along n1.
+//  - strides: k1 = min(j1, log2 T); second-order rows j1 < j2 at total stride
+//    s2 = min(j2, log2 T); frequential k_fr = min(j_fr, floor(log2 F)).
+//  - N_fr = next power of two >= N1 + 2^(J_fr + 1).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "jtfs.h"
+#include "jtfs_internal.h"
+
+namespace jtfs {
+namespace {
+
+constexpr double kSigma0 = 0.1;  // §3.1 listing
+
+// §3.1 generator: constant-Q geometric progression down to the elbow
+// sigma_min = sigma0 / 2^J, then Q-1 constant-bandwidth filters.
+std::vector<FilterH> filterbank(int J, int Q) {
+  std::vector<FilterH> out;
+  const double r_psi = std::sqrt(0.5);
+  double xi = std::max(1.0 / (1.0 + std::pow(2.0, 3.0 / Q)), 0.35);
+  const double factor = 1.0 / std::pow(2.0, 1.0 / Q);
+  double sigma = (1.0 - factor) / (1.0 + factor) * xi / std::sqrt(2.0 * std::log(1.0 / r_psi));
+  const double sigma_min = kSigma0 / std::pow(2.0, J);
+  if (sigma <= sigma_min) {
+    xi = sigma;
+  } else {
+    out.push_back({xi, sigma, 0});
+    while (sigma > sigma_min * std::pow(2.0, 1.0 / Q)) {
+      xi /= std::pow(2.0, 1.0 / Q);
+      sigma /= std::pow(2.0, 1.0 / Q);
+      out.push_back({xi, sigma, 0});
+    }
+  }
+  const double elbow_xi = xi;
+  for (int q = 0; q < Q - 1; ++q) {
+    xi -= 1.0 / Q * elbow_xi;
+    out.push_back({xi, sigma_min, 0});
+  }
+  return out;
+}
+
+int max_subsampling(double xi, double sigma) {
+  const int j = static_cast<int>(std::floor(std::log2(0.5 / (xi + 3.0 * sigma))));
+  return j < 0 ? 0 : j;
+}
+
+int ilog2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << l) < v) ++l;
+  return l;
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Filter on an n-bin grid for the kernels (see FiltD).
+FiltD make_filt(double xi, double sigma, int n, int k, int j, bool lowpass) {
+  FiltD f{};
+  const double c0 = xi * n;
+  const double sn = sigma * n;
+  f.c0 = static_cast<float>(c0);
+  f.a = static_cast<float>(1.0 / (2.0 * sn * sn));
+  double kappa = lowpass ? 0.0 : std::exp(-xi * xi / (2.0 * sigma * sigma));
+  if (kappa < 1e-35) kappa = 0.0;
+  f.kappa = static_cast<float>(kappa);
+  const double w = kBandSigmas * sn;
+  double lo = std::floor(c0 - w), hi = std::ceil(c0 + w);
+  if (kappa > 0.0) {
+    lo = std::min(lo, std::floor(-w));
+    hi = std::max(hi, std::ceil(w));
+  }
+  lo = std::max(lo, -double(n / 2));
+  hi = std::min(hi, double(n / 2 - 1));
+  f.lo = static_cast<int>(lo);
+  f.hi = static_cast<int>(hi);
+  f.k = k;
+  f.j = j;
+  return f;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace
+
+int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
+               int64_t T, int F, int batch, uint32_t flags) {
+  if (!is_pow2(N) || N < 16 || N > (int64_t(1) << 20)) return JTFS_ERR_SHAPE;
+  if (!is_pow2(T) || T < 2 || T > N) return JTFS_ERR_SHAPE;
+  if (F < 1 || batch < 1 || J < 1 || Q < 1 || Q2 < 1 || J_fr < 1 || Q_fr < 1) return JTFS_ERR_SHAPE;
+  if (J > 24 || Q > 64 || Q2 > 64 || J_fr > 12 || Q_fr > 16) return JTFS_ERR_SHAPE;
+  p.N = N; p.J = J; p.Q = Q; p.Q2 = Q2; p.J_fr = J_fr; p.Q_fr = Q_fr;
+  p.T = T; p.F = F; p.batch = batch; p.flags = flags;
+  p.logN = ilog2(N);
+  p.lT = ilog2(T);
+  p.lF = static_cast<int>(std::floor(std::log2(double(F))));
+
+  p.psi1 = filterbank(J, Q);
+  p.psi2 = filterbank(J, Q2);
+  p.psifr = filterbank(J_fr, Q_fr);
+  if (p.psi1.empty() || p.psi2.empty() || p.psifr.empty()) return JTFS_ERR_SHAPE;
+  for (auto* fb : {&p.psi1, &p.psi2, &p.psifr})
+    for (auto& f : *fb) f.j = max_subsampling(f.xi, f.sigma);
+  p.phiT = {0.0, kSigma0 / double(T), 0};
+  p.phiT.j = max_subsampling(0.0, p.phiT.sigma);
+  p.phiF = {0.0, kSigma0 / double(F), 0};
+  p.phiF.j = max_subsampling(0.0, p.phiF.sigma);
+
+  p.N1 = static_cast<int>(p.psi1.size());
+  p.N2 = static_cast<int>(p.psi2.size());
+  p.K = static_cast<int>(p.psifr.size());
+  p.N_fr = 1;
+  while (p.N_fr < p.N1 + (1 << (J_fr + 1))) p.N_fr <<= 1;
+  p.logNfr = ilog2(p.N_fr);
+  if (p.lF > p.logNfr) return JTFS_ERR_SHAPE;
+  if (p.N_fr > (1 << kSmallLogMax) || p.N_fr > 1024) return JTFS_ERR_SHAPE;
+  p.R_out = p.N_fr >> p.lF;
+  p.n_frames = static_cast<int>(N >> p.lT);
+  p.log_frames = p.logN - p.lT;
+  p.n_beta1 = 1 + p.K;
+  p.n_beta2 = 1 + 2 * p.K;
+
+  p.k1.resize(p.N1);
+  for (int n1 = 0; n1 < p.N1; ++n1) p.k1[n1] = std::min(p.psi1[n1].j, p.lT);
+  p.n1max.assign(p.N2, 0);
+  for (int n2 = 0; n2 < p.N2; ++n2)
+    for (int n1 = 0; n1 < p.N1; ++n1)
+      if (p.psi1[n1].j < p.psi2[n2].j) p.n1max[n2]++;
+  p.active.clear();
+  p.s2.clear();
+  for (int n2 = 0; n2 < p.N2; ++n2)
+    if (p.n1max[n2] > 0) {
+      p.active.push_back(n2);
+      p.s2.push_back(std::min(p.psi2[n2].j, p.lT));
+    }
+  p.n_active = static_cast<int>(p.active.size());
+  // Rows with j1 < j2 are a prefix of n1 because j1 is non-decreasing in n1.
+  for (int n1 = 1; n1 < p.N1; ++n1)
+    if (p.psi1[n1].j < p.psi1[n1 - 1].j) return JTFS_ERR_SHAPE;
+
+  // Frequential filters on the N_fr grid: phi_F, then +xi_n, then -xi_n.
+  p.h_beta.clear();
+  p.beta_k.clear();
+  {
+    const int kphi = std::min(p.phiF.j, p.lF);
+    p.h_beta.push_back(make_filt(0.0, p.phiF.sigma, p.N_fr, kphi, p.phiF.j, true));
+    for (int s = 0; s < 2; ++s)
+      for (auto& f : p.psifr) {
+        const int k = std::min(f.j, p.lF);
+        p.h_beta.push_back(make_filt(s == 0 ? f.xi : -f.xi, f.sigma, p.N_fr, k, f.j, false));
+      }
+    for (auto& f : p.h_beta) p.beta_k.push_back(f.k);
+  }
+  p.h_psi1.clear();
+  for (int n1 = 0; n1 < p.N1; ++n1)
+    p.h_psi1.push_back(make_filt(p.psi1[n1].xi, p.psi1[n1].sigma, int(N), p.k1[n1], p.psi1[n1].j, false));
+  p.h_psi2.clear();
+  for (int n2 = 0; n2 < p.N2; ++n2)
+    p.h_psi2.push_back(make_filt(p.psi2[n2].xi, p.psi2[n2].sigma, int(N),
+                                 std::min(p.psi2[n2].j, p.lT), p.psi2[n2].j, false));
+  p.h_phiT = make_filt(0.0, p.phiT.sigma, int(N), p.lT, p.phiT.j, true);
+  p.h_phiF = make_filt(0.0, p.phiF.sigma, p.N_fr, p.lF, p.phiF.j, true);
+
+  // Per-clip layouts.
+  p.u1_off.resize(p.N1);
+  p.u1_tot = 0;
+  for (int n1 = 0; n1 < p.N1; ++n1) {
+    p.u1_off[n1] = p.u1_tot;
+    p.u1_tot += N >> p.k1[n1];
+  }
+  p.y2_off.resize(p.n_active);
+  p.v2_off.resize(p.n_active);
+  p.phi2_off.resize(p.n_active);
+  p.y2_tot = 0;
+  p.v2_tot = 0;
+  const int64_t per_path = int64_t(p.R_out) * p.n_frames;
+  p.phi1_off = p.n_frames;
+  for (int a = 0; a < p.n_active; ++a) {
+    const int64_t L2 = N >> p.s2[a];
+    p.y2_off[a] = p.y2_tot;
+    p.y2_tot += int64_t(p.n1max[p.active[a]]) * L2;
+    p.v2_off[a] = p.v2_tot;
+    p.v2_tot += int64_t(p.n_beta2) * p.R_out * L2;
+    p.phi2_off[a] = p.phi1_off + p.n_beta1 * per_path + int64_t(a) * p.n_beta2 * per_path;
+  }
+  p.phi_size = p.n_frames + p.n_beta1 * per_path + int64_t(p.n_active) * p.n_beta2 * per_path;
+
+  // Time-pooling taps g_s[t] = 2^s phi_T[2^s t] for every level s <= log2 T,
+  // where phi_T[tau] = (1/N) sum_m phi_hat_T(m/N) e^{2 pi i m tau / N}
+  // = sigma sqrt(2 pi) sum_p exp(-2 pi^2 sigma^2 (tau - p N)^2) (Poisson
+  // summation; phi_hat_T(1/2) <= exp(-12.5 T^2) is negligible for T >= 2).
+  p.tap_off.resize(p.lT + 1);
+  p.tap_tot = 0;
+  for (int s = 0; s <= p.lT; ++s) {
+    p.tap_off[s] = p.tap_tot;
+    p.tap_tot += N >> s;
+  }
+  p.h_taps.assign(p.tap_tot, 0.f);
+  {
+    const double sg = p.phiT.sigma;
+    const double c = 2.0 * M_PI * M_PI * sg * sg;
+    const double amp = sg * std::sqrt(2.0 * M_PI);
+    const int P = static_cast<int>(std::ceil(std::sqrt(60.0 / c) / double(N))) + 1;
+    for (int s = 0; s <= p.lT; ++s) {
+      const int64_t L = N >> s;
+      for (int64_t t = 0; t < L; ++t) {
+        const int64_t tau = t << s;
+        double acc = 0.0;
+        for (int q = -P; q <= P; ++q) {
+          const double d = double(tau) - double(q) * double(N);
+          acc += std::exp(-c * d * d);
+        }
+        p.h_taps[p.tap_off[s] + t] = static_cast<float>(double(int64_t(1) << s) * amp * acc);
+      }
+    }
+  }
+
+  // Launch descriptions.
+  p.jobs.clear();
+  auto add = [&](std::vector<FftLaunch>& L, int logn, const std::vector<Job>& js) {
+    if (js.empty()) return;
+    L.push_back({logn, static_cast<int>(js.size()), static_cast<int>(p.jobs.size())});
+    p.jobs.insert(p.jobs.end(), js.begin(), js.end());
+  };
+  const int B = batch;
+  p.L_x.clear(); p.L_u1.clear(); p.L_s0.clear(); p.L_s1.clear(); p.L_y2.clear();
+  p.L_u1inplace.clear(); p.L_y2inplace.clear(); p.L_ds1.clear(); p.L_ds0.clear();
+  {
+    std::vector<Job> js;
+    for (int b = 0; b < B; ++b) js.push_back({int64_t(b) * N, int64_t(b) * N, -1, p.logN, b, 0});
+    add(p.L_x, p.logN, js);
+  }
+  for (int lev = 0; lev <= p.lT; ++lev) {
+    std::vector<Job> band, rows;
+    for (int b = 0; b < B; ++b)
+      for (int n1 = 0; n1 < p.N1; ++n1)
+        if (p.k1[n1] == lev) {
+          const int64_t o = int64_t(b) * p.u1_tot + p.u1_off[n1];
+          band.push_back({int64_t(b) * N, o, n1, p.logN, b, 0});
+          rows.push_back({o, o, n1, p.logN - lev, b, 0});
+        }
+    add(p.L_u1, p.logN - lev, band);
+    add(p.L_u1inplace, p.logN - lev, rows);
+  }
+  {
+    std::vector<Job> s0, ds0, s1, ds1;
+    for (int b = 0; b < B; ++b) {
+      s0.push_back({int64_t(b) * N, int64_t(b) * p.phi_size, -1, p.logN, b, 0});
+      ds0.push_back({int64_t(b) * p.phi_size, int64_t(b) * p.n_frames, -1, p.log_frames, b, 0});
+      for (int n1 = 0; n1 < p.N1; ++n1) {
+        const int64_t row = (int64_t(b) * p.N1 + n1) * p.n_frames;
+        s1.push_back({int64_t(b) * p.u1_tot + p.u1_off[n1], row, n1, p.logN - p.k1[n1], b, 0});
+        ds1.push_back({row, row, n1, p.log_frames, b, 0});
+      }
+    }
+    add(p.L_s0, p.log_frames, s0);
+    add(p.L_ds0, p.log_frames, ds0);
+    add(p.L_s1, p.log_frames, s1);
+    add(p.L_ds1, p.log_frames, ds1);
+  }
+  for (int lev = 0; lev <= p.lT; ++lev) {
+    std::vector<Job> band, rows;
+    for (int b = 0; b < B; ++b)
+      for (int a = 0; a < p.n_active; ++a) {
+        if (p.s2[a] != lev) continue;
+        const int n2 = p.active[a];
+        const int64_t L2 = N >> lev;
+        for (int n1 = 0; n1 < p.n1max[n2]; ++n1) {
+          const int64_t o = int64_t(b) * p.y2_tot + p.y2_off[a] + int64_t(n1) * L2;
+          band.push_back({int64_t(b) * p.u1_tot + p.u1_off[n1], o, n2, p.logN - p.k1[n1], b, 0});
+          rows.push_back({o, o, n2, p.logN - lev, b, 0});
+        }
+      }
+    add(p.L_y2, p.logN - lev, band);
+    add(p.L_y2inplace, p.logN - lev, rows);
+  }
+
+  // Frequential tiles.
+  p.freq_cols = std::max(1, std::min(kFreqCols, 4096 / p.N_fr));
+  p.tiles1.clear();
+  p.tiles2.clear();
+  for (int b = 0; b < B; ++b)
+    for (int t0 = 0; t0 < p.n_frames; t0 += p.freq_cols)
+      p.tiles1.push_back({b, -1, t0, std::min(p.freq_cols, p.n_frames - t0)});
+  for (int b = 0; b < B; ++b)
+    for (int a = 0; a < p.n_active; ++a) {
+      const int L2 = static_cast<int>(N >> p.s2[a]);
+      for (int t0 = 0; t0 < L2; t0 += p.freq_cols)
+        p.tiles2.push_back({b, a, t0, std::min(p.freq_cols, L2 - t0)});
+    }
+
+  // Four-step scratch: the largest large-size launch.
+  p.scr_elems = 0;
+  for (auto* L : {&p.L_x, &p.L_u1, &p.L_u1inplace, &p.L_y2, &p.L_y2inplace})
+    for (auto& l : *L)
+      if (l.logn > kSmallLogMax) p.scr_elems = std::max(p.scr_elems, int64_t(l.njobs) << l.logn);
+
+  // Workspace layout.
+  size_t o = 0;
+  auto take = [&](size_t bytes) { const size_t r = o; o = align256(o + bytes); return r; };
+  const size_t c8 = sizeof(float2), f4 = sizeof(float);
+  p.ws_Xh = take(size_t(B) * N * c8);
+  p.ws_U1h = take(size_t(B) * p.u1_tot * c8);
+  p.ws_Zs = take(size_t(B) * p.u1_tot * c8);
+  p.ws_S1 = take(size_t(B) * p.N1 * p.n_frames * f4);
+  p.ws_dS1h = take(size_t(B) * p.N1 * p.n_frames * c8);
+  p.ws_Y2 = take(size_t(B) * p.y2_tot * c8);
+  p.ws_dY2 = take(size_t(B) * p.y2_tot * c8);
+  p.ws_V2 = take(size_t(B) * p.v2_tot * f4);
+  p.ws_phi = take(size_t(B) * p.phi_size * f4);
+  p.ws_dphi = take(size_t(B) * p.phi_size * f4);
+  p.ws_dXh = take(size_t(B) * N * c8);
+  p.ws_dS0h = take(size_t(B) * p.n_frames * c8);
+  p.ws_dy = take(size_t(B) * N * f4);
+  p.ws_scr = take(size_t(std::max<int64_t>(p.scr_elems, 1)) * c8);
+  p.ws_bytes = o;
+  return JTFS_OK;
+}
+
+int upload_plan(Plan& p) {
+  // Twiddles W^k = exp(-2 pi i k / TW) for the largest transform, in double.
+  int64_t TW = std::max<int64_t>(p.N, p.N_fr);
+  p.twlog = ilog2(TW);
+  std::vector<float2> tw(TW);
+  for (int64_t k = 0; k < TW; ++k) {
+    const double ang = -2.0 * M_PI * double(k) / double(TW);
+    tw[k] = make_float2(static_cast<float>(std::cos(ang)), static_cast<float>(std::sin(ang)));
+  }
+  std::vector<int> act_n2(p.active), n1max_act(p.n_active);
+  for (int a = 0; a < p.n_active; ++a) n1max_act[a] = p.n1max[p.active[a]];
+
+  struct Part { const void* src; size_t bytes; size_t off; };
+  std::vector<Part> parts;
+  size_t total = 0;
+  auto put = [&](const void* src, size_t bytes) {
+    const size_t off = total;
+    parts.push_back({src, bytes, off});
+    total = align256(total + std::max<size_t>(bytes, 1));
+    return off;
+  };
+  const size_t o_tw = put(tw.data(), tw.size() * sizeof(float2));
+  const size_t o_psi1 = put(p.h_psi1.data(), p.h_psi1.size() * sizeof(FiltD));
+  const size_t o_psi2 = put(p.h_psi2.data(), p.h_psi2.size() * sizeof(FiltD));
+  const size_t o_beta = put(p.h_beta.data(), p.h_beta.size() * sizeof(FiltD));
+  const size_t o_taps = put(p.h_taps.data(), p.h_taps.size() * sizeof(float));
+  const size_t o_jobs = put(p.jobs.data(), p.jobs.size() * sizeof(Job));
+  const size_t o_t1 = put(p.tiles1.data(), p.tiles1.size() * sizeof(Tile));
+  const size_t o_t2 = put(p.tiles2.data(), p.tiles2.size() * sizeof(Tile));
+  const size_t o_s2 = put(p.s2.data(), p.s2.size() * sizeof(int));
+  const size_t o_n1m = put(n1max_act.data(), n1max_act.size() * sizeof(int));
+  const size_t o_y2o = put(p.y2_off.data(), p.y2_off.size() * sizeof(int64_t));
+  const size_t o_v2o = put(p.v2_off.data(), p.v2_off.size() * sizeof(int64_t));
+  const size_t o_p2o = put(p.phi2_off.data(), p.phi2_off.size() * sizeof(int64_t));
+  const size_t o_u1o = put(p.u1_off.data(), p.u1_off.size() * sizeof(int64_t));
+  const size_t o_k1 = put(p.k1.data(), p.k1.size() * sizeof(int));
+  const size_t o_act = put(act_n2.data(), act_n2.size() * sizeof(int));
+  const size_t o_tapo = put(p.tap_off.data(), p.tap_off.size() * sizeof(int64_t));
+
+  if (cudaGetDevice(&p.device) != cudaSuccess) return JTFS_ERR_CUDA;
+  void* blob = nullptr;
+  if (cudaMalloc(&blob, total) != cudaSuccess) return JTFS_ERR_NOMEM;
+  std::vector<unsigned char> host(total, 0);
+  for (auto& pt : parts)
+    if (pt.bytes) std::memcpy(host.data() + pt.off, pt.src, pt.bytes);
+  if (cudaMemcpy(blob, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(blob);
+    return JTFS_ERR_CUDA;
+  }
+  auto at = [&](size_t off) { return static_cast<unsigned char*>(blob) + off; };
+  p.d_blob = blob;
+  p.d_tw = reinterpret_cast<const float2*>(at(o_tw));
+  p.d_psi1 = reinterpret_cast<const FiltD*>(at(o_psi1));
+  p.d_psi2 = reinterpret_cast<const FiltD*>(at(o_psi2));
+  p.d_beta = reinterpret_cast<const FiltD*>(at(o_beta));
+  p.d_taps = reinterpret_cast<const float*>(at(o_taps));
+  p.d_jobs = reinterpret_cast<const Job*>(at(o_jobs));
+  p.d_tiles1 = reinterpret_cast<const Tile*>(at(o_t1));
+  p.d_tiles2 = reinterpret_cast<const Tile*>(at(o_t2));
+  p.d_s2 = reinterpret_cast<const int*>(at(o_s2));
+  p.d_n1max_act = reinterpret_cast<const int*>(at(o_n1m));
+  p.d_y2_off = reinterpret_cast<const int64_t*>(at(o_y2o));
+  p.d_v2_off = reinterpret_cast<const int64_t*>(at(o_v2o));
+  p.d_phi2_off = reinterpret_cast<const int64_t*>(at(o_p2o));
+  p.d_u1_off = reinterpret_cast<const int64_t*>(at(o_u1o));
+  p.d_k1 = reinterpret_cast<const int*>(at(o_k1));
+  p.d_act_n2 = reinterpret_cast<const int*>(at(o_act));
+  p.d_tap_off = reinterpret_cast<const int64_t*>(at(o_tapo));
+  p.on_device = true;
+  return JTFS_OK;
+}
+
+void release_plan(Plan& p) {
+  if (p.d_blob) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (p.device >= 0 && cur != p.device) cudaSetDevice(p.device);
+    cudaFree(p.d_blob);
+    if (cur >= 0 && cur != p.device) cudaSetDevice(cur);
+  }
+  p.d_blob = nullptr;
+  p.on_device = false;
+}
+
+}  // namespace jtfs
+
+// ---------------------------------------------------------------------------
+// C ABI: plan management and inspection.
+// ---------------------------------------------------------------------------
+
+extern "C" int jtfs_plan(jtfs_plan_t* out, int64_t N, int J, int Q, int Q2, int J_fr,
+                         int Q_fr, int64_t T, int F, int batch, uint32_t flags) {
+  if (!out) return JTFS_ERR_ARG;
+  *out = nullptr;
+  jtfs_plan_s* h = new (std::nothrow) jtfs_plan_s();
+  if (!h) return JTFS_ERR_NOMEM;
+  int rc;
+  try {
+    rc = jtfs::build_plan(h->p, N, J, Q, Q2, J_fr, Q_fr, T, F, batch, flags);
+    if (rc == JTFS_OK && !(flags & JTFS_PLAN_HOST_ONLY)) rc = jtfs::upload_plan(h->p);
+  } catch (...) {
+    rc = JTFS_ERR_NOMEM;
+  }
+  if (rc != JTFS_OK) {
+    jtfs::release_plan(h->p);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return JTFS_OK;
+}
+
+extern "C" int jtfs_plan_destroy(jtfs_plan_t plan) {
+  if (!plan) return JTFS_OK;
+  jtfs::release_plan(plan->p);
+  delete plan;
+  return JTFS_OK;
+}
+
+extern "C" int64_t jtfs_phi_size(jtfs_plan_t plan) {
+  return plan ? plan->p.phi_size : JTFS_ERR_ARG;
+}
+
+extern "C" size_t jtfs_workspace_bytes(jtfs_plan_t plan) {
+  return plan ? plan->p.ws_bytes : 0;
+}
+
+extern "C" int jtfs_plan_info(jtfs_plan_t plan, int64_t* info, int count) {
+  if (!plan || (count > 0 && !info)) return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  const int64_t v[19] = {p.N, p.J, p.Q, p.Q2, p.J_fr, p.Q_fr, p.T, p.F, p.batch, p.N1,
+                         p.N2, p.K, p.N_fr, p.lT, p.lF, p.R_out, p.n_frames, p.n_active,
+                         p.phi_size};
+  for (int i = 0; i < count && i < 19; ++i) info[i] = v[i];
+  return 19;
+}
+
+extern "C" int jtfs_plan_filters(jtfs_plan_t plan, int which, double* xi, double* sigma,
+                                 int32_t* j, int count) {
+  if (!plan) return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  std::vector<jtfs::FilterH> fb;
+  switch (which) {
+    case 0: fb = p.psi1; break;
+    case 1: fb = p.psi2; break;
+    case 2: fb = p.psifr; break;
+    case 3: fb = {p.phiT, p.phiF}; break;
+    default: return JTFS_ERR_ARG;
+  }
+  const int n = static_cast<int>(fb.size());
+  for (int i = 0; i < count && i < n; ++i) {
+    if (xi) xi[i] = fb[i].xi;
+    if (sigma) sigma[i] = fb[i].sigma;
+    if (j) j[i] = fb[i].j;
+  }
+  return n;
+}
+
+extern "C" const char* jtfs_error_string(int code) {
+  switch (code) {
+    case JTFS_OK: return "success";
+    case JTFS_ERR_ARG: return "invalid argument";
+    case JTFS_ERR_SHAPE: return "unsupported sizes";
+    case JTFS_ERR_WORKSPACE: return "workspace missing or misaligned";
+    case JTFS_ERR_CUDA: return "CUDA runtime error";
+    case JTFS_ERR_NOMEM: return "allocation failed";
+    case JTFS_ERR_NODEVICE: return "plan has no device tables (host-only)";
+    default: return "unknown error";
+  }
+}

@@ -1,0 +1,156 @@
+"""PyTorch-facing API over the C ABI: plans, forward, adjoint, loss and Adam step.
+
+PyTorch supplies device memory and the current CUDA stream; every step of the
+transform runs in the library's CUDA kernels.  Inputs must be contiguous
+float32 CUDA tensors of shape [batch, N]; anything else raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from ctypes import c_double, c_int32, c_int64, c_void_p
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+import torch
+
+from . import _native
+
+INFO_KEYS = ("N", "J", "Q", "Q2", "J_fr", "Q_fr", "T", "F", "batch", "N1", "N2", "K", "N_fr",
+             "log2_T", "log2_F", "R_out", "n_frames", "n_active", "phi_size")
+
+
+def _ptr(t: torch.Tensor) -> c_void_p:
+    return c_void_p(t.data_ptr())
+
+
+def _stream() -> c_void_p:
+    return c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class JTFSPlan:
+    """A JTFS configuration (filterbanks, schedule, device tables) for one batch size.
+
+    Parameters follow ``jtfs_plan`` in include/jtfs.h: N samples (power of
+    two), J octaves, Q and Q2 filters per octave of the first- and
+    second-order time filterbanks, J_fr and Q_fr of the frequential
+    filterbank, time averaging T (power of two) and frequency averaging F.
+    """
+
+    def __init__(self, N: int, J: int, Q: int, Q2: int, J_fr: int, Q_fr: int, T: int, F: int,
+                 batch: int = 1, host_only: bool = False):
+        lib = _native.load()
+        h = c_void_p()
+        flags = _native.PLAN_HOST_ONLY if host_only else 0
+        if not host_only and not torch.cuda.is_available():
+            raise RuntimeError("JTFSPlan needs a CUDA device (or host_only=True for inspection)")
+        _native.check(lib.jtfs_plan(ctypes.byref(h), N, J, Q, Q2, J_fr, Q_fr, T, F, batch, flags),
+                      "jtfs_plan")
+        self._h = h
+        self._lib = lib
+        self.host_only = host_only
+        buf = (c_int64 * len(INFO_KEYS))()
+        n = lib.jtfs_plan_info(h, buf, len(INFO_KEYS))
+        if n < len(INFO_KEYS):
+            raise RuntimeError("jtfs_plan_info returned too few values")
+        self.info: Dict[str, int] = {k: int(buf[i]) for i, k in enumerate(INFO_KEYS)}
+        self.N = self.info["N"]
+        self.batch = self.info["batch"]
+        self.phi_size = int(lib.jtfs_phi_size(h))
+        self.workspace_bytes = int(lib.jtfs_workspace_bytes(h))
+        self._ws: Optional[torch.Tensor] = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.jtfs_plan_destroy(h)
+            self._h = None
+
+    # -- inspection -------------------------------------------------------
+    def filters(self, which: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+        """(xi, sigma, j) of filterbank `which` (0 psi1, 1 psi2, 2 psi_fr, 3 phi_T/phi_F)."""
+        n = self._lib.jtfs_plan_filters(self._h, which, None, None, None, 0)
+        _native.check(0 if n >= 0 else n, "jtfs_plan_filters")
+        xi = (c_double * n)()
+        sg = (c_double * n)()
+        jj = (c_int32 * n)()
+        self._lib.jtfs_plan_filters(self._h, which, xi, sg, jj, n)
+        return np.array(xi[:]), np.array(sg[:]), np.array(jj[:], dtype=np.int64)
+
+    # -- compute ----------------------------------------------------------
+    def workspace(self, device: Optional[torch.device] = None) -> torch.Tensor:
+        """Device scratch of jtfs_workspace_bytes(), cached (calls on one stream serialise)."""
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if self._ws is None or self._ws.device != dev:
+            self._ws = torch.empty(max(self.workspace_bytes, 1), dtype=torch.uint8, device=dev)
+        return self._ws
+
+    def _check(self, t: torch.Tensor, cols: int, name: str) -> None:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise TypeError(f"{name} must be contiguous float32")
+        if tuple(t.shape) != (self.batch, cols):
+            raise ValueError(f"{name} must have shape {(self.batch, cols)}, got {tuple(t.shape)}")
+
+    def forward(self, x: torch.Tensor, out: Optional[torch.Tensor] = None,
+                workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        self._check(x, self.N, "x")
+        phi = out if out is not None else torch.empty(self.batch, self.phi_size, device=x.device)
+        ws = workspace if workspace is not None else self.workspace(x.device)
+        _native.check(self._lib.jtfs_forward(self._h, _ptr(x), _ptr(phi), _ptr(ws), _stream()), "jtfs_forward")
+        return phi
+
+    def backward(self, x: torch.Tensor, dphi: torch.Tensor, out: Optional[torch.Tensor] = None,
+                 workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        self._check(x, self.N, "x")
+        self._check(dphi, self.phi_size, "dphi")
+        dx = out if out is not None else torch.empty_like(x)
+        ws = workspace if workspace is not None else self.workspace(x.device)
+        _native.check(self._lib.jtfs_backward(self._h, _ptr(x), _ptr(dphi), _ptr(dx), _ptr(ws), _stream()),
+                      "jtfs_backward")
+        return dx
+
+    def loss_grad(self, y: torch.Tensor, phi_target: torch.Tensor, need_grad: bool = True,
+                  loss_out: Optional[torch.Tensor] = None, grad_out: Optional[torch.Tensor] = None,
+                  workspace: Optional[torch.Tensor] = None) -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
+        self._check(y, self.N, "y")
+        self._check(phi_target, self.phi_size, "phi_target")
+        loss = loss_out if loss_out is not None else torch.empty(self.batch, device=y.device)
+        dy = (grad_out if grad_out is not None else torch.empty_like(y)) if need_grad else None
+        ws = workspace if workspace is not None else self.workspace(y.device)
+        _native.check(self._lib.jtfs_loss_grad(self._h, _ptr(y), _ptr(phi_target), _ptr(loss),
+                                               _ptr(dy) if dy is not None else c_void_p(0), _ptr(ws),
+                                               _stream()), "jtfs_loss_grad")
+        return loss, dy
+
+    def metamer_step(self, y: torch.Tensor, phi_target: torch.Tensor, adam_m: torch.Tensor,
+                     adam_v: torch.Tensor, step: int, lr: float, loss_out: Optional[torch.Tensor] = None,
+                     workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        for t, n in ((y, "y"), (adam_m, "adam_m"), (adam_v, "adam_v")):
+            self._check(t, self.N, n)
+        self._check(phi_target, self.phi_size, "phi_target")
+        loss = loss_out if loss_out is not None else torch.empty(self.batch, device=y.device)
+        ws = workspace if workspace is not None else self.workspace(y.device)
+        _native.check(self._lib.metamer_step(self._h, _ptr(y), _ptr(phi_target), _ptr(adam_m), _ptr(adam_v),
+                                             int(step), float(lr), _ptr(loss), _ptr(ws), _stream()),
+                      "metamer_step")
+        return loss
+
+
+class _JTFSFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, plan: JTFSPlan) -> torch.Tensor:  # type: ignore[override]
+        ctx.plan = plan
+        ctx.save_for_backward(x)
+        return plan.forward(x.contiguous())
+
+    @staticmethod
+    def backward(ctx, dphi: torch.Tensor):  # type: ignore[override]
+        (x,) = ctx.saved_tensors
+        return ctx.plan.backward(x.contiguous(), dphi.contiguous()), None
+
+
+def jtfs(x: torch.Tensor, plan: JTFSPlan) -> torch.Tensor:
+    """Phi(x) with a hand-written adjoint as its autograd backward (recomputes U1)."""
+    return _JTFSFunction.apply(x, plan)

@@ -1,0 +1,105 @@
+"""C-ABI library on the host: it loads, exports every declared symbol, and its
+host-only plans agree with the oracle's filterbanks and schedule.
+
+No compute call touches a GPU here; compute entry points are only checked
+for their argument and host-only error paths.
+"""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import jtfs_oracle as O
+from paper_2602_11896_gb300 import JTFSPlan, _native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "jtfs.h")
+
+PARAMS = [
+    dict(N=256, J=4, Q=4, Q2=1, J_fr=2, Q_fr=1, T=16, F=2),
+    dict(N=512, J=5, Q=3, Q2=2, J_fr=2, Q_fr=2, T=32, F=3),
+    dict(N=2 ** 13, J=6, Q=8, Q2=1, J_fr=3, Q_fr=1, T=64, F=4),
+    dict(N=2 ** 16, J=12, Q=12, Q2=1, J_fr=5, Q_fr=2, T=2 ** 11, F=12),
+    dict(N=2 ** 20, J=14, Q=16, Q2=2, J_fr=6, Q_fr=2, T=2 ** 13, F=16),
+]
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                                 src, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _native.load()
+    names = declared_functions()
+    assert "jtfs_forward" in names and "metamer_step" in names and len(names) >= 11
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(_native.SIGNATURES)
+
+
+@pytest.mark.parametrize("params", PARAMS)
+def test_host_plan_matches_oracle(params):
+    plan = JTFSPlan(**params, batch=2, host_only=True)
+    ref = O.Plan(**params)
+    info = plan.info
+    assert info["N1"] == ref.N1 and info["N2"] == len(ref.psi2) and info["K"] == ref.K
+    assert info["N_fr"] == ref.N_fr and info["R_out"] == ref.R_out
+    assert info["n_frames"] == ref.n_frames and info["log2_T"] == ref.lT and info["log2_F"] == ref.lF
+    assert info["n_active"] == len(ref.active)
+    assert plan.phi_size == ref.phi_size == info["phi_size"]
+    for which, fb in ((0, ref.psi1), (1, ref.psi2), (2, ref.psi_fr)):
+        xi, sg, j = plan.filters(which)
+        assert len(xi) == len(fb)
+        assert np.abs(xi - [f.xi for f in fb]).max() <= 1e-15
+        assert np.abs(sg - [f.sigma for f in fb]).max() <= 1e-15
+        assert (j == [f.j for f in fb]).all()
+    xi, sg, j = plan.filters(3)
+    assert xi.tolist() == [0.0, 0.0]
+    assert abs(sg[0] - ref.sigma_phiT) < 1e-18 and abs(sg[1] - ref.sigma_phiF) < 1e-18
+    assert j[1] == ref.j_phiF
+    assert plan.workspace_bytes > 0
+
+
+def test_plan_rejects_bad_shapes():
+    lib = _native.load()
+    h = ctypes.c_void_p()
+    bad = [
+        (300, 4, 4, 1, 2, 1, 16, 2),       # N not a power of two
+        (256, 4, 4, 1, 2, 1, 24, 2),       # T not a power of two
+        (256, 4, 4, 1, 2, 1, 512, 2),      # T > N
+        (256, 4, 4, 1, 2, 1, 16, 0),       # F < 1
+        (2 ** 21, 4, 4, 1, 2, 1, 16, 2),   # N too large
+    ]
+    for args in bad:
+        rc = lib.jtfs_plan(ctypes.byref(h), *args, 1, _native.PLAN_HOST_ONLY)
+        assert rc == -2, args
+    assert lib.jtfs_plan(None, 256, 4, 4, 1, 2, 1, 16, 2, 1, 1) == -1
+    assert lib.jtfs_phi_size(None) == -1
+    assert lib.jtfs_workspace_bytes(None) == 0
+    assert _native.error_string(-6).startswith("plan has no device")
+
+
+def test_host_only_plan_refuses_compute():
+    plan = JTFSPlan(**PARAMS[0], host_only=True)
+    lib = _native.load()
+    fake = ctypes.c_void_p(4096)  # never dereferenced: the call fails before any launch
+    assert lib.jtfs_forward(plan._h, fake, fake, fake, None) == -6
+    assert lib.jtfs_backward(plan._h, fake, fake, fake, fake, None) == -6
+    assert lib.jtfs_loss_grad(plan._h, fake, fake, fake, fake, fake, None) == -6
+    assert lib.metamer_step(plan._h, fake, fake, fake, fake, 1, 0.1, fake, fake, None) == -6
+    assert lib.metamer_step(plan._h, fake, fake, fake, fake, 0, 0.1, fake, fake, None) == -1
+    assert lib.jtfs_forward(plan._h, None, fake, fake, None) == -1
+    assert lib.jtfs_forward(plan._h, ctypes.c_void_p(4100), fake, fake, None) == -1  # misaligned
+
+
+def test_python_api_refuses_cpu_tensors():
+    import torch
+    plan = JTFSPlan(**PARAMS[0], host_only=True)
+    with pytest.raises(TypeError):
+        plan.forward(torch.zeros(1, 256))
