@@ -145,6 +145,132 @@ __device__ float2* cta_fft(float2* a, float2* b, int logn, int count, int bstrid
 }
 
 // ---------------------------------------------------------------------------
+// Register DFTs of size 2, 4, 8, 16 (natural order in and out) and a
+// batched Stockham FFT over *interleaved* transforms: element i of transform
+// f lives at a[i * cnt + f].  Consecutive threads take consecutive f, so every
+// load and store of a pass is contiguous across the warp (no bank conflicts
+// whatever the Stockham stride), and all threads of a warp read the same
+// twiddle (a broadcast).  Twiddles come from a shared-memory table.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {  // * (-i) forward, * (+i) inverse
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// exp(-2 pi i m / 16) (forward) or its conjugate; m is a compile-time constant after unrolling.
+template <bool INV>
+__device__ __forceinline__ float2 w16(int m) {
+  constexpr float C1 = 0.92387953251128674f, S1 = 0.38268343236508978f, H = 0.70710678118654752f;
+  const float c[16] = {1.f, C1, H, S1, 0.f, -S1, -H, -C1, -1.f, -C1, -H, -S1, 0.f, S1, H, C1};
+  const float sn[16] = {0.f, S1, H, C1, 1.f, C1, H, S1, 0.f, -S1, -H, -C1, -1.f, -C1, -H, -S1};
+  return make_float2(c[m & 15], INV ? sn[m & 15] : -sn[m & 15]);
+}
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
+  const float2 s02 = cadd(v0, v2), d02 = csub(v0, v2), s13 = cadd(v1, v3), d13 = mul_mi<INV>(csub(v1, v3));
+  v0 = cadd(s02, s13);
+  v2 = csub(s02, s13);
+  v1 = cadd(d02, d13);
+  v3 = csub(d02, d13);
+}
+template <bool INV, int R>
+__device__ __forceinline__ void dft_reg(float2* v) {
+  if constexpr (R == 2) {
+    const float2 t = v[0];
+    v[0] = cadd(t, v[1]);
+    v[1] = csub(t, v[1]);
+  } else if constexpr (R == 4) {
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 8) {
+    // n = 2 n1 + n2, k = k1 + 4 k2: DFT4 over n1, twiddle W8^(n2 k1), DFT2 over n2.
+    dft4<INV>(v[0], v[2], v[4], v[6]);
+    dft4<INV>(v[1], v[3], v[5], v[7]);
+    float2 b[4] = {v[1], cmul(v[3], w16<INV>(2)), mul_mi<INV>(v[5]), cmul(v[7], w16<INV>(6))};
+    float2 a[4] = {v[0], v[2], v[4], v[6]};
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      v[k1] = cadd(a[k1], b[k1]);
+      v[k1 + 4] = csub(a[k1], b[k1]);
+    }
+  } else {  // R == 16: n = 4 n1 + n2, k = k1 + 4 k2
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    // now Y[n2][k1] sits at v[4 k1 + n2]; twiddle by W16^(n2 k1)
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1)
+#pragma unroll
+      for (int n2 = 1; n2 < 4; ++n2) v[4 * k1 + n2] = cmul(v[4 * k1 + n2], w16<INV>(n2 * k1));
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    // X[k1 + 4 k2] sits at v[4 k1 + k2]: transpose the 4 x 4 register block
+    float2 t[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
+  }
+}
+
+template <bool INV, int R, int LR>
+__device__ __forceinline__ void il_pass(const float2* __restrict__ src, float2* __restrict__ dst, int logn,
+                                        int lcnt, int lNs, const float2* __restrict__ tw, int twlog) {
+  const int lq = logn - LR;
+  const int total = 1 << (lq + lcnt);
+  const int Ns = 1 << lNs;
+  const int shift = twlog - (lNs + LR);
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int f = idx & ((1 << lcnt) - 1), j = idx >> lcnt;
+    const int k = j & (Ns - 1);
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[((j + (r << lq)) << lcnt) + f];
+    if (lNs > 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = tw[(r * k) << shift];
+        if (INV) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    dft_reg<INV, R>(v);
+    const int d = ((j - k) << LR) + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) dst[((d + (q << lNs)) << lcnt) + f] = v[q];
+  }
+}
+
+// 2^lcnt interleaved transforms of size 2^logn; tw = shared table of
+// exp(-2 pi i e / 2^twlog), 2^twlog >= 2^logn.  Returns the result buffer.
+template <bool INV>
+__device__ float2* cta_fft_il(float2* a, float2* b, int logn, int lcnt, const float2* __restrict__ tw, int twlog) {
+  int lNs = 0;
+  while (lNs < logn) {
+    const int rem = logn - lNs;
+    int lr;
+    if (rem == 5 || rem == 6 || rem == 9 || rem == 3) {
+      il_pass<INV, 8, 3>(a, b, logn, lcnt, lNs, tw, twlog);
+      lr = 3;
+    } else if (rem >= 4) {
+      il_pass<INV, 16, 4>(a, b, logn, lcnt, lNs, tw, twlog);
+      lr = 4;
+    } else if (rem == 2) {
+      il_pass<INV, 4, 2>(a, b, logn, lcnt, lNs, tw, twlog);
+      lr = 2;
+    } else {
+      il_pass<INV, 2, 1>(a, b, logn, lcnt, lNs, tw, twlog);
+      lr = 1;
+    }
+    __syncthreads();
+    float2* t = a; a = b; b = t;
+    lNs += lr;
+  }
+  return a;
+}
+
+// ---------------------------------------------------------------------------
 // Loaders: element idx of the input of the FFT described by a job.
 // ---------------------------------------------------------------------------
 struct LdReal {  // real row -> complex
@@ -340,10 +466,13 @@ int run_fft(const Plan& p, const std::vector<FftLaunch>& L, const Ld& ld, const 
 // MODE 2: second order, input Y2 (complex), all betas, output V2.
 // ---------------------------------------------------------------------------
 struct FreqArgs {
-  int N1, N_fr, logNfr, R_out, logRout, n_frames, logN, W, logW, n_beta1, n_beta2;
+  int N1, N_fr, logNfr, R_out, logRout, n_frames, logN, W, logW, n_beta1, n_beta2, n_ftab;
   int64_t phi_size, phi1_off, y2_tot, v2_tot;
   const FiltD* beta;
   FiltD phiF;
+  const float* ftab;
+  const FreqChunk* chunks;
+  int n_chunks;
   const int* s2;
   const int* n1max_act;
   const int64_t* y2_off;
@@ -352,10 +481,46 @@ struct FreqArgs {
   int twlog;
 };
 
+// Shared-memory layout of the frequential kernels (all in float2 units):
+//   tw    [N_fr]                twiddles exp(-2 pi i e / N_fr)
+//   bufs  nbuf x [W * N_fr]     interleaved transforms
+//   tab   [n_ftab * N_fr] float filter tables
+//   band  [n_beta2] int2        (lo, hi) of each frequential filter
+//   chk   [n_chunks] FreqChunk
+struct FreqSmem {
+  float2* tw;
+  float2* buf;
+  float* tab;
+  int2* band;
+  FreqChunk* chk;
+};
+
+__device__ __forceinline__ FreqSmem freq_smem_carve(const FreqArgs& A, float2* sm, int nbuf) {
+  FreqSmem S;
+  const int WN = A.W * A.N_fr;
+  S.tw = sm;
+  S.buf = sm + A.N_fr;
+  S.tab = reinterpret_cast<float*>(S.buf + nbuf * WN);
+  S.band = reinterpret_cast<int2*>(S.tab + A.n_ftab * A.N_fr);
+  S.chk = reinterpret_cast<FreqChunk*>(S.band + A.n_beta2);
+  return S;
+}
+
+__device__ __forceinline__ void freq_stage_tables(const FreqArgs& A, const FreqSmem& S) {
+  const int sh = A.twlog - A.logNfr;
+  for (int i = threadIdx.x; i < A.N_fr; i += blockDim.x) S.tw[i] = __ldg(A.tw + (i << sh));
+  for (int i = threadIdx.x; i < A.n_ftab * A.N_fr; i += blockDim.x) S.tab[i] = __ldg(A.ftab + i);
+  for (int i = threadIdx.x; i < A.n_beta2; i += blockDim.x) S.band[i] = make_int2(A.beta[i].lo, A.beta[i].hi);
+  const int* csrc = reinterpret_cast<const int*>(A.chunks);
+  int* cdst = reinterpret_cast<int*>(S.chk);
+  for (int i = threadIdx.x; i < A.n_chunks * static_cast<int>(sizeof(FreqChunk) / sizeof(int)); i += blockDim.x)
+    cdst[i] = csrc[i];
+}
+
+// Columns of the tile into interleaved layout dst[r * W + w], zero-padded to N_fr rows.
 template <int MODE>
 __device__ __forceinline__ void freq_load_columns(const FreqArgs& A, const Tile& tl, const float* S1,
-                                                  const float2* Y2, float2* dst, int& stride) {
-  int n1m;
+                                                  const float2* Y2, float2* dst, int& stride, int& n1m) {
   const float2* ysrc = nullptr;
   const float* ssrc = nullptr;
   if (MODE == 1) {
@@ -367,15 +532,64 @@ __device__ __forceinline__ void freq_load_columns(const FreqArgs& A, const Tile&
     stride = 1 << (A.logN - A.s2[tl.a]);
     ysrc = Y2 + static_cast<int64_t>(tl.b) * A.y2_tot + A.y2_off[tl.a] + tl.t0;
   }
-  const int W = A.W;
-  for (int i = threadIdx.x; i < W * A.N_fr; i += blockDim.x) {
-    const int r = i >> A.logW, w = i & (W - 1);
+  for (int i = threadIdx.x; i < A.W * A.N_fr; i += blockDim.x) {
+    const int w = i & (A.W - 1), r = i >> A.logW;
     float2 v = make_float2(0.f, 0.f);
     if (r < n1m && w < tl.ncols) {
       if (MODE == 1) v = make_float2(ssrc[static_cast<int64_t>(r) * stride + w], 0.f);
       else v = ysrc[static_cast<int64_t>(r) * stride + w];
     }
-    dst[w * A.N_fr + r] = v;
+    dst[i] = v;
+  }
+}
+
+__device__ __forceinline__ int ceil_log2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+// Z[m][f] = (1/N_fr) sum_{s in band, s = m mod R} yhat[s][w] psi_beta(s), transform f = bc*W + w.
+__device__ __forceinline__ void freq_fold(const FreqArgs& A, const FreqSmem& S, const FreqChunk& ch, int lc,
+                                          const float2* yh, float2* out, int lR) {
+  const int R = 1 << lR, Nfr = A.N_fr;
+  const float inv = 1.f / static_cast<float>(Nfr);
+  for (int i = threadIdx.x; i < (R << lc); i += blockDim.x) {
+    const int f = i & ((1 << lc) - 1), m = i >> lc;
+    const int bc = f >> A.logW, w = f & (A.W - 1);
+    const int b = bc < ch.n ? ch.beta[bc] : -1;
+    float2 acc = make_float2(0.f, 0.f);
+    if (b >= 0) {
+      const int2 bd = S.band[b];
+      const float* t = S.tab + b * Nfr;
+      for (int sb = bd.x + ((m - bd.x) & (R - 1)); sb <= bd.y; sb += R) {
+        const int q = sb & (Nfr - 1);
+        const float g = t[q];
+        const float2 y = yh[(q << A.logW) + w];
+        acc.x += g * y.x;
+        acc.y += g * y.y;
+      }
+    }
+    out[i] = cscale(acc, inv);
+  }
+}
+
+// W[m][f] = (1/R) sum_{s in phi_F band, s = m mod R_out} uhat[s mod R][f] phi_F(s).
+__device__ __forceinline__ void freq_pool_fold(const FreqArgs& A, const FreqSmem& S, int lc, const float2* uh,
+                                               float2* out, int lR) {
+  const int R = 1 << lR, Nfr = A.N_fr, Ro = A.R_out;
+  const float* t = S.tab + A.n_beta2 * Nfr;
+  const float inv = 1.f / static_cast<float>(R);
+  for (int i = threadIdx.x; i < (Ro << lc); i += blockDim.x) {
+    const int f = i & ((1 << lc) - 1), m = i >> lc;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int sb = A.phiF.lo + ((m - A.phiF.lo) & (Ro - 1)); sb <= A.phiF.hi; sb += Ro) {
+      const float g = t[sb & (Nfr - 1)];
+      const float2 v = uh[((sb & (R - 1)) << lc) + f];
+      acc.x += g * v.x;
+      acc.y += g * v.y;
+    }
+    out[i] = cscale(acc, inv);
   }
 }
 
@@ -385,52 +599,49 @@ k_freq_fwd(FreqArgs A, const Tile* __restrict__ tiles, const float* __restrict__
            const float2* __restrict__ Y2, float* __restrict__ out) {
   extern __shared__ float2 sm[];
   const Tile tl = tiles[blockIdx.x];
-  const int W = A.W, Nfr = A.N_fr;
-  float2* buf0 = sm;
-  float2* buf1 = sm + W * Nfr;
-  float2* buf2 = sm + 2 * W * Nfr;
-  int stride;
-  freq_load_columns<MODE>(A, tl, S1, Y2, buf0, stride);
+  const int W = A.W, WN = W * A.N_fr;
+  const FreqSmem S = freq_smem_carve(A, sm, 3);
+  float2* buf0 = S.buf;
+  float2* buf1 = buf0 + WN;
+  float2* buf2 = buf1 + WN;
+  freq_stage_tables(A, S);
+  int stride, n1m;
+  freq_load_columns<MODE>(A, tl, S1, Y2, buf0, stride, n1m);
   __syncthreads();
-  float2* yh = cta_fft<false>(buf0, buf1, A.logNfr, W, Nfr, A.tw, A.twlog);
+  float2* yh = cta_fft_il<false>(buf0, buf1, A.logNfr, A.logW, S.tw, A.logNfr);
   float2* f1 = (yh == buf0) ? buf1 : buf0;
   float2* f2 = buf2;
-  const int nb = (MODE == 1) ? A.n_beta1 : A.n_beta2;
-  const float invNfr = 1.f / static_cast<float>(Nfr);
-  for (int bi = 0; bi < nb; ++bi) {
-    const FiltD fb = A.beta[bi];
-    const int lR = A.logNfr - fb.k, R = 1 << lR;
-    for (int i = threadIdx.x; i < W * R; i += blockDim.x) {
-      const int w = i >> lR, m = i & (R - 1);
-      f1[i] = cscale(band_gather(yh + w * Nfr, Nfr, R, m, fb), invNfr);
-    }
+  const int Ro = A.R_out, lRo = A.logRout;
+  for (int c = 0; c < A.n_chunks; ++c) {
+    const FreqChunk& ch = S.chk[c];
+    const int lR = A.logNfr - ch.k;
+    const int lc = ceil_log2(ch.n) + A.logW;
+    freq_fold(A, S, ch, lc, yh, f1, lR);
     __syncthreads();
-    float2* z = cta_fft<true>(f1, f2, lR, W, R, A.tw, A.twlog);
-    for (int i = threadIdx.x; i < W * R; i += blockDim.x) {
+    float2* z = cta_fft_il<true>(f1, f2, lR, lc, S.tw, A.logNfr);
+    for (int i = threadIdx.x; i < (1 << (lR + lc)); i += blockDim.x) {
       const float2 v = z[i];
       z[i] = make_float2(sqrtf(v.x * v.x + v.y * v.y), 0.f);
     }
     __syncthreads();
     float2* zo = (z == f1) ? f2 : f1;
-    float2* uh = cta_fft<false>(z, zo, lR, W, R, A.tw, A.twlog);
+    float2* uh = cta_fft_il<false>(z, zo, lR, lc, S.tw, A.logNfr);
     float2* g = (uh == f1) ? f2 : f1;
-    const float invR = 1.f / static_cast<float>(R);
-    for (int i = threadIdx.x; i < W * A.R_out; i += blockDim.x) {
-      const int w = i >> A.logRout, m = i & (A.R_out - 1);
-      g[i] = cscale(band_gather(uh + w * R, R, A.R_out, m, A.phiF), invR);
-    }
+    freq_pool_fold(A, S, lc, uh, g, lR);
     __syncthreads();
-    float2* pr = cta_fft<true>(g, uh, A.logRout, W, A.R_out, A.tw, A.twlog);
-    for (int i = threadIdx.x; i < A.R_out * W; i += blockDim.x) {
-      const int row = i >> A.logW, w = i & (W - 1);
-      if (w < tl.ncols) {
-        const float v = pr[w * A.R_out + row].x;
+    float2* pr = cta_fft_il<true>(g, uh, lRo, lc, S.tw, A.logNfr);
+    for (int i = threadIdx.x; i < (Ro << lc); i += blockDim.x) {
+      const int f = i & ((1 << lc) - 1), row = i >> lc;
+      const int bc = f >> A.logW, w = f & (W - 1);
+      if (bc < ch.n && w < tl.ncols) {
+        const int b = ch.beta[bc];
+        const float v = pr[i].x;
         if (MODE == 1)
           out[static_cast<int64_t>(tl.b) * A.phi_size + A.phi1_off +
-              (static_cast<int64_t>(bi) * A.R_out + row) * A.n_frames + tl.t0 + w] = v;
+              (static_cast<int64_t>(b) * Ro + row) * A.n_frames + tl.t0 + w] = v;
         else
           out[static_cast<int64_t>(tl.b) * A.v2_tot + A.v2_off[tl.a] +
-              (static_cast<int64_t>(bi) * A.R_out + row) * stride + tl.t0 + w] = v;
+              (static_cast<int64_t>(b) * Ro + row) * stride + tl.t0 + w] = v;
       }
     }
     __syncthreads();
@@ -447,87 +658,93 @@ k_freq_adj(FreqArgs A, const Tile* __restrict__ tiles, const float* S1, const fl
   extern __shared__ float2 sm[];
   const Tile tl = tiles[blockIdx.x];
   const int W = A.W, Nfr = A.N_fr, WN = W * Nfr;
-  float2* buf0 = sm;
-  float2* buf1 = sm + WN;
-  float2* zb = sm + 2 * WN;
-  float2* f1 = sm + 3 * WN;
-  float2* f2 = sm + 4 * WN;
-  int stride;
-  freq_load_columns<MODE>(A, tl, S1, Y2, buf0, stride);
+  const FreqSmem S = freq_smem_carve(A, sm, 5);
+  float2* buf0 = S.buf;
+  float2* buf1 = buf0 + WN;
+  float2* zb = buf1 + WN;
+  float2* f1 = zb + WN;
+  float2* f2 = f1 + WN;
+  freq_stage_tables(A, S);
+  int stride, n1m;
+  freq_load_columns<MODE>(A, tl, S1, Y2, buf0, stride, n1m);
   __syncthreads();
-  float2* yh = cta_fft<false>(buf0, buf1, A.logNfr, W, Nfr, A.tw, A.twlog);
+  float2* yh = cta_fft_il<false>(buf0, buf1, A.logNfr, A.logW, S.tw, A.logNfr);
   float2* D = (yh == buf0) ? buf1 : buf0;
   for (int i = threadIdx.x; i < WN; i += blockDim.x) D[i] = make_float2(0.f, 0.f);
-  const int nb = (MODE == 1) ? A.n_beta1 : A.n_beta2;
   const float invNfr = 1.f / static_cast<float>(Nfr);
-  const int Rout = A.R_out, lRo = A.logRout;
-  for (int bi = 0; bi < nb; ++bi) {
-    const FiltD fb = A.beta[bi];
-    const int lR = A.logNfr - fb.k, R = 1 << lR;
+  const int Ro = A.R_out, lRo = A.logRout;
+  for (int c = 0; c < A.n_chunks; ++c) {
+    const FreqChunk& ch = S.chk[c];
+    const int lR = A.logNfr - ch.k, R = 1 << lR;
+    const int lc = ceil_log2(ch.n) + A.logW, cnt = 1 << lc;
     const float invR = 1.f / static_cast<float>(R);
-    // Recompute z = F^H(fold(psi_beta * yhat)) / N_fr and keep it in zb.
-    for (int i = threadIdx.x; i < W * R; i += blockDim.x) {
-      const int w = i >> lR, m = i & (R - 1);
-      f1[i] = cscale(band_gather(yh + w * Nfr, Nfr, R, m, fb), invNfr);
-    }
+    // Recompute z and keep it in zb.
+    freq_fold(A, S, ch, lc, yh, f1, lR);
     __syncthreads();
-    float2* z = cta_fft<true>(f1, f2, lR, W, R, A.tw, A.twlog);
-    for (int i = threadIdx.x; i < W * R; i += blockDim.x) zb[i] = z[i];
-    // dW = F(dw), dw the output gradient of this beta's R_out rows.
-    for (int i = threadIdx.x; i < W * Rout; i += blockDim.x) {
-      const int w = i >> lRo, row = i & (Rout - 1);
+    float2* z = cta_fft_il<true>(f1, f2, lR, lc, S.tw, A.logNfr);
+    float2* dwb = (z == f1) ? f2 : f1;
+    for (int i = threadIdx.x; i < (R << lc); i += blockDim.x) zb[i] = z[i];
+    // dw: the output gradient of the chunk, interleaved [row][f].
+    for (int i = threadIdx.x; i < (Ro << lc); i += blockDim.x) {
+      const int f = i & (cnt - 1), row = i >> lc;
+      const int bc = f >> A.logW, w = f & (W - 1);
       float v = 0.f;
-      if (w < tl.ncols) {
+      if (bc < ch.n && w < tl.ncols) {
+        const int b = ch.beta[bc];
         if (MODE == 1)
           v = dout[static_cast<int64_t>(tl.b) * A.phi_size + A.phi1_off +
-                   (static_cast<int64_t>(bi) * Rout + row) * A.n_frames + tl.t0 + w];
+                   (static_cast<int64_t>(b) * Ro + row) * A.n_frames + tl.t0 + w];
         else
           v = dout[static_cast<int64_t>(tl.b) * A.v2_tot + A.v2_off[tl.a] +
-                   (static_cast<int64_t>(bi) * Rout + row) * stride + tl.t0 + w];
+                   (static_cast<int64_t>(b) * Ro + row) * stride + tl.t0 + w];
       }
-      f1[i] = make_float2(v, 0.f);
+      dwb[i] = make_float2(v, 0.f);
     }
     __syncthreads();
-    float2* dW = cta_fft<false>(f1, f2, lRo, W, Rout, A.tw, A.twlog);
-    float2* X = (dW == f1) ? f2 : f1;
-    // du_hat[m] = (1/R) phi_F-level(m) dW[m mod R_out]  (adjoint of the fold)
-    for (int i = threadIdx.x; i < W * R; i += blockDim.x) {
-      const int w = i >> lR, m = i & (R - 1);
-      X[i] = cscale(dW[w * Rout + (m & (Rout - 1))], band_lev(m, R, A.phiF) * invR);
+    float2* dW = cta_fft_il<false>(dwb, z, lRo, lc, S.tw, A.logNfr);
+    float2* X = (dW == dwb) ? z : dwb;
+    // du_hat[m] = (1/R) phi_F level_k(m) dW[m mod R_out]   (adjoint of the pooling fold)
+    const float* lev = S.tab + (A.n_beta2 + 1 + ch.k) * Nfr;
+    for (int i = threadIdx.x; i < (R << lc); i += blockDim.x) {
+      const int f = i & (cnt - 1), m = i >> lc;
+      X[i] = cscale(dW[((m & (Ro - 1)) << lc) + f], lev[m] * invR);
     }
     __syncthreads();
-    float2* du = cta_fft<true>(X, dW, lR, W, R, A.tw, A.twlog);
-    // dz = Re(du) z / |z|
-    for (int i = threadIdx.x; i < W * R; i += blockDim.x) {
-      const float g = du[i].x;
+    float2* du = cta_fft_il<true>(X, dW, lR, lc, S.tw, A.logNfr);
+    // dz = Re(du) z / |z|  (0 where z = 0)
+    for (int i = threadIdx.x; i < (R << lc); i += blockDim.x) {
+      const float gr = du[i].x;
       const float2 v = zb[i];
       const float mg = sqrtf(v.x * v.x + v.y * v.y);
-      du[i] = mg > 0.f ? make_float2(g * v.x / mg, g * v.y / mg) : make_float2(0.f, 0.f);
+      du[i] = mg > 0.f ? make_float2(gr * v.x / mg, gr * v.y / mg) : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    float2* other = (du == f1) ? f2 : f1;
-    float2* dZ = cta_fft<false>(du, other, lR, W, R, A.tw, A.twlog);
-    // D[m] += (1/N_fr) psi_beta(s(m)) dZ[m mod R]
+    float2* other = (du == X) ? dW : X;
+    float2* dZ = cta_fft_il<false>(du, other, lR, lc, S.tw, A.logNfr);
+    // D[m][w] += (1/N_fr) sum_beta psi_beta(s(m)) dZ_beta[m mod R][w]
     for (int i = threadIdx.x; i < WN; i += blockDim.x) {
-      const int w = i >> A.logNfr, m = i & (Nfr - 1);
-      const int s = m < (Nfr >> 1) ? m : m - Nfr;
-      if (s >= fb.lo && s <= fb.hi) {
-        const float g = fval(fb, s) * invNfr;
-        const float2 v = dZ[w * R + (m & (R - 1))];
-        D[i].x += g * v.x;
-        D[i].y += g * v.y;
+      const int w = i & (W - 1), m = i >> A.logW;
+      const int sgn = m < (Nfr >> 1) ? m : m - Nfr;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int bc = 0; bc < ch.n; ++bc) {
+        const int b = ch.beta[bc];
+        const int2 bd = S.band[b];
+        if (sgn < bd.x || sgn > bd.y) continue;
+        const float gg = S.tab[b * Nfr + m];
+        const float2 v = dZ[((m & (R - 1)) << lc) + (bc << A.logW) + w];
+        acc.x += gg * v.x;
+        acc.y += gg * v.y;
       }
+      D[i].x += acc.x * invNfr;
+      D[i].y += acc.y * invNfr;
     }
     __syncthreads();
   }
-  float2* dy = cta_fft<true>(D, f1, A.logNfr, W, Nfr, A.tw, A.twlog);
-  int n1m;
-  if (MODE == 1) n1m = A.N1;
-  else n1m = A.n1max_act[tl.a];
+  float2* dy = cta_fft_il<true>(D, f1, A.logNfr, A.logW, S.tw, A.logNfr);
   for (int i = threadIdx.x; i < n1m * W; i += blockDim.x) {
-    const int r = i >> A.logW, w = i & (W - 1);
+    const int w = i & (W - 1), r = i >> A.logW;
     if (w < tl.ncols) {
-      const float2 v = dy[w * Nfr + r];
+      const float2 v = dy[i];
       if (MODE == 1)
         dS1[(static_cast<int64_t>(tl.b) * A.N1 + r) * A.n_frames + tl.t0 + w] = v.x;
       else
@@ -541,7 +758,7 @@ k_freq_adj(FreqArgs A, const Tile* __restrict__ tiles, const float* S1, const fl
 // adjoint.  out[f] = sum_t v[t] g_s[(f D - t) mod L], L = N/2^s, D = T/2^s.
 // ---------------------------------------------------------------------------
 struct PoolArgs {
-  int logN, lT, n_frames, R_out, n_beta2, n_active, half;  // half = kPoolHalfT * T
+  int logN, lT, n_frames, R_out, n_beta2, n_active;
   int64_t phi_size, v2_tot;
   const int* s2;
   const int64_t* v2_off;
@@ -550,55 +767,133 @@ struct PoolArgs {
   const int64_t* tap_off;
 };
 
-__global__ void __launch_bounds__(kThreads)
-k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ phi, int64_t nwarps) {
-  const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (gw >= nwarps) return;
-  const int64_t per_a = static_cast<int64_t>(A.n_beta2) * A.R_out * A.n_frames;
-  const int64_t per_b = per_a * A.n_active;
-  const int b = static_cast<int>(gw / per_b);
-  int64_t r = gw % per_b;
-  const int a = static_cast<int>(r / per_a);
-  r %= per_a;
-  const int64_t rowid = r / A.n_frames;
-  const int f = static_cast<int>(r % A.n_frames);
-  const int s = A.s2[a];
-  const int L = 1 << (A.logN - s);
-  const int D = 1 << (A.lT - s);
-  const float* v = V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a] + rowid * L;
-  const float* g = A.taps + A.tap_off[s];
-  const int H = A.half >> s;
-  const int c = f * D;
-  float acc = 0.f;
-  if (2 * H + 1 >= L) {
-    for (int t = lane; t < L; t += 32) acc += v[t] * g[(c - t) & (L - 1)];
-  } else {
-    for (int d = -H + lane; d <= H; d += 32) acc += v[(c - d) & (L - 1)] * g[d & (L - 1)];
-  }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) phi[static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a] + rowid * A.n_frames + f] = acc;
-}
+// Both directions are dense products with the tap matrix
+// G[t][f] = g_s[(f D - t) mod L]:  Phi2[rows x nf] = V2[rows x L] G and
+// dV2[rows x L] = dPhi2[rows x nf] G^T, where rows = (1+2K) R_out paths-rows
+// of one (clip, n2).  Register-blocked SIMT tiles; V2 is read once.
+constexpr int kPoolRows = 64;   // rows per CTA
+constexpr int kPoolK = 32;      // time samples per shared-memory stage (forward)
+constexpr int kPoolT = 64;      // time samples per CTA (adjoint)
 
+// Forward: thread (ty = tid / 8 in [0,32), tx = tid % 8) owns rows ty + 32 i (i < 2)
+// and frames tx + 8 j (j < FPT) of a 64-row x 8*FPT-frame tile.
+template <int FPT>
 __global__ void __launch_bounds__(kThreads)
-k_pool_adj(PoolArgs A, const float* __restrict__ dphi, float* __restrict__ dV2, int64_t total) {
-  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int b = static_cast<int>(idx / A.v2_tot);
-  const int64_t loc = idx % A.v2_tot;
-  int a = A.n_active - 1;
-  while (a > 0 && A.v2_off[a] > loc) --a;
+k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ phi, int row_tiles) {
+  __shared__ float Vs[kPoolK][kPoolRows + 1];
+  __shared__ float Gs[kPoolK][8 * FPT];
+  const int tile = blockIdx.x % row_tiles;
+  const int ba = blockIdx.x / row_tiles;
+  const int a = ba % A.n_active, b = ba / A.n_active;
+  const int fb = blockIdx.y * 8 * FPT;   // first frame of this CTA
   const int s = A.s2[a];
   const int lL = A.logN - s, L = 1 << lL;
   const int D = 1 << (A.lT - s);
-  const int64_t within = loc - A.v2_off[a];
-  const int64_t rowid = within >> lL;
-  const int t = static_cast<int>(within & (L - 1));
+  const int rows = A.n_beta2 * A.R_out;
+  const int r0 = tile * kPoolRows;
+  const float* v = V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
   const float* g = A.taps + A.tap_off[s];
-  const float* dp = dphi + static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a] + rowid * A.n_frames;
-  float acc = 0.f;
-  for (int f = 0; f < A.n_frames; ++f) acc += dp[f] * g[(f * D - t) & (L - 1)];
-  dV2[idx] = acc;
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  float acc[2][FPT];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < FPT; ++j) acc[i][j] = 0.f;
+  for (int t0 = 0; t0 < L; t0 += kPoolK) {
+    for (int i = threadIdx.x; i < kPoolRows * kPoolK; i += blockDim.x) {
+      const int rr = i / kPoolK, tt = i % kPoolK;
+      const int r = r0 + rr;
+      Vs[tt][rr] = (r < rows && t0 + tt < L) ? v[static_cast<int64_t>(r) * L + t0 + tt] : 0.f;
+    }
+    for (int i = threadIdx.x; i < kPoolK * 8 * FPT; i += blockDim.x) {
+      const int tt = i % kPoolK, ff = i / kPoolK;  // consecutive threads: consecutive taps
+      const int f = fb + ff;
+      Gs[tt][ff] = (f < A.n_frames && t0 + tt < L) ? g[(f * D - (t0 + tt)) & (L - 1)] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int tt = 0; tt < kPoolK; ++tt) {
+      const float v0 = Vs[tt][ty], v1 = Vs[tt][ty + 32];
+#pragma unroll
+      for (int j = 0; j < FPT; ++j) {
+        const float gg = Gs[tt][tx + 8 * j];
+        acc[0][j] += v0 * gg;
+        acc[1][j] += v1 * gg;
+      }
+    }
+    __syncthreads();
+  }
+  float* out = phi + static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int r = r0 + ty + 32 * i;
+    if (r >= rows) continue;
+#pragma unroll
+    for (int j = 0; j < FPT; ++j) {
+      const int f = fb + tx + 8 * j;
+      if (f < A.n_frames) out[static_cast<int64_t>(r) * A.n_frames + f] = acc[i][j];
+    }
+  }
+}
+
+// Adjoint: a CTA owns 64 rows x 64 time samples; thread (ty = tid / 16,
+// tx = tid % 16) computes rows ty + 16 i (i < 4) and times tx + 16 j (j < 4).
+__global__ void __launch_bounds__(kThreads)
+k_pool_adj(PoolArgs A, const float* __restrict__ dphi, float* __restrict__ dV2, const int4* __restrict__ tiles) {
+  __shared__ float Ps[32][kPoolRows + 1];
+  __shared__ float Gs[32][kPoolT + 1];
+  const int4 tl = tiles[blockIdx.x];  // (b, a, row tile, time tile)
+  const int b = tl.x, a = tl.y;
+  const int s = A.s2[a];
+  const int lL = A.logN - s, L = 1 << lL;
+  const int D = 1 << (A.lT - s);
+  const int rows = A.n_beta2 * A.R_out;
+  const int r0 = tl.z * kPoolRows, t0 = tl.w * kPoolT;
+  const float* dp = dphi + static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a];
+  const float* g = A.taps + A.tap_off[s];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int f0 = 0; f0 < A.n_frames; f0 += 32) {
+    for (int i = threadIdx.x; i < kPoolRows * 32; i += blockDim.x) {
+      const int rr = i / 32, ff = i % 32;
+      const int r = r0 + rr, f = f0 + ff;
+      Ps[ff][rr] = (r < rows && f < A.n_frames) ? dp[static_cast<int64_t>(r) * A.n_frames + f] : 0.f;
+    }
+    for (int i = threadIdx.x; i < 32 * kPoolT; i += blockDim.x) {
+      const int ff = i / kPoolT, tt = i % kPoolT;
+      const int f = f0 + ff, t = t0 + tt;
+      Gs[ff][tt] = (f < A.n_frames && t < L) ? g[(f * D - t) & (L - 1)] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ff = 0; ff < 32; ++ff) {
+      float pv[4], gv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) pv[i] = Ps[ff][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) gv[j] = Gs[ff][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += pv[i] * gv[j];
+    }
+    __syncthreads();
+  }
+  float* out = dV2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty + 16 * i;
+    if (r >= rows) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int t = t0 + tx + 16 * j;
+      if (t < L) out[static_cast<int64_t>(r) * L + t] = acc[i][j];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -746,8 +1041,10 @@ Bufs bufs(const Plan& p, void* ws) {
   return w;
 }
 
-FreqArgs freq_args(const Plan& p) {
+FreqArgs freq_args(const Plan& p, int mode) {
   FreqArgs A{};
+  A.chunks = mode == 1 ? p.d_chunks1 : p.d_chunks2;
+  A.n_chunks = static_cast<int>(mode == 1 ? p.chunks1.size() : p.chunks2.size());
   A.N1 = p.N1;
   A.N_fr = p.N_fr;
   A.logNfr = p.logNfr;
@@ -761,6 +1058,8 @@ FreqArgs freq_args(const Plan& p) {
   A.logW = lw;
   A.n_beta1 = p.n_beta1;
   A.n_beta2 = p.n_beta2;
+  A.n_ftab = p.n_ftab;
+  A.ftab = p.d_ftab;
   A.phi_size = p.phi_size;
   A.phi1_off = p.phi1_off;
   A.y2_tot = p.y2_tot;
@@ -784,7 +1083,6 @@ PoolArgs pool_args(const Plan& p) {
   A.R_out = p.R_out;
   A.n_beta2 = p.n_beta2;
   A.n_active = p.n_active;
-  A.half = static_cast<int>(std::min<int64_t>(int64_t(kPoolHalfT) * p.T, p.N));
   A.phi_size = p.phi_size;
   A.v2_tot = p.v2_tot;
   A.s2 = p.d_s2;
@@ -858,7 +1156,11 @@ int64_t backward_launches(const Plan& p) {
   return n;
 }
 
-size_t freq_smem(const Plan& p, int nbuf) { return size_t(nbuf) * p.freq_cols * p.N_fr * sizeof(float2); }
+size_t freq_smem(const Plan& p, int nbuf) {
+  return size_t(p.N_fr) * sizeof(float2) + size_t(nbuf) * p.freq_cols * p.N_fr * sizeof(float2) +
+         size_t(p.n_ftab) * p.N_fr * sizeof(float) + size_t(p.n_beta2) * sizeof(int2) +
+         std::max(p.chunks1.size(), p.chunks2.size()) * sizeof(FreqChunk);
+}
 
 // Forward stages.  `full` = false stops after what the adjoint needs
 // (Xhat, U1hat, S1, Y2) and skips writing Phi.
@@ -868,7 +1170,8 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
   JTFS_TRY((run_fft<false>(p, p.L_u1inplace, LdMod{w.U1h}, StC{w.U1h}, w.scr, s)));
   if (full) JTFS_TRY((run_fft<true>(p, p.L_s0, LdBand{w.Xh, nullptr, p.h_phiT}, StR{phi}, w.scr, s)));
   JTFS_TRY((run_fft<true>(p, p.L_s1, LdBand{w.U1h, nullptr, p.h_phiT}, StR{w.S1}, w.scr, s)));
-  const FreqArgs FA = freq_args(p);
+  const FreqArgs FA = freq_args(p, 1);
+  const FreqArgs FA2 = freq_args(p, 2);
   if (full) {
     allow_big_smem<k_freq_fwd<1>>();
     k_freq_fwd<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 3), s>>>(
@@ -881,14 +1184,23 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
       allow_big_smem<k_freq_fwd<2>>();
       prof_begin(p, JTFS_STAGE_FREQ2_FWD, s);
       k_freq_fwd<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 3), s>>>(
-          FA, p.d_tiles2, nullptr, w.Y2, w.V2);
+          FA2, p.d_tiles2, nullptr, w.Y2, w.V2);
       prof_end(p, JTFS_STAGE_FREQ2_FWD, s);
       JTFS_TRY(check_launch());
       const PoolArgs PA = pool_args(p);
-      const int64_t nwarps = int64_t(p.batch) * p.n_active * p.n_beta2 * p.R_out * p.n_frames;
-      const int64_t blocks = (nwarps * 32 + kThreads - 1) / kThreads;
+      const int rows = p.n_beta2 * p.R_out;
+      const int row_tiles = (rows + kPoolRows - 1) / kPoolRows;
+      const int fpt = p.n_frames >= 128 ? 16 : p.n_frames >= 64 ? 8 : p.n_frames >= 32 ? 4 : p.n_frames >= 16 ? 2 : 1;
+      dim3 grid(static_cast<unsigned>(p.batch * p.n_active * row_tiles),
+                static_cast<unsigned>((p.n_frames + 8 * fpt - 1) / (8 * fpt)));
       prof_begin(p, JTFS_STAGE_POOL_FWD, s);
-      k_pool_fwd<<<static_cast<unsigned>(blocks), kThreads, 0, s>>>(PA, w.V2, phi, nwarps);
+      switch (fpt) {
+        case 16: k_pool_fwd<16><<<grid, kThreads, 0, s>>>(PA, w.V2, phi, row_tiles); break;
+        case 8: k_pool_fwd<8><<<grid, kThreads, 0, s>>>(PA, w.V2, phi, row_tiles); break;
+        case 4: k_pool_fwd<4><<<grid, kThreads, 0, s>>>(PA, w.V2, phi, row_tiles); break;
+        case 2: k_pool_fwd<2><<<grid, kThreads, 0, s>>>(PA, w.V2, phi, row_tiles); break;
+        default: k_pool_fwd<1><<<grid, kThreads, 0, s>>>(PA, w.V2, phi, row_tiles); break;
+      }
       prof_end(p, JTFS_STAGE_POOL_FWD, s);
       JTFS_TRY(check_launch());
     }
@@ -899,20 +1211,19 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
 // Backward stages from dphi (device, [batch][phi_size]) to dx.  Requires
 // forward_stages(full or not) to have filled Xh, U1h, S1 and Y2.
 int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, cudaStream_t s) {
-  const FreqArgs FA = freq_args(p);
+  const FreqArgs FA = freq_args(p, 1);
+  const FreqArgs FA2 = freq_args(p, 2);
   const GradArgs GA = grad_args(p);
   if (p.n_active > 0) {
     const PoolArgs PA = pool_args(p);
-    const int64_t total = int64_t(p.batch) * p.v2_tot;
     prof_begin(p, JTFS_STAGE_POOL_ADJ, s);
-    k_pool_adj<<<static_cast<unsigned>((total + kThreads - 1) / kThreads), kThreads, 0, s>>>(PA, dphi, w.V2,
-                                                                                             total);
+    k_pool_adj<<<static_cast<unsigned>(p.pool_tiles.size()), kThreads, 0, s>>>(PA, dphi, w.V2, p.d_pool_tiles);
     prof_end(p, JTFS_STAGE_POOL_ADJ, s);
     JTFS_TRY(check_launch());
     allow_big_smem<k_freq_adj<2>>();
     prof_begin(p, JTFS_STAGE_FREQ2_ADJ, s);
     k_freq_adj<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 5), s>>>(
-        FA, p.d_tiles2, nullptr, w.Y2, w.V2, nullptr, w.dY2);
+        FA2, p.d_tiles2, nullptr, w.Y2, w.V2, nullptr, w.dY2);
     prof_end(p, JTFS_STAGE_FREQ2_ADJ, s);
     JTFS_TRY(check_launch());
   }

@@ -47,6 +47,15 @@ struct Tile {
   int ncols;  // columns in this tile
 };
 
+// Frequential filters of equal stride level k processed together by the
+// frequential kernels: `n` filter indices (<= 16), each folded onto
+// N_fr / 2^k bins.
+struct FreqChunk {
+  int k;
+  int n;
+  int beta[16];
+};
+
 // A batched FFT launch: `njobs` transforms of size 2^logn described by
 // jobs[job0 .. job0 + njobs).
 struct FftLaunch {
@@ -63,8 +72,6 @@ struct FilterH {
 
 // Number of sigmas beyond which a Gaussian term is dropped (exp(-72)).
 constexpr double kBandSigmas = 12.0;
-// Time-pooling taps: half window in units of T (exp(-28) relative).
-constexpr int kPoolHalfT = 12;
 // Largest FFT done by one CTA in shared memory (2^13 complex, ping-pong).
 constexpr int kSmallLogMax = 13;
 // Columns per CTA in the frequential kernels.
@@ -128,6 +135,13 @@ struct Plan {
   std::vector<FftLaunch> L_ds0;      // B7a: FFT of dS0
   std::vector<Tile> tiles1, tiles2;
   int freq_cols = kFreqCols;
+  std::vector<FreqChunk> chunks1, chunks2;
+  std::vector<int4> pool_tiles;  // adjoint time pooling: (clip, active n2, row tile, time tile)  // first order (phi_F, +xi) / second order (all)
+  // Frequential tables on the N_fr grid, one row of N_fr floats each:
+  // rows [0, n_beta2): psi_beta; row n_beta2: phi_F; row n_beta2 + 1 + k:
+  // phi_F periodised onto N_fr / 2^k bins (k = 0 .. log2 F).
+  std::vector<float> h_ftab;
+  int n_ftab = 0;
 
   // Host copies of the device tables.
   std::vector<FiltD> h_psi1, h_psi2, h_beta;  // psi1/psi2 on grid N; beta on N_fr
@@ -147,6 +161,10 @@ struct Plan {
   const Job* d_jobs = nullptr;
   const Tile* d_tiles1 = nullptr;
   const Tile* d_tiles2 = nullptr;
+  const FreqChunk* d_chunks1 = nullptr;
+  const FreqChunk* d_chunks2 = nullptr;
+  const float* d_ftab = nullptr;
+  const int4* d_pool_tiles = nullptr;
   const int* d_s2 = nullptr;          // per active index
   const int* d_n1max_act = nullptr;   // per active index
   const int64_t* d_y2_off = nullptr;  // per active index

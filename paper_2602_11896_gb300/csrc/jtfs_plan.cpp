@@ -299,6 +299,64 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
         p.tiles2.push_back({b, a, t0, std::min(p.freq_cols, L2 - t0)});
     }
 
+  // Frequential tables (double precision on the host, stored as float).
+  {
+    const int n = p.N_fr;
+    p.n_ftab = p.n_beta2 + 1 + (p.lF + 1);
+    p.h_ftab.assign(size_t(p.n_ftab) * n, 0.f);
+    auto omega = [n](int m) { return double(m < n / 2 ? m : m - n) / double(n); };
+    auto gauss = [](double w, double c, double sg) { return std::exp(-(w - c) * (w - c) / (2.0 * sg * sg)); };
+    for (int b = 0; b < p.n_beta2; ++b) {
+      const FilterH& f = b == 0 ? p.phiF : p.psifr[(b - 1) % p.K];
+      const double xi = b == 0 ? 0.0 : (b <= p.K ? f.xi : -f.xi);
+      const double kappa = b == 0 ? 0.0 : std::exp(-f.xi * f.xi / (2.0 * f.sigma * f.sigma));
+      for (int m = 0; m < n; ++m)
+        p.h_ftab[size_t(b) * n + m] =
+            static_cast<float>(gauss(omega(m), xi, f.sigma) - kappa * gauss(omega(m), 0.0, f.sigma));
+    }
+    for (int m = 0; m < n; ++m)
+      p.h_ftab[size_t(p.n_beta2) * n + m] = static_cast<float>(gauss(omega(m), 0.0, p.phiF.sigma));
+    for (int k = 0; k <= p.lF; ++k) {
+      const int R = n >> k;
+      for (int m = 0; m < R; ++m) {
+        double acc = 0.0;
+        for (int r = 0; r < (1 << k); ++r) acc += gauss(omega(m + r * R), 0.0, p.phiF.sigma);
+        p.h_ftab[size_t(p.n_beta2 + 1 + k) * n + m] = static_cast<float>(acc);
+      }
+    }
+  }
+  // Chunks of frequential filters with equal stride level.
+  auto make_chunks = [&](int nb, std::vector<FreqChunk>& out) {
+    out.clear();
+    for (int k = 0; k <= p.lF; ++k) {
+      const int cap = std::min(16, 1 << k);
+      FreqChunk c{};
+      c.k = k;
+      for (int b = 0; b < nb; ++b) {
+        if (p.beta_k[b] != k) continue;
+        c.beta[c.n++] = b;
+        if (c.n == cap) {
+          out.push_back(c);
+          c.n = 0;
+        }
+      }
+      if (c.n) out.push_back(c);
+    }
+  };
+  make_chunks(p.n_beta1, p.chunks1);
+  make_chunks(p.n_beta2, p.chunks2);
+  // Tiles of the adjoint time pooling: 64 path-rows x 64 time samples.
+  p.pool_tiles.clear();
+  {
+    const int rows = p.n_beta2 * p.R_out;
+    for (int b = 0; b < B; ++b)
+      for (int a = 0; a < p.n_active; ++a) {
+        const int L = static_cast<int>(N >> p.s2[a]);
+        for (int rt = 0; rt < (rows + 63) / 64; ++rt)
+          for (int tt = 0; tt < (L + 63) / 64; ++tt) p.pool_tiles.push_back(make_int4(b, a, rt, tt));
+      }
+  }
+
   // Four-step scratch: the largest large-size launch.
   p.scr_elems = 0;
   for (auto* L : {&p.L_x, &p.L_u1, &p.L_u1inplace, &p.L_y2, &p.L_y2inplace})
@@ -356,6 +414,10 @@ int upload_plan(Plan& p) {
   const size_t o_jobs = put(p.jobs.data(), p.jobs.size() * sizeof(Job));
   const size_t o_t1 = put(p.tiles1.data(), p.tiles1.size() * sizeof(Tile));
   const size_t o_t2 = put(p.tiles2.data(), p.tiles2.size() * sizeof(Tile));
+  const size_t o_c1 = put(p.chunks1.data(), p.chunks1.size() * sizeof(FreqChunk));
+  const size_t o_c2 = put(p.chunks2.data(), p.chunks2.size() * sizeof(FreqChunk));
+  const size_t o_ftab = put(p.h_ftab.data(), p.h_ftab.size() * sizeof(float));
+  const size_t o_pt = put(p.pool_tiles.data(), p.pool_tiles.size() * sizeof(int4));
   const size_t o_s2 = put(p.s2.data(), p.s2.size() * sizeof(int));
   const size_t o_n1m = put(n1max_act.data(), n1max_act.size() * sizeof(int));
   const size_t o_y2o = put(p.y2_off.data(), p.y2_off.size() * sizeof(int64_t));
@@ -386,6 +448,10 @@ int upload_plan(Plan& p) {
   p.d_jobs = reinterpret_cast<const Job*>(at(o_jobs));
   p.d_tiles1 = reinterpret_cast<const Tile*>(at(o_t1));
   p.d_tiles2 = reinterpret_cast<const Tile*>(at(o_t2));
+  p.d_chunks1 = reinterpret_cast<const FreqChunk*>(at(o_c1));
+  p.d_chunks2 = reinterpret_cast<const FreqChunk*>(at(o_c2));
+  p.d_ftab = reinterpret_cast<const float*>(at(o_ftab));
+  p.d_pool_tiles = reinterpret_cast<const int4*>(at(o_pt));
   p.d_s2 = reinterpret_cast<const int*>(at(o_s2));
   p.d_n1max_act = reinterpret_cast<const int*>(at(o_n1m));
   p.d_y2_off = reinterpret_cast<const int64_t*>(at(o_y2o));
