@@ -484,13 +484,12 @@ struct FreqArgs {
 // Shared-memory layout of the frequential kernels (all in float2 units):
 //   tw    [N_fr]                twiddles exp(-2 pi i e / N_fr)
 //   bufs  nbuf x [W * N_fr]     interleaved transforms
-//   tab   [n_ftab * N_fr] float filter tables
 //   band  [n_beta2] int2        (lo, hi) of each frequential filter
 //   chk   [n_chunks] FreqChunk
 struct FreqSmem {
   float2* tw;
   float2* buf;
-  float* tab;
+  const float* tab;  // global (read through L1): [n_ftab][N_fr]
   int2* band;
   FreqChunk* chk;
 };
@@ -500,8 +499,8 @@ __device__ __forceinline__ FreqSmem freq_smem_carve(const FreqArgs& A, float2* s
   const int WN = A.W * A.N_fr;
   S.tw = sm;
   S.buf = sm + A.N_fr;
-  S.tab = reinterpret_cast<float*>(S.buf + nbuf * WN);
-  S.band = reinterpret_cast<int2*>(S.tab + A.n_ftab * A.N_fr);
+  S.tab = A.ftab;
+  S.band = reinterpret_cast<int2*>(S.buf + nbuf * WN);
   S.chk = reinterpret_cast<FreqChunk*>(S.band + A.n_beta2);
   return S;
 }
@@ -509,7 +508,6 @@ __device__ __forceinline__ FreqSmem freq_smem_carve(const FreqArgs& A, float2* s
 __device__ __forceinline__ void freq_stage_tables(const FreqArgs& A, const FreqSmem& S) {
   const int sh = A.twlog - A.logNfr;
   for (int i = threadIdx.x; i < A.N_fr; i += blockDim.x) S.tw[i] = __ldg(A.tw + (i << sh));
-  for (int i = threadIdx.x; i < A.n_ftab * A.N_fr; i += blockDim.x) S.tab[i] = __ldg(A.ftab + i);
   for (int i = threadIdx.x; i < A.n_beta2; i += blockDim.x) S.band[i] = make_int2(A.beta[i].lo, A.beta[i].hi);
   const int* csrc = reinterpret_cast<const int*>(A.chunks);
   int* cdst = reinterpret_cast<int*>(S.chk);
@@ -774,23 +772,27 @@ struct PoolArgs {
 constexpr int kPoolRows = 64;   // rows per CTA
 constexpr int kPoolK = 32;      // time samples per shared-memory stage (forward)
 constexpr int kPoolT = 64;      // time samples per CTA (adjoint)
+constexpr int kPoolSplit = kPoolSplitPlan;  // time samples per CTA (forward, split-K)
 
-// Forward: thread (ty = tid / 8 in [0,32), tx = tid % 8) owns rows ty + 32 i (i < 2)
-// and frames tx + 8 j (j < FPT) of a 64-row x 8*FPT-frame tile.
+// Forward, split over time: a CTA owns a 64-row x 8*FPT-frame tile of one
+// (clip, n2) and the time samples [split * kPoolSplit, +kPoolSplit); thread
+// (ty = tid / 8, tx = tid % 8) owns rows ty + 32 i (i < 2) and frames
+// tx + 8 j (j < FPT).  Partial sums go to `part`, reduced in a fixed order
+// by k_pool_reduce (deterministic).
 template <int FPT>
 __global__ void __launch_bounds__(kThreads)
-k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ phi, int row_tiles) {
+k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ part, const int4* __restrict__ tiles) {
   __shared__ float Vs[kPoolK][kPoolRows + 1];
   __shared__ float Gs[kPoolK][8 * FPT];
-  const int tile = blockIdx.x % row_tiles;
-  const int ba = blockIdx.x / row_tiles;
-  const int a = ba % A.n_active, b = ba / A.n_active;
-  const int fb = blockIdx.y * 8 * FPT;   // first frame of this CTA
+  const int4 tl = tiles[blockIdx.x];  // (clip, active n2, row tile, split)
+  const int b = tl.x, a = tl.y, split = tl.w;
+  const int fb = blockIdx.y * 8 * FPT;
   const int s = A.s2[a];
   const int lL = A.logN - s, L = 1 << lL;
   const int D = 1 << (A.lT - s);
   const int rows = A.n_beta2 * A.R_out;
-  const int r0 = tile * kPoolRows;
+  const int r0 = tl.z * kPoolRows;
+  const int tbeg = split * kPoolSplit, tend = min(L, tbeg + kPoolSplit);
   const float* v = V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
   const float* g = A.taps + A.tap_off[s];
   const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
@@ -799,16 +801,16 @@ k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ phi, in
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < FPT; ++j) acc[i][j] = 0.f;
-  for (int t0 = 0; t0 < L; t0 += kPoolK) {
+  for (int t0 = tbeg; t0 < tend; t0 += kPoolK) {
     for (int i = threadIdx.x; i < kPoolRows * kPoolK; i += blockDim.x) {
       const int rr = i / kPoolK, tt = i % kPoolK;
       const int r = r0 + rr;
-      Vs[tt][rr] = (r < rows && t0 + tt < L) ? v[static_cast<int64_t>(r) * L + t0 + tt] : 0.f;
+      Vs[tt][rr] = (r < rows && t0 + tt < tend) ? v[static_cast<int64_t>(r) * L + t0 + tt] : 0.f;
     }
     for (int i = threadIdx.x; i < kPoolK * 8 * FPT; i += blockDim.x) {
       const int tt = i % kPoolK, ff = i / kPoolK;  // consecutive threads: consecutive taps
       const int f = fb + ff;
-      Gs[tt][ff] = (f < A.n_frames && t0 + tt < L) ? g[(f * D - (t0 + tt)) & (L - 1)] : 0.f;
+      Gs[tt][ff] = (f < A.n_frames && t0 + tt < tend) ? g[(f * D - (t0 + tt)) & (L - 1)] : 0.f;
     }
     __syncthreads();
 #pragma unroll 4
@@ -823,17 +825,40 @@ k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ phi, in
     }
     __syncthreads();
   }
-  float* out = phi + static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a];
+  // partial layout: [tile index][64 rows][n_frames]
+  float* out = part + static_cast<int64_t>(blockIdx.x) * kPoolRows * A.n_frames;
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    const int r = r0 + ty + 32 * i;
-    if (r >= rows) continue;
+    const int rr = ty + 32 * i;
 #pragma unroll
     for (int j = 0; j < FPT; ++j) {
       const int f = fb + tx + 8 * j;
-      if (f < A.n_frames) out[static_cast<int64_t>(r) * A.n_frames + f] = acc[i][j];
+      if (f < A.n_frames) out[rr * A.n_frames + f] = acc[i][j];
     }
   }
+}
+
+// Phi2[b][a][r][f] = sum over splits (ascending) of the partials.
+__global__ void __launch_bounds__(kThreads)
+k_pool_reduce(PoolArgs A, const float* __restrict__ part, float* __restrict__ phi, const int* __restrict__ tile0,
+              int row_tiles, int64_t total) {
+  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int rows = A.n_beta2 * A.R_out;
+  const int64_t per_a = static_cast<int64_t>(rows) * A.n_frames;
+  const int64_t ba = idx / per_a;
+  const int rf = static_cast<int>(idx % per_a);
+  const int r = rf / A.n_frames, f = rf % A.n_frames;
+  const int a = static_cast<int>(ba % A.n_active), b = static_cast<int>(ba / A.n_active);
+  const int L = 1 << (A.logN - A.s2[a]);
+  const int nsplit = (L + kPoolSplit - 1) / kPoolSplit;
+  // tiles of (b, a) start at tile0[ba]; ordered by row tile then split
+  const int64_t t = tile0[ba] + static_cast<int64_t>(r / kPoolRows) * nsplit;
+  const float* pp = part + (t * kPoolRows + (r % kPoolRows)) * A.n_frames + f;
+  float acc = 0.f;
+  for (int sp = 0; sp < nsplit; ++sp) acc += pp[static_cast<int64_t>(sp) * kPoolRows * A.n_frames];
+  phi[static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a] + static_cast<int64_t>(r) * A.n_frames + f] = acc;
+  (void)row_tiles;
 }
 
 // Adjoint: a CTA owns 64 rows x 64 time samples; thread (ty = tid / 16,
@@ -1018,7 +1043,7 @@ k_adam(float* __restrict__ y, float* __restrict__ m, float* __restrict__ v, cons
 // ---------------------------------------------------------------------------
 struct Bufs {
   float2 *Xh, *U1h, *Zs, *dS1h, *Y2, *dY2, *dXh, *dS0h, *scr;
-  float *S1, *V2, *phi, *dphi, *dy;
+  float *S1, *V2, *phi, *dphi, *dy, *part;
 };
 
 Bufs bufs(const Plan& p, void* ws) {
@@ -1038,6 +1063,7 @@ Bufs bufs(const Plan& p, void* ws) {
   w.dS0h = reinterpret_cast<float2*>(c + p.ws_dS0h);
   w.dy = reinterpret_cast<float*>(c + p.ws_dy);
   w.scr = reinterpret_cast<float2*>(c + p.ws_scr);
+  w.part = reinterpret_cast<float*>(c + p.ws_part);
   return w;
 }
 
@@ -1144,7 +1170,7 @@ int64_t fft_launches(const std::vector<FftLaunch>& L) {
 int64_t forward_launches(const Plan& p, bool full) {
   int64_t n = fft_launches(p.L_x) + fft_launches(p.L_u1) + fft_launches(p.L_u1inplace) + fft_launches(p.L_s1);
   if (full) n += fft_launches(p.L_s0) + 1;
-  if (p.n_active > 0) n += fft_launches(p.L_y2) + (full ? 2 : 0);
+  if (p.n_active > 0) n += fft_launches(p.L_y2) + (full ? 3 : 0);
   return n;
 }
 
@@ -1158,7 +1184,7 @@ int64_t backward_launches(const Plan& p) {
 
 size_t freq_smem(const Plan& p, int nbuf) {
   return size_t(p.N_fr) * sizeof(float2) + size_t(nbuf) * p.freq_cols * p.N_fr * sizeof(float2) +
-         size_t(p.n_ftab) * p.N_fr * sizeof(float) + size_t(p.n_beta2) * sizeof(int2) +
+         size_t(p.n_beta2) * sizeof(int2) +
          std::max(p.chunks1.size(), p.chunks2.size()) * sizeof(FreqChunk);
 }
 
@@ -1188,18 +1214,22 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
       prof_end(p, JTFS_STAGE_FREQ2_FWD, s);
       JTFS_TRY(check_launch());
       const PoolArgs PA = pool_args(p);
-      const int rows = p.n_beta2 * p.R_out;
-      const int row_tiles = (rows + kPoolRows - 1) / kPoolRows;
       const int fpt = p.n_frames >= 128 ? 16 : p.n_frames >= 64 ? 8 : p.n_frames >= 32 ? 4 : p.n_frames >= 16 ? 2 : 1;
-      dim3 grid(static_cast<unsigned>(p.batch * p.n_active * row_tiles),
+      dim3 grid(static_cast<unsigned>(p.pool_fwd_tiles.size()),
                 static_cast<unsigned>((p.n_frames + 8 * fpt - 1) / (8 * fpt)));
       prof_begin(p, JTFS_STAGE_POOL_FWD, s);
       switch (fpt) {
-        case 16: k_pool_fwd<16><<<grid, kThreads, 0, s>>>(PA, w.V2, phi, row_tiles); break;
-        case 8: k_pool_fwd<8><<<grid, kThreads, 0, s>>>(PA, w.V2, phi, row_tiles); break;
-        case 4: k_pool_fwd<4><<<grid, kThreads, 0, s>>>(PA, w.V2, phi, row_tiles); break;
-        case 2: k_pool_fwd<2><<<grid, kThreads, 0, s>>>(PA, w.V2, phi, row_tiles); break;
-        default: k_pool_fwd<1><<<grid, kThreads, 0, s>>>(PA, w.V2, phi, row_tiles); break;
+        case 16: k_pool_fwd<16><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, p.d_pool_fwd_tiles); break;
+        case 8: k_pool_fwd<8><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, p.d_pool_fwd_tiles); break;
+        case 4: k_pool_fwd<4><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, p.d_pool_fwd_tiles); break;
+        case 2: k_pool_fwd<2><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, p.d_pool_fwd_tiles); break;
+        default: k_pool_fwd<1><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, p.d_pool_fwd_tiles); break;
+      }
+      JTFS_TRY(check_launch());
+      {
+        const int64_t total = int64_t(p.batch) * p.n_active * p.n_beta2 * p.R_out * p.n_frames;
+        k_pool_reduce<<<static_cast<unsigned>((total + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+            PA, w.part, phi, p.d_pool_tile0, 0, total);
       }
       prof_end(p, JTFS_STAGE_POOL_FWD, s);
       JTFS_TRY(check_launch());

@@ -74,8 +74,10 @@ struct FilterH {
 constexpr double kBandSigmas = 12.0;
 // Largest FFT done by one CTA in shared memory (2^13 complex, ping-pong).
 constexpr int kSmallLogMax = 13;
-// Columns per CTA in the frequential kernels.
+// Columns per CTA in the frequential kernels (at most; fewer for long N_fr).
 constexpr int kFreqCols = 16;
+// Time samples per forward time-pooling CTA (split over time).
+constexpr int kPoolSplitPlan = 2048;
 
 struct Plan {
   // Parameters.
@@ -119,7 +121,7 @@ struct Plan {
   // Workspace layout (byte offsets).
   size_t ws_Xh = 0, ws_U1h = 0, ws_Zs = 0, ws_S1 = 0, ws_dS1h = 0, ws_Y2 = 0,
          ws_dY2 = 0, ws_V2 = 0, ws_phi = 0, ws_dphi = 0, ws_scr = 0,
-         ws_dXh = 0, ws_dS0h = 0, ws_dy = 0, ws_bytes = 0;
+         ws_dXh = 0, ws_dS0h = 0, ws_dy = 0, ws_part = 0, ws_bytes = 0;
   int64_t scr_elems = 0;  // four-step scratch, complex elements
 
   // Launch descriptions.
@@ -136,7 +138,9 @@ struct Plan {
   std::vector<Tile> tiles1, tiles2;
   int freq_cols = kFreqCols;
   std::vector<FreqChunk> chunks1, chunks2;
-  std::vector<int4> pool_tiles;  // adjoint time pooling: (clip, active n2, row tile, time tile)  // first order (phi_F, +xi) / second order (all)
+  std::vector<int4> pool_tiles;  // adjoint time pooling: (clip, active n2, row tile, time tile)
+  std::vector<int4> pool_fwd_tiles;  // forward time pooling: (clip, active n2, row tile, split)
+  std::vector<int> pool_tile0;       // per (clip, active n2): first forward tile  // first order (phi_F, +xi) / second order (all)
   // Frequential tables on the N_fr grid, one row of N_fr floats each:
   // rows [0, n_beta2): psi_beta; row n_beta2: phi_F; row n_beta2 + 1 + k:
   // phi_F periodised onto N_fr / 2^k bins (k = 0 .. log2 F).
@@ -165,6 +169,8 @@ struct Plan {
   const FreqChunk* d_chunks2 = nullptr;
   const float* d_ftab = nullptr;
   const int4* d_pool_tiles = nullptr;
+  const int4* d_pool_fwd_tiles = nullptr;
+  const int* d_pool_tile0 = nullptr;
   const int* d_s2 = nullptr;          // per active index
   const int* d_n1max_act = nullptr;   // per active index
   const int64_t* d_y2_off = nullptr;  // per active index
