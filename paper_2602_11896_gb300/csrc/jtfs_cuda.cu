@@ -20,22 +20,15 @@
 #include <cstdint>
 
 #include "jtfs.h"
+#include "jtfs_device.cuh"
 #include "jtfs_internal.h"
 
 namespace jtfs {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kMaxSmem = 227 * 1024;
-
 // ---------------------------------------------------------------------------
 // Complex helpers and filters
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-
 // Filter value at signed bin s of its grid (see FiltD).
 __device__ __forceinline__ float fval(const FiltD& f, int s) {
   const float d = static_cast<float>(s) - f.c0;
@@ -152,97 +145,50 @@ __device__ float2* cta_fft(float2* a, float2* b, int logn, int count, int bstrid
 // whatever the Stockham stride), and all threads of a warp read the same
 // twiddle (a broadcast).  Twiddles come from a shared-memory table.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-template <bool INV>
-__device__ __forceinline__ float2 mul_mi(float2 a) {  // * (-i) forward, * (+i) inverse
-  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
-}
-// exp(-2 pi i m / 16) (forward) or its conjugate; m is a compile-time constant after unrolling.
-template <bool INV>
-__device__ __forceinline__ float2 w16(int m) {
-  constexpr float C1 = 0.92387953251128674f, S1 = 0.38268343236508978f, H = 0.70710678118654752f;
-  const float c[16] = {1.f, C1, H, S1, 0.f, -S1, -H, -C1, -1.f, -C1, -H, -S1, 0.f, S1, H, C1};
-  const float sn[16] = {0.f, S1, H, C1, 1.f, C1, H, S1, 0.f, -S1, -H, -C1, -1.f, -C1, -H, -S1};
-  return make_float2(c[m & 15], INV ? sn[m & 15] : -sn[m & 15]);
-}
-template <bool INV>
-__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
-  const float2 s02 = cadd(v0, v2), d02 = csub(v0, v2), s13 = cadd(v1, v3), d13 = mul_mi<INV>(csub(v1, v3));
-  v0 = cadd(s02, s13);
-  v2 = csub(s02, s13);
-  v1 = cadd(d02, d13);
-  v3 = csub(d02, d13);
-}
-template <bool INV, int R>
-__device__ __forceinline__ void dft_reg(float2* v) {
-  if constexpr (R == 2) {
-    const float2 t = v[0];
-    v[0] = cadd(t, v[1]);
-    v[1] = csub(t, v[1]);
-  } else if constexpr (R == 4) {
-    dft4<INV>(v[0], v[1], v[2], v[3]);
-  } else if constexpr (R == 8) {
-    // n = 2 n1 + n2, k = k1 + 4 k2: DFT4 over n1, twiddle W8^(n2 k1), DFT2 over n2.
-    dft4<INV>(v[0], v[2], v[4], v[6]);
-    dft4<INV>(v[1], v[3], v[5], v[7]);
-    float2 b[4] = {v[1], cmul(v[3], w16<INV>(2)), mul_mi<INV>(v[5]), cmul(v[7], w16<INV>(6))};
-    float2 a[4] = {v[0], v[2], v[4], v[6]};
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
-      v[k1] = cadd(a[k1], b[k1]);
-      v[k1 + 4] = csub(a[k1], b[k1]);
-    }
-  } else {  // R == 16: n = 4 n1 + n2, k = k1 + 4 k2
-#pragma unroll
-    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
-    // now Y[n2][k1] sits at v[4 k1 + n2]; twiddle by W16^(n2 k1)
-#pragma unroll
-    for (int k1 = 1; k1 < 4; ++k1)
-#pragma unroll
-      for (int n2 = 1; n2 < 4; ++n2) v[4 * k1 + n2] = cmul(v[4 * k1 + n2], w16<INV>(n2 * k1));
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
-    // X[k1 + 4 k2] sits at v[4 k1 + k2]: transpose the 4 x 4 register block
-    float2 t[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) t[i] = v[i];
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1)
-#pragma unroll
-      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
-  }
-}
-
+// One radix-R pass over interleaved transforms, two adjacent transforms per
+// thread (16-byte accesses; both share index arithmetic and twiddles).
 template <bool INV, int R, int LR>
 __device__ __forceinline__ void il_pass(const float2* __restrict__ src, float2* __restrict__ dst, int logn,
                                         int lcnt, int lNs, const float2* __restrict__ tw, int twlog) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  float4* d4 = reinterpret_cast<float4*>(dst);
   const int lq = logn - LR;
-  const int total = 1 << (lq + lcnt);
+  const int lp = lcnt - 1;                 // log2(pairs per bin)
+  const int total = 1 << (lq + lp);
   const int Ns = 1 << lNs;
   const int shift = twlog - (lNs + LR);
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int f = idx & ((1 << lcnt) - 1), j = idx >> lcnt;
+  const int sstride = 1 << (lq + lp);      // float4 stride between the R inputs
+  const int dstride = Ns << lp;            // float4 stride between the R outputs
+  for (int idx = threadIdx.x; idx < total; idx += kThreads) {
+    const int fp = idx & ((1 << lp) - 1), j = idx >> lp;
     const int k = j & (Ns - 1);
-    float2 v[R];
+    float2 va[R], vb[R];
+    const float4* sp = s4 + ((j << lp) + fp);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[((j + (r << lq)) << lcnt) + f];
+    for (int r = 0; r < R; ++r) {
+      const float4 t = sp[r * sstride];
+      va[r] = make_float2(t.x, t.y);
+      vb[r] = make_float2(t.z, t.w);
+    }
     if (lNs > 0) {
+      const int e = k << shift;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        float2 w = tw[(r * k) << shift];
+        float2 w = tw[r * e];
         if (INV) w.y = -w.y;
-        v[r] = cmul(v[r], w);
+        va[r] = cmul(va[r], w);
+        vb[r] = cmul(vb[r], w);
       }
     }
-    dft_reg<INV, R>(v);
-    const int d = ((j - k) << LR) + k;
+    dft_reg<INV, R>(va);
+    dft_reg<INV, R>(vb);
+    float4* dp = d4 + (((((j - k) << LR) + k) << lp) + fp);
 #pragma unroll
-    for (int q = 0; q < R; ++q) dst[((d + (q << lNs)) << lcnt) + f] = v[q];
+    for (int q = 0; q < R; ++q) dp[q * dstride] = make_float4(va[q].x, va[q].y, vb[q].x, vb[q].y);
   }
 }
 
-// 2^lcnt interleaved transforms of size 2^logn; tw = shared table of
+// 2^lcnt (>= 2) interleaved transforms of size 2^logn; tw = shared table of
 // exp(-2 pi i e / 2^twlog), 2^twlog >= 2^logn.  Returns the result buffer.
 template <bool INV>
 __device__ float2* cta_fft_il(float2* a, float2* b, int logn, int lcnt, const float2* __restrict__ tw, int twlog) {
@@ -465,110 +411,36 @@ int run_fft(const Plan& p, const std::vector<FftLaunch>& L, const Ld& ld, const 
 // MODE 1: first order, input S1 (real), betas {phi_F, +xi}, output Phi.
 // MODE 2: second order, input Y2 (complex), all betas, output V2.
 // ---------------------------------------------------------------------------
-struct FreqArgs {
-  int N1, N_fr, logNfr, R_out, logRout, n_frames, logN, W, logW, n_beta1, n_beta2, n_ftab;
-  int64_t phi_size, phi1_off, y2_tot, v2_tot;
-  const FiltD* beta;
-  FiltD phiF;
-  const float* ftab;
-  const FreqChunk* chunks;
-  int n_chunks;
-  const int* s2;
-  const int* n1max_act;
-  const int64_t* y2_off;
-  const int64_t* v2_off;
-  const float2* tw;
-  int twlog;
-};
-
-// Shared-memory layout of the frequential kernels (all in float2 units):
-//   tw    [N_fr]                twiddles exp(-2 pi i e / N_fr)
-//   bufs  nbuf x [W * N_fr]     interleaved transforms
-//   band  [n_beta2] int2        (lo, hi) of each frequential filter
-//   chk   [n_chunks] FreqChunk
-struct FreqSmem {
-  float2* tw;
-  float2* buf;
-  const float* tab;  // global (read through L1): [n_ftab][N_fr]
-  int2* band;
-  FreqChunk* chk;
-};
-
-__device__ __forceinline__ FreqSmem freq_smem_carve(const FreqArgs& A, float2* sm, int nbuf) {
-  FreqSmem S;
-  const int WN = A.W * A.N_fr;
-  S.tw = sm;
-  S.buf = sm + A.N_fr;
-  S.tab = A.ftab;
-  S.band = reinterpret_cast<int2*>(S.buf + nbuf * WN);
-  S.chk = reinterpret_cast<FreqChunk*>(S.band + A.n_beta2);
-  return S;
-}
-
-__device__ __forceinline__ void freq_stage_tables(const FreqArgs& A, const FreqSmem& S) {
-  const int sh = A.twlog - A.logNfr;
-  for (int i = threadIdx.x; i < A.N_fr; i += blockDim.x) S.tw[i] = __ldg(A.tw + (i << sh));
-  for (int i = threadIdx.x; i < A.n_beta2; i += blockDim.x) S.band[i] = make_int2(A.beta[i].lo, A.beta[i].hi);
-  const int* csrc = reinterpret_cast<const int*>(A.chunks);
-  int* cdst = reinterpret_cast<int*>(S.chk);
-  for (int i = threadIdx.x; i < A.n_chunks * static_cast<int>(sizeof(FreqChunk) / sizeof(int)); i += blockDim.x)
-    cdst[i] = csrc[i];
-}
-
-// Columns of the tile into interleaved layout dst[r * W + w], zero-padded to N_fr rows.
-template <int MODE>
-__device__ __forceinline__ void freq_load_columns(const FreqArgs& A, const Tile& tl, const float* S1,
-                                                  const float2* Y2, float2* dst, int& stride, int& n1m) {
-  const float2* ysrc = nullptr;
-  const float* ssrc = nullptr;
-  if (MODE == 1) {
-    n1m = A.N1;
-    stride = A.n_frames;
-    ssrc = S1 + static_cast<int64_t>(tl.b) * A.N1 * A.n_frames + tl.t0;
-  } else {
-    n1m = A.n1max_act[tl.a];
-    stride = 1 << (A.logN - A.s2[tl.a]);
-    ysrc = Y2 + static_cast<int64_t>(tl.b) * A.y2_tot + A.y2_off[tl.a] + tl.t0;
-  }
-  for (int i = threadIdx.x; i < A.W * A.N_fr; i += blockDim.x) {
-    const int w = i & (A.W - 1), r = i >> A.logW;
-    float2 v = make_float2(0.f, 0.f);
-    if (r < n1m && w < tl.ncols) {
-      if (MODE == 1) v = make_float2(ssrc[static_cast<int64_t>(r) * stride + w], 0.f);
-      else v = ysrc[static_cast<int64_t>(r) * stride + w];
-    }
-    dst[i] = v;
-  }
-}
-
-__device__ __forceinline__ int ceil_log2(int n) {
-  int l = 0;
-  while ((1 << l) < n) ++l;
-  return l;
-}
-
 // Z[m][f] = (1/N_fr) sum_{s in band, s = m mod R} yhat[s][w] psi_beta(s), transform f = bc*W + w.
+// Two adjacent transforms (same filter) per thread.
 __device__ __forceinline__ void freq_fold(const FreqArgs& A, const FreqSmem& S, const FreqChunk& ch, int lc,
                                           const float2* yh, float2* out, int lR) {
   const int R = 1 << lR, Nfr = A.N_fr;
   const float inv = 1.f / static_cast<float>(Nfr);
-  for (int i = threadIdx.x; i < (R << lc); i += blockDim.x) {
-    const int f = i & ((1 << lc) - 1), m = i >> lc;
-    const int bc = f >> A.logW, w = f & (A.W - 1);
+  const int lp = lc - 1;
+  const float4* y4 = reinterpret_cast<const float4*>(yh);
+  float4* o4 = reinterpret_cast<float4*>(out);
+  const int lWp = A.logW - 1;
+  for (int i = threadIdx.x; i < (R << lp); i += kThreads) {
+    const int fp = i & ((1 << lp) - 1), m = i >> lp;
+    const int bc = fp >> lWp, wp = fp & ((1 << lWp) - 1);
     const int b = bc < ch.n ? ch.beta[bc] : -1;
-    float2 acc = make_float2(0.f, 0.f);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (b >= 0) {
       const int2 bd = S.band[b];
       const float* t = S.tab + b * Nfr;
+      const float4* yc = y4 + wp;
       for (int sb = bd.x + ((m - bd.x) & (R - 1)); sb <= bd.y; sb += R) {
         const int q = sb & (Nfr - 1);
-        const float g = t[q];
-        const float2 y = yh[(q << A.logW) + w];
+        const float g = __ldg(t + q);
+        const float4 y = yc[q << lWp];
         acc.x += g * y.x;
         acc.y += g * y.y;
+        acc.z += g * y.z;
+        acc.w += g * y.w;
       }
     }
-    out[i] = cscale(acc, inv);
+    o4[i] = make_float4(acc.x * inv, acc.y * inv, acc.z * inv, acc.w * inv);
   }
 }
 
@@ -578,16 +450,21 @@ __device__ __forceinline__ void freq_pool_fold(const FreqArgs& A, const FreqSmem
   const int R = 1 << lR, Nfr = A.N_fr, Ro = A.R_out;
   const float* t = S.tab + A.n_beta2 * Nfr;
   const float inv = 1.f / static_cast<float>(R);
-  for (int i = threadIdx.x; i < (Ro << lc); i += blockDim.x) {
-    const int f = i & ((1 << lc) - 1), m = i >> lc;
-    float2 acc = make_float2(0.f, 0.f);
+  const int lp = lc - 1;
+  const float4* u4 = reinterpret_cast<const float4*>(uh);
+  float4* o4 = reinterpret_cast<float4*>(out);
+  for (int i = threadIdx.x; i < (Ro << lp); i += kThreads) {
+    const int fp = i & ((1 << lp) - 1), m = i >> lp;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int sb = A.phiF.lo + ((m - A.phiF.lo) & (Ro - 1)); sb <= A.phiF.hi; sb += Ro) {
-      const float g = t[sb & (Nfr - 1)];
-      const float2 v = uh[((sb & (R - 1)) << lc) + f];
+      const float g = __ldg(t + (sb & (Nfr - 1)));
+      const float4 v = u4[((sb & (R - 1)) << lp) + fp];
       acc.x += g * v.x;
       acc.y += g * v.y;
+      acc.z += g * v.z;
+      acc.w += g * v.w;
     }
-    out[i] = cscale(acc, inv);
+    o4[i] = make_float4(acc.x * inv, acc.y * inv, acc.z * inv, acc.w * inv);
   }
 }
 
@@ -617,9 +494,12 @@ k_freq_fwd(FreqArgs A, const Tile* __restrict__ tiles, const float* __restrict__
     freq_fold(A, S, ch, lc, yh, f1, lR);
     __syncthreads();
     float2* z = cta_fft_il<true>(f1, f2, lR, lc, S.tw, A.logNfr);
-    for (int i = threadIdx.x; i < (1 << (lR + lc)); i += blockDim.x) {
-      const float2 v = z[i];
-      z[i] = make_float2(sqrtf(v.x * v.x + v.y * v.y), 0.f);
+    {
+      float4* z4 = reinterpret_cast<float4*>(z);
+      for (int i = threadIdx.x; i < (1 << (lR + lc - 1)); i += kThreads) {
+        const float4 v = z4[i];
+        z4[i] = make_float4(sqrtf(v.x * v.x + v.y * v.y), 0.f, sqrtf(v.z * v.z + v.w * v.w), 0.f);
+      }
     }
     __syncthreads();
     float2* zo = (z == f1) ? f2 : f1;
@@ -703,14 +583,21 @@ k_freq_adj(FreqArgs A, const Tile* __restrict__ tiles, const float* S1, const fl
     float2* X = (dW == dwb) ? z : dwb;
     // du_hat[m] = (1/R) phi_F level_k(m) dW[m mod R_out]   (adjoint of the pooling fold)
     const float* lev = S.tab + (A.n_beta2 + 1 + ch.k) * Nfr;
-    for (int i = threadIdx.x; i < (R << lc); i += blockDim.x) {
-      const int f = i & (cnt - 1), m = i >> lc;
-      X[i] = cscale(dW[((m & (Ro - 1)) << lc) + f], lev[m] * invR);
+    {
+      const int lp = lc - 1;
+      const float4* dW4 = reinterpret_cast<const float4*>(dW);
+      float4* X4 = reinterpret_cast<float4*>(X);
+      for (int i = threadIdx.x; i < (R << lp); i += kThreads) {
+        const int fp = i & ((1 << lp) - 1), m = i >> lp;
+        const float sc = __ldg(lev + m) * invR;
+        const float4 v = dW4[((m & (Ro - 1)) << lp) + fp];
+        X4[i] = make_float4(v.x * sc, v.y * sc, v.z * sc, v.w * sc);
+      }
     }
     __syncthreads();
     float2* du = cta_fft_il<true>(X, dW, lR, lc, S.tw, A.logNfr);
     // dz = Re(du) z / |z|  (0 where z = 0)
-    for (int i = threadIdx.x; i < (R << lc); i += blockDim.x) {
+    for (int i = threadIdx.x; i < (R << lc); i += kThreads) {
       const float gr = du[i].x;
       const float2 v = zb[i];
       const float mg = sqrtf(v.x * v.x + v.y * v.y);
@@ -720,21 +607,32 @@ k_freq_adj(FreqArgs A, const Tile* __restrict__ tiles, const float* S1, const fl
     float2* other = (du == X) ? dW : X;
     float2* dZ = cta_fft_il<false>(du, other, lR, lc, S.tw, A.logNfr);
     // D[m][w] += (1/N_fr) sum_beta psi_beta(s(m)) dZ_beta[m mod R][w]
-    for (int i = threadIdx.x; i < WN; i += blockDim.x) {
-      const int w = i & (W - 1), m = i >> A.logW;
-      const int sgn = m < (Nfr >> 1) ? m : m - Nfr;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int bc = 0; bc < ch.n; ++bc) {
-        const int b = ch.beta[bc];
-        const int2 bd = S.band[b];
-        if (sgn < bd.x || sgn > bd.y) continue;
-        const float gg = S.tab[b * Nfr + m];
-        const float2 v = dZ[((m & (R - 1)) << lc) + (bc << A.logW) + w];
-        acc.x += gg * v.x;
-        acc.y += gg * v.y;
+    {
+      const int lWp = A.logW - 1, lp = lc - 1;
+      const float4* dZ4 = reinterpret_cast<const float4*>(dZ);
+      float4* D4 = reinterpret_cast<float4*>(D);
+      for (int i = threadIdx.x; i < (WN >> 1); i += kThreads) {
+        const int wp = i & ((1 << lWp) - 1), m = i >> lWp;
+        const int sgn = m < (Nfr >> 1) ? m : m - Nfr;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int bc = 0; bc < ch.n; ++bc) {
+          const int b = ch.beta[bc];
+          const int2 bd = S.band[b];
+          if (sgn < bd.x || sgn > bd.y) continue;
+          const float gg = __ldg(S.tab + b * Nfr + m);
+          const float4 v = dZ4[((m & (R - 1)) << lp) + (bc << lWp) + wp];
+          acc.x += gg * v.x;
+          acc.y += gg * v.y;
+          acc.z += gg * v.z;
+          acc.w += gg * v.w;
+        }
+        float4 d = D4[i];
+        d.x += acc.x * invNfr;
+        d.y += acc.y * invNfr;
+        d.z += acc.z * invNfr;
+        d.w += acc.w * invNfr;
+        D4[i] = d;
       }
-      D[i].x += acc.x * invNfr;
-      D[i].y += acc.y * invNfr;
     }
     __syncthreads();
   }
@@ -1199,9 +1097,12 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
   const FreqArgs FA = freq_args(p, 1);
   const FreqArgs FA2 = freq_args(p, 2);
   if (full) {
-    allow_big_smem<k_freq_fwd<1>>();
-    k_freq_fwd<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 3), s>>>(
-        FA, p.d_tiles1, w.S1, nullptr, phi);
+    if (!launch_freq_fwd_ct(1, FA, p.lF, static_cast<unsigned>(p.tiles1.size()), freq_smem(p, 3), s, p.d_tiles1,
+                            w.S1, nullptr, phi)) {
+      allow_big_smem<k_freq_fwd<1>>();
+      k_freq_fwd<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 3), s>>>(
+          FA, p.d_tiles1, w.S1, nullptr, phi);
+    }
     JTFS_TRY(check_launch());
   }
   if (p.n_active > 0) {
@@ -1209,8 +1110,10 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
     if (full) {
       allow_big_smem<k_freq_fwd<2>>();
       prof_begin(p, JTFS_STAGE_FREQ2_FWD, s);
-      k_freq_fwd<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 3), s>>>(
-          FA2, p.d_tiles2, nullptr, w.Y2, w.V2);
+      if (!launch_freq_fwd_ct(2, FA2, p.lF, static_cast<unsigned>(p.tiles2.size()), freq_smem(p, 3), s,
+                              p.d_tiles2, nullptr, w.Y2, w.V2))
+        k_freq_fwd<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 3), s>>>(
+            FA2, p.d_tiles2, nullptr, w.Y2, w.V2);
       prof_end(p, JTFS_STAGE_FREQ2_FWD, s);
       JTFS_TRY(check_launch());
       const PoolArgs PA = pool_args(p);
@@ -1252,14 +1155,18 @@ int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, 
     JTFS_TRY(check_launch());
     allow_big_smem<k_freq_adj<2>>();
     prof_begin(p, JTFS_STAGE_FREQ2_ADJ, s);
-    k_freq_adj<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 5), s>>>(
-        FA2, p.d_tiles2, nullptr, w.Y2, w.V2, nullptr, w.dY2);
+    if (!launch_freq_adj_ct(2, FA2, p.lF, static_cast<unsigned>(p.tiles2.size()), freq_smem(p, 5), s, p.d_tiles2,
+                            nullptr, w.Y2, w.V2, nullptr, w.dY2))
+      k_freq_adj<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 5), s>>>(
+          FA2, p.d_tiles2, nullptr, w.Y2, w.V2, nullptr, w.dY2);
     prof_end(p, JTFS_STAGE_FREQ2_ADJ, s);
     JTFS_TRY(check_launch());
   }
   allow_big_smem<k_freq_adj<1>>();
-  k_freq_adj<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 5), s>>>(
-      FA, p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr);
+  if (!launch_freq_adj_ct(1, FA, p.lF, static_cast<unsigned>(p.tiles1.size()), freq_smem(p, 5), s, p.d_tiles1, w.S1,
+                          nullptr, dphi, w.S1, nullptr))
+    k_freq_adj<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 5), s>>>(
+        FA, p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr);
   JTFS_TRY(check_launch());
   if (p.n_active > 0) JTFS_TRY((run_fft<false>(p, p.L_y2inplace, LdC{w.dY2}, StC{w.dY2}, w.scr, s)));
   JTFS_TRY((run_fft<false>(p, p.L_ds1, LdReal{w.S1}, StC{w.dS1h}, w.scr, s)));

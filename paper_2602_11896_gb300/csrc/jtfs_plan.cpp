@@ -286,7 +286,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   }
 
   // Frequential tiles.
-  p.freq_cols = std::max(1, std::min(kFreqCols, 2048 / p.N_fr));
+  p.freq_cols = std::max(2, std::min(kFreqCols, 2048 / p.N_fr));  // >= 2: kernels pair columns
   p.tiles1.clear();
   p.tiles2.clear();
   for (int b = 0; b < B; ++b)
