@@ -44,6 +44,8 @@ extern "C" {
 #define JTFS_ERR_CUDA      -4  /* a CUDA runtime call failed                */
 #define JTFS_ERR_NOMEM     -5  /* host or device allocation failed          */
 #define JTFS_ERR_NODEVICE  -6  /* plan was created host-only                */
+#define JTFS_ERR_TOOBIG    -7  /* plan needs more scratch than the fixed
+                                  array of jtfs_forward_noalloc holds       */
 
 /* Plan flags. */
 #define JTFS_PLAN_HOST_ONLY 1u /* build the tables on the host only; compute
@@ -165,6 +167,37 @@ int jtfs_loss_grad(jtfs_plan_t plan, const float* y, const float* phi_target,
 int metamer_step(jtfs_plan_t plan, float* y, const float* phi_target,
                  float* adam_m, float* adam_v, int step, float lr,
                  float* loss_out, void* workspace, void* stream);
+
+/*
+ * jtfs_forward_noalloc -- the forward transform of jtfs_forward, for callers
+ * that cannot allocate device memory: code that runs where cudaMalloc is not
+ * allowed or not available to it (for example a real-time audio callback
+ * that must not block on the allocator, or a plug-in whose host owns all
+ * device memory and hands it only a stream).  It takes no workspace and
+ * allocates nothing; it is an addition of this library, with no counterpart
+ * in the paper.
+ *
+ * Scratch: a fixed array of JTFS_NOALLOC_SCRATCH_BYTES (32 MiB) compiled into
+ * the library, so every GPU that loads the library holds those 32 MiB until
+ * the process exits.  Plans whose jtfs_workspace_bytes() exceed it are
+ * rejected with JTFS_ERR_TOOBIG before any work is enqueued (the 8192-sample
+ * single-clip plan needs about 10 MiB).
+ *   x   [batch][N] float32 (device), phi [batch][phi_size] float32 (device),
+ *   as for jtfs_forward; results are identical to jtfs_forward's.
+ * Set-up: the first call on each device looks up the array's device address
+ * (a runtime query, no allocation); make that first call before starting any
+ * stream capture.  The device that was current when the plan was created must
+ * be current.
+ * Sharing: all calls on a device use the same array and leave their data in
+ * it.  The forward pass writes every scratch byte before reading it, so no
+ * clearing is needed, but calls that can overlap on the GPU (different
+ * streams, different threads) race on the array and corrupt each other's
+ * results; serialise them.
+ * Errors: JTFS_ERR_ARG, JTFS_ERR_NODEVICE, JTFS_ERR_TOOBIG, JTFS_ERR_CUDA.
+ */
+#define JTFS_NOALLOC_SCRATCH_BYTES (32u << 20)
+int jtfs_forward_noalloc(jtfs_plan_t plan, const float* x, float* phi,
+                         void* stream);
 
 /*
  * Measurement hooks (host-side bookkeeping; not thread-safe).

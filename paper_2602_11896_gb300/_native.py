@@ -23,6 +23,7 @@ SIGNATURES = {
     "jtfs_plan_filters": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_double),
                                   POINTER(c_int32), c_int]),
     "jtfs_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "jtfs_forward_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "jtfs_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "jtfs_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                c_void_p]),

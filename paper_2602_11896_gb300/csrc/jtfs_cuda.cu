@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "jtfs.h"
 #include "jtfs_device.cuh"
@@ -1208,6 +1209,52 @@ extern "C" int jtfs_forward(jtfs_plan_t plan, const float* x, float* phi, void* 
   const jtfs::Plan& p = plan->p;
   JTFS_TRY(jtfs::check_call(p, workspace));
   const Bufs w = jtfs::bufs(p, workspace);
+  return jtfs::forward_stages(p, x, phi, w, true, static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------
+// No-allocation forward: scratch in a fixed array of the library image.
+// ---------------------------------------------------------------------------
+namespace jtfs {
+namespace {
+
+// File-scope device array used as the workspace of jtfs_forward_noalloc.  In
+// host code `g_noalloc_scratch` names a host-side stand-in, never a device
+// address: the device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[JTFS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::once_flag g_scratch_once[kMaxDevices];
+void* g_scratch_ptr[kMaxDevices] = {};
+cudaError_t g_scratch_err[kMaxDevices] = {};
+
+// Device address of the array on the current device (looked up once per device).
+int noalloc_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return JTFS_ERR_ARG;
+  std::call_once(g_scratch_once[dev], [dev] {
+    void* ptr = nullptr;
+    g_scratch_err[dev] = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (g_scratch_err[dev] == cudaSuccess) g_scratch_ptr[dev] = ptr;
+    else cudaGetLastError();
+  });
+  if (g_scratch_err[dev] != cudaSuccess || !g_scratch_ptr[dev]) return JTFS_ERR_CUDA;
+  *out = g_scratch_ptr[dev];
+  return JTFS_OK;
+}
+
+}  // namespace
+}  // namespace jtfs
+
+extern "C" int jtfs_forward_noalloc(jtfs_plan_t plan, const float* x, float* phi, void* stream) {
+  if (!plan || !x || !phi || jtfs::misaligned(x) || jtfs::misaligned(phi)) return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  if (!p.on_device) return JTFS_ERR_NODEVICE;
+  if (p.ws_bytes > JTFS_NOALLOC_SCRATCH_BYTES) return JTFS_ERR_TOOBIG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != p.device) return JTFS_ERR_ARG;
+  void* scratch = nullptr;
+  JTFS_TRY(jtfs::noalloc_scratch(dev, &scratch));
+  const Bufs w = jtfs::bufs(p, scratch);
   return jtfs::forward_stages(p, x, phi, w, true, static_cast<cudaStream_t>(stream));
 }
 

@@ -578,6 +578,7 @@ extern "C" const char* jtfs_error_string(int code) {
     case JTFS_ERR_CUDA: return "CUDA runtime error";
     case JTFS_ERR_NOMEM: return "allocation failed";
     case JTFS_ERR_NODEVICE: return "plan has no device tables (host-only)";
+    case JTFS_ERR_TOOBIG: return "plan needs more scratch than the fixed 32 MiB array of jtfs_forward_noalloc";
     default: return "unknown error";
   }
 }

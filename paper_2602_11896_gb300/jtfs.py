@@ -101,6 +101,19 @@ class JTFSPlan:
         _native.check(self._lib.jtfs_forward(self._h, _ptr(x), _ptr(phi), _ptr(ws), _stream()), "jtfs_forward")
         return phi
 
+    def forward_noalloc(self, x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Forward transform without a workspace (fixed 32 MiB library scratch).
+
+        For callers that cannot allocate device memory; see
+        jtfs_forward_noalloc in include/jtfs.h for the limits and the
+        sharing rule (calls overlapping on the GPU race on the scratch).
+        """
+        self._check(x, self.N, "x")
+        phi = out if out is not None else torch.empty(self.batch, self.phi_size, device=x.device)
+        _native.check(self._lib.jtfs_forward_noalloc(self._h, _ptr(x), _ptr(phi), _stream()),
+                      "jtfs_forward_noalloc")
+        return phi
+
     def backward(self, x: torch.Tensor, dphi: torch.Tensor, out: Optional[torch.Tensor] = None,
                  workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
         self._check(x, self.N, "x")
