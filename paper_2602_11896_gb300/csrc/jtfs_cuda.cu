@@ -1081,8 +1081,9 @@ int64_t backward_launches(const Plan& p) {
   return n;
 }
 
-size_t freq_smem(const Plan& p, int nbuf) {
-  return size_t(p.N_fr) * sizeof(float2) + size_t(nbuf) * p.freq_cols * p.N_fr * sizeof(float2) +
+size_t freq_smem(const Plan& p, int nbuf, int cols = 0) {
+  if (cols == 0) cols = p.freq_cols;
+  return size_t(p.N_fr) * sizeof(float2) + size_t(nbuf) * cols * p.N_fr * sizeof(float2) +
          size_t(p.n_beta2) * sizeof(int2) +
          std::max(p.chunks1.size(), p.chunks2.size()) * sizeof(FreqChunk);
 }
@@ -1111,7 +1112,12 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
     if (full) {
       allow_big_smem<k_freq_fwd<2>>();
       prof_begin(p, JTFS_STAGE_FREQ2_FWD, s);
-      if (!launch_freq_fwd_ct(2, FA2, p.lF, static_cast<unsigned>(p.tiles2.size()), freq_smem(p, 3), s,
+      FreqArgs FA2w = FA2;
+      FA2w.W = p.freq_cols_wide;
+      FA2w.logW = ceil_log2(p.freq_cols_wide);
+      if (!launch_freq_fwd_ct(2, FA2w, p.lF, static_cast<unsigned>(p.tiles2w.size()),
+                              freq_smem(p, 3, p.freq_cols_wide), s, p.d_tiles2w, nullptr, w.Y2, w.V2) &&
+          !launch_freq_fwd_ct(2, FA2, p.lF, static_cast<unsigned>(p.tiles2.size()), freq_smem(p, 3), s,
                               p.d_tiles2, nullptr, w.Y2, w.V2))
         k_freq_fwd<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 3), s>>>(
             FA2, p.d_tiles2, nullptr, w.Y2, w.V2);

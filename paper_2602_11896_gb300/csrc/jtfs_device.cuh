@@ -164,7 +164,7 @@ __device__ __forceinline__ void freq_load_columns(const FreqArgs& A, const Tile&
   }
 }
 
-__device__ __forceinline__ int ceil_log2(int n) {
+__host__ __device__ __forceinline__ int ceil_log2(int n) {
   int l = 0;
   while ((1 << l) < n) ++l;
   return l;

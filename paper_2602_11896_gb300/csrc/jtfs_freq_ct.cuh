@@ -23,52 +23,86 @@ __host__ __device__ constexpr int radix_log(int rem) {
   return (rem == 3 || rem == 5 || rem == 6 || rem == 9) ? 3 : (rem >= 4 ? 4 : rem);
 }
 
-// One radix pass over 2^LCNT interleaved transforms of size 2^LOGN, two
-// adjacent transforms per thread; twiddle table of 2^LOGTW entries.
+// One radix pass over 2^LCNT interleaved transforms of size 2^LOGN; twiddle
+// table of 2^LOGTW entries.  When the pass has at least one pair of adjacent
+// transforms per thread, each thread takes two (16-byte accesses, shared
+// index arithmetic and twiddles); otherwise one, to keep more threads busy.
 template <bool INV, int LOGN, int LCNT, int LNS, int LOGTW>
 __device__ __forceinline__ void ct_pass(const float2* __restrict__ src, float2* __restrict__ dst,
                                         const float2* __restrict__ tw) {
   constexpr int LR = radix_log(LOGN - LNS);
   constexpr int R = 1 << LR;
   constexpr int LQ = LOGN - LR;
-  constexpr int LP = LCNT - 1;
-  constexpr int TOTAL = 1 << (LQ + LP);
   constexpr int NS = 1 << LNS;
   constexpr int SHIFT = LOGTW - (LNS + LR);
-  constexpr int SSTRIDE = 1 << (LQ + LP);
-  constexpr int DSTRIDE = NS << LP;
-  constexpr int ITERS = (TOTAL + kThreads - 1) / kThreads;
-  const float4* s4 = reinterpret_cast<const float4*>(src);
-  float4* d4 = reinterpret_cast<float4*>(dst);
+  constexpr bool PAIR = (1 << (LQ + LCNT - 1)) >= kThreads;
+  if constexpr (PAIR) {
+    constexpr int LP = LCNT - 1;
+    constexpr int TOTAL = 1 << (LQ + LP);
+    constexpr int SSTRIDE = 1 << (LQ + LP);
+    constexpr int DSTRIDE = NS << LP;
+    constexpr int ITERS = (TOTAL + kThreads - 1) / kThreads;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll 1
-  for (int it = 0; it < ITERS; ++it) {
-    const int idx = static_cast<int>(threadIdx.x) + it * kThreads;
-    if ((TOTAL % kThreads) != 0 && idx >= TOTAL) break;
-    const int fp = idx & ((1 << LP) - 1), j = idx >> LP;
-    const int k = j & (NS - 1);
-    float2 va[R], vb[R];
-    const float4* sp = s4 + ((j << LP) + fp);
+    for (int it = 0; it < ITERS; ++it) {
+      const int idx = static_cast<int>(threadIdx.x) + it * kThreads;
+      if ((TOTAL % kThreads) != 0 && idx >= TOTAL) break;
+      const int fp = idx & ((1 << LP) - 1), j = idx >> LP;
+      const int k = j & (NS - 1);
+      float2 va[R], vb[R];
+      const float4* sp = s4 + ((j << LP) + fp);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const float4 t = sp[r * SSTRIDE];
-      va[r] = make_float2(t.x, t.y);
-      vb[r] = make_float2(t.z, t.w);
-    }
-    if constexpr (LNS > 0) {
-      const int e = k << SHIFT;
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 w = tw[r * e];
-        if (INV) w.y = -w.y;
-        va[r] = cmul(va[r], w);
-        vb[r] = cmul(vb[r], w);
+      for (int r = 0; r < R; ++r) {
+        const float4 t = sp[r * SSTRIDE];
+        va[r] = make_float2(t.x, t.y);
+        vb[r] = make_float2(t.z, t.w);
       }
-    }
-    dft_reg<INV, R>(va);
-    dft_reg<INV, R>(vb);
-    float4* dp = d4 + (((((j - k) << LR) + k) << LP) + fp);
+      if constexpr (LNS > 0) {
+        const int e = k << SHIFT;
 #pragma unroll
-    for (int q = 0; q < R; ++q) dp[q * DSTRIDE] = make_float4(va[q].x, va[q].y, vb[q].x, vb[q].y);
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[r * e];
+          if (INV) w.y = -w.y;
+          va[r] = cmul(va[r], w);
+          vb[r] = cmul(vb[r], w);
+        }
+      }
+      dft_reg<INV, R>(va);
+      dft_reg<INV, R>(vb);
+      float4* dp = d4 + (((((j - k) << LR) + k) << LP) + fp);
+#pragma unroll
+      for (int q = 0; q < R; ++q) dp[q * DSTRIDE] = make_float4(va[q].x, va[q].y, vb[q].x, vb[q].y);
+    }
+  } else {
+    constexpr int TOTAL = 1 << (LQ + LCNT);
+    constexpr int SSTRIDE = 1 << (LQ + LCNT);
+    constexpr int DSTRIDE = NS << LCNT;
+    constexpr int ITERS = (TOTAL + kThreads - 1) / kThreads;
+#pragma unroll 1
+    for (int it = 0; it < ITERS; ++it) {
+      const int idx = static_cast<int>(threadIdx.x) + it * kThreads;
+      if ((TOTAL % kThreads) != 0 && idx >= TOTAL) break;
+      const int f = idx & ((1 << LCNT) - 1), j = idx >> LCNT;
+      const int k = j & (NS - 1);
+      float2 v[R];
+      const float2* sp = src + ((j << LCNT) + f);
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = sp[r * SSTRIDE];
+      if constexpr (LNS > 0) {
+        const int e = k << SHIFT;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[r * e];
+          if (INV) w.y = -w.y;
+          v[r] = cmul(v[r], w);
+        }
+      }
+      dft_reg<INV, R>(v);
+      float2* dp = dst + (((((j - k) << LR) + k) << LCNT) + f);
+#pragma unroll
+      for (int q = 0; q < R; ++q) dp[q * DSTRIDE] = v[q];
+    }
   }
 }
 
@@ -411,11 +445,10 @@ void opt_in_smem() {
   (void)once;
 }
 
-// Specialised shapes: (log2 N_fr, log2 W, log2 F) of the workloads this
-// library is tuned for (second-order kernels only; the first-order ones
-// process N/T columns per clip and use the generic kernels).
-#define JTFS_CT_SHAPES(X) \
-  X(8, 3, 3)
+// Specialised shapes, (log2 N_fr, log2 W, log2 F), are listed in the two
+// launchers (jtfs_freq_ct_fwd.cu, jtfs_freq_ct_adj.cu): second-order kernels
+// only; the first-order ones process N/T columns per clip and use the generic
+// kernels.
 
 }  // namespace
 }  // namespace jtfs

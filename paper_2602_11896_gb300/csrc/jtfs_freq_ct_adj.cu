@@ -15,7 +15,7 @@ bool launch_freq_adj_ct(int mode, const FreqArgs& A, int lF, unsigned grid, size
     k_freq_adj_ct<2, LN, LW, LFv><<<grid, kThreads, smem, s>>>(A, tiles, S1, Y2, dout, dS1, dY2);     \
     return true;                                                                                     \
   }
-  JTFS_CT_SHAPES(JTFS_CT_ADJ)
+  JTFS_CT_ADJ(8, 3, 3)
 #undef JTFS_CT_ADJ
   return false;
 }

@@ -14,7 +14,7 @@ bool launch_freq_fwd_ct(int mode, const FreqArgs& A, int lF, unsigned grid, size
     k_freq_fwd_ct<2, LN, LW, LFv><<<grid, kThreads, smem, s>>>(A, tiles, S1, Y2, out);          \
     return true;                                                                               \
   }
-  JTFS_CT_SHAPES(JTFS_CT_FWD)
+  JTFS_CT_FWD(8, 4, 3)
 #undef JTFS_CT_FWD
   return false;
 }

@@ -137,6 +137,8 @@ struct Plan {
   std::vector<FftLaunch> L_ds0;      // B7a: FFT of dS0
   std::vector<Tile> tiles1, tiles2;
   int freq_cols = kFreqCols;
+  std::vector<Tile> tiles2w;  // second order, twice the columns (forward kernel)
+  int freq_cols_wide = kFreqCols;
   std::vector<FreqChunk> chunks1, chunks2;
   std::vector<int4> pool_tiles;  // adjoint time pooling: (clip, active n2, row tile, time tile)
   std::vector<int4> pool_fwd_tiles;  // forward time pooling: (clip, active n2, row tile, split)
@@ -165,6 +167,7 @@ struct Plan {
   const Job* d_jobs = nullptr;
   const Tile* d_tiles1 = nullptr;
   const Tile* d_tiles2 = nullptr;
+  const Tile* d_tiles2w = nullptr;
   const FreqChunk* d_chunks1 = nullptr;
   const FreqChunk* d_chunks2 = nullptr;
   const float* d_ftab = nullptr;

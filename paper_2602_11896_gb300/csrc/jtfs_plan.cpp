@@ -292,11 +292,15 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   for (int b = 0; b < B; ++b)
     for (int t0 = 0; t0 < p.n_frames; t0 += p.freq_cols)
       p.tiles1.push_back({b, -1, t0, std::min(p.freq_cols, p.n_frames - t0)});
+  p.freq_cols_wide = std::min(kFreqCols, 2 * p.freq_cols);
+  p.tiles2w.clear();
   for (int b = 0; b < B; ++b)
     for (int a = 0; a < p.n_active; ++a) {
       const int L2 = static_cast<int>(N >> p.s2[a]);
       for (int t0 = 0; t0 < L2; t0 += p.freq_cols)
         p.tiles2.push_back({b, a, t0, std::min(p.freq_cols, L2 - t0)});
+      for (int t0 = 0; t0 < L2; t0 += p.freq_cols_wide)
+        p.tiles2w.push_back({b, a, t0, std::min(p.freq_cols_wide, L2 - t0)});
     }
 
   // Frequential tables (double precision on the host, stored as float).
@@ -428,6 +432,7 @@ int upload_plan(Plan& p) {
   const size_t o_jobs = put(p.jobs.data(), p.jobs.size() * sizeof(Job));
   const size_t o_t1 = put(p.tiles1.data(), p.tiles1.size() * sizeof(Tile));
   const size_t o_t2 = put(p.tiles2.data(), p.tiles2.size() * sizeof(Tile));
+  const size_t o_t2w = put(p.tiles2w.data(), p.tiles2w.size() * sizeof(Tile));
   const size_t o_c1 = put(p.chunks1.data(), p.chunks1.size() * sizeof(FreqChunk));
   const size_t o_c2 = put(p.chunks2.data(), p.chunks2.size() * sizeof(FreqChunk));
   const size_t o_ftab = put(p.h_ftab.data(), p.h_ftab.size() * sizeof(float));
@@ -464,6 +469,7 @@ int upload_plan(Plan& p) {
   p.d_jobs = reinterpret_cast<const Job*>(at(o_jobs));
   p.d_tiles1 = reinterpret_cast<const Tile*>(at(o_t1));
   p.d_tiles2 = reinterpret_cast<const Tile*>(at(o_t2));
+  p.d_tiles2w = reinterpret_cast<const Tile*>(at(o_t2w));
   p.d_chunks1 = reinterpret_cast<const FreqChunk*>(at(o_c1));
   p.d_chunks2 = reinterpret_cast<const FreqChunk*>(at(o_c2));
   p.d_ftab = reinterpret_cast<const float*>(at(o_ftab));
