@@ -38,6 +38,10 @@ UNIT = "audio-samples/s"
 L2_FLUSH_BYTES = 256 << 20
 # FP32 ALU peak of a GB300 from unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per clip of one launch of the second-order frequential kernels, from an
+# ncu capture of the 1-clip case of this workload (traffic scales with the clips processed).  Valid for
+# the kernel versions it was taken on; set to None when those kernels change.
+DRAM_BYTES_PER_CLIP = {0: 13.3696e6 + 137.13792e6, 1: 206.394112e6 + 8.64768e6}
 
 
 def parse():
@@ -47,6 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="clips per GPU (default: the workload's 8); smaller values only for ncu captures")
     return ap.parse_args()
 
 
@@ -213,11 +219,15 @@ def main():
         return
 
     from paper_2602_11896_gb300 import JTFSPlan, _native
+    if args.batch:
+        import dataclasses
+        wl = dataclasses.replace(wl, batch=args.batch, target_seeds=wl.target_seeds[:args.batch],
+                                 init_seeds=wl.init_seeds[:args.batch])
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     plan = JTFSPlan(**wl.params, batch=wl.batch)
     seed_off = 1000 * rank
-    targets = np.stack([get_workload(WORKLOAD).targets()[b] for b in range(wl.batch)]) if rank == 0 else None
+    targets = wl.targets() if rank == 0 else None
     if rank != 0:
         from workloads import signals
         targets = np.stack([signals.chirp_am_mix(wl.N, wl.sr, s + seed_off) for s in wl.target_seeds])
@@ -286,9 +296,9 @@ def main():
     for st, (evs, _) in stage_events.items():
         d = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(K)]
         stage_ms[st] = float(np.mean(d))
-    names = {0: "k_freq_fwd<2> (second-order frequential scattering + modulus + phi_F)",
-             1: "k_freq_adj<2> (adjoint of the second-order frequential scattering)",
-             2: "k_pool_fwd (phi_T averaging FIR)", 3: "k_pool_adj (adjoint phi_T FIR)"}
+    names = {0: "k_freq_fwd_ct<2,8,4,3> (second-order frequential scattering + modulus + phi_F)",
+             1: "k_freq_adj_ct<2,8,3,3> (adjoint of the second-order frequential scattering)",
+             2: "k_pool_fwd + k_pool_reduce (phi_T averaging)", 3: "k_pool_adj (adjoint of phi_T averaging)"}
     dom = max(stage_ms, key=stage_ms.get)
     cols = columns_per_launch(plan)
     flops = None
@@ -300,8 +310,13 @@ def main():
     roofline = None
     if flops is not None:
         ach = flops / (stage_ms[dom] / 1e3) / 1e12
+        per_clip = DRAM_BYTES_PER_CLIP.get(dom)
         roofline = {"bound": "alu", "kernel": names[dom], "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                    "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                    "traffic": per_clip * wl.batch if per_clip is not None else None,
+                    "traffic_note": "ncu dram bytes of the 1-clip capture x clips per launch",
+                    "hbm_gbs_at_traffic": (per_clip * wl.batch / (stage_ms[dom] / 1e3) / 1e9
+                                           if per_clip is not None else None),
                     "flops_per_launch": flops, "launch_ms": stage_ms[dom],
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (no measured FP32 peak)",
                     "stage_ms": {names[s].split(" ")[0]: round(t, 4) for s, t in stage_ms.items()},
