@@ -200,6 +200,51 @@ int jtfs_forward_noalloc(jtfs_plan_t plan, const float* x, float* phi,
                          void* stream);
 
 /*
+ * Ragged batches: clips of any lengths solved together.
+ *
+ * A clip of length L is zero-padded on the right to N = the next power of
+ * two >= max(L, T) (the padding of §3.2 with the periodic boundary), its Phi
+ * is computed at that N and only the first ceil(L/T) frames of every row are
+ * kept (the crop's adjoint fills zeros).  Clips are grouped by N; each group
+ * runs on its own plan, all on the caller's stream.
+ *
+ * Packed layouts (all device, float32):
+ *   samples: clip b occupies [sample_off[b], sample_off[b+1]), L_b samples;
+ *   Phi:     clip b occupies [phi_off[b], phi_off[b+1]) as rows x ceil(L_b/T)
+ *            frames, rows in the order of the Phi layout above (S0 is one row).
+ */
+typedef struct jtfs_batch_s* jtfs_batch_t;
+
+/* Create a ragged batch of `count` clips (1 <= count, 1 <= lengths[b] <= 2^20);
+ * other parameters as jtfs_plan.  Errors as jtfs_plan. */
+int jtfs_batch_create(jtfs_batch_t* out, const int64_t* lengths, int count, int J,
+                      int Q, int Q2, int J_fr, int Q_fr, int64_t T, int F,
+                      uint32_t flags);
+int jtfs_batch_destroy(jtfs_batch_t batch);
+
+/* Host arrays of count+1 offsets (may be NULL); returns the number of clips. */
+int jtfs_batch_layout(jtfs_batch_t batch, int64_t* sample_off, int64_t* phi_off);
+
+/* Bytes of device workspace the batch calls need (0 if batch is NULL). */
+size_t jtfs_batch_workspace_bytes(jtfs_batch_t batch);
+
+/* Phi of every clip (cropped), packed.  Errors as jtfs_forward. */
+int jtfs_batch_forward(jtfs_batch_t batch, const float* x, float* phi,
+                       void* workspace, void* stream);
+
+/*
+ * One Adam metamer step on every clip (as metamer_step), with the 1-based step
+ * index read from, and then incremented in, device memory (`step`, one int32)
+ * so that repeated calls can be recorded once and replayed.  y, adam_m, adam_v
+ * are packed samples; loss [count] receives each clip's loss at the y given on
+ * entry.  Errors as metamer_step.
+ */
+int jtfs_batch_metamer_step(jtfs_batch_t batch, float* y, const float* phi_target,
+                            float* adam_m, float* adam_v, int32_t* step,
+                            float lr, float* loss, void* workspace,
+                            void* stream);
+
+/*
  * Measurement hooks (host-side bookkeeping; not thread-safe).
  *
  * jtfs_profile_stage registers `count` CUDA events (cudaEvent_t passed as

@@ -58,6 +58,9 @@ reason in the repository's design notes):
       second order per active n2 ascending [1+2K][R_out][N/T].
   R13 E = sum over all Phi entries of (Phi(y) - Phi(x))^2; modulus
       derivative at 0 is 0 (torch's convention for |z|).
+  R15 Clips whose length L is not a power of two: zero-padded on the right
+      to the next power of two, Phi computed there, and only the first
+      ceil(L/T) frames of each row kept (the crop's adjoint fills zeros).
 """
 
 from __future__ import annotations
@@ -370,4 +373,39 @@ def loss_and_grad(y: torch.Tensor, phi_target: torch.Tensor, plan: Plan,
         phi = jtfs(y, plan, checkpoint_blocks=checkpoint_blocks)["phi"]
         E = ((phi - phi_target.to(F64)) ** 2).sum(-1)
         (g,) = torch.autograd.grad(E.sum(), y)
+    return E.detach(), g.detach()
+
+
+# ---------------------------------------------------------------------------
+# Clips of any length (reading R15): zero-pad on the right to the next power
+# of two (the padding of §3.2 with a periodic boundary), compute Phi at that
+# length, keep the first ceil(L / T) frames of every row.
+# ---------------------------------------------------------------------------
+
+def padded_length(L: int) -> int:
+    """Next power of two >= L."""
+    return _next_pow2(L)
+
+
+def jtfs_uneven(y: torch.Tensor, params: Dict[str, int]) -> torch.Tensor:
+    """Phi of one clip y [L] (any L >= 1): flat vector of rows x ceil(L/T) frames.
+
+    Every Phi block is [..., frame] with n_frames = N_pad / T frames per row;
+    the crop keeps frames [0, ceil(L/T)) of each row (S0 counts as one row).
+    """
+    L = y.shape[-1]
+    plan = Plan(N=padded_length(max(L, params["T"])), **{k: v for k, v in params.items() if k != "N"})
+    yp = torch.cat([y.reshape(1, L).to(F64), torch.zeros(1, plan.N - L, dtype=F64)], dim=1)
+    phi = jtfs(yp, plan)["phi"].reshape(-1, plan.n_frames)
+    nf = -(-L // plan.T)
+    return phi[:, :nf].reshape(-1)
+
+
+def loss_and_grad_uneven(y: torch.Tensor, phi_target: torch.Tensor,
+                         params: Dict[str, int]) -> Tuple[torch.Tensor, torch.Tensor]:
+    """E = ||Phi_cropped(y) - target||^2 and dE/dy for one clip of any length."""
+    y = y.detach().to(F64).clone().requires_grad_(True)
+    with torch.enable_grad():
+        E = ((jtfs_uneven(y, params) - phi_target.to(F64)) ** 2).sum()
+        (g,) = torch.autograd.grad(E, y)
     return E.detach(), g.detach()

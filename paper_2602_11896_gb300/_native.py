@@ -29,6 +29,14 @@ SIGNATURES = {
                                c_void_p]),
     "metamer_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_float,
                              c_void_p, c_void_p, c_void_p]),
+    "jtfs_batch_create": (c_int, [POINTER(c_void_p), POINTER(c_int64), c_int, c_int, c_int, c_int, c_int,
+                                  c_int, c_int64, c_int, c_uint32]),
+    "jtfs_batch_destroy": (c_int, [c_void_p]),
+    "jtfs_batch_layout": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
+    "jtfs_batch_workspace_bytes": (c_size_t, [c_void_p]),
+    "jtfs_batch_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "jtfs_batch_metamer_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float,
+                                        c_void_p, c_void_p, c_void_p]),
     "jtfs_profile_stage": (c_int, [c_void_p, c_int, POINTER(c_void_p), c_int]),
     "jtfs_launch_count": (c_int64, [c_void_p, c_int]),
     "jtfs_error_string": (c_char_p, [c_int]),

@@ -1,0 +1,302 @@
+// Ragged batches: clips of any lengths, grouped by padded length, each group
+// on its own plan.  A clip of length L is zero-padded on the right to the
+// next power of two >= max(L, T) (§3.2's padding, periodic boundary), its Phi
+// computed there and cropped to the first ceil(L/T) frames of every row; the
+// loss runs over the kept frames only, so the crop's adjoint fills zeros.
+// Packed layouts are described in include/jtfs.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "jtfs.h"
+#include "jtfs_internal.h"
+
+namespace jtfs {
+namespace {
+
+constexpr int kThreadsB = 256;
+
+// Per clip (device copy): packed offsets, offsets of its group's buffers in
+// the workspace (in floats), sizes.
+struct ClipD {
+  int64_t so;     // packed samples
+  int64_t po;     // packed Phi
+  int64_t ypad;   // padded input row
+  int64_t phi;    // full (uncropped) Phi
+  int64_t dphi;   // its gradient
+  int64_t dy;     // gradient w.r.t. the padded row
+  int L, N, nf, nf_full, rows, pad;
+};
+
+struct Group {
+  Plan plan;
+  std::vector<int> clips;
+  size_t ws_off = 0, ypad_off = 0, phi_off = 0, dphi_off = 0, dy_off = 0;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Padded rows from packed samples (zeros beyond L).
+__global__ void __launch_bounds__(kThreadsB) k_gather(const ClipD* __restrict__ clips, const float* __restrict__ y,
+                                                     float* __restrict__ ws) {
+  const ClipD c = clips[blockIdx.y];
+  for (int t = blockIdx.x * kThreadsB + threadIdx.x; t < c.N; t += gridDim.x * kThreadsB)
+    ws[c.ypad + t] = t < c.L ? y[c.so + t] : 0.f;
+}
+
+// Loss over the kept frames, dPhi = 2 (Phi - target) there and 0 on cropped
+// frames; one block per clip, fixed-order reduction.
+__global__ void __launch_bounds__(512) k_masked_loss(const ClipD* __restrict__ clips, const float* __restrict__ tgt,
+                                                    float* ws, float* __restrict__ loss) {
+  __shared__ double red[512];
+  const ClipD c = clips[blockIdx.x];
+  const int64_t total = static_cast<int64_t>(c.rows) * c.nf_full;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+    const int r = static_cast<int>(i / c.nf_full), f = static_cast<int>(i % c.nf_full);
+    float d = 0.f;
+    if (f < c.nf) {
+      d = ws[c.phi + i] - tgt[c.po + static_cast<int64_t>(r) * c.nf + f];
+      acc += static_cast<double>(d) * d;
+    }
+    ws[c.dphi + i] = 2.f * d;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[blockIdx.x] = static_cast<float>(red[0]);
+}
+
+// Cropped Phi, packed.
+__global__ void __launch_bounds__(kThreadsB) k_crop(const ClipD* __restrict__ clips, const float* __restrict__ ws,
+                                                   float* __restrict__ phi) {
+  const ClipD c = clips[blockIdx.y];
+  const int64_t total = static_cast<int64_t>(c.rows) * c.nf;
+  for (int64_t i = blockIdx.x * kThreadsB + threadIdx.x; i < total; i += static_cast<int64_t>(gridDim.x) * kThreadsB) {
+    const int64_t r = i / c.nf, f = i % c.nf;
+    phi[c.po + i] = ws[c.phi + r * c.nf_full + f];
+  }
+}
+
+// Adam on the packed samples (gradient = first L samples of the padded
+// gradient); the 1-based step index is read from device memory.
+__global__ void __launch_bounds__(kThreadsB) k_adam_packed(const ClipD* __restrict__ clips, const float* __restrict__ ws,
+                                                          float* __restrict__ y, float* __restrict__ m,
+                                                          float* __restrict__ v, const int* __restrict__ step,
+                                                          float lr) {
+  const ClipD c = clips[blockIdx.y];
+  const int t_step = *step;
+  const float c1 = 1.f / (1.f - powf(0.9f, static_cast<float>(t_step)));
+  const float c2 = 1.f / (1.f - powf(0.999f, static_cast<float>(t_step)));
+  for (int t = blockIdx.x * kThreadsB + threadIdx.x; t < c.L; t += gridDim.x * kThreadsB) {
+    const int64_t i = c.so + t;
+    const float g = ws[c.dy + t];
+    const float mi = 0.9f * m[i] + 0.1f * g;
+    const float vi = 0.999f * v[i] + 0.001f * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    y[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+  }
+}
+
+__global__ void k_step_increment(int* step) { *step += 1; }
+
+}  // namespace
+}  // namespace jtfs
+
+struct jtfs_batch_s {
+  std::vector<int64_t> lengths, so, po;
+  std::vector<jtfs::Group> groups;
+  std::vector<jtfs::ClipD> clips;
+  jtfs::ClipD* d_clips = nullptr;
+  size_t ws_bytes = 0;
+  int max_blocks_x = 1;
+  bool on_device = false;
+};
+
+namespace {
+
+void destroy_batch(jtfs_batch_s* b) {
+  if (!b) return;
+  for (auto& g : b->groups) jtfs::release_plan(g.plan);
+  if (b->d_clips) cudaFree(b->d_clips);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" int jtfs_batch_create(jtfs_batch_t* out, const int64_t* lengths, int count, int J, int Q, int Q2,
+                                 int J_fr, int Q_fr, int64_t T, int F, uint32_t flags) {
+  if (!out || !lengths || count < 1) return JTFS_ERR_ARG;
+  *out = nullptr;
+  if (T < 2 || (T & (T - 1))) return JTFS_ERR_SHAPE;
+  jtfs_batch_s* b = new (std::nothrow) jtfs_batch_s();
+  if (!b) return JTFS_ERR_NOMEM;
+  int rc = JTFS_OK;
+  try {
+    std::map<int64_t, std::vector<int>> by_n;
+    for (int i = 0; i < count; ++i) {
+      const int64_t L = lengths[i];
+      if (L < 1 || L > (int64_t(1) << 20)) {
+        rc = JTFS_ERR_SHAPE;
+        break;
+      }
+      int64_t n = 1;
+      while (n < std::max<int64_t>(L, T)) n <<= 1;
+      by_n[n].push_back(i);
+      b->lengths.push_back(L);
+    }
+    if (rc == JTFS_OK) {
+      b->groups.resize(by_n.size());
+      size_t gi = 0, off = 0;
+      b->clips.assign(count, jtfs::ClipD{});
+      for (auto& kv : by_n) {
+        jtfs::Group& g = b->groups[gi++];
+        g.clips = kv.second;
+        rc = jtfs::build_plan(g.plan, kv.first, J, Q, Q2, J_fr, Q_fr, T, F, static_cast<int>(g.clips.size()), flags);
+        if (rc != JTFS_OK) break;
+        if (!(flags & JTFS_PLAN_HOST_ONLY)) {
+          rc = jtfs::upload_plan(g.plan);
+          if (rc != JTFS_OK) break;
+        }
+        const size_t B = g.clips.size(), N = static_cast<size_t>(kv.first), P = static_cast<size_t>(g.plan.phi_size);
+        g.ws_off = off;
+        off = jtfs::align256(off + g.plan.ws_bytes);
+        g.ypad_off = off;
+        off = jtfs::align256(off + B * N * sizeof(float));
+        g.phi_off = off;
+        off = jtfs::align256(off + B * P * sizeof(float));
+        g.dphi_off = off;
+        off = jtfs::align256(off + B * P * sizeof(float));
+        g.dy_off = off;
+        off = jtfs::align256(off + B * N * sizeof(float));
+        for (size_t k = 0; k < B; ++k) {
+          jtfs::ClipD& c = b->clips[g.clips[k]];
+          c.L = static_cast<int>(lengths[g.clips[k]]);
+          c.N = static_cast<int>(N);
+          c.nf_full = g.plan.n_frames;
+          c.nf = static_cast<int>((c.L + T - 1) / T);
+          c.rows = static_cast<int>(P / g.plan.n_frames);
+          c.ypad = static_cast<int64_t>(g.ypad_off / sizeof(float) + k * N);
+          c.phi = static_cast<int64_t>(g.phi_off / sizeof(float) + k * P);
+          c.dphi = static_cast<int64_t>(g.dphi_off / sizeof(float) + k * P);
+          c.dy = static_cast<int64_t>(g.dy_off / sizeof(float) + k * N);
+        }
+        b->max_blocks_x = std::max<int>(b->max_blocks_x, static_cast<int>((N + 255) / 256));
+      }
+      b->ws_bytes = off;
+      b->so.assign(count + 1, 0);
+      b->po.assign(count + 1, 0);
+      for (int i = 0; i < count && rc == JTFS_OK; ++i) {
+        jtfs::ClipD& c = b->clips[i];
+        b->so[i + 1] = b->so[i] + c.L;
+        b->po[i + 1] = b->po[i] + static_cast<int64_t>(c.rows) * c.nf;
+        c.so = b->so[i];
+        c.po = b->po[i];
+      }
+      if (rc == JTFS_OK && !(flags & JTFS_PLAN_HOST_ONLY)) {
+        if (cudaMalloc(&b->d_clips, count * sizeof(jtfs::ClipD)) != cudaSuccess) rc = JTFS_ERR_NOMEM;
+        else if (cudaMemcpy(b->d_clips, b->clips.data(), count * sizeof(jtfs::ClipD), cudaMemcpyHostToDevice) !=
+                 cudaSuccess)
+          rc = JTFS_ERR_CUDA;
+        b->on_device = rc == JTFS_OK;
+      }
+    }
+  } catch (...) {
+    rc = JTFS_ERR_NOMEM;
+  }
+  if (rc != JTFS_OK) {
+    destroy_batch(b);
+    return rc;
+  }
+  *out = b;
+  return JTFS_OK;
+}
+
+extern "C" int jtfs_batch_destroy(jtfs_batch_t batch) {
+  destroy_batch(batch);
+  return JTFS_OK;
+}
+
+extern "C" int jtfs_batch_layout(jtfs_batch_t batch, int64_t* sample_off, int64_t* phi_off) {
+  if (!batch) return JTFS_ERR_ARG;
+  const int n = static_cast<int>(batch->lengths.size());
+  for (int i = 0; i <= n; ++i) {
+    if (sample_off) sample_off[i] = batch->so[i];
+    if (phi_off) phi_off[i] = batch->po[i];
+  }
+  return n;
+}
+
+extern "C" size_t jtfs_batch_workspace_bytes(jtfs_batch_t batch) { return batch ? batch->ws_bytes : 0; }
+
+namespace {
+
+int batch_check(jtfs_batch_t b, void* ws) {
+  if (!b) return JTFS_ERR_ARG;
+  if (!b->on_device) return JTFS_ERR_NODEVICE;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return JTFS_ERR_WORKSPACE;
+  return JTFS_OK;
+}
+
+int launched() { return cudaGetLastError() == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA; }
+
+int gather_and_forward(jtfs_batch_t b, const float* x, void* ws, bool full, cudaStream_t s) {
+  auto* base = static_cast<unsigned char*>(ws);
+  const int count = static_cast<int>(b->lengths.size());
+  jtfs::k_gather<<<dim3(std::min(b->max_blocks_x, 1024), count), jtfs::kThreadsB, 0, s>>>(
+      b->d_clips, x, reinterpret_cast<float*>(base));
+  if (launched() != JTFS_OK) return JTFS_ERR_CUDA;
+  for (const auto& g : b->groups) {
+    const int rc = jtfs::run_forward(g.plan, reinterpret_cast<const float*>(base + g.ypad_off),
+                                     reinterpret_cast<float*>(base + g.phi_off), base + g.ws_off, full, s);
+    if (rc != JTFS_OK) return rc;
+  }
+  return JTFS_OK;
+}
+
+}  // namespace
+
+extern "C" int jtfs_batch_forward(jtfs_batch_t batch, const float* x, float* phi, void* workspace, void* stream) {
+  const int rc0 = batch_check(batch, workspace);
+  if (rc0 != JTFS_OK) return rc0;
+  if (!x || !phi) return JTFS_ERR_ARG;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = gather_and_forward(batch, x, workspace, true, s);
+  if (rc != JTFS_OK) return rc;
+  const int count = static_cast<int>(batch->lengths.size());
+  jtfs::k_crop<<<dim3(64, count), jtfs::kThreadsB, 0, s>>>(batch->d_clips, static_cast<const float*>(workspace), phi);
+  return launched();
+}
+
+extern "C" int jtfs_batch_metamer_step(jtfs_batch_t batch, float* y, const float* phi_target, float* adam_m,
+                                       float* adam_v, int32_t* step, float lr, float* loss, void* workspace,
+                                       void* stream) {
+  const int rc0 = batch_check(batch, workspace);
+  if (rc0 != JTFS_OK) return rc0;
+  if (!y || !phi_target || !adam_m || !adam_v || !step || !loss || !(lr > 0.f)) return JTFS_ERR_ARG;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto* base = static_cast<unsigned char*>(workspace);
+  const int count = static_cast<int>(batch->lengths.size());
+  int rc = gather_and_forward(batch, y, workspace, true, s);
+  if (rc != JTFS_OK) return rc;
+  jtfs::k_masked_loss<<<count, 512, 0, s>>>(batch->d_clips, phi_target, reinterpret_cast<float*>(base), loss);
+  if (launched() != JTFS_OK) return JTFS_ERR_CUDA;
+  for (const auto& g : batch->groups) {
+    rc = jtfs::run_backward(g.plan, reinterpret_cast<const float*>(base + g.dphi_off),
+                            reinterpret_cast<float*>(base + g.dy_off), base + g.ws_off, s);
+    if (rc != JTFS_OK) return rc;
+  }
+  jtfs::k_adam_packed<<<dim3(std::min(batch->max_blocks_x, 1024), count), jtfs::kThreadsB, 0, s>>>(
+      batch->d_clips, reinterpret_cast<const float*>(base), y, adam_m, adam_v, step, lr);
+  if (launched() != JTFS_OK) return JTFS_ERR_CUDA;
+  jtfs::k_step_increment<<<1, 1, 0, s>>>(step);
+  return launched();
+}

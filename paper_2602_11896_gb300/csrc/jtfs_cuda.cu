@@ -1205,6 +1205,14 @@ int check_call(const Plan& p, void* ws) {
 bool misaligned(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15) != 0; }
 
 }  // namespace
+
+int run_forward(const Plan& p, const float* x, float* phi, void* ws, bool full, cudaStream_t s) {
+  return forward_stages(p, x, phi, bufs(p, ws), full, s);
+}
+int run_backward(const Plan& p, const float* dphi, float* dx, void* ws, cudaStream_t s) {
+  return backward_stages(p, dphi, dx, bufs(p, ws), s);
+}
+
 }  // namespace jtfs
 
 

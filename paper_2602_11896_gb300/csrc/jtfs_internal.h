@@ -195,6 +195,12 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
 int upload_plan(Plan& p);
 void release_plan(Plan& p);
 
+// Stages of one plan on a caller workspace (jtfs_cuda.cu).  run_forward with
+// full = false computes only what run_backward needs (phi may be NULL);
+// run_backward needs a preceding run_forward on the same workspace.
+int run_forward(const Plan& p, const float* x, float* phi, void* ws, bool full, cudaStream_t s);
+int run_backward(const Plan& p, const float* dphi, float* dx, void* ws, cudaStream_t s);
+
 }  // namespace jtfs
 
 // Opaque handle of the C ABI.

@@ -151,6 +151,87 @@ class JTFSPlan:
         return loss
 
 
+class JTFSBatch:
+    """Clips of uneven lengths solved together (jtfs_batch_* in include/jtfs.h).
+
+    Each clip is zero-padded to the next power of two >= max(L, T) and its Phi
+    cropped to ceil(L/T) frames per row.  Samples and Phi are packed:
+    ``sample_offsets`` / ``phi_offsets`` give each clip's slice.
+    """
+
+    def __init__(self, lengths, J: int, Q: int, Q2: int, J_fr: int, Q_fr: int, T: int, F: int,
+                 host_only: bool = False):
+        lib = _native.load()
+        if not host_only and not torch.cuda.is_available():
+            raise RuntimeError("JTFSBatch needs a CUDA device (or host_only=True for inspection)")
+        lens = [int(v) for v in lengths]
+        arr = (c_int64 * len(lens))(*lens)
+        h = c_void_p()
+        _native.check(lib.jtfs_batch_create(ctypes.byref(h), arr, len(lens), J, Q, Q2, J_fr, Q_fr, T, F,
+                                            _native.PLAN_HOST_ONLY if host_only else 0), "jtfs_batch_create")
+        self._h, self._lib = h, lib
+        so = (c_int64 * (len(lens) + 1))()
+        po = (c_int64 * (len(lens) + 1))()
+        lib.jtfs_batch_layout(h, so, po)
+        self.lengths = lens
+        self.sample_offsets = [int(v) for v in so]
+        self.phi_offsets = [int(v) for v in po]
+        self.n_samples = self.sample_offsets[-1]
+        self.phi_size = self.phi_offsets[-1]
+        self.workspace_bytes = int(lib.jtfs_batch_workspace_bytes(h))
+        self._ws: Optional[torch.Tensor] = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.jtfs_batch_destroy(h)
+            self._h = None
+
+    def workspace(self, device=None) -> torch.Tensor:
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if self._ws is None or self._ws.device != dev:
+            self._ws = torch.empty(max(self.workspace_bytes, 1), dtype=torch.uint8, device=dev)
+        return self._ws
+
+    @staticmethod
+    def _need(t: torch.Tensor, n: int, name: str, dtype=torch.float32) -> None:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous {dtype} CUDA tensor")
+        if t.numel() != n:
+            raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+
+    def pack(self, clips) -> torch.Tensor:
+        """Concatenate per-clip 1-D tensors (lengths must match) into packed samples."""
+        for c, L in zip(clips, self.lengths):
+            if c.numel() != L:
+                raise ValueError("clip length does not match the batch")
+        return torch.cat([c.reshape(-1) for c in clips]).contiguous()
+
+    def forward(self, x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        self._need(x, self.n_samples, "x")
+        phi = out if out is not None else torch.empty(self.phi_size, device=x.device)
+        ws = self.workspace(x.device)
+        _native.check(self._lib.jtfs_batch_forward(self._h, _ptr(x), _ptr(phi), _ptr(ws), _stream()),
+                      "jtfs_batch_forward")
+        return phi
+
+    def metamer_step(self, y: torch.Tensor, phi_target: torch.Tensor, adam_m: torch.Tensor,
+                     adam_v: torch.Tensor, step: torch.Tensor, lr: float,
+                     loss_out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """One Adam step on every clip; `step` is a 1-element int32 CUDA tensor (1-based,
+        incremented on the device), so the call can be captured in a CUDA graph."""
+        for t, n in ((y, "y"), (adam_m, "adam_m"), (adam_v, "adam_v")):
+            self._need(t, self.n_samples, n)
+        self._need(phi_target, self.phi_size, "phi_target")
+        self._need(step, 1, "step", torch.int32)
+        loss = loss_out if loss_out is not None else torch.empty(len(self.lengths), device=y.device)
+        ws = self.workspace(y.device)
+        _native.check(self._lib.jtfs_batch_metamer_step(self._h, _ptr(y), _ptr(phi_target), _ptr(adam_m),
+                                                        _ptr(adam_v), _ptr(step), float(lr), _ptr(loss),
+                                                        _ptr(ws), _stream()), "jtfs_batch_metamer_step")
+        return loss
+
+
 class _JTFSFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x: torch.Tensor, plan: JTFSPlan) -> torch.Tensor:  # type: ignore[override]

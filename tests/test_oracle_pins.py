@@ -306,3 +306,33 @@ def test_pins_catch_wrong_spin(monkeypatch):
     monkeypatch.setattr(O, "freq_filter_hat", lambda n, xi, sigma: orig(n, -xi, sigma))
     a = O.jtfs(torch.tensor(x), p)["phi"].numpy()
     assert _rel(a, ref) > 1e-3
+
+
+# --------------------------------------------------------------------------- uneven lengths (R15)
+
+def test_uneven_length_power_of_two_is_plain_phi():
+    """For L a power of two the pad and the crop are identities."""
+    p = dict(TINY[0])
+    x = torch.tensor(np.random.default_rng(21).standard_normal(p["N"]))
+    a = O.jtfs_uneven(x, p)
+    b = O.jtfs(x[None], O.Plan(**p))["phi"][0]
+    assert torch.equal(a, b)
+
+
+def test_uneven_length_is_padded_and_cropped():
+    """Phi of a clip of length L equals Phi of its zero-padded copy, cropped to ceil(L/T) frames;
+    the gradient never touches the padding (it has no samples there)."""
+    p = dict(TINY[0])
+    L = 200
+    x = torch.tensor(np.random.default_rng(22).standard_normal(L))
+    a = O.jtfs_uneven(x, p)
+    plan = O.Plan(**p)
+    xp = torch.cat([x, torch.zeros(p["N"] - L, dtype=torch.float64)])[None]
+    full = O.jtfs(xp, plan)["phi"].reshape(-1, plan.n_frames)
+    nf = -(-L // p["T"])
+    assert nf < plan.n_frames
+    assert torch.equal(a, full[:, :nf].reshape(-1))
+    tgt = torch.zeros_like(a)
+    E, g = O.loss_and_grad_uneven(x, tgt, p)
+    assert g.shape == (L,)
+    assert abs(E.item() - (a ** 2).sum().item()) <= 1e-12 * E.item()
