@@ -245,6 +245,28 @@ int jtfs_batch_metamer_step(jtfs_batch_t batch, float* y, const float* phi_targe
                             void* stream);
 
 /*
+ * Autotuning.  A plan has three execution choices that change no result:
+ *   choice[0]  wide column tiles (1) or narrow ones (0) for the second-order
+ *              frequential forward kernel;
+ *   choice[1]  time samples per CTA of the phi_T averaging forward
+ *              (1024, 2048 or 4096);
+ *   choice[2]  points per CTA of the batched small FFTs (1024 .. 8192).
+ * jtfs_autotune times jtfs_loss_grad on the caller's y and phi_target (device
+ * arrays as for jtfs_loss_grad; loss [batch] and dy [batch][N] are scratch
+ * outputs) for each candidate, one choice at a time, keeps the fastest, and
+ * writes the choices to choice[0..n) (host, may be NULL).  It synchronises
+ * the stream (it is a set-up call, not a hot-path one).  jtfs_set_tuning
+ * applies saved choices; jtfs_get_tuning reads the current ones.  All return
+ * the number of choices (3) or an error code.  Not thread-safe with concurrent
+ * compute calls on the same plan.
+ */
+int jtfs_autotune(jtfs_plan_t plan, const float* y, const float* phi_target,
+                  float* loss, float* dy, void* workspace, void* stream,
+                  int64_t* choice, int n);
+int jtfs_set_tuning(jtfs_plan_t plan, const int64_t* choice, int n);
+int jtfs_get_tuning(jtfs_plan_t plan, int64_t* choice, int n);
+
+/*
  * Measurement hooks (host-side bookkeeping; not thread-safe).
  *
  * jtfs_profile_stage registers `count` CUDA events (cudaEvent_t passed as

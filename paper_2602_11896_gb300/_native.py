@@ -37,6 +37,10 @@ SIGNATURES = {
     "jtfs_batch_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "jtfs_batch_metamer_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float,
                                         c_void_p, c_void_p, c_void_p]),
+    "jtfs_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                              POINTER(c_int64), c_int]),
+    "jtfs_set_tuning": (c_int, [c_void_p, POINTER(c_int64), c_int]),
+    "jtfs_get_tuning": (c_int, [c_void_p, POINTER(c_int64), c_int]),
     "jtfs_profile_stage": (c_int, [c_void_p, c_int, POINTER(c_void_p), c_int]),
     "jtfs_launch_count": (c_int64, [c_void_p, c_int]),
     "jtfs_error_string": (c_char_p, [c_int]),

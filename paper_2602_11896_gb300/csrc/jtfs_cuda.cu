@@ -368,7 +368,7 @@ int run_fft(const Plan& p, const std::vector<FftLaunch>& L, const Ld& ld, const 
     const Job* jobs = p.d_jobs + l.job0;
     if (l.logn <= kSmallLogMax) {
       const int n = 1 << l.logn;
-      const int per = std::max(1, (1 << 12) >> l.logn);
+      const int per = std::max(1, std::min(p.tune_fft_points, 1 << kSmallLogMax) >> l.logn);
       const int grid = (l.njobs + per - 1) / per;
       const size_t smem = 2 * size_t(per) * n * sizeof(float2);
       allow_big_smem<k_fft_small<INV, Ld, St>>();
@@ -671,16 +671,16 @@ struct PoolArgs {
 constexpr int kPoolRows = 64;   // rows per CTA
 constexpr int kPoolK = 32;      // time samples per shared-memory stage (forward)
 constexpr int kPoolT = 64;      // time samples per CTA (adjoint)
-constexpr int kPoolSplit = kPoolSplitPlan;  // time samples per CTA (forward, split-K)
 
 // Forward, split over time: a CTA owns a 64-row x 8*FPT-frame tile of one
-// (clip, n2) and the time samples [split * kPoolSplit, +kPoolSplit); thread
+// (clip, n2) and the time samples [split * split_len, +split_len); thread
 // (ty = tid / 8, tx = tid % 8) owns rows ty + 32 i (i < 2) and frames
 // tx + 8 j (j < FPT).  Partial sums go to `part`, reduced in a fixed order
 // by k_pool_reduce (deterministic).
 template <int FPT>
 __global__ void __launch_bounds__(kThreads)
-k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ part, const int4* __restrict__ tiles) {
+k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ part, const int4* __restrict__ tiles,
+           int split_len) {
   __shared__ float Vs[kPoolK][kPoolRows + 1];
   __shared__ float Gs[kPoolK][8 * FPT];
   const int4 tl = tiles[blockIdx.x];  // (clip, active n2, row tile, split)
@@ -691,7 +691,7 @@ k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ part, c
   const int D = 1 << (A.lT - s);
   const int rows = A.n_beta2 * A.R_out;
   const int r0 = tl.z * kPoolRows;
-  const int tbeg = split * kPoolSplit, tend = min(L, tbeg + kPoolSplit);
+  const int tbeg = split * split_len, tend = min(L, tbeg + split_len);
   const float* v = V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
   const float* g = A.taps + A.tap_off[s];
   const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
@@ -740,7 +740,7 @@ k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ part, c
 // Phi2[b][a][r][f] = sum over splits (ascending) of the partials.
 __global__ void __launch_bounds__(kThreads)
 k_pool_reduce(PoolArgs A, const float* __restrict__ part, float* __restrict__ phi, const int* __restrict__ tile0,
-              int row_tiles, int64_t total) {
+              int split_len, int64_t total) {
   const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   const int rows = A.n_beta2 * A.R_out;
@@ -750,14 +750,13 @@ k_pool_reduce(PoolArgs A, const float* __restrict__ part, float* __restrict__ ph
   const int r = rf / A.n_frames, f = rf % A.n_frames;
   const int a = static_cast<int>(ba % A.n_active), b = static_cast<int>(ba / A.n_active);
   const int L = 1 << (A.logN - A.s2[a]);
-  const int nsplit = (L + kPoolSplit - 1) / kPoolSplit;
+  const int nsplit = (L + split_len - 1) / split_len;
   // tiles of (b, a) start at tile0[ba]; ordered by row tile then split
   const int64_t t = tile0[ba] + static_cast<int64_t>(r / kPoolRows) * nsplit;
   const float* pp = part + (t * kPoolRows + (r % kPoolRows)) * A.n_frames + f;
   float acc = 0.f;
   for (int sp = 0; sp < nsplit; ++sp) acc += pp[static_cast<int64_t>(sp) * kPoolRows * A.n_frames];
   phi[static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a] + static_cast<int64_t>(r) * A.n_frames + f] = acc;
-  (void)row_tiles;
 }
 
 // Adjoint: a CTA owns 64 rows x 64 time samples; thread (ty = tid / 16,
@@ -1115,8 +1114,9 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
       FreqArgs FA2w = FA2;
       FA2w.W = p.freq_cols_wide;
       FA2w.logW = ceil_log2(p.freq_cols_wide);
-      if (!launch_freq_fwd_ct(2, FA2w, p.lF, static_cast<unsigned>(p.tiles2w.size()),
-                              freq_smem(p, 3, p.freq_cols_wide), s, p.d_tiles2w, nullptr, w.Y2, w.V2) &&
+      if (!(p.tune_wide && launch_freq_fwd_ct(2, FA2w, p.lF, static_cast<unsigned>(p.tiles2w.size()),
+                                              freq_smem(p, 3, p.freq_cols_wide), s, p.d_tiles2w, nullptr, w.Y2,
+                                              w.V2)) &&
           !launch_freq_fwd_ct(2, FA2, p.lF, static_cast<unsigned>(p.tiles2.size()), freq_smem(p, 3), s,
                               p.d_tiles2, nullptr, w.Y2, w.V2))
         k_freq_fwd<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 3), s>>>(
@@ -1125,21 +1125,24 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
       JTFS_TRY(check_launch());
       const PoolArgs PA = pool_args(p);
       const int fpt = p.n_frames >= 128 ? 16 : p.n_frames >= 64 ? 8 : p.n_frames >= 32 ? 4 : p.n_frames >= 16 ? 2 : 1;
-      dim3 grid(static_cast<unsigned>(p.pool_fwd_tiles.size()),
+      const int si = p.tune_split;
+      const int split_len = kPoolSplits[si];
+      dim3 grid(static_cast<unsigned>(p.pool_fwd_tiles[si].size()),
                 static_cast<unsigned>((p.n_frames + 8 * fpt - 1) / (8 * fpt)));
       prof_begin(p, JTFS_STAGE_POOL_FWD, s);
+      const int4* pt = p.d_pool_fwd_tiles[si];
       switch (fpt) {
-        case 16: k_pool_fwd<16><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, p.d_pool_fwd_tiles); break;
-        case 8: k_pool_fwd<8><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, p.d_pool_fwd_tiles); break;
-        case 4: k_pool_fwd<4><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, p.d_pool_fwd_tiles); break;
-        case 2: k_pool_fwd<2><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, p.d_pool_fwd_tiles); break;
-        default: k_pool_fwd<1><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, p.d_pool_fwd_tiles); break;
+        case 16: k_pool_fwd<16><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
+        case 8: k_pool_fwd<8><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
+        case 4: k_pool_fwd<4><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
+        case 2: k_pool_fwd<2><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
+        default: k_pool_fwd<1><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
       }
       JTFS_TRY(check_launch());
       {
         const int64_t total = int64_t(p.batch) * p.n_active * p.n_beta2 * p.R_out * p.n_frames;
         k_pool_reduce<<<static_cast<unsigned>((total + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-            PA, w.part, phi, p.d_pool_tile0, 0, total);
+            PA, w.part, phi, p.d_pool_tile0[si], split_len, total);
       }
       prof_end(p, JTFS_STAGE_POOL_FWD, s);
       JTFS_TRY(check_launch());
@@ -1336,4 +1339,92 @@ extern "C" int64_t jtfs_launch_count(jtfs_plan_t plan, int call) {
     case 3: return jtfs::forward_launches(p, true) + 2 + jtfs::backward_launches(p);
     default: return JTFS_ERR_ARG;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning of execution choices that do not change results.
+// ---------------------------------------------------------------------------
+extern "C" int jtfs_get_tuning(jtfs_plan_t plan, int64_t* choice, int n) {
+  if (!plan) return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  const int64_t v[3] = {p.tune_wide, jtfs::kPoolSplits[p.tune_split], p.tune_fft_points};
+  for (int i = 0; i < n && i < 3 && choice; ++i) choice[i] = v[i];
+  return 3;
+}
+
+extern "C" int jtfs_set_tuning(jtfs_plan_t plan, const int64_t* choice, int n) {
+  if (!plan || !choice || n < 3) return JTFS_ERR_ARG;
+  int si = -1;
+  for (int i = 0; i < 3; ++i)
+    if (jtfs::kPoolSplits[i] == choice[1]) si = i;
+  const int64_t pts = choice[2];
+  if ((choice[0] != 0 && choice[0] != 1) || si < 0 || pts < 1024 || pts > 8192 || (pts & (pts - 1))) return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  p.tune_wide = static_cast<int>(choice[0]);
+  p.tune_split = si;
+  p.tune_fft_points = static_cast<int>(pts);
+  return 3;
+}
+
+extern "C" int jtfs_autotune(jtfs_plan_t plan, const float* y, const float* phi_target, float* loss, float* dy,
+                             void* workspace, void* stream, int64_t* choice, int n) {
+  if (!plan || !y || !phi_target || !loss || !dy) return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  JTFS_TRY(jtfs::check_call(p, workspace));
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return JTFS_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return JTFS_ERR_CUDA;
+  }
+  auto time_it = [&](float* ms) -> int {
+    JTFS_TRY(jtfs_loss_grad(plan, y, phi_target, loss, dy, workspace, stream));  // warm-up / set-up
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      if (cudaEventRecord(e0, s) != cudaSuccess) return JTFS_ERR_CUDA;
+      JTFS_TRY(jtfs_loss_grad(plan, y, phi_target, loss, dy, workspace, stream));
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return JTFS_ERR_CUDA;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      best = std::min(best, t);
+    }
+    *ms = best;
+    return JTFS_OK;
+  };
+  int rc = JTFS_OK;
+  {
+    float best = 1e30f, t = 0.f;
+    int best_pts = p.tune_fft_points;
+    for (int pts : {1024, 2048, 4096, 8192}) {
+      p.tune_fft_points = pts;
+      if ((rc = time_it(&t)) != JTFS_OK) break;
+      if (t < best) best = t, best_pts = pts;
+    }
+    p.tune_fft_points = best_pts;
+  }
+  if (rc == JTFS_OK) {
+    float best = 1e30f, t = 0.f;
+    int best_si = p.tune_split;
+    for (int si = 0; si < 3; ++si) {
+      p.tune_split = si;
+      if ((rc = time_it(&t)) != JTFS_OK) break;
+      if (t < best) best = t, best_si = si;
+    }
+    p.tune_split = best_si;
+  }
+  if (rc == JTFS_OK) {
+    float best = 1e30f, t = 0.f;
+    int best_w = p.tune_wide;
+    for (int wv : {0, 1}) {
+      p.tune_wide = wv;
+      if ((rc = time_it(&t)) != JTFS_OK) break;
+      if (t < best) best = t, best_w = wv;
+    }
+    p.tune_wide = best_w;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != JTFS_OK) return rc;
+  return jtfs_get_tuning(plan, choice, n);
 }

@@ -16,6 +16,7 @@ bool launch_freq_adj_ct(int mode, const FreqArgs& A, int lF, unsigned grid, size
     return true;                                                                                     \
   }
   JTFS_CT_ADJ(8, 3, 3)
+  JTFS_CT_ADJ(6, 4, 2)
 #undef JTFS_CT_ADJ
   return false;
 }

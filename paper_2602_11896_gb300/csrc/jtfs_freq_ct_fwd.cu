@@ -15,6 +15,8 @@ bool launch_freq_fwd_ct(int mode, const FreqArgs& A, int lF, unsigned grid, size
     return true;                                                                               \
   }
   JTFS_CT_FWD(8, 4, 3)
+  JTFS_CT_FWD(8, 3, 3)
+  JTFS_CT_FWD(6, 4, 2)
 #undef JTFS_CT_FWD
   return false;
 }

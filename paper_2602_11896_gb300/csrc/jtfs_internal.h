@@ -76,8 +76,9 @@ constexpr double kBandSigmas = 12.0;
 constexpr int kSmallLogMax = 13;
 // Columns per CTA in the frequential kernels (at most; fewer for long N_fr).
 constexpr int kFreqCols = 16;
-// Time samples per forward time-pooling CTA (split over time).
-constexpr int kPoolSplitPlan = 2048;
+// Candidate time samples per forward time-pooling CTA (split over time); the
+// plan's tuning state picks one.
+constexpr int kPoolSplits[3] = {1024, 2048, 4096};
 
 struct Plan {
   // Parameters.
@@ -141,8 +142,8 @@ struct Plan {
   int freq_cols_wide = kFreqCols;
   std::vector<FreqChunk> chunks1, chunks2;
   std::vector<int4> pool_tiles;  // adjoint time pooling: (clip, active n2, row tile, time tile)
-  std::vector<int4> pool_fwd_tiles;  // forward time pooling: (clip, active n2, row tile, split)
-  std::vector<int> pool_tile0;       // per (clip, active n2): first forward tile  // first order (phi_F, +xi) / second order (all)
+  std::vector<int4> pool_fwd_tiles[3];  // forward time pooling per split: (clip, active n2, row tile, split)
+  std::vector<int> pool_tile0[3];       // per split and (clip, active n2): first forward tile  // first order (phi_F, +xi) / second order (all)
   // Frequential tables on the N_fr grid, one row of N_fr floats each:
   // rows [0, n_beta2): psi_beta; row n_beta2: phi_F; row n_beta2 + 1 + k:
   // phi_F periodised onto N_fr / 2^k bins (k = 0 .. log2 F).
@@ -172,8 +173,15 @@ struct Plan {
   const FreqChunk* d_chunks2 = nullptr;
   const float* d_ftab = nullptr;
   const int4* d_pool_tiles = nullptr;
-  const int4* d_pool_fwd_tiles = nullptr;
-  const int* d_pool_tile0 = nullptr;
+  const int4* d_pool_fwd_tiles[3] = {nullptr, nullptr, nullptr};
+  const int* d_pool_tile0[3] = {nullptr, nullptr, nullptr};
+
+  // Tuning state (jtfs_autotune / jtfs_set_tuning): wide forward tiles for the
+  // second-order frequential kernel, index into kPoolSplits, and the points
+  // per CTA of batched small FFTs.
+  mutable int tune_wide = 1;
+  mutable int tune_split = 1;
+  mutable int tune_fft_points = 4096;
   const int* d_s2 = nullptr;          // per active index
   const int* d_n1max_act = nullptr;   // per active index
   const int64_t* d_y2_off = nullptr;  // per active index

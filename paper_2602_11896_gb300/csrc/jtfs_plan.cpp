@@ -360,17 +360,17 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
           for (int tt = 0; tt < (L + 63) / 64; ++tt) p.pool_tiles.push_back(make_int4(b, a, rt, tt));
       }
   }
-  p.pool_fwd_tiles.clear();
-  p.pool_tile0.clear();
-  {
+  for (int si = 0; si < 3; ++si) {
+    p.pool_fwd_tiles[si].clear();
+    p.pool_tile0[si].clear();
     const int rows = p.n_beta2 * p.R_out;
     for (int b = 0; b < B; ++b)
       for (int a = 0; a < p.n_active; ++a) {
         const int L = static_cast<int>(N >> p.s2[a]);
-        const int nsplit = (L + kPoolSplitPlan - 1) / kPoolSplitPlan;
-        p.pool_tile0.push_back(static_cast<int>(p.pool_fwd_tiles.size()));
+        const int nsplit = (L + kPoolSplits[si] - 1) / kPoolSplits[si];
+        p.pool_tile0[si].push_back(static_cast<int>(p.pool_fwd_tiles[si].size()));
         for (int rt = 0; rt < (rows + 63) / 64; ++rt)
-          for (int sp = 0; sp < nsplit; ++sp) p.pool_fwd_tiles.push_back(make_int4(b, a, rt, sp));
+          for (int sp = 0; sp < nsplit; ++sp) p.pool_fwd_tiles[si].push_back(make_int4(b, a, rt, sp));
       }
   }
 
@@ -398,7 +398,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   p.ws_dS0h = take(size_t(B) * p.n_frames * c8);
   p.ws_dy = take(size_t(B) * N * f4);
   p.ws_scr = take(size_t(std::max<int64_t>(p.scr_elems, 1)) * c8);
-  p.ws_part = take(std::max<size_t>(p.pool_fwd_tiles.size(), 1) * 64 * p.n_frames * f4);
+  p.ws_part = take(std::max<size_t>(p.pool_fwd_tiles[0].size(), 1) * 64 * p.n_frames * f4);
   p.ws_bytes = o;
   return JTFS_OK;
 }
@@ -437,8 +437,11 @@ int upload_plan(Plan& p) {
   const size_t o_c2 = put(p.chunks2.data(), p.chunks2.size() * sizeof(FreqChunk));
   const size_t o_ftab = put(p.h_ftab.data(), p.h_ftab.size() * sizeof(float));
   const size_t o_pt = put(p.pool_tiles.data(), p.pool_tiles.size() * sizeof(int4));
-  const size_t o_pft = put(p.pool_fwd_tiles.data(), p.pool_fwd_tiles.size() * sizeof(int4));
-  const size_t o_pt0 = put(p.pool_tile0.data(), p.pool_tile0.size() * sizeof(int));
+  size_t o_pft[3], o_pt0[3];
+  for (int si = 0; si < 3; ++si) {
+    o_pft[si] = put(p.pool_fwd_tiles[si].data(), p.pool_fwd_tiles[si].size() * sizeof(int4));
+    o_pt0[si] = put(p.pool_tile0[si].data(), p.pool_tile0[si].size() * sizeof(int));
+  }
   const size_t o_s2 = put(p.s2.data(), p.s2.size() * sizeof(int));
   const size_t o_n1m = put(n1max_act.data(), n1max_act.size() * sizeof(int));
   const size_t o_y2o = put(p.y2_off.data(), p.y2_off.size() * sizeof(int64_t));
@@ -474,8 +477,10 @@ int upload_plan(Plan& p) {
   p.d_chunks2 = reinterpret_cast<const FreqChunk*>(at(o_c2));
   p.d_ftab = reinterpret_cast<const float*>(at(o_ftab));
   p.d_pool_tiles = reinterpret_cast<const int4*>(at(o_pt));
-  p.d_pool_fwd_tiles = reinterpret_cast<const int4*>(at(o_pft));
-  p.d_pool_tile0 = reinterpret_cast<const int*>(at(o_pt0));
+  for (int si = 0; si < 3; ++si) {
+    p.d_pool_fwd_tiles[si] = reinterpret_cast<const int4*>(at(o_pft[si]));
+    p.d_pool_tile0[si] = reinterpret_cast<const int*>(at(o_pt0[si]));
+  }
   p.d_s2 = reinterpret_cast<const int*>(at(o_s2));
   p.d_n1max_act = reinterpret_cast<const int*>(at(o_n1m));
   p.d_y2_off = reinterpret_cast<const int64_t*>(at(o_y2o));

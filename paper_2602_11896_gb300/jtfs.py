@@ -77,6 +77,62 @@ class JTFSPlan:
         self._lib.jtfs_plan_filters(self._h, which, xi, sg, jj, n)
         return np.array(xi[:]), np.array(sg[:]), np.array(jj[:], dtype=np.int64)
 
+    # -- tuning -----------------------------------------------------------
+    def tuning(self) -> Tuple[int, int, int]:
+        """(wide forward tiles, pooling split, small-FFT points per CTA) in use."""
+        buf = (c_int64 * 3)()
+        self._lib.jtfs_get_tuning(self._h, buf, 3)
+        return int(buf[0]), int(buf[1]), int(buf[2])
+
+    def set_tuning(self, choice) -> None:
+        buf = (c_int64 * 3)(*[int(c) for c in choice])
+        n = self._lib.jtfs_set_tuning(self._h, buf, 3)
+        _native.check(0 if n >= 0 else n, "jtfs_set_tuning")
+
+    def _tune_key(self) -> str:
+        name = torch.cuda.get_device_name() if torch.cuda.is_available() else "host"
+        return f"{name}|" + ",".join(f"{k}={self.info[k]}" for k in INFO_KEYS[:9])
+
+    def autotune(self, y: torch.Tensor, phi_target: torch.Tensor, cache: Optional[str] = None) -> Tuple[int, int, int]:
+        """Pick the fastest execution choices for this plan by timing jtfs_loss_grad on (y, phi_target).
+
+        With ``cache`` (default: the JTFS_TUNE_CACHE environment variable) the choices are read
+        from / written to that JSON file, keyed by device name and plan parameters.
+        """
+        import json
+        import os
+        path = cache if cache is not None else os.environ.get("JTFS_TUNE_CACHE")
+        key = self._tune_key()
+        if path and os.path.exists(path):
+            try:
+                table = json.load(open(path))
+            except (OSError, ValueError):
+                table = {}
+            if key in table:
+                self.set_tuning(table[key])
+                return self.tuning()
+        self._check(y, self.N, "y")
+        self._check(phi_target, self.phi_size, "phi_target")
+        loss = torch.empty(self.batch, device=y.device)
+        dy = torch.empty_like(y)
+        ws = self.workspace(y.device)
+        buf = (c_int64 * 3)()
+        n = self._lib.jtfs_autotune(self._h, _ptr(y), _ptr(phi_target), _ptr(loss), _ptr(dy), _ptr(ws), _stream(),
+                                    buf, 3)
+        _native.check(0 if n >= 0 else n, "jtfs_autotune")
+        choice = [int(buf[0]), int(buf[1]), int(buf[2])]
+        if path:
+            table = {}
+            if os.path.exists(path):
+                try:
+                    table = json.load(open(path))
+                except (OSError, ValueError):
+                    table = {}
+            table[key] = choice
+            with open(path, "w") as f:
+                json.dump(table, f, indent=1)
+        return tuple(choice)
+
     # -- compute ----------------------------------------------------------
     def workspace(self, device: Optional[torch.device] = None) -> torch.Tensor:
         """Device scratch of jtfs_workspace_bytes(), cached (calls on one stream serialise)."""

@@ -1,0 +1,57 @@
+"""Autotuned execution choices change speed, not results."""
+
+import itertools
+import json
+
+import numpy as np
+import pytest
+import torch
+
+from workloads import get_workload, signals
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _rel(a, b):
+    return float((a.double() - b.double()).norm() / b.double().norm())
+
+
+@pytest.mark.parametrize("name", ["tones8k_n8192", "chirps22k_b8_n65536"])
+def test_every_tuning_choice_gives_the_same_gradient(name):
+    from paper_2602_11896_gb300 import JTFSPlan
+    wl = get_workload(name)
+    B = 2
+    plan = JTFSPlan(**wl.params, batch=B)
+    y = torch.tensor(np.stack([signals.white_noise(wl.N, 7 + b) for b in range(B)]), device="cuda")
+    tgt = plan.forward(torch.tensor(np.stack([signals.white_noise(wl.N, 17 + b) for b in range(B)]), device="cuda"))
+    ref_choice = plan.tuning()
+    l0, g0 = plan.loss_grad(y, tgt)
+    for wide, split, pts in itertools.product((0, 1), (1024, 2048, 4096), (1024, 8192)):
+        plan.set_tuning((wide, split, pts))
+        assert plan.tuning() == (wide, split, pts)
+        l1, g1 = plan.loss_grad(y, tgt)
+        assert _rel(l1, l0) <= 1e-6 and _rel(g1, g0) <= 1e-6, (wide, split, pts)
+        if split == ref_choice[1]:   # only the pooling split reorders a sum
+            assert torch.equal(l1, l0) and torch.equal(g1, g0), (wide, split, pts)
+    plan.set_tuning(ref_choice)
+
+
+def test_autotune_picks_a_valid_choice_and_caches_it(tmp_path):
+    from paper_2602_11896_gb300 import JTFSPlan
+    wl = get_workload("tones8k_n8192")
+    plan = JTFSPlan(**wl.params, batch=4)
+    y = torch.tensor(np.stack([signals.white_noise(wl.N, b) for b in range(4)]), device="cuda")
+    tgt = plan.forward(y.flip(0).contiguous())
+    cache = tmp_path / "tune.json"
+    choice = plan.autotune(y, tgt, cache=str(cache))
+    assert choice[0] in (0, 1) and choice[1] in (1024, 2048, 4096) and choice[2] in (1024, 2048, 4096, 8192)
+    table = json.load(open(cache))
+    assert list(table.values()) == [list(choice)]
+    other = JTFSPlan(**wl.params, batch=4)
+    assert other.autotune(y, tgt, cache=str(cache)) == choice
