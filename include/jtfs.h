@@ -267,6 +267,44 @@ int jtfs_set_tuning(jtfs_plan_t plan, const int64_t* choice, int n);
 int jtfs_get_tuning(jtfs_plan_t plan, int64_t* choice, int n);
 
 /*
+ * Learned initialiser layers (BF16 operands as uint16_t bit patterns, FP32
+ * accumulation on the tensor cores).  A transposed 1-D convolution with stride
+ * 2, kernel 9, padding 4 and output padding 1 maps x [B][Ci][T] to
+ * y [B][Co][2T]:  y[b][co][t] = bias[co] + sum over (ci, u, k) with
+ * t = 2u - 4 + k of x[b][ci][u] W[ci][co][k],  W [Ci][Co][9].  The paper has
+ * no such network: it refines a noise initialisation (§2.3); this decoder
+ * proposes the initial waveform from the target's Phi instead.  All pointers
+ * are device pointers; calls are asynchronous on `stream`.
+ *   jtfs_convt_forward         y (float32) from x, W (bf16) and bias (float32, may be NULL)
+ *   jtfs_convt_backward_data   dx [B][Ci][T] (float32) from dy [B][Co][2T] (bf16) and W
+ *   jtfs_convt_backward_weight dW [Ci][Co][9] (float32) from x and dy (bf16); db [Co] from
+ *                              dy_f32 (float32 copy of dy; both may be NULL); needs a workspace
+ *                              of jtfs_convt_weight_workspace_bytes(B, Ci, Co, T) bytes
+ *   jtfs_gelu_forward          h = GELU(z) (bf16), GELU(z) = z (1 + erf(z/sqrt 2)) / 2
+ *   jtfs_gelu_backward         dz = dh GELU'(z) (float32)
+ *   jtfs_cast_bf16             round-to-nearest float32 -> bf16
+ *   jtfs_adam_update           Adam (0.9, 0.999, 1e-8, bias-corrected, 1-based step) on float32
+ *                              parameters, also writing their bf16 copy if param_bf16 != NULL
+ * Errors: JTFS_ERR_ARG (NULL pointer, sizes < 1 or too large), JTFS_ERR_CUDA.
+ */
+int jtfs_convt_forward(const uint16_t* x, const uint16_t* w, const float* bias,
+                       float* y, int B, int Ci, int Co, int T, void* stream);
+int jtfs_convt_backward_data(const uint16_t* dy, const uint16_t* w, float* dx,
+                             int B, int Ci, int Co, int T, void* stream);
+size_t jtfs_convt_weight_workspace_bytes(int B, int Ci, int Co, int T);
+int jtfs_convt_backward_weight(const uint16_t* x, const uint16_t* dy,
+                               const float* dy_f32, float* dw, float* db, int B,
+                               int Ci, int Co, int T, void* workspace,
+                               void* stream);
+int jtfs_gelu_forward(const float* z, uint16_t* h, int64_t n, void* stream);
+int jtfs_gelu_backward(const float* dh, const float* z, float* dz, int64_t n,
+                       void* stream);
+int jtfs_cast_bf16(const float* x, uint16_t* y, int64_t n, void* stream);
+int jtfs_adam_update(float* param, const float* grad, float* m, float* v,
+                     uint16_t* param_bf16, int64_t n, float lr, int step,
+                     void* stream);
+
+/*
  * Measurement hooks (host-side bookkeeping; not thread-safe).
  *
  * jtfs_profile_stage registers `count` CUDA events (cudaEvent_t passed as

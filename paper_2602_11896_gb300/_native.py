@@ -41,6 +41,16 @@ SIGNATURES = {
                               POINTER(c_int64), c_int]),
     "jtfs_set_tuning": (c_int, [c_void_p, POINTER(c_int64), c_int]),
     "jtfs_get_tuning": (c_int, [c_void_p, POINTER(c_int64), c_int]),
+    "jtfs_convt_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p]),
+    "jtfs_convt_backward_data": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p]),
+    "jtfs_convt_weight_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int]),
+    "jtfs_convt_backward_weight": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int,
+                                           c_int, c_void_p, c_void_p]),
+    "jtfs_gelu_forward": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
+    "jtfs_gelu_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
+    "jtfs_cast_bf16": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
+    "jtfs_adam_update": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_int,
+                                 c_void_p]),
     "jtfs_profile_stage": (c_int, [c_void_p, c_int, POINTER(c_void_p), c_int]),
     "jtfs_launch_count": (c_int64, [c_void_p, c_int]),
     "jtfs_error_string": (c_char_p, [c_int]),

@@ -18,7 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libjtfs.so")
-SOURCES = ["jtfs_plan.cpp", "jtfs_cuda.cu", "jtfs_batch.cu", "jtfs_freq_ct_fwd.cu", "jtfs_freq_ct_adj.cu"]
+SOURCES = ["jtfs_plan.cpp", "jtfs_cuda.cu", "jtfs_batch.cu", "jtfs_decoder.cu", "jtfs_freq_ct_fwd.cu",
+           "jtfs_freq_ct_adj.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

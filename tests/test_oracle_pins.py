@@ -336,3 +336,26 @@ def test_uneven_length_is_padded_and_cropped():
     E, g = O.loss_and_grad_uneven(x, tgt, p)
     assert g.shape == (L,)
     assert abs(E.item() - (a ** 2).sum().item()) <= 1e-12 * E.item()
+
+
+# --------------------------------------------------------------------------- decoder layers
+
+def test_decoder_conv_transpose_reference_is_the_defining_sum():
+    from oracle import decoder_oracle as D
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((2, 3, 7))
+    w = rng.standard_normal((3, 4, 9))
+    b = rng.standard_normal(4)
+    a = D.conv_transpose(torch.tensor(x), torch.tensor(w), torch.tensor(b)).numpy()
+    assert a.shape == (2, 4, 14)
+    assert np.abs(a - D.conv_transpose_direct(x, w, b)).max() < 1e-12
+
+
+def test_decoder_gelu_closed_form_points():
+    from oracle import decoder_oracle as D
+    z = torch.tensor([0.0, 1.0, -1.0, 3.0])
+    g = D.gelu(z)
+    assert g[0].item() == 0.0
+    assert abs(g[1].item() - 0.8413447460685429) < 1e-12          # Phi_N(1)
+    assert abs(g[2].item() + 0.15865525393145707) < 1e-12          # -(1 - Phi_N(1))
+    assert abs(g[3].item() - 3 * 0.9986501019683699) < 1e-12
