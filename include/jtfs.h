@@ -283,6 +283,8 @@ int jtfs_get_tuning(jtfs_plan_t plan, int64_t* choice, int n);
  *   jtfs_gelu_forward          h = GELU(z) (bf16), GELU(z) = z (1 + erf(z/sqrt 2)) / 2
  *   jtfs_gelu_backward         dz = dh GELU'(z) (float32)
  *   jtfs_cast_bf16             round-to-nearest float32 -> bf16
+ *   jtfs_cast_bf16_rows        y[b][c][t] = bf16(x[b][c][t] * row_scale[c]) for x [B][C][T]
+ *                              (the decoder's per-channel input normalisation)
  *   jtfs_adam_update           Adam (0.9, 0.999, 1e-8, bias-corrected, 1-based step) on float32
  *                              parameters, also writing their bf16 copy if param_bf16 != NULL
  * Errors: JTFS_ERR_ARG (NULL pointer, sizes < 1 or too large), JTFS_ERR_CUDA.
@@ -300,6 +302,8 @@ int jtfs_gelu_forward(const float* z, uint16_t* h, int64_t n, void* stream);
 int jtfs_gelu_backward(const float* dh, const float* z, float* dz, int64_t n,
                        void* stream);
 int jtfs_cast_bf16(const float* x, uint16_t* y, int64_t n, void* stream);
+int jtfs_cast_bf16_rows(const float* x, const float* row_scale, uint16_t* y,
+                        int B, int C, int64_t T, void* stream);
 int jtfs_adam_update(float* param, const float* grad, float* m, float* v,
                      uint16_t* param_bf16, int64_t n, float lr, int step,
                      void* stream);

@@ -49,6 +49,7 @@ SIGNATURES = {
     "jtfs_gelu_forward": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
     "jtfs_gelu_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "jtfs_cast_bf16": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
+    "jtfs_cast_bf16_rows": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int64, c_void_p]),
     "jtfs_adam_update": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_int,
                                  c_void_p]),
     "jtfs_profile_stage": (c_int, [c_void_p, c_int, POINTER(c_void_p), c_int]),

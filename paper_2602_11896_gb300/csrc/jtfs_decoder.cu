@@ -232,6 +232,12 @@ __global__ void k_cast_bf16(const float* __restrict__ x, uint16_t* __restrict__ 
   if (i < n) y[i] = f2bf(x[i]);
 }
 
+__global__ void k_cast_bf16_rows(const float* __restrict__ x, const float* __restrict__ s, uint16_t* __restrict__ y,
+                                 int C, int64_t T, int64_t n) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = f2bf(x[i] * s[(i / T) % C]);
+}
+
 __global__ void k_adam_params(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                               float* __restrict__ v, uint16_t* __restrict__ pb, int64_t n, float lr, float c1,
                               float c2) {
@@ -320,6 +326,14 @@ extern "C" int jtfs_gelu_backward(const float* dh, const float* z, float* dz, in
 extern "C" int jtfs_cast_bf16(const float* x, uint16_t* y, int64_t n, void* stream) {
   if (!x || !y || n < 0) return JTFS_ERR_ARG;
   if (n) k_cast_bf16<<<blocks(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n);
+  return ok();
+}
+
+extern "C" int jtfs_cast_bf16_rows(const float* x, const float* row_scale, uint16_t* y, int B, int C, int64_t T,
+                                   void* stream) {
+  if (!x || !row_scale || !y || B < 0 || C < 1 || T < 0) return JTFS_ERR_ARG;
+  const int64_t n = static_cast<int64_t>(B) * C * T;
+  if (n) k_cast_bf16_rows<<<blocks(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, row_scale, y, C, T, n);
   return ok();
 }
 

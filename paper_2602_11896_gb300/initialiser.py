@@ -2,7 +2,8 @@
 
 Six transposed 1-D convolutions (stride 2, kernel 9; 128 channels; GELU
 between layers) map the Phi of a clip, read as (rows of Phi) channels x
-(frames) time steps, to N = frames * 2^6 samples.  With T = 2^6 this is
+(frames) time steps and scaled per channel (``row_scale``), to
+N = frames * 2^6 samples.  With T = 2^6 this is
 exactly the clip length.  Operands are BF16 and products accumulate in FP32
 on the tensor cores (library kernels ``jtfs_convt_*``); parameters are kept
 in FP32 and updated with the library's Adam kernel.  It is trained with the
@@ -17,7 +18,7 @@ from __future__ import annotations
 import ctypes
 import math
 from ctypes import c_void_p
-from typing import List, Optional
+from typing import List, Optional, Tuple
 
 import numpy as np
 import torch
@@ -43,7 +44,7 @@ class Decoder:
     """
 
     def __init__(self, in_channels: int, frames: int, channels: int = 128, layers: int = 6, seed: int = 0,
-                 in_scale: Optional[np.ndarray] = None, device: str = "cuda"):
+                 row_scale: Optional[np.ndarray] = None, device: str = "cuda"):
         self._lib = _native.load()
         self.dims = [in_channels] + [channels] * (layers - 1) + [1]
         self.frames = frames
@@ -56,10 +57,12 @@ class Decoder:
             ci, co = self.dims[li], self.dims[li + 1]
             std = math.sqrt(2.0 / (ci * KERNEL / 2.0))
             w = rng.standard_normal((ci, co, KERNEL)) * std
-            if li == 0 and in_scale is not None:
-                w = w / np.asarray(in_scale, dtype=np.float64)[:, None, None]
             self.w.append(torch.tensor(w, dtype=torch.float32, device=self.device))
             self.b.append(torch.zeros(co, dtype=torch.float32, device=self.device))
+        scale = np.ones(in_channels) if row_scale is None else np.asarray(row_scale, dtype=np.float64)
+        if scale.shape != (in_channels,):
+            raise ValueError("row_scale must have one entry per input channel")
+        self.row_scale = torch.tensor(scale, dtype=torch.float32, device=self.device)
         self._alloc_state()
 
     def _alloc_state(self):
@@ -88,7 +91,8 @@ class Decoder:
         phi = phi.contiguous()
         B, _, T = phi.shape
         h = torch.empty(phi.shape, dtype=torch.int16, device=self.device)
-        _native.check(self._lib.jtfs_cast_bf16(_p(phi), _p(h), phi.numel(), _s()), "jtfs_cast_bf16")
+        _native.check(self._lib.jtfs_cast_bf16_rows(_p(phi), _p(self.row_scale), _p(h), B, self.dims[0], T, _s()),
+                      "jtfs_cast_bf16_rows")
         self._h, self._z = [h], []
         for li in range(self.layers):
             ci, co = self.dims[li], self.dims[li + 1]
@@ -109,7 +113,7 @@ class Decoder:
         return out.reshape(B, T)
 
     def backward(self, dy: torch.Tensor) -> None:
-        """Accumulate parameter gradients (into gw, gb) from dL/dy [B][N] of the last forward."""
+        """Parameter gradients (written into gw, gb) from dL/dy [B][N] of the last forward."""
         if not self._h:
             raise RuntimeError("backward needs a forward with keep=True")
         B = dy.shape[0]
@@ -145,7 +149,7 @@ class Decoder:
                           "jtfs_adam_update")
 
     def state_dict(self) -> dict:
-        d = {"dims": np.array(self.dims), "frames": np.array(self.frames)}
+        d = {"dims": np.array(self.dims), "frames": np.array(self.frames), "row_scale": self.row_scale.cpu().numpy()}
         for li in range(self.layers):
             d[f"w{li}"] = self.w[li].cpu().numpy()
             d[f"b{li}"] = self.b[li].cpu().numpy()
@@ -158,9 +162,117 @@ class Decoder:
     def load(cls, path: str, device: str = "cuda") -> "Decoder":
         d = np.load(path)
         dims = [int(v) for v in d["dims"]]
-        dec = cls(dims[0], int(d["frames"]), channels=dims[1], layers=len(dims) - 1, device=device)
+        dec = cls(dims[0], int(d["frames"]), channels=dims[1], layers=len(dims) - 1, row_scale=d["row_scale"],
+                  device=device)
         for li in range(dec.layers):
             dec.w[li] = torch.tensor(d[f"w{li}"], device=dec.device)
             dec.b[li] = torch.tensor(d[f"b{li}"], device=dec.device)
         dec._alloc_state()
         return dec
+
+
+def phi_shape(plan) -> Tuple[int, int]:
+    """(rows, frames) of one clip's Phi: every block of the layout is rows of N/T frames."""
+    frames = plan.info["n_frames"]
+    return plan.phi_size // frames, frames
+
+
+def channel_scale(phi: torch.Tensor, floor: float = 1e-6) -> np.ndarray:
+    """1 / RMS of each Phi row over a sample of clips ([B][rows][frames]); rows with
+    RMS below ``floor`` times the largest are clamped there."""
+    rms = phi.double().pow(2).mean(dim=(0, 2)).sqrt().cpu().numpy()
+    return 1.0 / np.maximum(rms, floor * rms.max())
+
+
+def train(dec: Decoder, plan, clips: torch.Tensor, steps: int, lr: float = 1e-3, lr_min: float = 1e-5,
+          seed: int = 0, log_every: int = 50, log=print) -> List[Tuple[int, float]]:
+    """Fit the decoder with the JTFS loss: for a batch of clips x, minimise
+    sum ||Phi(dec(Phi x)) - Phi x||^2 (Eq. 5) over the decoder's parameters.
+
+    ``clips`` [n][N] float32 on the device; ``plan`` a JTFSPlan whose batch is the
+    training batch.  Cosine learning-rate decay from ``lr`` to ``lr_min``.
+    Returns (step, mean loss per clip) every ``log_every`` steps.
+    """
+    B = plan.batch
+    rows, frames = phi_shape(plan)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    order = torch.randperm(clips.shape[0], generator=g)
+    pos, history, acc, cnt = 0, [], torch.zeros((), device=clips.device), 0
+    ws = plan.workspace(clips.device)
+    for it in range(steps):
+        if pos + B > order.numel():
+            order, pos = torch.randperm(clips.shape[0], generator=g), 0
+        idx = order[pos:pos + B].to(clips.device)
+        pos += B
+        x = clips.index_select(0, idx)
+        phi_t = plan.forward(x, workspace=ws)
+        y = dec.forward(phi_t.view(B, rows, frames))
+        loss, grad = plan.loss_grad(y, phi_t, workspace=ws)
+        dec.backward(grad)
+        dec.step(lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * it / max(steps - 1, 1))))
+        acc += loss.sum()
+        cnt += B
+        if (it + 1) % log_every == 0 or it + 1 == steps:
+            history.append((it + 1, float(acc) / cnt))
+            log(f"step {it + 1}/{steps}  mean JTFS loss per clip {history[-1][1]:.5g}")
+            acc.zero_()
+            cnt = 0
+    return history
+
+
+def propose(dec: Decoder, plan, phi_target: torch.Tensor) -> torch.Tensor:
+    """Initial waveforms [B][N] for the targets' Phi [B][phi_size]."""
+    rows, frames = phi_shape(plan)
+    return dec.forward(phi_target.view(-1, rows, frames), keep=False).contiguous()
+
+
+def descend(plan, y: torch.Tensor, phi_target: torch.Tensor, steps: int, lr: float) -> Tuple[torch.Tensor, float]:
+    """``steps`` Adam metamer steps from y (modified in place); returns the loss of
+    every step [steps][B] (loss of the iterate before each update) and the device
+    time in ms."""
+    m = torch.zeros_like(y)
+    v = torch.zeros_like(y)
+    losses = torch.empty(steps, plan.batch, device=y.device)
+    ws = plan.workspace(y.device)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(steps):
+        plan.metamer_step(y, phi_target, m, v, s + 1, lr, loss_out=losses[s], workspace=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return losses, e0.elapsed_time(e1)
+
+
+def compare_initialisations(dec: Decoder, plan, phi_target: torch.Tensor, noise: torch.Tensor, steps: int = 200,
+                            lr: float = 0.1) -> dict:
+    """Metamers of one batch of targets from white noise and from the decoder's
+    proposal, each refined by ``steps`` Adam steps.  Reports, for the proposal,
+    the first step whose batch loss is at or below the noise run's final loss
+    and the wall time to get there (decoder forward included)."""
+    y_plain = noise.clone()
+    loss_plain, ms_plain = descend(plan, y_plain, phi_target, steps, lr)
+    final_plain = float(plan.loss_grad(y_plain, phi_target, need_grad=False)[0].sum())
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    y = propose(dec, plan, phi_target)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_decoder = e0.elapsed_time(e1)
+    loss_learned, ms_learned = descend(plan, y, phi_target, steps, lr)
+    final_learned = float(plan.loss_grad(y, phi_target, need_grad=False)[0].sum())
+    curve = loss_learned.sum(dim=1).cpu().numpy()
+    hit = np.nonzero(curve <= final_plain)[0]
+    reached = int(hit[0]) if hit.size else None
+    ms_step = ms_learned / steps
+    return {
+        "steps": steps, "lr": lr, "batch": plan.batch,
+        "plain_initial_loss": float(loss_plain[0].sum()), "plain_final_loss": final_plain,
+        "plain_ms": ms_plain,
+        "learned_initial_loss": float(curve[0]), "learned_final_loss": final_learned,
+        "decoder_ms": ms_decoder,
+        "learned_steps_to_plain_final": reached,
+        "learned_ms_to_plain_final": None if reached is None else ms_decoder + reached * ms_step,
+        "plain_curve": loss_plain.sum(dim=1).cpu().tolist(), "learned_curve": curve.tolist(),
+    }

@@ -70,7 +70,19 @@ WORKLOADS: Dict[str, Workload] = {
         T=2 ** 13, F=16, batch=4, sr=22050.0,
         target_seeds=list(range(400, 404)), init_seeds=list(range(500, 504)),
         target_kind="notes"),
+    # Held-out batch for the learned initialiser: 32 clips of 2^16 samples at 8 kHz,
+    # the single-clip tone parameters; training clips use seeds TRAIN_SEED0 + i.
+    "tones8k_b32_n65536": Workload(
+        name="tones8k_b32_n65536", N=2 ** 16, J=6, Q=8, Q2=1, J_fr=3, Q_fr=1,
+        T=2 ** 6, F=2 ** 2, batch=32, sr=8000.0,
+        target_seeds=[2_000_000 + i for i in range(32)], init_seeds=[3_000_000 + i for i in range(32)],
+        target_kind="tones"),
 }
+
+# Seeds of the decoder's training clips: TRAIN_SEED0 + i, i < 20000 (disjoint from
+# every target and initialisation seed above).
+TRAIN_SEED0 = 1_000_000
+TRAIN_CLIPS = 20_000
 
 
 def get_workload(name: str) -> Workload:
