@@ -662,6 +662,7 @@ struct PoolArgs {
   const int64_t* phi2_off;
   const float* taps;
   const int64_t* tap_off;
+  const int* pool_w;  // per active n2: banded half-width, 0 = dense
 };
 
 // Both directions are dense products with the tap matrix
@@ -749,6 +750,7 @@ k_pool_reduce(PoolArgs A, const float* __restrict__ part, float* __restrict__ ph
   const int rf = static_cast<int>(idx % per_a);
   const int r = rf / A.n_frames, f = rf % A.n_frames;
   const int a = static_cast<int>(ba % A.n_active), b = static_cast<int>(ba / A.n_active);
+  if (A.pool_w[a]) return;  // written by k_pool_fwd_band
   const int L = 1 << (A.logN - A.s2[a]);
   const int nsplit = (L + split_len - 1) / split_len;
   // tiles of (b, a) start at tile0[ba]; ordered by row tile then split
@@ -757,6 +759,70 @@ k_pool_reduce(PoolArgs A, const float* __restrict__ part, float* __restrict__ ph
   float acc = 0.f;
   for (int sp = 0; sp < nsplit; ++sp) acc += pp[static_cast<int64_t>(sp) * kPoolRows * A.n_frames];
   phi[static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a] + static_cast<int64_t>(r) * A.n_frames + f] = acc;
+}
+
+// Banded forward: a CTA owns 64 rows x 32 frames f0 .. f0+31 of one (clip,
+// n2) and sums over the window t in [f0 D - W, (f0+31) D + W] (mod L), the
+// only samples whose taps reach those frames (taps beyond W are below 2^-40 of
+// the peak).  Writes Phi2 directly.  Thread mapping as k_pool_fwd<4>.
+__global__ void __launch_bounds__(kThreads)
+k_pool_fwd_band(PoolArgs A, const float* __restrict__ V2, float* __restrict__ phi, const int4* __restrict__ tiles) {
+  constexpr int FPT = 4;
+  __shared__ float Vs[kPoolK][kPoolRows + 1];
+  __shared__ float Gs[kPoolK][8 * FPT];
+  const int4 tl = tiles[blockIdx.x];  // (clip, active n2, row tile, frame block)
+  const int b = tl.x, a = tl.y;
+  const int f0 = tl.w * 8 * FPT;
+  const int s = A.s2[a];
+  const int lL = A.logN - s, L = 1 << lL;
+  const int D = 1 << (A.lT - s);
+  const int W = A.pool_w[a];
+  const int rows = A.n_beta2 * A.R_out;
+  const int r0 = tl.z * kPoolRows;
+  const int tbeg = f0 * D - W, tend = (f0 + 8 * FPT - 1) * D + W + 1;
+  const float* v = V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
+  const float* g = A.taps + A.tap_off[s];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  float acc[2][FPT];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < FPT; ++j) acc[i][j] = 0.f;
+  for (int t0 = tbeg; t0 < tend; t0 += kPoolK) {
+    for (int i = threadIdx.x; i < kPoolRows * kPoolK; i += blockDim.x) {
+      const int rr = i / kPoolK, tt = i % kPoolK;
+      const int r = r0 + rr;
+      Vs[tt][rr] = (r < rows && t0 + tt < tend) ? v[static_cast<int64_t>(r) * L + ((t0 + tt) & (L - 1))] : 0.f;
+    }
+    for (int i = threadIdx.x; i < kPoolK * 8 * FPT; i += blockDim.x) {
+      const int tt = i % kPoolK, ff = i / kPoolK;
+      const int f = f0 + ff;
+      Gs[tt][ff] = (f < A.n_frames && t0 + tt < tend) ? g[(f * D - (t0 + tt)) & (L - 1)] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int tt = 0; tt < kPoolK; ++tt) {
+      const float v0 = Vs[tt][ty], v1 = Vs[tt][ty + 32];
+#pragma unroll
+      for (int j = 0; j < FPT; ++j) {
+        const float gg = Gs[tt][tx + 8 * j];
+        acc[0][j] += v0 * gg;
+        acc[1][j] += v1 * gg;
+      }
+    }
+    __syncthreads();
+  }
+  float* out = phi + static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int r = r0 + ty + 32 * i;
+    if (r >= rows) continue;
+#pragma unroll
+    for (int j = 0; j < FPT; ++j) {
+      const int f = f0 + tx + 8 * j;
+      if (f < A.n_frames) out[static_cast<int64_t>(r) * A.n_frames + f] = acc[i][j];
+    }
+  }
 }
 
 // Adjoint: a CTA owns 64 rows x 64 time samples; thread (ty = tid / 16,
@@ -775,21 +841,26 @@ k_pool_adj(PoolArgs A, const float* __restrict__ dphi, float* __restrict__ dV2, 
   const float* dp = dphi + static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a];
   const float* g = A.taps + A.tap_off[s];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  // Frames whose taps reach [t0, t0 + 64): all of them (dense), or the band
+  // f D in [t0 - W, t0 + 63 + W], taken mod n_frames (banded).
+  const int W = A.pool_w[a];
+  const int fbeg = W ? -((W - t0 + D - 1) >> (A.lT - s)) : 0;  // floor((t0 - W) / D); t0 - W may be < 0
+  const int fend = W ? ((t0 + kPoolT - 1 + W) >> (A.lT - s)) + 1 : A.n_frames;
   float acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int f0 = 0; f0 < A.n_frames; f0 += 32) {
+  for (int f0 = fbeg; f0 < fend; f0 += 32) {
     for (int i = threadIdx.x; i < kPoolRows * 32; i += blockDim.x) {
       const int rr = i / 32, ff = i % 32;
       const int r = r0 + rr, f = f0 + ff;
-      Ps[ff][rr] = (r < rows && f < A.n_frames) ? dp[static_cast<int64_t>(r) * A.n_frames + f] : 0.f;
+      Ps[ff][rr] = (r < rows && f < fend) ? dp[static_cast<int64_t>(r) * A.n_frames + (f & (A.n_frames - 1))] : 0.f;
     }
     for (int i = threadIdx.x; i < 32 * kPoolT; i += blockDim.x) {
       const int ff = i / kPoolT, tt = i % kPoolT;
       const int f = f0 + ff, t = t0 + tt;
-      Gs[ff][tt] = (f < A.n_frames && t < L) ? g[(f * D - t) & (L - 1)] : 0.f;
+      Gs[ff][tt] = (f < fend && t < L) ? g[(f * D - t) & (L - 1)] : 0.f;
     }
     __syncthreads();
 #pragma unroll 4
@@ -1013,6 +1084,7 @@ PoolArgs pool_args(const Plan& p) {
   A.v2_off = p.d_v2_off;
   A.phi2_off = p.d_phi2_off;
   A.taps = p.d_taps;
+  A.pool_w = p.d_pool_w;
   A.tap_off = p.d_tap_off;
   return A;
 }
@@ -1131,15 +1203,22 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
                 static_cast<unsigned>((p.n_frames + 8 * fpt - 1) / (8 * fpt)));
       prof_begin(p, JTFS_STAGE_POOL_FWD, s);
       const int4* pt = p.d_pool_fwd_tiles[si];
-      switch (fpt) {
-        case 16: k_pool_fwd<16><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
-        case 8: k_pool_fwd<8><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
-        case 4: k_pool_fwd<4><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
-        case 2: k_pool_fwd<2><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
-        default: k_pool_fwd<1><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
+      if (!p.pool_band_tiles.empty()) {
+        k_pool_fwd_band<<<static_cast<unsigned>(p.pool_band_tiles.size()), kThreads, 0, s>>>(PA, w.V2, phi,
+                                                                                            p.d_pool_band_tiles);
+        JTFS_TRY(check_launch());
       }
-      JTFS_TRY(check_launch());
-      {
+      if (grid.x) {
+        switch (fpt) {
+          case 16: k_pool_fwd<16><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
+          case 8: k_pool_fwd<8><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
+          case 4: k_pool_fwd<4><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
+          case 2: k_pool_fwd<2><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
+          default: k_pool_fwd<1><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
+        }
+        JTFS_TRY(check_launch());
+      }
+      if (grid.x) {
         const int64_t total = int64_t(p.batch) * p.n_active * p.n_beta2 * p.R_out * p.n_frames;
         k_pool_reduce<<<static_cast<unsigned>((total + kThreads - 1) / kThreads), kThreads, 0, s>>>(
             PA, w.part, phi, p.d_pool_tile0[si], split_len, total);

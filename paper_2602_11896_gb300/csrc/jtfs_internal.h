@@ -143,7 +143,12 @@ struct Plan {
   std::vector<FreqChunk> chunks1, chunks2;
   std::vector<int4> pool_tiles;  // adjoint time pooling: (clip, active n2, row tile, time tile)
   std::vector<int4> pool_fwd_tiles[3];  // forward time pooling per split: (clip, active n2, row tile, split)
-  std::vector<int> pool_tile0[3];       // per split and (clip, active n2): first forward tile  // first order (phi_F, +xi) / second order (all)
+  std::vector<int> pool_tile0[3];       // per split and (clip, active n2): first forward tile
+  // Banded time pooling: per active n2 the tap half-width W (level samples)
+  // beyond which g_s is below 2^-40 g_s[0], or 0 where the dense product is
+  // used; forward tiles of the banded levels: (clip, active n2, row tile, 32-frame block).
+  std::vector<int> pool_w;
+  std::vector<int4> pool_band_tiles;
   // Frequential tables on the N_fr grid, one row of N_fr floats each:
   // rows [0, n_beta2): psi_beta; row n_beta2: phi_F; row n_beta2 + 1 + k:
   // phi_F periodised onto N_fr / 2^k bins (k = 0 .. log2 F).
@@ -183,6 +188,8 @@ struct Plan {
   mutable int tune_split = 1;
   mutable int tune_fft_points = 4096;
   const int* d_s2 = nullptr;          // per active index
+  const int* d_pool_w = nullptr;      // per active index
+  const int4* d_pool_band_tiles = nullptr;
   const int* d_n1max_act = nullptr;   // per active index
   const int64_t* d_y2_off = nullptr;  // per active index
   const int64_t* d_v2_off = nullptr;

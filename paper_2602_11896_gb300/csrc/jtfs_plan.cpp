@@ -360,6 +360,32 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
           for (int tt = 0; tt < (L + 63) / 64; ++tt) p.pool_tiles.push_back(make_int4(b, a, rt, tt));
       }
   }
+  // Banded pooling where the taps' reach is small against the circle: g_s[d] /
+  // g_s[0] = exp(-c (2^s d)^2) (c = 2 pi^2 sigma_T^2) is below 2^-40 once
+  // 2^s |d| > sqrt(40 ln 2 / c), so a frame only sees W = floor(that / 2^s) + 1
+  // level samples on either side.  Chosen when a 32-frame window (forward) and
+  // the frames of a 64-sample tile (adjoint) stay within the circle.
+  p.pool_w.assign(p.n_active, 0);
+  {
+    const double c = 2.0 * M_PI * M_PI * p.phiT.sigma * p.phiT.sigma;
+    const double reach = std::sqrt(40.0 * std::log(2.0) / c);
+    for (int a = 0; a < p.n_active; ++a) {
+      const int s = p.s2[a];
+      const int64_t L = N >> s, D = int64_t(1) << (p.lT - s);
+      const int64_t W = static_cast<int64_t>(std::floor(reach / double(int64_t(1) << s))) + 1;
+      if (2 * W + 32 * D <= L / 2 && (63 + 2 * W) / D + 2 <= p.n_frames) p.pool_w[a] = static_cast<int>(W);
+    }
+  }
+  p.pool_band_tiles.clear();
+  {
+    const int rows = p.n_beta2 * p.R_out;
+    for (int b = 0; b < B; ++b)
+      for (int a = 0; a < p.n_active; ++a) {
+        if (!p.pool_w[a]) continue;
+        for (int rt = 0; rt < (rows + 63) / 64; ++rt)
+          for (int fb = 0; fb < (p.n_frames + 31) / 32; ++fb) p.pool_band_tiles.push_back(make_int4(b, a, rt, fb));
+      }
+  }
   for (int si = 0; si < 3; ++si) {
     p.pool_fwd_tiles[si].clear();
     p.pool_tile0[si].clear();
@@ -369,6 +395,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
         const int L = static_cast<int>(N >> p.s2[a]);
         const int nsplit = (L + kPoolSplits[si] - 1) / kPoolSplits[si];
         p.pool_tile0[si].push_back(static_cast<int>(p.pool_fwd_tiles[si].size()));
+        if (p.pool_w[a]) continue;
         for (int rt = 0; rt < (rows + 63) / 64; ++rt)
           for (int sp = 0; sp < nsplit; ++sp) p.pool_fwd_tiles[si].push_back(make_int4(b, a, rt, sp));
       }
@@ -443,6 +470,8 @@ int upload_plan(Plan& p) {
     o_pt0[si] = put(p.pool_tile0[si].data(), p.pool_tile0[si].size() * sizeof(int));
   }
   const size_t o_s2 = put(p.s2.data(), p.s2.size() * sizeof(int));
+  const size_t o_pw = put(p.pool_w.data(), p.pool_w.size() * sizeof(int));
+  const size_t o_pbt = put(p.pool_band_tiles.data(), p.pool_band_tiles.size() * sizeof(int4));
   const size_t o_n1m = put(n1max_act.data(), n1max_act.size() * sizeof(int));
   const size_t o_y2o = put(p.y2_off.data(), p.y2_off.size() * sizeof(int64_t));
   const size_t o_v2o = put(p.v2_off.data(), p.v2_off.size() * sizeof(int64_t));
@@ -482,6 +511,8 @@ int upload_plan(Plan& p) {
     p.d_pool_tile0[si] = reinterpret_cast<const int*>(at(o_pt0[si]));
   }
   p.d_s2 = reinterpret_cast<const int*>(at(o_s2));
+  p.d_pool_w = reinterpret_cast<const int*>(at(o_pw));
+  p.d_pool_band_tiles = reinterpret_cast<const int4*>(at(o_pbt));
   p.d_n1max_act = reinterpret_cast<const int*>(at(o_n1m));
   p.d_y2_off = reinterpret_cast<const int64_t*>(at(o_y2o));
   p.d_v2_off = reinterpret_cast<const int64_t*>(at(o_v2o));
