@@ -52,8 +52,9 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip autotuning at set-up")
-    ap.add_argument("--workload", default="chirps", choices=["chirps", "uneven64"],
-                    help="chirps: the 8 x 2^16 benchmark (default); uneven64: 64 clips of 2^14..2^18 samples")
+    ap.add_argument("--workload", default="chirps", choices=["chirps", "uneven64", "initialiser"],
+                    help="chirps: the 8 x 2^16 benchmark (default); uneven64: 64 clips of 2^14..2^18 samples; "
+                         "initialiser: 32 tone clips of 2^16 samples from the learned decoder vs white noise")
     ap.add_argument("--batch", type=int, default=0,
                     help="clips per GPU (default: the workload's 8); smaller values only for ncu captures")
     return ap.parse_args()
@@ -258,8 +259,49 @@ def run_uneven(args):
     print(json.dumps(line), flush=True)
 
 
+def run_initialiser(args):
+    """32 held-out tone clips (2^16 samples, 8 kHz parameters): 200 Adam steps (lr 0.1) from white noise,
+    then from the trained decoder's proposal; wall time for the latter to reach the former's final loss."""
+    from paper_2602_11896_gb300 import JTFSPlan
+    from paper_2602_11896_gb300.initialiser import Decoder, compare_initialisations
+    wl = get_workload("tones8k_b32_n65536")
+    weights = os.path.join(ROOT, "paper_2602_11896_gb300", "weights", "decoder_tones8k_n65536.npz")
+    plan = JTFSPlan(**wl.params, batch=wl.batch)
+    dec = Decoder.load(weights)
+    phi_t = plan.forward(torch.tensor(wl.targets(), device="cuda"))
+    noise = torch.tensor(wl.inits(), device="cuda")
+    for _ in range(max(args.warmup, 1)):   # warm-up: one short run of each arm
+        compare_initialisations(dec, plan, phi_t, noise, steps=3)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev = compare_initialisations(dec, plan, phi_t, noise, steps=200, lr=0.1)
+    clk = clocks.stop()
+    line = {"metric": "learned-initialiser wall time to the noise run's 200-step loss", "unit": "ms",
+            "value": ev["learned_ms_to_plain_final"], "n_gpus": 1, "steps": 200, "warmup": max(args.warmup, 1),
+            "ms_per_step": ev["plain_ms"] / 200, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (decoder: bf16 operands, f32 accumulate)", "data": "synthetic",
+            "config": {"workload": wl.name, "batch": wl.batch, **wl.params, "sample_rate_hz": wl.sr,
+                       "decoder": "6 transposed convs, 128 channels, kernel 9, GELU; 801 x 1024 -> 65536",
+                       "train": "20k tone clips (seeds 1e6 + i), JTFS loss, 2500 Adam steps of 32",
+                       "l2": "each arm's 200 steps timed as one region; inputs and workspace exceed L2"},
+            "noise_ms_200_steps": ev["plain_ms"], "decoder_ms": ev["decoder_ms"],
+            "learned_steps_to_noise_final": ev["learned_steps_to_plain_final"],
+            "noise_loss": [ev["plain_initial_loss"], ev["plain_final_loss"]],
+            "learned_loss": [ev["learned_initial_loss"], ev["learned_final_loss"]],
+            "speedup_wall": (ev["plain_ms"] / ev["learned_ms_to_plain_final"]
+                             if ev["learned_ms_to_plain_final"] else None),
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "initialiser":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the chirps workload"}))
+            return
+        run_initialiser(args)
+        return
     if args.workload == "uneven64":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the chirps workload"}))
