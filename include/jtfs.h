@@ -267,43 +267,74 @@ int jtfs_set_tuning(jtfs_plan_t plan, const int64_t* choice, int n);
 int jtfs_get_tuning(jtfs_plan_t plan, int64_t* choice, int n);
 
 /*
- * Learned initialiser layers (BF16 operands as uint16_t bit patterns, FP32
- * accumulation on the tensor cores).  A transposed 1-D convolution with stride
- * 2, kernel 9, padding 4 and output padding 1 maps x [B][Ci][T] to
- * y [B][Co][2T]:  y[b][co][t] = bias[co] + sum over (ci, u, k) with
- * t = 2u - 4 + k of x[b][ci][u] W[ci][co][k],  W [Ci][Co][9].  The paper has
- * no such network: it refines a noise initialisation (§2.3); this decoder
- * proposes the initial waveform from the target's Phi instead.  All pointers
- * are device pointers; calls are asynchronous on `stream`.
- *   jtfs_convt_forward         y (float32) from x, W (bf16) and bias (float32, may be NULL)
- *   jtfs_convt_backward_data   dx [B][Ci][T] (float32) from dy [B][Co][2T] (bf16) and W
- *   jtfs_convt_backward_weight dW [Ci][Co][9] (float32) from x and dy (bf16); db [Co] from
- *                              dy_f32 (float32 copy of dy; both may be NULL); needs a workspace
- *                              of jtfs_convt_weight_workspace_bytes(B, Ci, Co, T) bytes
- *   jtfs_gelu_forward          h = GELU(z) (bf16), GELU(z) = z (1 + erf(z/sqrt 2)) / 2
- *   jtfs_gelu_backward         dz = dh GELU'(z) (float32)
+ * Learned initialiser layers.  The paper has no such network: it refines a
+ * noise initialisation (Sec. 2.3); this decoder proposes the initial waveform
+ * from the target's Phi instead.  A layer is a transposed 1-D convolution with
+ * stride 2, kernel 9, padding 4 and output padding 1, mapping x [B][T][Ci] to
+ * z [B][2T][Co] (activations channels-last):
+ *   z[b][t][co] = bias[co] + sum over (ci, u, k) with t = 2u - 4 + k of x[b][u][ci] W[ci][co][k],
+ * W [Ci][Co][9] float32 (the master copy).  BF16 tensors are uint16_t bit
+ * patterns.  Hidden layers have Co = 128 and run on the tensor cores (BF16
+ * operands, FP32 accumulation); the output layer (Ci = 128, Co = 1) runs on
+ * the FMA units.  Input widths are padded to Cip = jtfs_convt_padded_channels(Ci)
+ * (a multiple of 128) with zero channels.  All pointers are device pointers,
+ * 16-byte aligned; calls are asynchronous on `stream`.
+ *   jtfs_convt_pack_input      x [B][T][Cip] bf16 = phi [B][C][T] * row_scale[c] (zero for c >= C)
+ *   jtfs_convt_pack_weights    wf [256][5 Cip] bf16, wf[(p, co)][(j, ci)] = W[ci][co][2j + p] (0 if 2j+p > 8);
+ *                              wd [128][9 x 128] bf16, wd[ci][(k, co)] = W[ci][co][k] (only for Ci = 128;
+ *                              may be NULL).  Call after every update of W.
+ *   jtfs_convt_forward         z (float32, may be NULL) and h = GELU(z) (bf16, may be NULL) from x [B][T][Cip]
+ *   jtfs_convt_backward_data   g_prev[b][u][ci] = (sum over k, co of g[b][2u-4+k][co] W[ci][co][k]) * GELU'(zprev[b][u][ci])
+ *                              (the GELU' factor only when zprev != NULL), from g [B][2T][128] bf16;
+ *                              writes float32 and/or bf16 (either may be NULL); Ci = Co = 128
+ *   jtfs_convt_backward_weight dW [Ci][128][9] (float32) = sum over b, u of x[b][u][ci] g[b][2u-4+k][co],
+ *                              split over positions with a fixed-order reduction; workspace of
+ *                              jtfs_convt_weight_workspace_bytes(B, Cip, Co, T) bytes
+ *   jtfs_convt_bias_grad       db [128] = column sums of g [rows][128] (float32); workspace of
+ *                              jtfs_convt_bias_workspace_bytes(rows) bytes
+ *   jtfs_convt_out_forward     y [B][2T] (float32) from x [B][T][128] bf16, w [128][1][9], bias [1]
+ *   jtfs_convt_out_backward_data   as jtfs_convt_backward_data for the output layer, from dy [B][2T] float32
+ *   jtfs_convt_out_backward_weight dw [128][1][9] and db [1] (db may be NULL); workspace of
+ *                              jtfs_convt_out_workspace_bytes(B, T) bytes
+ *   jtfs_decoder_error         1 if a tensor-core kernel gave up waiting on one of its barriers since the
+ *                              last call (its outputs are then invalid), else 0; synchronous; clears the flag
  *   jtfs_cast_bf16             round-to-nearest float32 -> bf16
- *   jtfs_cast_bf16_rows        y[b][c][t] = bf16(x[b][c][t] * row_scale[c]) for x [B][C][T]
- *                              (the decoder's per-channel input normalisation)
  *   jtfs_adam_update           Adam (0.9, 0.999, 1e-8, bias-corrected, 1-based step) on float32
  *                              parameters, also writing their bf16 copy if param_bf16 != NULL
- * Errors: JTFS_ERR_ARG (NULL pointer, sizes < 1 or too large), JTFS_ERR_CUDA.
+ * Errors: JTFS_ERR_ARG (NULL pointer, unsupported width, misaligned pointer,
+ * sizes < 1 or too large), JTFS_ERR_CUDA.
  */
-int jtfs_convt_forward(const uint16_t* x, const uint16_t* w, const float* bias,
-                       float* y, int B, int Ci, int Co, int T, void* stream);
-int jtfs_convt_backward_data(const uint16_t* dy, const uint16_t* w, float* dx,
-                             int B, int Ci, int Co, int T, void* stream);
-size_t jtfs_convt_weight_workspace_bytes(int B, int Ci, int Co, int T);
-int jtfs_convt_backward_weight(const uint16_t* x, const uint16_t* dy,
-                               const float* dy_f32, float* dw, float* db, int B,
-                               int Ci, int Co, int T, void* workspace,
-                               void* stream);
-int jtfs_gelu_forward(const float* z, uint16_t* h, int64_t n, void* stream);
-int jtfs_gelu_backward(const float* dh, const float* z, float* dz, int64_t n,
+int jtfs_convt_padded_channels(int C);
+int jtfs_convt_pack_input(const float* phi, const float* row_scale, uint16_t* x,
+                          int B, int C, int T, void* stream);
+int jtfs_convt_pack_weights(const float* w, uint16_t* wf, uint16_t* wd, int Ci,
+                            int Co, void* stream);
+int jtfs_convt_forward(const uint16_t* x, const uint16_t* wf, const float* bias,
+                       float* z, uint16_t* h, int B, int Cip, int Co, int T,
                        void* stream);
+int jtfs_convt_backward_data(const uint16_t* g, const uint16_t* wd,
+                             const float* zprev, float* g_prev,
+                             uint16_t* g_prev_bf16, int B, int Ci, int Co,
+                             int T, void* stream);
+size_t jtfs_convt_weight_workspace_bytes(int B, int Cip, int Co, int T);
+int jtfs_convt_backward_weight(const uint16_t* x, const uint16_t* g, float* dw,
+                               int B, int Ci, int Cip, int Co, int T,
+                               void* workspace, void* stream);
+size_t jtfs_convt_bias_workspace_bytes(int64_t rows);
+int jtfs_convt_bias_grad(const float* g, float* db, int64_t rows, int Co,
+                         void* workspace, void* stream);
+int jtfs_convt_out_forward(const uint16_t* x, const float* w, const float* bias,
+                           float* y, int B, int Ci, int T, void* stream);
+int jtfs_convt_out_backward_data(const float* dy, const float* w,
+                                 const float* zprev, float* g_prev,
+                                 uint16_t* g_prev_bf16, int B, int Ci, int T,
+                                 void* stream);
+size_t jtfs_convt_out_workspace_bytes(int B, int T);
+int jtfs_convt_out_backward_weight(const uint16_t* x, const float* dy, float* dw,
+                                   float* db, int B, int Ci, int T,
+                                   void* workspace, void* stream);
+int jtfs_decoder_error(void);
 int jtfs_cast_bf16(const float* x, uint16_t* y, int64_t n, void* stream);
-int jtfs_cast_bf16_rows(const float* x, const float* row_scale, uint16_t* y,
-                        int B, int C, int64_t T, void* stream);
 int jtfs_adam_update(float* param, const float* grad, float* m, float* v,
                      uint16_t* param_bf16, int64_t n, float lr, int step,
                      void* stream);

@@ -41,15 +41,26 @@ SIGNATURES = {
                               POINTER(c_int64), c_int]),
     "jtfs_set_tuning": (c_int, [c_void_p, POINTER(c_int64), c_int]),
     "jtfs_get_tuning": (c_int, [c_void_p, POINTER(c_int64), c_int]),
-    "jtfs_convt_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p]),
-    "jtfs_convt_backward_data": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p]),
+    "jtfs_convt_padded_channels": (c_int, [c_int]),
+    "jtfs_convt_pack_input": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
+    "jtfs_convt_pack_weights": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "jtfs_convt_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int,
+                                   c_void_p]),
+    "jtfs_convt_backward_data": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int,
+                                         c_int, c_void_p]),
     "jtfs_convt_weight_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int]),
-    "jtfs_convt_backward_weight": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int,
-                                           c_int, c_void_p, c_void_p]),
-    "jtfs_gelu_forward": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
-    "jtfs_gelu_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
+    "jtfs_convt_backward_weight": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int,
+                                           c_void_p, c_void_p]),
+    "jtfs_convt_bias_workspace_bytes": (c_size_t, [c_int64]),
+    "jtfs_convt_bias_grad": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_void_p, c_void_p]),
+    "jtfs_convt_out_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
+    "jtfs_convt_out_backward_data": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int,
+                                             c_void_p]),
+    "jtfs_convt_out_workspace_bytes": (c_size_t, [c_int, c_int]),
+    "jtfs_convt_out_backward_weight": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int,
+                                               c_void_p, c_void_p]),
+    "jtfs_decoder_error": (c_int, []),
     "jtfs_cast_bf16": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
-    "jtfs_cast_bf16_rows": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int64, c_void_p]),
     "jtfs_adam_update": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_int,
                                  c_void_p]),
     "jtfs_profile_stage": (c_int, [c_void_p, c_int, POINTER(c_void_p), c_int]),

@@ -1,241 +1,559 @@
 // Learned initialiser layers: transposed 1-D convolution (stride 2, kernel 9,
-// padding 4, output padding 1), its data and weight gradients, GELU, and an
-// Adam update, on BF16 operands with FP32 accumulation.
+// padding 4, output padding 1) with its data and weight gradients, BF16
+// operands and FP32 accumulation, activations channels-last ([B][T][C]).
 //
-// The three convolution products are implicit GEMMs run on the tensor cores
-// with mma.sync m16n8k16 (BF16 in, FP32 accumulate).  A CTA of 4 warps owns a
-// 64 x 64 output tile; operands are gathered through small functors (zero
-// outside the signal) into shared memory, 32 reduction steps at a time.
+// Output time t = 2v + p (parity p) of a layer sees input samples v + 2 - j:
+//   z[b][2v+p][co] = bias[co] + sum_{j<5, ci} x[b][v+2-j][ci] W[ci][co][2j+p]   (2j+p <= 8)
+//   dx[b][u][ci]   = sum_{k<9, co} g[b][2u-4+k][co] W[ci][co][k]
+//   dW[ci][co][k]  = sum_{b, u} x[b][u][ci] g[b][2u-4+k][co]
+// With g [B][2T][C] read as [B][T][2C] (row u holds times 2u and 2u+1), time
+// 2u-4+k is row u-2+m, half q, for k = 2m+q.  Every shift is therefore a shift
+// of whole rows, which a TMA tile load takes as its row coordinate (rows outside
+// the clip read as zero), so the three products are GEMMs on the 5th-generation
+// tensor cores with no gather:
+//   forward   M = 128 positions v, N = 256 = (p, co), K = (ci block, j)
+//   data grad M = 128 positions u, N = 128 = ci,      K = (k, co block)
+//   weight    M = 128 channels ci, N = 256 = (q, co), K = positions (split, fixed-order reduction)
+// One CTA of 4 warps per output tile: thread 0 issues TMA loads into a ring of
+// shared-memory stages, thread 32 issues tcgen05.mma (accumulator in TMEM) and
+// frees each stage with tcgen05.commit, then all four warps read the
+// accumulator back with tcgen05.ld and run the fused epilogue (bias + GELU,
+// GELU', or the split-K partial store).  Every mbarrier wait is bounded; a
+// wait that runs out sets an abort flag, the CTA drains and frees its TMEM,
+// and jtfs_decoder_error() reports it.
 //
-//   forward, parity p of the output time t = 2v + p:
-//     y[b][co][2v+p] = bias[co] + sum_{ci, j<5} W[ci][co][p + 8 - 2j] x[b][ci][v + j - 2]
-//   data gradient:
-//     dx[b][ci][u] = sum_{co, k<9} W[ci][co][k] dy[b][co][2u - 4 + k]
-//   weight gradient (split over b, u; fixed-order reduction):
-//     dW[ci][co][k] = sum_{b, u} x[b][ci][u] dy[b][co][2u - 4 + k]
+// The output layer (128 -> 1 channel) is too narrow for the tensor cores and
+// runs as plain FMA kernels.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "jtfs.h"
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 32, kGemmThreads = 128;
-constexpr int kDwSplit = 4096;  // reduction length per CTA of the weight gradient
+constexpr int kC = 128;                    // hidden width (tensor-core layers)
+constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier waits (>= 64 ns each)
 
-__device__ __forceinline__ uint16_t f2bf(float f) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+__device__ int g_decoder_err;
+
+__device__ __forceinline__ uint16_t f2bf(float f) { return __bfloat16_as_ushort(__float2bfloat16_rn(f)); }
+__device__ __forceinline__ float bf2f(uint16_t u) { return __bfloat162float(__ushort_as_bfloat16(u)); }
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
+// ---------------------------------------------------------------------------
+// PTX wrappers: mbarrier, TMA, tcgen05.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of the given parity to complete.  Gives up (and raises the
+// CTA's abort flag) after kSpinLimit polls, or early once another role aborted.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (i >= 8) __nanosleep(64);
+  }
+  *abort = 1;
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// C[m][n] = sum_k A(m, k) B(k, n) over the CTA's 64 x 64 tile and the
-// reduction range [k_begin, k_end); epilogue epi(m, n, value).
-template <class LA, class LB, class EPI>
-__global__ void __launch_bounds__(kGemmThreads)
-k_gemm_bf16(LA la, LB lb, EPI epi, int M, int N, int k_len_per_z, int K_total) {
-  __shared__ __align__(16) uint16_t As[BM][BK + 8];
-  __shared__ __align__(16) uint16_t Bs[BN][BK + 8];  // stored [n][k]
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int k_begin = blockIdx.z * k_len_per_z;
-  const int k_end = min(K_total, k_begin + k_len_per_z);
+// Shared-memory matrix descriptor, 128-byte swizzle (tiles written by TMA with
+// CU_TENSOR_MAP_SWIZZLE_128B, 1024-byte aligned).  K-major: rows of 64 BF16
+// along K, 8-row groups SBO = 1024 B apart, LBO unused.  MN-major: 64 BF16
+// along M (or N) per 128-byte row, one row per K index, 8-row groups SBO =
+// 1024 B apart, successive 64-wide M (N) blocks LBO bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((addr >> 4) & 0x3FFF) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFF) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46) | (uint64_t(2) << 61);
+}
+// Instruction descriptor, kind::f16: BF16 A and B, FP32 D, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int N, bool a_mn, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(a_mn) << 15) | (uint32_t(b_mn) << 16) |
+         (uint32_t(N >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+}
+
+// ---------------------------------------------------------------------------
+// The tensor-core GEMM skeleton.
+// ---------------------------------------------------------------------------
+struct Ctl {
+  unsigned long long full[4], empty[4], done;
+  uint32_t tmem;
+  int abort;
+};
+
+template <class Op>
+constexpr size_t umma_smem_bytes() {
+  return sizeof(Ctl) + 1024 + size_t(Op::kStages) * (128 * 64 * 2 + Op::kBN * 64 * 2);
+}
+
+template <class Op>
+__global__ void __launch_bounds__(128, 1)
+k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Op op) {
+  constexpr int S = Op::kStages, BN = Op::kBN;
+  constexpr uint32_t kA = 128 * 64 * 2, kB = BN * 64 * 2, kStage = kA + kB;
+  extern __shared__ uint8_t smem_raw[];
+  Ctl* ctl = reinterpret_cast<Ctl*>(smem_raw);
+  const uint32_t base = (smem_u32(smem_raw) + sizeof(Ctl) + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int g = lane >> 2, tg = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-  for (int k0 = k_begin; k0 < k_end; k0 += BK) {
-    for (int i = threadIdx.x; i < BM * BK; i += kGemmThreads) {
-      const int mm = i / BK, kk = i % BK;
-      const int m = m0 + mm, k = k0 + kk;
-      As[mm][kk] = (m < M && k < k_end) ? la(m, k) : uint16_t(0);
+  const int nk = op.num_kblocks();
+  volatile int* abort = &ctl->abort;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&ctl->full[s]), 1);
+      mbar_init(smem_u32(&ctl->empty[s]), 1);
     }
-    for (int i = threadIdx.x; i < BN * BK; i += kGemmThreads) {
-      const int nn = i % BN, kk = i / BN;
-      const int n = n0 + nn, k = k0 + kk;
-      Bs[nn][kk] = (n < N && k < k_end) ? lb(k, n) : uint16_t(0);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < BK; ks += 16) {
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16 + g;
-        af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * tg]);
-        af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * tg]);
-        af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * tg + 8]);
-        af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * tg + 8]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn + j * 8 + g;
-        bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + 2 * tg]);
-        bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + 2 * tg + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
-    }
-    __syncthreads();
+    mbar_init(smem_u32(&ctl->done), 1);
+    ctl->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int r = m0 + wm + i * 16 + g, c = n0 + wn + j * 8 + 2 * tg;
-      if (r < M && c < N) epi(r, c, acc[i][j][0]);
-      if (r < M && c + 1 < N) epi(r, c + 1, acc[i][j][1]);
-      if (r + 8 < M && c < N) epi(r + 8, c, acc[i][j][2]);
-      if (r + 8 < M && c + 1 < N) epi(r + 8, c + 1, acc[i][j][3]);
-    }
-}
-
-// ---- forward ---------------------------------------------------------------
-struct FwdA {  // A_p[co][ci*5 + j] = W[ci][co][p + 8 - 2j] (0 outside the kernel)
-  const uint16_t* w;
-  int Co, p;
-  __device__ uint16_t operator()(int co, int kk) const {
-    const int ci = kk / 5, j = kk % 5, k = p + 8 - 2 * j;
-    return (k >= 0 && k < 9) ? w[(static_cast<int64_t>(ci) * Co + co) * 9 + k] : uint16_t(0);
-  }
-};
-struct FwdB {  // B[ci*5 + j][b*T + v] = x[b][ci][v + j - 2]
-  const uint16_t* x;
-  int Ci, T;
-  __device__ uint16_t operator()(int kk, int n) const {
-    const int ci = kk / 5, j = kk % 5, b = n / T, v = n % T, u = v + j - 2;
-    return (u >= 0 && u < T) ? x[(static_cast<int64_t>(b) * Ci + ci) * T + u] : uint16_t(0);
-  }
-};
-struct FwdEpi {  // y[b][co][2v + p] = acc + bias[co]
-  float* y;
-  const float* bias;
-  int Co, T, p;
-  __device__ void operator()(int co, int n, float v) const {
-    const int b = n / T, vv = n % T;
-    y[(static_cast<int64_t>(b) * Co + co) * (2 * T) + 2 * vv + p] = v + (bias ? bias[co] : 0.f);
-  }
-};
-
-// ---- data gradient ----------------------------------------------------------
-struct DxA {  // A[ci][co*9 + k] = W[ci][co][k]
-  const uint16_t* w;
-  int Co;
-  __device__ uint16_t operator()(int ci, int kk) const { return w[static_cast<int64_t>(ci) * Co * 9 + kk]; }
-};
-struct DxB {  // B[co*9 + k][b*T + u] = dy[b][co][2u - 4 + k]
-  const uint16_t* dy;
-  int Co, T;
-  __device__ uint16_t operator()(int kk, int n) const {
-    const int co = kk / 9, k = kk % 9, b = n / T, u = n % T, t = 2 * u - 4 + k;
-    return (t >= 0 && t < 2 * T) ? dy[(static_cast<int64_t>(b) * Co + co) * (2 * T) + t] : uint16_t(0);
-  }
-};
-struct DxEpi {
-  float* dx;
-  int Ci, T;
-  __device__ void operator()(int ci, int n, float v) const {
-    const int b = n / T, u = n % T;
-    dx[(static_cast<int64_t>(b) * Ci + ci) * T + u] = v;
-  }
-};
-
-// ---- weight gradient --------------------------------------------------------
-struct DwA {  // A[ci][b*T + u] = x[b][ci][u]
-  const uint16_t* x;
-  int Ci, T;
-  __device__ uint16_t operator()(int ci, int kk) const {
-    const int b = kk / T, u = kk % T;
-    return x[(static_cast<int64_t>(b) * Ci + ci) * T + u];
-  }
-};
-struct DwB {  // B[b*T + u][co] = dy[b][co][2u - 4 + k]
-  const uint16_t* dy;
-  int Co, T, k;
-  __device__ uint16_t operator()(int kk, int co) const {
-    const int b = kk / T, u = kk % T, t = 2 * u - 4 + k;
-    return (t >= 0 && t < 2 * T) ? dy[(static_cast<int64_t>(b) * Co + co) * (2 * T) + t] : uint16_t(0);
-  }
-};
-struct DwEpi {  // partial[split][ci][co] for tap k
-  float* part;
-  int Ci, Co;
-  int64_t split_stride;
-  __device__ void operator()(int ci, int co, float v) const {
-    part[static_cast<int64_t>(blockIdx.z) * split_stride + static_cast<int64_t>(ci) * Co + co] = v;
-  }
-};
-
-__global__ void k_dw_reduce(const float* __restrict__ part, float* __restrict__ dw, int Ci, int Co, int k, int nsplit) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t cc = static_cast<int64_t>(Ci) * Co;
-  if (i >= cc) return;
-  float acc = 0.f;
-  for (int s = 0; s < nsplit; ++s) acc += part[s * cc + i];
-  dw[i * 9 + k] = acc;
-}
-
-// db[co] = sum_{b, t} dy[b][co][t]; one block per co, fixed-order reduction.
-__global__ void k_bias_grad(const float* __restrict__ dy, float* __restrict__ db, int B, int Co, int L) {
-  __shared__ float red[256];
-  const int co = blockIdx.x;
-  float acc = 0.f;
-  for (int64_t i = threadIdx.x; i < static_cast<int64_t>(B) * L; i += blockDim.x) {
-    const int64_t b = i / L, t = i % L;
-    acc += dy[(b * Co + co) * L + t];
-  }
-  red[threadIdx.x] = acc;
+  if (warp == 2) tmem_alloc(smem_u32(&ctl->tmem), BN);
+  tc_fence_before();
   __syncthreads();
-  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem;
+
+  int issued = 0;
+  if (threadIdx.x == 0) {  // TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % S;
+      if (kb >= S && !mbar_wait(smem_u32(&ctl->empty[s]), ((kb / S) - 1) & 1, abort)) break;
+      const uint32_t bar = smem_u32(&ctl->full[s]);
+      mbar_expect_tx(bar, kStage);
+      op.load(kb, &tmA, &tmB, base + s * kStage, base + s * kStage + kA, bar);
+      issued = kb + 1;
+    }
+  } else if (threadIdx.x == 32) {  // MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BN, Op::kAMN, Op::kBMN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % S;
+      if (!mbar_wait(smem_u32(&ctl->full[s]), (kb / S) & 1, abort)) break;
+      tc_fence_after();
+      const uint32_t a = base + s * kStage, b = a + kA;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) umma_bf16(tmem, Op::adesc(a, kk), Op::bdesc(b, kk), idesc, (kb | kk) != 0);
+      umma_commit(smem_u32(&ctl->empty[s]));
+    }
+    umma_commit(smem_u32(&ctl->done));  // arrives once every MMA issued above has completed
+  }
+  const bool got = mbar_wait(smem_u32(&ctl->done), 0, abort);
+  tc_fence_after();
+  const int good = __syncthreads_and(got && !*abort && nk > 0);
+  if (good) op.epilogue(tmem, warp, lane);
+  tc_fence_before();
+  __syncthreads();
+  if (!good && threadIdx.x == 0) {
+    // Let this thread's TMA copies still in flight land before the CTA exits.
+    for (int kb = max(0, issued - S); kb < issued; ++kb) {
+      const uint32_t bar = smem_u32(&ctl->full[kb % S]);
+      for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(bar, (kb / S) & 1); ++i) __nanosleep(64);
+    }
+    if (nk > 0) atomicExch(&g_decoder_err, 1);
+  }
+  if (warp == 2) tmem_dealloc(tmem, BN);
+}
+
+// Epilogue store helpers: 32 consecutive values of one row.
+__device__ __forceinline__ void store32_f32(float* dst, const float (&v)[32]) {
+  float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+__device__ __forceinline__ void store32_bf16(uint16_t* dst, const float (&v)[32]) {
+  uint4* d = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      w[k] = uint32_t(f2bf(v[8 * i + 2 * k])) | (uint32_t(f2bf(v[8 * i + 2 * k + 1])) << 16);
+    d[i] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// Forward: grid (ceil(T / 128), B).  A = x rows v0 + 2 - j (box 64 ch x 128 rows),
+// B = Wf [(p, co)][(j, ci)] (box 64 x 256).
+struct FwdOp {
+  static constexpr int kBN = 256, kStages = 4;
+  static constexpr bool kAMN = false, kBMN = false;
+  int T, Cip;
+  const float* bias;
+  float* z;
+  uint16_t* h;
+  __device__ int num_kblocks() const { return 5 * (Cip / 64); }
+  __device__ void load(int kb, const CUtensorMap* ta, const CUtensorMap* tb, uint32_t sa, uint32_t sb,
+                       uint32_t bar) const {
+    const int c = kb / 5, j = kb % 5;
+    tma_load_3d(sa, ta, bar, c * 64, int(blockIdx.x) * 128 + 2 - j, int(blockIdx.y));
+    tma_load_2d(sb, tb, bar, j * Cip + c * 64, 0);
+  }
+  __device__ static uint64_t adesc(uint32_t a, int kk) { return sdesc(a + kk * 32, 16, 1024); }
+  __device__ static uint64_t bdesc(uint32_t b, int kk) { return sdesc(b + kk * 32, 16, 1024); }
+  __device__ void epilogue(uint32_t tmem, int warp, int lane) const {
+    const int v = int(blockIdx.x) * 128 + warp * 32 + lane;
+    const bool valid = v < T;
+    const int64_t row0 = (int64_t(blockIdx.y) * 2 * T + 2 * int64_t(v)) * kC;
+#pragma unroll 1
+    for (int col = 0; col < 2 * kC; col += 32) {
+      float acc[32];
+      tmem_ld32(tmem + (uint32_t(warp * 32) << 16) + col, acc);
+      const int p = col / kC, co = col % kC;
+      const float4* bb = reinterpret_cast<const float4*>(bias + co);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float4 q = bb[i];
+        acc[4 * i] += q.x;
+        acc[4 * i + 1] += q.y;
+        acc[4 * i + 2] += q.z;
+        acc[4 * i + 3] += q.w;
+      }
+      if (valid) {
+        const int64_t off = row0 + int64_t(p) * kC + co;
+        if (z) store32_f32(z + off, acc);
+        if (h) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[i] = gelu(acc[i]);
+          store32_bf16(h + off, acc);
+        }
+      }
+    }
+  }
+};
+
+// Data gradient: grid (ceil(T / 128), B).  A = g read as [B][T][256], rows
+// u0 - 2 + m, half q (box 64 x 128 rows); B = Wd [ci][(k, co)] (box 64 x 128).
+struct BwdDataOp {
+  static constexpr int kBN = 128, kStages = 3;
+  static constexpr bool kAMN = false, kBMN = false;
+  int T;
+  const float* zprev;  // GELU' applied when non-null
+  float* g32;
+  uint16_t* g16;
+  __device__ int num_kblocks() const { return 9 * (kC / 64); }
+  __device__ void load(int kb, const CUtensorMap* ta, const CUtensorMap* tb, uint32_t sa, uint32_t sb,
+                       uint32_t bar) const {
+    const int k = kb / (kC / 64), c = kb % (kC / 64);
+    const int m = k >> 1, q = k & 1;
+    tma_load_3d(sa, ta, bar, q * kC + c * 64, int(blockIdx.x) * 128 - 2 + m, int(blockIdx.y));
+    tma_load_2d(sb, tb, bar, k * kC + c * 64, 0);
+  }
+  __device__ static uint64_t adesc(uint32_t a, int kk) { return sdesc(a + kk * 32, 16, 1024); }
+  __device__ static uint64_t bdesc(uint32_t b, int kk) { return sdesc(b + kk * 32, 16, 1024); }
+  __device__ void epilogue(uint32_t tmem, int warp, int lane) const {
+    const int u = int(blockIdx.x) * 128 + warp * 32 + lane;
+    const bool valid = u < T;
+    const int64_t row = (int64_t(blockIdx.y) * T + u) * kC;
+#pragma unroll 1
+    for (int col = 0; col < kC; col += 32) {
+      float acc[32];
+      tmem_ld32(tmem + (uint32_t(warp * 32) << 16) + col, acc);
+      if (valid) {
+        if (zprev) {
+          const float4* zz = reinterpret_cast<const float4*>(zprev + row + col);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float4 q = zz[i];
+            acc[4 * i] *= gelu_grad(q.x);
+            acc[4 * i + 1] *= gelu_grad(q.y);
+            acc[4 * i + 2] *= gelu_grad(q.z);
+            acc[4 * i + 3] *= gelu_grad(q.w);
+          }
+        }
+        if (g32) store32_f32(g32 + row + col, acc);
+        if (g16) store32_bf16(g16 + row + col, acc);
+      }
+    }
+  }
+};
+
+// Weight gradient: grid (5, Cip / 128, splits).  blockIdx.x = m (taps 2m, 2m+1),
+// blockIdx.z = (clip, position chunk).  A = x [positions][ci] MN-major (two
+// boxes 64 ch x 64 rows), B = g as [B][T][256] rows u - 2 + m MN-major (four
+// boxes 64 x 64 rows).  Partial sums D[ci][(q, co)] go to part[split][m][ci][256].
+struct DwOp {
+  static constexpr int kBN = 256, kStages = 4;
+  static constexpr bool kAMN = true, kBMN = true;
+  int T, Cip, chunk, spc;  // spc = chunks per clip
+  float* part;
+  __device__ int u_begin() const { return (int(blockIdx.z) % spc) * chunk; }
+  __device__ int num_kblocks() const { return (min(chunk, T - u_begin()) + 63) / 64; }
+  __device__ void load(int kb, const CUtensorMap* ta, const CUtensorMap* tb, uint32_t sa, uint32_t sb,
+                       uint32_t bar) const {
+    const int b = int(blockIdx.z) / spc, u = u_begin() + kb * 64, m = int(blockIdx.x);
+    const int ci0 = int(blockIdx.y) * 128;
+    tma_load_3d(sa, ta, bar, ci0, u, b);
+    tma_load_3d(sa + 8192, ta, bar, ci0 + 64, u, b);
+#pragma unroll
+    for (int n = 0; n < 4; ++n) tma_load_3d(sb + n * 8192, tb, bar, n * 64, u - 2 + m, b);
+  }
+  __device__ static uint64_t adesc(uint32_t a, int kk) { return sdesc(a + kk * 2048, 8192, 1024); }
+  __device__ static uint64_t bdesc(uint32_t b, int kk) { return sdesc(b + kk * 2048, 8192, 1024); }
+  __device__ void epilogue(uint32_t tmem, int warp, int lane) const {
+    const int ci = int(blockIdx.y) * 128 + warp * 32 + lane;
+    float* dst = part + ((int64_t(blockIdx.z) * 5 + blockIdx.x) * Cip + ci) * 256;
+#pragma unroll 1
+    for (int col = 0; col < 256; col += 32) {
+      float acc[32];
+      tmem_ld32(tmem + (uint32_t(warp * 32) << 16) + col, acc);
+      store32_f32(dst + col, acc);
+    }
+  }
+};
+
+// dW[ci][co][k] = sum over splits (ascending) of part[split][k/2][ci][(k%2) C + co], ci < Ci.
+__global__ void k_dw_reduce(const float* __restrict__ part, float* __restrict__ dw, int Ci, int Cip, int splits) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(Ci) * kC * 9) return;
+  const int k = int(idx % 9), co = int((idx / 9) % kC), ci = int(idx / (9 * kC));
+  const int64_t step = int64_t(5) * Cip * 256;
+  const float* p = part + (int64_t(k >> 1) * Cip + ci) * 256 + (k & 1) * kC + co;
+  float acc = 0.f;
+  for (int s = 0; s < splits; ++s) acc += p[s * step];
+  dw[idx] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Output layer (C -> 1 channel): plain FMA kernels.
+// ---------------------------------------------------------------------------
+constexpr int kOutV = 64;  // positions per CTA
+
+// y[b][2v+p] = bias + sum_{j, ci} x[b][v+2-j][ci] w[ci][2j+p]; grid (ceil(T/64), B), 128 threads.
+__global__ void __launch_bounds__(128)
+k_out_fwd(const uint16_t* __restrict__ x, const float* __restrict__ w, const float* __restrict__ bias,
+          float* __restrict__ y, int T) {
+  __shared__ float xs[kC][kOutV + 5];
+  __shared__ float ws[kC][9];
+  const int b = blockIdx.y, v0 = blockIdx.x * kOutV;
+  for (int i = threadIdx.x; i < kC * 9; i += blockDim.x) ws[i / 9][i % 9] = w[i];
+  for (int i = threadIdx.x; i < (kOutV + 4) * kC; i += blockDim.x) {
+    const int r = i / kC, ci = i % kC, v = v0 - 2 + r;
+    xs[ci][r] = (v >= 0 && v < T) ? bf2f(x[(int64_t(b) * T + v) * kC + ci]) : 0.f;
+  }
+  __syncthreads();
+  const int vl = threadIdx.x >> 1, p = threadIdx.x & 1, v = v0 + vl;
+  float acc = bias[0];
+  for (int ci = 0; ci < kC; ++ci) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+      if (2 * j + p <= 8) acc += xs[ci][vl + 4 - j] * ws[ci][2 * j + p];
+  }
+  if (v < T) y[int64_t(b) * 2 * T + 2 * v + p] = acc;
+}
+
+// g[b][u][ci] = (sum_k dy[b][2u-4+k] w[ci][k]) * GELU'(zprev[b][u][ci]).
+__global__ void k_out_bwd_data(const float* __restrict__ dy, const float* __restrict__ w,
+                               const float* __restrict__ zprev, float* __restrict__ g32, uint16_t* __restrict__ g16,
+                               int T, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int ci = int(i % kC);
+  const int64_t bu = i / kC;
+  const int u = int(bu % T);
+  const float* d = dy + (bu / T) * 2 * T;
+  float acc = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int t = 2 * u - 4 + k;
+    if (t >= 0 && t < 2 * T) acc += d[t] * w[ci * 9 + k];
+  }
+  if (zprev) acc *= gelu_grad(zprev[i]);
+  if (g32) g32[i] = acc;
+  if (g16) g16[i] = f2bf(acc);
+}
+
+constexpr int kOutChunk = 256;  // positions per CTA of the output layer's weight gradient
+
+// part[chunk][ci][k] = sum over the chunk's u of x[b][u][ci] dy[b][2u-4+k];
+// part_db[chunk] = sum of dy over the chunk's times [2 u0, 2 uend).  grid (ceil(T/256), B).
+__global__ void __launch_bounds__(128)
+k_out_bwd_weight(const uint16_t* __restrict__ x, const float* __restrict__ dy, float* __restrict__ part,
+                 float* __restrict__ part_db, int T) {
+  __shared__ float ds[2 * kOutChunk + 8];
+  __shared__ float red[128];
+  const int b = blockIdx.y, u0 = blockIdx.x * kOutChunk;
+  const float* d = dy + int64_t(b) * 2 * T;
+  for (int i = threadIdx.x; i < 2 * kOutChunk + 8; i += blockDim.x) {
+    const int t = 2 * u0 - 4 + i;
+    ds[i] = (t >= 0 && t < 2 * T) ? d[t] : 0.f;
+  }
+  __syncthreads();
+  const int ci = threadIdx.x;
+  float acc[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = 0.f;
+  const int uend = min(T, u0 + kOutChunk);
+  for (int u = u0; u < uend; ++u) {
+    const float xv = bf2f(x[(int64_t(b) * T + u) * kC + ci]);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] += xv * ds[2 * (u - u0) + k];
+  }
+  const int64_t chunk = int64_t(blockIdx.y) * gridDim.x + blockIdx.x;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) part[(chunk * kC + ci) * 9 + k] = acc[k];
+  // bias: this chunk's times, fixed-order tree
+  float s = 0.f;
+  for (int i = threadIdx.x; i < 2 * (uend - u0); i += blockDim.x) s += ds[4 + i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) db[co] = red[0];
+  if (threadIdx.x == 0) part_db[chunk] = red[0];
 }
 
-__global__ void k_gelu_fwd(const float* __restrict__ z, uint16_t* __restrict__ h, int64_t n) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float v = z[i];
-  h[i] = f2bf(0.5f * v * (1.f + erff(v * 0.70710678118654752f)));
+__global__ void k_out_reduce(const float* __restrict__ part, const float* __restrict__ part_db,
+                             float* __restrict__ dw, float* __restrict__ db, int chunks) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kC * 9) {
+    float acc = 0.f;
+    for (int c = 0; c < chunks; ++c) acc += part[int64_t(c) * kC * 9 + i];
+    dw[i] = acc;
+  } else if (i == kC * 9 && db) {
+    float acc = 0.f;
+    for (int c = 0; c < chunks; ++c) acc += part_db[c];
+    db[0] = acc;
+  }
 }
 
-// dz = dh * GELU'(z), GELU'(z) = (1 + erf(z/sqrt2))/2 + z exp(-z^2/2)/sqrt(2 pi)
-__global__ void k_gelu_bwd(const float* __restrict__ dh, const float* __restrict__ z, float* __restrict__ dz,
-                           int64_t n) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+// ---------------------------------------------------------------------------
+// Bias gradient of a tensor-core layer, packing, cast, Adam.
+// ---------------------------------------------------------------------------
+constexpr int kColChunk = 512;  // rows per CTA
+
+__global__ void __launch_bounds__(128)
+k_colsum(const float* __restrict__ g, int64_t rows, float* __restrict__ part) {
+  const int64_t r0 = int64_t(blockIdx.x) * kColChunk;
+  const int64_t r1 = min(rows, r0 + kColChunk);
+  float acc = 0.f;
+  for (int64_t r = r0; r < r1; ++r) acc += g[r * kC + threadIdx.x];
+  part[int64_t(blockIdx.x) * kC + threadIdx.x] = acc;
+}
+
+__global__ void k_colsum_reduce(const float* __restrict__ part, float* __restrict__ db, int chunks) {
+  const int c = threadIdx.x;
+  float acc = 0.f;
+  for (int i = 0; i < chunks; ++i) acc += part[int64_t(i) * kC + c];
+  db[c] = acc;
+}
+
+// x[b][t][c] = bf16(phi[b][c][t] * s[c]) for c < C, 0 for C <= c < Cip.  32 x 32 tiles.
+__global__ void k_pack_input(const float* __restrict__ phi, const float* __restrict__ s, uint16_t* __restrict__ x,
+                             int C, int Cip, int T) {
+  __shared__ float tile[32][33];
+  const int b = blockIdx.z, c0 = blockIdx.y * 32, t0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 256 threads: 8 rows per pass
+  for (int r = ty; r < 32; r += 8) {
+    const int c = c0 + r, t = t0 + tx;
+    tile[r][tx] = (c < C && t < T) ? phi[(int64_t(b) * C + c) * T + t] * s[c] : 0.f;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int t = t0 + r, c = c0 + tx;
+    if (t < T && c < Cip) x[(int64_t(b) * T + t) * Cip + c] = f2bf(tile[tx][r]);
+  }
+}
+
+// wf[(p, co)][(j, ci)] = W[ci][co][2j+p] (0 where 2j+p > 8 or ci >= Ci), [2C][5 Cip].
+__global__ void k_pack_wf(const float* __restrict__ w, uint16_t* __restrict__ wf, int Ci, int Cip) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t n = int64_t(2 * kC) * 5 * Cip;
   if (i >= n) return;
-  const float v = z[i];
-  const float d = 0.5f * (1.f + erff(v * 0.70710678118654752f)) + v * expf(-0.5f * v * v) * 0.39894228040143268f;
-  dz[i] = dh[i] * d;
+  const int col = int(i % (5 * Cip)), row = int(i / (5 * Cip));
+  const int p = row / kC, co = row % kC, j = col / Cip, ci = col % Cip;
+  const int k = 2 * j + p;
+  wf[i] = (k <= 8 && ci < Ci) ? f2bf(w[(int64_t(ci) * kC + co) * 9 + k]) : uint16_t(0);
+}
+
+// wd[ci][(k, co)] = W[ci][co][k], [C][9 C].
+__global__ void k_pack_wd(const float* __restrict__ w, uint16_t* __restrict__ wd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kC * 9 * kC) return;
+  const int col = i % (9 * kC), ci = i / (9 * kC);
+  const int k = col / kC, co = col % kC;
+  wd[i] = f2bf(w[(ci * kC + co) * 9 + k]);
 }
 
 __global__ void k_cast_bf16(const float* __restrict__ x, uint16_t* __restrict__ y, int64_t n) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i < n) y[i] = f2bf(x[i]);
-}
-
-__global__ void k_cast_bf16_rows(const float* __restrict__ x, const float* __restrict__ s, uint16_t* __restrict__ y,
-                                 int C, int64_t T, int64_t n) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = f2bf(x[i] * s[(i / T) % C]);
 }
 
 __global__ void k_adam_params(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -253,87 +571,193 @@ __global__ void k_adam_params(float* __restrict__ p, const float* __restrict__ g
   if (pb) pb[i] = f2bf(pi);
 }
 
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
 int ok() { return cudaGetLastError() == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA; }
 unsigned blocks(int64_t n) { return static_cast<unsigned>((n + 255) / 256); }
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-bool bad_dims(int B, int Ci, int Co, int T) {
-  return B < 1 || Ci < 1 || Co < 1 || T < 1 || static_cast<int64_t>(B) * T > (int64_t(1) << 30) ||
-         static_cast<int64_t>(Ci) * 9 > (int64_t(1) << 30);
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// BF16 tensor map with 128-byte swizzle over a [d2][d1][d0] array (d0 innermost).
+bool make_map(CUtensorMap* m, const void* base, int rank, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0,
+              uint32_t b1) {
+  auto fn = encode_fn();
+  if (!fn || !aligned16(base)) return false;
+  const cuuint64_t dims[3] = {d0, d1, d2};
+  const cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
+  const cuuint32_t box[3] = {b0, b1, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class Op>
+int launch_umma(const CUtensorMap& ta, const CUtensorMap& tb, const Op& op, dim3 grid, cudaStream_t s) {
+  constexpr size_t smem = umma_smem_bytes<Op>();
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_umma<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (attr != cudaSuccess) return JTFS_ERR_CUDA;
+  k_umma<Op><<<grid, 128, smem, s>>>(ta, tb, op);
+  return ok();
+}
+
+bool bad(int B, int T) { return B < 1 || T < 1 || int64_t(B) * T > (int64_t(1) << 28) || T > (1 << 24); }
+
+// Weight-gradient split: about 8 waves of 152 CTAs, chunks of whole 64-row blocks within one clip.
+void dw_split(int B, int Cip, int T, int* chunk, int* spc) {
+  const int64_t per_clip = std::max<int64_t>(1, std::llround(1216.0 / (5.0 * (Cip / 128) * B)));
+  *chunk = static_cast<int>(cdiv(cdiv(T, per_clip), 64) * 64);
+  *spc = static_cast<int>(cdiv(T, *chunk));
 }
 
 }  // namespace
 
-extern "C" int jtfs_convt_forward(const uint16_t* x, const uint16_t* w, const float* bias, float* y, int B, int Ci,
-                                  int Co, int T, void* stream) {
-  if (!x || !w || !y || bad_dims(B, Ci, Co, T)) return JTFS_ERR_ARG;
-  const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int N = B * T, K = Ci * 5;
-  dim3 grid((N + BN - 1) / BN, (Co + BM - 1) / BM, 1);
-  for (int p = 0; p < 2; ++p)
-    k_gemm_bf16<<<grid, kGemmThreads, 0, s>>>(FwdA{w, Co, p}, FwdB{x, Ci, T}, FwdEpi{y, bias, Co, T, p}, Co, N, K, K);
+extern "C" int jtfs_convt_padded_channels(int C) { return C < 1 ? 0 : static_cast<int>(cdiv(C, 128) * 128); }
+
+extern "C" int jtfs_convt_pack_input(const float* phi, const float* row_scale, uint16_t* x, int B, int C, int T,
+                                     void* stream) {
+  if (!phi || !row_scale || !x || C < 1 || bad(B, T)) return JTFS_ERR_ARG;
+  const int Cip = jtfs_convt_padded_channels(C);
+  dim3 grid(static_cast<unsigned>(cdiv(T, 32)), static_cast<unsigned>(cdiv(Cip, 32)), static_cast<unsigned>(B));
+  k_pack_input<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(phi, row_scale, x, C, Cip, T);
   return ok();
 }
 
-extern "C" int jtfs_convt_backward_data(const uint16_t* dy, const uint16_t* w, float* dx, int B, int Ci, int Co,
-                                        int T, void* stream) {
-  if (!dy || !w || !dx || bad_dims(B, Ci, Co, T)) return JTFS_ERR_ARG;
-  const int N = B * T, K = Co * 9;
-  dim3 grid((N + BN - 1) / BN, (Ci + BM - 1) / BM, 1);
-  k_gemm_bf16<<<grid, kGemmThreads, 0, static_cast<cudaStream_t>(stream)>>>(DxA{w, Co}, DxB{dy, Co, T},
-                                                                            DxEpi{dx, Ci, T}, Ci, N, K, K);
+extern "C" int jtfs_convt_pack_weights(const float* w, uint16_t* wf, uint16_t* wd, int Ci, int Co, void* stream) {
+  if (!w || !wf || Ci < 1 || Co != kC || (wd && Ci != kC)) return JTFS_ERR_ARG;
+  const int Cip = jtfs_convt_padded_channels(Ci);
+  auto s = static_cast<cudaStream_t>(stream);
+  k_pack_wf<<<blocks(int64_t(2 * kC) * 5 * Cip), 256, 0, s>>>(w, wf, Ci, Cip);
+  if (wd) k_pack_wd<<<blocks(kC * 9 * kC), 256, 0, s>>>(w, wd);
   return ok();
 }
 
-extern "C" size_t jtfs_convt_weight_workspace_bytes(int B, int Ci, int Co, int T) {
-  if (bad_dims(B, Ci, Co, T)) return 0;
-  const int64_t K = static_cast<int64_t>(B) * T;
-  const int64_t nsplit = (K + kDwSplit - 1) / kDwSplit;
-  return static_cast<size_t>(nsplit) * Ci * Co * sizeof(float);
+extern "C" int jtfs_convt_forward(const uint16_t* x, const uint16_t* wf, const float* bias, float* z, uint16_t* h,
+                                  int B, int Cip, int Co, int T, void* stream) {
+  if (!x || !wf || !bias || (!z && !h) || Co != kC || Cip < 128 || Cip % 128 || bad(B, T)) return JTFS_ERR_ARG;
+  if (!aligned16(bias) || (z && !aligned16(z)) || (h && !aligned16(h))) return JTFS_ERR_ARG;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, x, 3, Cip, T, B, 64, 128) || !make_map(&tb, wf, 2, 5 * Cip, 2 * kC, 1, 64, 2 * kC))
+    return JTFS_ERR_ARG;
+  FwdOp op{T, Cip, bias, z, h};
+  return launch_umma(ta, tb, op, dim3(static_cast<unsigned>(cdiv(T, 128)), static_cast<unsigned>(B)),
+                     static_cast<cudaStream_t>(stream));
 }
 
-extern "C" int jtfs_convt_backward_weight(const uint16_t* x, const uint16_t* dy, const float* dy_f32, float* dw,
-                                          float* db, int B, int Ci, int Co, int T, void* workspace, void* stream) {
-  if (!x || !dy || !dw || !workspace || bad_dims(B, Ci, Co, T)) return JTFS_ERR_ARG;
-  const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int K = B * T;
-  const int nsplit = (K + kDwSplit - 1) / kDwSplit;
+extern "C" int jtfs_convt_backward_data(const uint16_t* g, const uint16_t* wd, const float* zprev, float* g_prev,
+                                        uint16_t* g_prev_bf16, int B, int Ci, int Co, int T, void* stream) {
+  if (!g || !wd || (!g_prev && !g_prev_bf16) || Ci != kC || Co != kC || bad(B, T)) return JTFS_ERR_ARG;
+  if ((zprev && !aligned16(zprev)) || (g_prev && !aligned16(g_prev)) || (g_prev_bf16 && !aligned16(g_prev_bf16)))
+    return JTFS_ERR_ARG;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, g, 3, 2 * kC, T, B, 64, 128) || !make_map(&tb, wd, 2, 9 * kC, kC, 1, 64, kC))
+    return JTFS_ERR_ARG;
+  BwdDataOp op{T, zprev, g_prev, g_prev_bf16};
+  return launch_umma(ta, tb, op, dim3(static_cast<unsigned>(cdiv(T, 128)), static_cast<unsigned>(B)),
+                     static_cast<cudaStream_t>(stream));
+}
+
+extern "C" size_t jtfs_convt_weight_workspace_bytes(int B, int Cip, int Co, int T) {
+  if (Co != kC || Cip < 128 || Cip % 128 || bad(B, T)) return 0;
+  int chunk, spc;
+  dw_split(B, Cip, T, &chunk, &spc);
+  return size_t(B) * spc * 5 * Cip * 256 * sizeof(float);
+}
+
+extern "C" int jtfs_convt_backward_weight(const uint16_t* x, const uint16_t* g, float* dw, int B, int Ci, int Cip,
+                                          int Co, int T, void* workspace, void* stream) {
+  if (!x || !g || !dw || !workspace || Co != kC || Ci < 1 || Ci > Cip || Cip % 128 || bad(B, T))
+    return JTFS_ERR_ARG;
+  if (!aligned16(workspace)) return JTFS_ERR_ARG;
+  int chunk, spc;
+  dw_split(B, Cip, T, &chunk, &spc);
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, x, 3, Cip, T, B, 64, 64) || !make_map(&tb, g, 3, 2 * kC, T, B, 64, 64)) return JTFS_ERR_ARG;
   float* part = static_cast<float*>(workspace);
-  const int64_t cc = static_cast<int64_t>(Ci) * Co;
-  dim3 grid((Co + BN - 1) / BN, (Ci + BM - 1) / BM, nsplit);
-  for (int k = 0; k < 9; ++k) {
-    k_gemm_bf16<<<grid, kGemmThreads, 0, s>>>(DwA{x, Ci, T}, DwB{dy, Co, T, k}, DwEpi{part, Ci, Co, cc}, Ci, Co,
-                                              kDwSplit, K);
-    if (ok() != JTFS_OK) return JTFS_ERR_CUDA;
-    k_dw_reduce<<<blocks(cc), 256, 0, s>>>(part, dw, Ci, Co, k, nsplit);
-    if (ok() != JTFS_OK) return JTFS_ERR_CUDA;
-  }
-  if (db && dy_f32) k_bias_grad<<<Co, 256, 0, s>>>(dy_f32, db, B, Co, 2 * T);
+  DwOp op{T, Cip, chunk, spc, part};
+  auto s = static_cast<cudaStream_t>(stream);
+  const int rc =
+      launch_umma(ta, tb, op, dim3(5, static_cast<unsigned>(Cip / 128), static_cast<unsigned>(B * spc)), s);
+  if (rc != JTFS_OK) return rc;
+  k_dw_reduce<<<blocks(int64_t(Ci) * kC * 9), 256, 0, s>>>(part, dw, Ci, Cip, B * spc);
   return ok();
 }
 
-extern "C" int jtfs_gelu_forward(const float* z, uint16_t* h, int64_t n, void* stream) {
-  if (!z || !h || n < 0) return JTFS_ERR_ARG;
-  if (n) k_gelu_fwd<<<blocks(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(z, h, n);
+extern "C" size_t jtfs_convt_bias_workspace_bytes(int64_t rows) {
+  return rows < 1 ? 0 : size_t(cdiv(rows, kColChunk)) * kC * sizeof(float);
+}
+
+extern "C" int jtfs_convt_bias_grad(const float* g, float* db, int64_t rows, int Co, void* workspace, void* stream) {
+  if (!g || !db || !workspace || Co != kC || rows < 1) return JTFS_ERR_ARG;
+  const int chunks = static_cast<int>(cdiv(rows, kColChunk));
+  auto s = static_cast<cudaStream_t>(stream);
+  float* part = static_cast<float*>(workspace);
+  k_colsum<<<chunks, kC, 0, s>>>(g, rows, part);
+  k_colsum_reduce<<<1, kC, 0, s>>>(part, db, chunks);
   return ok();
 }
 
-extern "C" int jtfs_gelu_backward(const float* dh, const float* z, float* dz, int64_t n, void* stream) {
-  if (!dh || !z || !dz || n < 0) return JTFS_ERR_ARG;
-  if (n) k_gelu_bwd<<<blocks(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(dh, z, dz, n);
+extern "C" int jtfs_convt_out_forward(const uint16_t* x, const float* w, const float* bias, float* y, int B, int Ci,
+                                      int T, void* stream) {
+  if (!x || !w || !bias || !y || Ci != kC || bad(B, T)) return JTFS_ERR_ARG;
+  dim3 grid(static_cast<unsigned>(cdiv(T, kOutV)), static_cast<unsigned>(B));
+  k_out_fwd<<<grid, 128, 0, static_cast<cudaStream_t>(stream)>>>(x, w, bias, y, T);
   return ok();
+}
+
+extern "C" int jtfs_convt_out_backward_data(const float* dy, const float* w, const float* zprev, float* g_prev,
+                                            uint16_t* g_prev_bf16, int B, int Ci, int T, void* stream) {
+  if (!dy || !w || (!g_prev && !g_prev_bf16) || Ci != kC || bad(B, T)) return JTFS_ERR_ARG;
+  const int64_t n = int64_t(B) * T * kC;
+  k_out_bwd_data<<<blocks(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(dy, w, zprev, g_prev, g_prev_bf16, T, n);
+  return ok();
+}
+
+extern "C" size_t jtfs_convt_out_workspace_bytes(int B, int T) {
+  if (bad(B, T)) return 0;
+  const int64_t chunks = int64_t(B) * cdiv(T, kOutChunk);
+  return size_t(chunks) * (kC * 9 + 1) * sizeof(float);
+}
+
+extern "C" int jtfs_convt_out_backward_weight(const uint16_t* x, const float* dy, float* dw, float* db, int B,
+                                              int Ci, int T, void* workspace, void* stream) {
+  if (!x || !dy || !dw || !workspace || Ci != kC || bad(B, T)) return JTFS_ERR_ARG;
+  const int per = static_cast<int>(cdiv(T, kOutChunk));
+  const int chunks = B * per;
+  auto s = static_cast<cudaStream_t>(stream);
+  float* part = static_cast<float*>(workspace);
+  float* part_db = part + int64_t(chunks) * kC * 9;
+  k_out_bwd_weight<<<dim3(per, B), 128, 0, s>>>(x, dy, part, part_db, T);
+  k_out_reduce<<<static_cast<unsigned>(cdiv(kC * 9 + 1, 256)), 256, 0, s>>>(part, part_db, dw, db, chunks);
+  return ok();
+}
+
+extern "C" int jtfs_decoder_error(void) {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_decoder_err, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
+  const int zero = 0;
+  if (v && cudaMemcpyToSymbol(g_decoder_err, &zero, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
+  return v;
 }
 
 extern "C" int jtfs_cast_bf16(const float* x, uint16_t* y, int64_t n, void* stream) {
   if (!x || !y || n < 0) return JTFS_ERR_ARG;
   if (n) k_cast_bf16<<<blocks(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n);
-  return ok();
-}
-
-extern "C" int jtfs_cast_bf16_rows(const float* x, const float* row_scale, uint16_t* y, int B, int C, int64_t T,
-                                   void* stream) {
-  if (!x || !row_scale || !y || B < 0 || C < 1 || T < 0) return JTFS_ERR_ARG;
-  const int64_t n = static_cast<int64_t>(B) * C * T;
-  if (n) k_cast_bf16_rows<<<blocks(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, row_scale, y, C, T, n);
   return ok();
 }
 

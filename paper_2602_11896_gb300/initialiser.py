@@ -5,8 +5,9 @@ between layers) map the Phi of a clip, read as (rows of Phi) channels x
 (frames) time steps and scaled per channel (``row_scale``), to
 N = frames * 2^6 samples.  With T = 2^6 this is
 exactly the clip length.  Operands are BF16 and products accumulate in FP32
-on the tensor cores (library kernels ``jtfs_convt_*``); parameters are kept
-in FP32 and updated with the library's Adam kernel.  It is trained with the
+on the tensor cores (library kernels ``jtfs_convt_*``: tcgen05 MMA with TMEM
+accumulators fed by TMA); parameters are kept in FP32, updated with the
+library's Adam kernel and repacked to BF16 after every update.  It is trained with the
 JTFS loss itself: the gradient reaching the waveform comes from
 ``jtfs_loss_grad`` (the hand-written adjoint).  Its proposal replaces the
 noise initialisation of metamer descent; plain noise initialisation stays the
@@ -40,16 +41,22 @@ class Decoder:
     """Transposed-convolution decoder; see the module docstring.
 
     ``in_channels`` = rows of Phi, ``frames`` = Phi frames per clip; the output
-    has frames * 2^layers samples.
+    has frames * 2^layers samples.  Hidden width 128 (the tensor-core layers);
+    activations are kept channels-last [B][T][C].
     """
+
+    WIDTH = 128
 
     def __init__(self, in_channels: int, frames: int, channels: int = 128, layers: int = 6, seed: int = 0,
                  row_scale: Optional[np.ndarray] = None, device: str = "cuda"):
+        if channels != self.WIDTH or layers < 2:
+            raise ValueError("the decoder's hidden width is 128 and it has at least 2 layers")
         self._lib = _native.load()
         self.dims = [in_channels] + [channels] * (layers - 1) + [1]
         self.frames = frames
         self.layers = layers
         self.device = torch.device(device)
+        self.cip0 = int(self._lib.jtfs_convt_padded_channels(in_channels))
         rng = np.random.default_rng(seed)
         self.w: List[torch.Tensor] = []
         self.b: List[torch.Tensor] = []
@@ -65,8 +72,15 @@ class Decoder:
         self.row_scale = torch.tensor(scale, dtype=torch.float32, device=self.device)
         self._alloc_state()
 
+    def _cip(self, li: int) -> int:
+        return self.cip0 if li == 0 else self.WIDTH
+
     def _alloc_state(self):
-        self.wb = [torch.empty(w.shape, dtype=torch.int16, device=self.device) for w in self.w]
+        C = self.WIDTH
+        self.wf = [torch.empty(2 * C, 5 * self._cip(li), dtype=torch.int16, device=self.device)
+                   for li in range(self.layers - 1)]
+        self.wd = [None] + [torch.empty(C, 9 * C, dtype=torch.int16, device=self.device)
+                            for _ in range(1, self.layers - 1)]
         self.mw = [torch.zeros_like(w) for w in self.w]
         self.vw = [torch.zeros_like(w) for w in self.w]
         self.mb = [torch.zeros_like(b) for b in self.b]
@@ -74,11 +88,17 @@ class Decoder:
         self.gw = [torch.zeros_like(w) for w in self.w]
         self.gb = [torch.zeros_like(b) for b in self.b]
         self.t = 0
-        self._sync_bf16()
+        self._a: List[torch.Tensor] = []
+        self._z: List[torch.Tensor] = []
+        self._pack()
 
-    def _sync_bf16(self):
-        for w, wb in zip(self.w, self.wb):
-            _native.check(self._lib.jtfs_cast_bf16(_p(w), _p(wb), w.numel(), _s()), "jtfs_cast_bf16")
+    def _pack(self):
+        for li in range(self.layers - 1):
+            wd = self.wd[li]
+            _native.check(self._lib.jtfs_convt_pack_weights(_p(self.w[li]), _p(self.wf[li]),
+                                                            _p(wd) if wd is not None else c_void_p(0),
+                                                            self.dims[li], self.WIDTH, _s()),
+                          "jtfs_convt_pack_weights")
 
     @property
     def n_params(self) -> int:
@@ -90,63 +110,85 @@ class Decoder:
             raise ValueError("phi must be a float32 CUDA tensor [B][in_channels][frames]")
         phi = phi.contiguous()
         B, _, T = phi.shape
-        h = torch.empty(phi.shape, dtype=torch.int16, device=self.device)
-        _native.check(self._lib.jtfs_cast_bf16_rows(_p(phi), _p(self.row_scale), _p(h), B, self.dims[0], T, _s()),
-                      "jtfs_cast_bf16_rows")
-        self._h, self._z = [h], []
-        for li in range(self.layers):
-            ci, co = self.dims[li], self.dims[li + 1]
-            z = torch.empty(B, co, 2 * T, dtype=torch.float32, device=self.device)
-            _native.check(self._lib.jtfs_convt_forward(_p(h), _p(self.wb[li]), _p(self.b[li]), _p(z), B, ci, co, T,
-                                                       _s()), "jtfs_convt_forward")
-            T *= 2
-            if li + 1 < self.layers:
-                h = torch.empty(z.shape, dtype=torch.int16, device=self.device)
-                _native.check(self._lib.jtfs_gelu_forward(_p(z), _p(h), z.numel(), _s()), "jtfs_gelu_forward")
-                if keep:
-                    self._z.append(z)
-                    self._h.append(h)
+        C = self.WIDTH
+        x = torch.empty(B, T, self.cip0, dtype=torch.int16, device=self.device)
+        _native.check(self._lib.jtfs_convt_pack_input(_p(phi), _p(self.row_scale), _p(x), B, self.dims[0], T, _s()),
+                      "jtfs_convt_pack_input")
+        a, zs = [x], []
+        for li in range(self.layers - 1):
+            z = torch.empty(B, 2 * T, C, dtype=torch.float32, device=self.device) if keep else None
+            h = torch.empty(B, 2 * T, C, dtype=torch.int16, device=self.device)
+            _native.check(self._lib.jtfs_convt_forward(_p(a[-1]), _p(self.wf[li]), _p(self.b[li]),
+                                                       _p(z) if z is not None else c_void_p(0), _p(h), B,
+                                                       self._cip(li), C, T, _s()), "jtfs_convt_forward")
+            if keep:
+                a.append(h)
+                zs.append(z)
             else:
-                out = z
-        if not keep:
-            self._h, self._z = [], []
-        return out.reshape(B, T)
+                a = [h]
+            T *= 2
+        y = torch.empty(B, 2 * T, dtype=torch.float32, device=self.device)
+        _native.check(self._lib.jtfs_convt_out_forward(_p(a[-1]), _p(self.w[-1]), _p(self.b[-1]), _p(y), B, C, T,
+                                                       _s()), "jtfs_convt_out_forward")
+        self._a, self._z = (a, zs) if keep else ([], [])
+        return y
 
     def backward(self, dy: torch.Tensor) -> None:
         """Parameter gradients (written into gw, gb) from dL/dy [B][N] of the last forward."""
-        if not self._h:
+        if not self._a:
             raise RuntimeError("backward needs a forward with keep=True")
+        C = self.WIDTH
+        dy = dy.contiguous().float()
         B = dy.shape[0]
-        dz = dy.reshape(B, 1, -1).contiguous().float()
-        for li in reversed(range(self.layers)):
-            ci, co = self.dims[li], self.dims[li + 1]
-            T = dz.shape[-1] // 2
-            dzb = torch.empty(dz.shape, dtype=torch.int16, device=self.device)
-            _native.check(self._lib.jtfs_cast_bf16(_p(dz), _p(dzb), dz.numel(), _s()), "jtfs_cast_bf16")
-            ws_bytes = self._lib.jtfs_convt_weight_workspace_bytes(B, ci, co, T)
-            ws = torch.empty(max(int(ws_bytes), 4), dtype=torch.uint8, device=self.device)
-            _native.check(self._lib.jtfs_convt_backward_weight(_p(self._h[li]), _p(dzb), _p(dz), _p(self.gw[li]),
-                                                               _p(self.gb[li]), B, ci, co, T, _p(ws), _s()),
+        L = self.layers
+        T = self._a[-1].shape[1]  # input length of the output layer
+        g32 = torch.empty(B, T, C, dtype=torch.float32, device=self.device)
+        g16 = torch.empty(B, T, C, dtype=torch.int16, device=self.device)
+        _native.check(self._lib.jtfs_convt_out_backward_data(_p(dy), _p(self.w[-1]), _p(self._z[-1]), _p(g32),
+                                                             _p(g16), B, C, T, _s()), "jtfs_convt_out_backward_data")
+        ws = torch.empty(max(int(self._lib.jtfs_convt_out_workspace_bytes(B, T)), 16), dtype=torch.uint8,
+                         device=self.device)
+        _native.check(self._lib.jtfs_convt_out_backward_weight(_p(self._a[-1]), _p(dy), _p(self.gw[-1]),
+                                                               _p(self.gb[-1]), B, C, T, _p(ws), _s()),
+                      "jtfs_convt_out_backward_weight")
+        for li in reversed(range(L - 1)):
+            T = self._a[li].shape[1]
+            cip = self._cip(li)
+            wsz = int(self._lib.jtfs_convt_weight_workspace_bytes(B, cip, C, T))
+            ws = torch.empty(max(wsz, 16), dtype=torch.uint8, device=self.device)
+            _native.check(self._lib.jtfs_convt_backward_weight(_p(self._a[li]), _p(g16), _p(self.gw[li]), B,
+                                                               self.dims[li], cip, C, T, _p(ws), _s()),
                           "jtfs_convt_backward_weight")
+            rows = B * 2 * T
+            ws = torch.empty(max(int(self._lib.jtfs_convt_bias_workspace_bytes(rows)), 16), dtype=torch.uint8,
+                             device=self.device)
+            _native.check(self._lib.jtfs_convt_bias_grad(_p(g32), _p(self.gb[li]), rows, C, _p(ws), _s()),
+                          "jtfs_convt_bias_grad")
             if li > 0:
-                dh = torch.empty(B, ci, T, dtype=torch.float32, device=self.device)
-                _native.check(self._lib.jtfs_convt_backward_data(_p(dzb), _p(self.wb[li]), _p(dh), B, ci, co, T, _s()),
+                n32 = torch.empty(B, T, C, dtype=torch.float32, device=self.device)
+                n16 = torch.empty(B, T, C, dtype=torch.int16, device=self.device)
+                _native.check(self._lib.jtfs_convt_backward_data(_p(g16), _p(self.wd[li]), _p(self._z[li - 1]),
+                                                                 _p(n32), _p(n16), B, C, C, T, _s()),
                               "jtfs_convt_backward_data")
-                z = self._z[li - 1]
-                dz = torch.empty_like(dh)
-                _native.check(self._lib.jtfs_gelu_backward(_p(dh), _p(z), _p(dz), dh.numel(), _s()),
-                              "jtfs_gelu_backward")
+                g32, g16 = n32, n16
 
     def step(self, lr: float) -> None:
         """One Adam update of every parameter from the gradients of the last backward."""
         self.t += 1
         for li in range(self.layers):
             _native.check(self._lib.jtfs_adam_update(_p(self.w[li]), _p(self.gw[li]), _p(self.mw[li]), _p(self.vw[li]),
-                                                     _p(self.wb[li]), self.w[li].numel(), float(lr), self.t, _s()),
+                                                     c_void_p(0), self.w[li].numel(), float(lr), self.t, _s()),
                           "jtfs_adam_update")
             _native.check(self._lib.jtfs_adam_update(_p(self.b[li]), _p(self.gb[li]), _p(self.mb[li]), _p(self.vb[li]),
                                                      c_void_p(0), self.b[li].numel(), float(lr), self.t, _s()),
                           "jtfs_adam_update")
+        self._pack()
+
+    def check_errors(self) -> None:
+        """Raise if a tensor-core kernel gave up waiting since the last check (synchronises)."""
+        torch.cuda.synchronize()
+        if self._lib.jtfs_decoder_error():
+            raise RuntimeError("a decoder tensor-core kernel timed out on a barrier; its outputs are invalid")
 
     def state_dict(self) -> dict:
         d = {"dims": np.array(self.dims), "frames": np.array(self.frames), "row_scale": self.row_scale.cpu().numpy()}
@@ -223,7 +265,7 @@ def train(dec: Decoder, plan, clips: torch.Tensor, steps: int, lr: float = 1e-3,
 def propose(dec: Decoder, plan, phi_target: torch.Tensor) -> torch.Tensor:
     """Initial waveforms [B][N] for the targets' Phi [B][phi_size]."""
     rows, frames = phi_shape(plan)
-    return dec.forward(phi_target.view(-1, rows, frames), keep=False).contiguous()
+    return dec.forward(phi_target.view(-1, rows, frames), keep=False)
 
 
 def descend(plan, y: torch.Tensor, phi_target: torch.Tensor, steps: int, lr: float) -> Tuple[torch.Tensor, float]:
