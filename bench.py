@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip autotuning at set-up")
-    ap.add_argument("--workload", default="chirps", choices=["chirps", "uneven64", "initialiser"],
+    ap.add_argument("--workload", default="chirps", choices=["chirps", "uneven64", "initialiser", "decoder"],
                     help="chirps: the 8 x 2^16 benchmark (default); uneven64: 64 clips of 2^14..2^18 samples; "
-                         "initialiser: 32 tone clips of 2^16 samples from the learned decoder vs white noise")
+                         "initialiser: 32 tone clips of 2^16 samples from the learned decoder vs white noise; "
+                         "decoder: the learned initialiser's training step on the tensor cores")
     ap.add_argument("--batch", type=int, default=0,
                     help="clips per GPU (default: the workload's 8); smaller values only for ncu captures")
     return ap.parse_args()
@@ -282,7 +283,7 @@ def run_initialiser(args):
             "dtype": "f32 (decoder: bf16 operands, f32 accumulate)", "data": "synthetic",
             "config": {"workload": wl.name, "batch": wl.batch, **wl.params, "sample_rate_hz": wl.sr,
                        "decoder": "6 transposed convs, 128 channels, kernel 9, GELU; 801 x 1024 -> 65536",
-                       "train": "20k tone clips (seeds 1e6 + i), JTFS loss, 2500 Adam steps of 32",
+                       "train": "20k tone clips (seeds 1e6 + i), JTFS loss, 6250 Adam steps of 32 (10 epochs)",
                        "l2": "each arm's 200 steps timed as one region; inputs and workspace exceed L2"},
             "noise_ms_200_steps": ev["plain_ms"], "decoder_ms": ev["decoder_ms"],
             "learned_steps_to_noise_final": ev["learned_steps_to_plain_final"],
@@ -294,8 +295,88 @@ def run_initialiser(args):
     print(json.dumps(line), flush=True)
 
 
+def run_decoder(args):
+    """The learned initialiser's own training step without the JTFS loss: decoder forward, backward from a
+    fixed waveform gradient, Adam and BF16 repacking, on B clips of Phi (801 rows x 1024 frames, the 2^16-
+    sample tone plan).  Throughput in algorithmic FLOP/s; roofline of the busiest tensor-core kernel."""
+    from paper_2602_11896_gb300.initialiser import Decoder
+    B = args.batch or 32
+    dec = Decoder(801, 1024, seed=0)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    phi = torch.rand(B, 801, 1024, device="cuda", generator=g)
+    dy = torch.randn(B, 1024 << dec.layers, device="cuda", generator=g)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+
+    def step():
+        dec.forward(phi)
+        dec.backward(dy)
+        dec.step(1e-5)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    dec.check_errors()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    dec.profile = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    for e0, e1 in ev:
+        flush.fill_(1.0)
+        e0.record()
+        step()
+        e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    dec.check_errors()
+    ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
+    lf = dec.layer_flops(B)
+    L = dec.layers
+    # forward: every layer; weight gradient: every layer; data gradient: layers 1 .. L-1
+    step_flops = sum(lf) * 2 + sum(lf[1:])
+    kinds = {"fwd": ("k_umma<FwdOp> (forward, layers 0-4)", sum(lf[:L - 1])),
+             "dw": ("k_umma<DwOp> (weight gradient, layers 0-4)", sum(lf[:L - 1])),
+             "dx": ("k_umma<BwdDataOp> (data gradient, layers 1-4)", sum(lf[1:L - 1]))}
+    per_kind = {}
+    for kind, li, e0, e1 in dec.profile:
+        t = e0.elapsed_time(e1)
+        per_kind.setdefault(kind, [0.0, 0])
+        per_kind[kind][0] += t
+        per_kind[kind][1] += 1
+    dec.profile = None
+    top = max(kinds, key=lambda k: per_kind.get(k, [0.0])[0])
+    top_ms = per_kind[top][0] / K  # per step, summed over the kind's launches
+    peak = None
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak = json.load(open(peaks_path)).get("bf16_tflops")
+    achieved = kinds[top][1] / (top_ms / 1e3) / 1e12
+    line = {"metric": "learned-initialiser training step TFLOP/s (algorithmic)", "unit": "TFLOP/s",
+            "value": step_flops / (ms / 1e3) / 1e12, "n_gpus": 1, "steps": K, "warmup": max(args.warmup, 3),
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 operands, f32 accumulate", "data": "synthetic",
+            "config": {"workload": f"decoder_801x1024_b{B}", "batch": B, "layers": L, "width": 128,
+                       "step": "decoder forward + backward (fixed dL/dy) + Adam + bf16 repack",
+                       "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written between timed steps (outside the events)"},
+            "roofline": {"bound": "tensor", "kernel": kinds[top][0], "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if peak else None,
+                         "peak_note": "measured bf16 burst (MEASURED_PEAKS.json), of measured",
+                         "traffic": None},
+            "kernel_ms_per_step": {k: v[0] / K for k, v in per_kind.items()},
+            # per step: forward 1 pack + (L-1) GEMMs + 1 output layer; backward 1 + 2 (output layer)
+            # + (L-1) x (2 weight-gradient + 2 bias) + (L-2) data-gradient; Adam 2 L + (2 L - 3) repacks
+            "gpu_launches": K * ((L + 1) + 3 + 4 * (L - 1) + (L - 2) + 2 * L + (2 * L - 3)), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "decoder":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the chirps workload"}))
+            return
+        run_decoder(args)
+        return
     if args.workload == "initialiser":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the chirps workload"}))

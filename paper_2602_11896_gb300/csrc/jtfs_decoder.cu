@@ -251,7 +251,7 @@ __device__ __forceinline__ void store32_bf16(uint16_t* dst, const float (&v)[32]
 // Forward: grid (ceil(T / 128), B).  A = x rows v0 + 2 - j (box 64 ch x 128 rows),
 // B = Wf [(p, co)][(j, ci)] (box 64 x 256).
 struct FwdOp {
-  static constexpr int kBN = 256, kStages = 4;
+  static constexpr int kBN = 256, kStages = 2;
   static constexpr bool kAMN = false, kBMN = false;
   int T, Cip;
   const float* bias;
@@ -348,7 +348,7 @@ struct BwdDataOp {
 // boxes 64 ch x 64 rows), B = g as [B][T][256] rows u - 2 + m MN-major (four
 // boxes 64 x 64 rows).  Partial sums D[ci][(q, co)] go to part[split][m][ci][256].
 struct DwOp {
-  static constexpr int kBN = 256, kStages = 4;
+  static constexpr int kBN = 256, kStages = 2;
   static constexpr bool kAMN = true, kBMN = true;
   int T, Cip, chunk, spc;  // spc = chunks per clip
   float* part;
@@ -417,25 +417,47 @@ k_out_fwd(const uint16_t* __restrict__ x, const float* __restrict__ w, const flo
   if (v < T) y[int64_t(b) * 2 * T + 2 * v + p] = acc;
 }
 
-// g[b][u][ci] = (sum_k dy[b][2u-4+k] w[ci][k]) * GELU'(zprev[b][u][ci]).
-__global__ void k_out_bwd_data(const float* __restrict__ dy, const float* __restrict__ w,
-                               const float* __restrict__ zprev, float* __restrict__ g32, uint16_t* __restrict__ g16,
-                               int T, int64_t n) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int ci = int(i % kC);
-  const int64_t bu = i / kC;
-  const int u = int(bu % T);
-  const float* d = dy + (bu / T) * 2 * T;
-  float acc = 0.f;
+// g[b][u][ci] = (sum_k dy[b][2u-4+k] w[ci][k]) * GELU'(zprev[b][u][ci]).  One warp per
+// position (b, u), four channels per lane (16-byte loads and stores).
+__global__ void __launch_bounds__(256)
+k_out_bwd_data(const float* __restrict__ dy, const float* __restrict__ w, const float* __restrict__ zprev,
+               float* __restrict__ g32, uint16_t* __restrict__ g16, int T, int64_t rows) {
+  __shared__ float4 ws[9][kC / 4];
+  for (int i = threadIdx.x; i < 9 * (kC / 4); i += blockDim.x) {
+    const int k = i / (kC / 4), c = 4 * (i % (kC / 4));
+    ws[k][i % (kC / 4)] = make_float4(w[c * 9 + k], w[(c + 1) * 9 + k], w[(c + 2) * 9 + k], w[(c + 3) * 9 + k]);
+  }
+  __syncthreads();
+  const int64_t row = int64_t(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (row >= rows) return;
+  const int c4 = threadIdx.x & 31;
+  const int u = int(row % T);
+  const float* d = dy + (row / T) * 2 * T;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int t = 2 * u - 4 + k;
-    if (t >= 0 && t < 2 * T) acc += d[t] * w[ci * 9 + k];
+    if (t >= 0 && t < 2 * T) {
+      const float dv = d[t];
+      const float4 q = ws[k][c4];
+      acc.x += dv * q.x;
+      acc.y += dv * q.y;
+      acc.z += dv * q.z;
+      acc.w += dv * q.w;
+    }
   }
-  if (zprev) acc *= gelu_grad(zprev[i]);
-  if (g32) g32[i] = acc;
-  if (g16) g16[i] = f2bf(acc);
+  const int64_t i4 = row * (kC / 4) + c4;
+  if (zprev) {
+    const float4 z = reinterpret_cast<const float4*>(zprev)[i4];
+    acc.x *= gelu_grad(z.x);
+    acc.y *= gelu_grad(z.y);
+    acc.z *= gelu_grad(z.z);
+    acc.w *= gelu_grad(z.w);
+  }
+  if (g32) reinterpret_cast<float4*>(g32)[i4] = acc;
+  if (g16)
+    reinterpret_cast<uint2*>(g16)[i4] = make_uint2(uint32_t(f2bf(acc.x)) | (uint32_t(f2bf(acc.y)) << 16),
+                                                   uint32_t(f2bf(acc.z)) | (uint32_t(f2bf(acc.w)) << 16));
 }
 
 constexpr int kOutChunk = 256;  // positions per CTA of the output layer's weight gradient
@@ -502,9 +524,17 @@ __global__ void __launch_bounds__(128)
 k_colsum(const float* __restrict__ g, int64_t rows, float* __restrict__ part) {
   const int64_t r0 = int64_t(blockIdx.x) * kColChunk;
   const int64_t r1 = min(rows, r0 + kColChunk);
-  float acc = 0.f;
-  for (int64_t r = r0; r < r1; ++r) acc += g[r * kC + threadIdx.x];
-  part[int64_t(blockIdx.x) * kC + threadIdx.x] = acc;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;  // four interleaved partial sums, combined in fixed order
+  const float* p = g + threadIdx.x;
+  int64_t r = r0;
+  for (; r + 4 <= r1; r += 4) {
+    a0 += p[r * kC];
+    a1 += p[(r + 1) * kC];
+    a2 += p[(r + 2) * kC];
+    a3 += p[(r + 3) * kC];
+  }
+  for (; r < r1; ++r) a0 += p[r * kC];
+  part[int64_t(blockIdx.x) * kC + threadIdx.x] = (a0 + a1) + (a2 + a3);
 }
 
 __global__ void k_colsum_reduce(const float* __restrict__ part, float* __restrict__ db, int chunks) {
@@ -723,8 +753,11 @@ extern "C" int jtfs_convt_out_forward(const uint16_t* x, const float* w, const f
 extern "C" int jtfs_convt_out_backward_data(const float* dy, const float* w, const float* zprev, float* g_prev,
                                             uint16_t* g_prev_bf16, int B, int Ci, int T, void* stream) {
   if (!dy || !w || (!g_prev && !g_prev_bf16) || Ci != kC || bad(B, T)) return JTFS_ERR_ARG;
-  const int64_t n = int64_t(B) * T * kC;
-  k_out_bwd_data<<<blocks(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(dy, w, zprev, g_prev, g_prev_bf16, T, n);
+  if ((zprev && !aligned16(zprev)) || (g_prev && !aligned16(g_prev)) || (g_prev_bf16 && !aligned16(g_prev_bf16)))
+    return JTFS_ERR_ARG;
+  const int64_t rows = int64_t(B) * T;
+  k_out_bwd_data<<<static_cast<unsigned>(cdiv(rows, 8)), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      dy, w, zprev, g_prev, g_prev_bf16, T, rows);
   return ok();
 }
 

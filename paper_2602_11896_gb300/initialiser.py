@@ -70,7 +70,20 @@ class Decoder:
         if scale.shape != (in_channels,):
             raise ValueError("row_scale must have one entry per input channel")
         self.row_scale = torch.tensor(scale, dtype=torch.float32, device=self.device)
+        # When a list, every layer call appends (kind, layer, start event, end event) to it.
+        self.profile: Optional[list] = None
         self._alloc_state()
+
+    def _call(self, kind: str, li: int, name: str, *args) -> None:
+        fn = getattr(self._lib, name)
+        if self.profile is None:
+            _native.check(fn(*args), name)
+            return
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _native.check(fn(*args), name)
+        e1.record()
+        self.profile.append((kind, li, e0, e1))
 
     def _cip(self, li: int) -> int:
         return self.cip0 if li == 0 else self.WIDTH
@@ -100,6 +113,15 @@ class Decoder:
                                                             self.dims[li], self.WIDTH, _s()),
                           "jtfs_convt_pack_weights")
 
+    def layer_flops(self, batch: int) -> List[float]:
+        """Algorithmic FLOPs of each layer's forward product: 2 x outputs x Co x Ci x 4.5
+        (a kernel-9, stride-2 transposed convolution reaches each output from 4.5 taps on average)."""
+        out, T = [], self.frames
+        for li in range(self.layers):
+            out.append(2.0 * batch * 2 * T * self.dims[li + 1] * self.dims[li] * KERNEL / 2.0)
+            T *= 2
+        return out
+
     @property
     def n_params(self) -> int:
         return sum(w.numel() for w in self.w) + sum(b.numel() for b in self.b)
@@ -118,9 +140,8 @@ class Decoder:
         for li in range(self.layers - 1):
             z = torch.empty(B, 2 * T, C, dtype=torch.float32, device=self.device) if keep else None
             h = torch.empty(B, 2 * T, C, dtype=torch.int16, device=self.device)
-            _native.check(self._lib.jtfs_convt_forward(_p(a[-1]), _p(self.wf[li]), _p(self.b[li]),
-                                                       _p(z) if z is not None else c_void_p(0), _p(h), B,
-                                                       self._cip(li), C, T, _s()), "jtfs_convt_forward")
+            self._call("fwd", li, "jtfs_convt_forward", _p(a[-1]), _p(self.wf[li]), _p(self.b[li]),
+                       _p(z) if z is not None else c_void_p(0), _p(h), B, self._cip(li), C, T, _s())
             if keep:
                 a.append(h)
                 zs.append(z)
@@ -128,8 +149,8 @@ class Decoder:
                 a = [h]
             T *= 2
         y = torch.empty(B, 2 * T, dtype=torch.float32, device=self.device)
-        _native.check(self._lib.jtfs_convt_out_forward(_p(a[-1]), _p(self.w[-1]), _p(self.b[-1]), _p(y), B, C, T,
-                                                       _s()), "jtfs_convt_out_forward")
+        self._call("out_fwd", self.layers - 1, "jtfs_convt_out_forward", _p(a[-1]), _p(self.w[-1]), _p(self.b[-1]),
+                   _p(y), B, C, T, _s())
         self._a, self._z = (a, zs) if keep else ([], [])
         return y
 
@@ -144,32 +165,28 @@ class Decoder:
         T = self._a[-1].shape[1]  # input length of the output layer
         g32 = torch.empty(B, T, C, dtype=torch.float32, device=self.device)
         g16 = torch.empty(B, T, C, dtype=torch.int16, device=self.device)
-        _native.check(self._lib.jtfs_convt_out_backward_data(_p(dy), _p(self.w[-1]), _p(self._z[-1]), _p(g32),
-                                                             _p(g16), B, C, T, _s()), "jtfs_convt_out_backward_data")
+        self._call("out_dx", L - 1, "jtfs_convt_out_backward_data", _p(dy), _p(self.w[-1]), _p(self._z[-1]), _p(g32),
+                   _p(g16), B, C, T, _s())
         ws = torch.empty(max(int(self._lib.jtfs_convt_out_workspace_bytes(B, T)), 16), dtype=torch.uint8,
                          device=self.device)
-        _native.check(self._lib.jtfs_convt_out_backward_weight(_p(self._a[-1]), _p(dy), _p(self.gw[-1]),
-                                                               _p(self.gb[-1]), B, C, T, _p(ws), _s()),
-                      "jtfs_convt_out_backward_weight")
+        self._call("out_dw", L - 1, "jtfs_convt_out_backward_weight", _p(self._a[-1]), _p(dy), _p(self.gw[-1]),
+                   _p(self.gb[-1]), B, C, T, _p(ws), _s())
         for li in reversed(range(L - 1)):
             T = self._a[li].shape[1]
             cip = self._cip(li)
             wsz = int(self._lib.jtfs_convt_weight_workspace_bytes(B, cip, C, T))
             ws = torch.empty(max(wsz, 16), dtype=torch.uint8, device=self.device)
-            _native.check(self._lib.jtfs_convt_backward_weight(_p(self._a[li]), _p(g16), _p(self.gw[li]), B,
-                                                               self.dims[li], cip, C, T, _p(ws), _s()),
-                          "jtfs_convt_backward_weight")
+            self._call("dw", li, "jtfs_convt_backward_weight", _p(self._a[li]), _p(g16), _p(self.gw[li]), B,
+                       self.dims[li], cip, C, T, _p(ws), _s())
             rows = B * 2 * T
             ws = torch.empty(max(int(self._lib.jtfs_convt_bias_workspace_bytes(rows)), 16), dtype=torch.uint8,
                              device=self.device)
-            _native.check(self._lib.jtfs_convt_bias_grad(_p(g32), _p(self.gb[li]), rows, C, _p(ws), _s()),
-                          "jtfs_convt_bias_grad")
+            self._call("db", li, "jtfs_convt_bias_grad", _p(g32), _p(self.gb[li]), rows, C, _p(ws), _s())
             if li > 0:
                 n32 = torch.empty(B, T, C, dtype=torch.float32, device=self.device)
                 n16 = torch.empty(B, T, C, dtype=torch.int16, device=self.device)
-                _native.check(self._lib.jtfs_convt_backward_data(_p(g16), _p(self.wd[li]), _p(self._z[li - 1]),
-                                                                 _p(n32), _p(n16), B, C, C, T, _s()),
-                              "jtfs_convt_backward_data")
+                self._call("dx", li, "jtfs_convt_backward_data", _p(g16), _p(self.wd[li]), _p(self._z[li - 1]),
+                           _p(n32), _p(n16), B, C, C, T, _s())
                 g32, g16 = n32, n16
 
     def step(self, lr: float) -> None:

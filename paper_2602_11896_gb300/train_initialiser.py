@@ -50,7 +50,7 @@ def main(argv=None) -> dict:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--clips", type=int, default=TRAIN_CLIPS)
     ap.add_argument("--batch", type=int, default=32)
-    ap.add_argument("--epochs", type=float, default=4.0)
+    ap.add_argument("--epochs", type=float, default=10.0)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--workers", type=int, default=min(16, mp.cpu_count()))
     ap.add_argument("--seed", type=int, default=0)
