@@ -52,10 +52,12 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip autotuning at set-up")
-    ap.add_argument("--workload", default="chirps", choices=["chirps", "uneven64", "initialiser", "decoder"],
+    ap.add_argument("--workload", default="chirps",
+                    choices=["chirps", "uneven64", "initialiser", "decoder", "long"],
                     help="chirps: the 8 x 2^16 benchmark (default); uneven64: 64 clips of 2^14..2^18 samples; "
                          "initialiser: 32 tone clips of 2^16 samples from the learned decoder vs white noise; "
-                         "decoder: the learned initialiser's training step on the tensor cores")
+                         "decoder: the learned initialiser's training step on the tensor cores; "
+                         "long: 4 clips of 2^20 samples, forward + loss + gradient")
     ap.add_argument("--batch", type=int, default=0,
                     help="clips per GPU (default: the workload's 8); smaller values only for ncu captures")
     return ap.parse_args()
@@ -295,6 +297,45 @@ def run_initialiser(args):
     print(json.dumps(line), flush=True)
 
 
+def run_long(args):
+    """4 clips of 2^20 samples (polyphonic notes + pink noise at 22.05 kHz; J=14, Q=16, Q2=2, J_fr=6,
+    Q_fr=2, T=2^13, F=16): one step = forward, loss against the targets' Phi and the hand-written adjoint
+    (jtfs_loss_grad; U1's phase and every un-pooled second-order column are recomputed, never stored)."""
+    from paper_2602_11896_gb300 import JTFSPlan
+    wl = get_workload("notes22k_b4_n1048576")
+    torch.cuda.reset_peak_memory_stats()
+    plan = JTFSPlan(**wl.params, batch=wl.batch)
+    phi_t = plan.forward(torch.tensor(wl.targets(), device="cuda"))
+    y = torch.tensor(wl.inits(), device="cuda")
+    loss = torch.empty(wl.batch, device="cuda")
+    grad = torch.empty_like(y)
+    ws = plan.workspace(y.device)
+    for _ in range(max(args.warmup, 3)):
+        plan.loss_grad(y, phi_t, loss_out=loss, grad_out=grad, workspace=ws)
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    for e0, e1 in ev:
+        e0.record()
+        plan.loss_grad(y, phi_t, loss_out=loss, grad_out=grad, workspace=ws)
+        e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
+    peak = torch.cuda.max_memory_allocated()
+    line = {"metric": METRIC, "value": wl.batch * wl.N / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {**config_dict(wl), "step": "jtfs_loss_grad: forward + loss + hand-written adjoint",
+                       "l2": "workspace and inputs exceed L2 (tens of GB)"},
+            "peak_hbm_gib": peak / 2 ** 30, "workspace_gib": plan.workspace_bytes / 2 ** 30,
+            "gpu_launches": int(plan._lib.jtfs_launch_count(plan._h, 2)) * K, "clocks": clk,
+            "loss_mean": float(loss.mean().item())}
+    print(json.dumps(line), flush=True)
+
+
 def run_decoder(args):
     """The learned initialiser's own training step without the JTFS loss: decoder forward, backward from a
     fixed waveform gradient, Adam and BF16 repacking, on B clips of Phi (801 rows x 1024 frames, the 2^16-
@@ -371,6 +412,12 @@ def run_decoder(args):
 
 def main():
     args = parse()
+    if args.workload == "long":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the chirps workload"}))
+            return
+        run_long(args)
+        return
     if args.workload == "decoder":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the chirps workload"}))

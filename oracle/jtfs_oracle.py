@@ -67,7 +67,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field
-from typing import Dict, List, Tuple
+from typing import Dict, List, Optional, Sequence, Tuple
 
 import torch
 
@@ -254,13 +254,16 @@ def pad_rows(z: torch.Tensor, n: int, dim: int) -> torch.Tensor:
 # ---------------------------------------------------------------------------
 
 def jtfs(x: torch.Tensor, plan: Plan, keep: bool = False,
-         checkpoint_blocks: bool = False) -> Dict[str, torch.Tensor]:
+         checkpoint_blocks: bool = False, active: Optional[Sequence[int]] = None) -> Dict[str, torch.Tensor]:
     """JTFS of x [B, N] (float64).  Returns {'phi': [B, phi_size], ...}.
 
     With ``keep`` the intermediates U1 (list over n1), S1 and Y2 (list over
     active n2) are returned too.  ``checkpoint_blocks`` recomputes each
     second-order block in the backward pass instead of storing it (same
-    arithmetic; only bounds autograd memory for long signals).
+    arithmetic; only bounds autograd memory for long signals).  ``active``
+    (positions in ``plan.active``) restricts the second order to those paths:
+    the result then has S0, Phi1 and {'Phi2_sel': {position: [B, 1+2K, R_out, N/T]}}
+    instead of 'phi' (for sampling long signals).
     """
     if x.dim() == 1:
         x = x[None]
@@ -314,6 +317,10 @@ def jtfs(x: torch.Tensor, plan: Plan, keep: bool = False,
             v = decimate(conv_circ(a, periodise(phiF, k_b), 1), lF - k_b, 1).real     # *_n1 phi_F
             blocks.append(v)
         return torch.stack(blocks, 1), Y2                                # [B, 1+2K, R_out, N/T]
+
+    if active is not None:
+        sel = {int(a): second_order_block(U1, plan.active[int(a)])[0] for a in active}
+        return {"S0": S0, "Phi1": Phi1, "Phi2_sel": sel}
 
     phi2, Y2s = [], []
     for n2 in plan.active:

@@ -252,6 +252,18 @@ def test_checkpointed_gradient_identical():
     assert (g1 - g2).abs().max().item() <= 1e-13 * g1.abs().max().item()
 
 
+def test_selected_second_order_paths_equal_the_full_transform():
+    """The path-subset evaluation (used to sample long signals) returns exactly the
+    blocks of the full transform."""
+    p = O.Plan(**TINY[1])
+    x = torch.tensor(np.random.default_rng(6).standard_normal((2, p.N)))
+    full = O.jtfs(x, p, keep=True)
+    sel = O.jtfs(x, p, active=[0, len(p.active) - 1])
+    assert torch.equal(sel["S0"], full["S0"]) and torch.equal(sel["Phi1"], full["Phi1"])
+    for a, blk in sel["Phi2_sel"].items():
+        assert torch.equal(blk, full["Phi2"][:, a])
+
+
 # --------------------------------------------------------------------------- planted mistakes
 
 def test_pins_catch_dropped_kappa(monkeypatch):
