@@ -171,13 +171,19 @@ __host__ __device__ __forceinline__ int ceil_log2(int n) {
 }
 
 
-// Shape-specialised frequential kernels (jtfs_freq_ct.cu).  Each returns
-// false, launching nothing, when no specialisation matches the plan's
-// (N_fr, columns per tile, log2 F).
+// Shape-specialised frequential kernels (jtfs_freq_ct_fwd.cu, jtfs_freq_ct_adj.cu;
+// the N_fr = 512 shapes in jtfs_freq_ct_long_*.cu).  Each returns false,
+// launching nothing, when no specialisation matches the plan's (N_fr, columns
+// per tile, log2 F).
 bool launch_freq_fwd_ct(int mode, const FreqArgs& A, int lF, unsigned grid, size_t smem, cudaStream_t s,
                         const Tile* tiles, const float* S1, const float2* Y2, float* out);
 bool launch_freq_adj_ct(int mode, const FreqArgs& A, int lF, unsigned grid, size_t smem, cudaStream_t s,
                         const Tile* tiles, const float* S1, const float2* Y2, const float* dout, float* dS1,
                         float2* dY2);
+bool launch_freq_fwd_ct_long(int mode, const FreqArgs& A, int lF, unsigned grid, size_t smem, cudaStream_t s,
+                             const Tile* tiles, const float* S1, const float2* Y2, float* out);
+bool launch_freq_adj_ct_long(int mode, const FreqArgs& A, int lF, unsigned grid, size_t smem, cudaStream_t s,
+                             const Tile* tiles, const float* S1, const float2* Y2, const float* dout, float* dS1,
+                             float2* dY2);
 
 }  // namespace jtfs

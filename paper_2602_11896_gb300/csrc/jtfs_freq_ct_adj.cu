@@ -18,7 +18,7 @@ bool launch_freq_adj_ct(int mode, const FreqArgs& A, int lF, unsigned grid, size
   JTFS_CT_ADJ(8, 3, 3)
   JTFS_CT_ADJ(6, 4, 2)
 #undef JTFS_CT_ADJ
-  return false;
+  return launch_freq_adj_ct_long(mode, A, lF, grid, smem, s, tiles, S1, Y2, dout, dS1, dY2);
 }
 
 }  // namespace jtfs

@@ -18,7 +18,7 @@ bool launch_freq_fwd_ct(int mode, const FreqArgs& A, int lF, unsigned grid, size
   JTFS_CT_FWD(8, 3, 3)
   JTFS_CT_FWD(6, 4, 2)
 #undef JTFS_CT_FWD
-  return false;
+  return launch_freq_fwd_ct_long(mode, A, lF, grid, smem, s, tiles, S1, Y2, out);
 }
 
 }  // namespace jtfs
