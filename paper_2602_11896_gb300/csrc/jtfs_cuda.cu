@@ -1067,6 +1067,12 @@ FreqArgs freq_args(const Plan& p, int mode) {
   A.v2_off = p.d_v2_off;
   A.tw = p.d_tw;
   A.twlog = p.twlog;
+  A.ftabc = p.d_ftabc;
+  A.ftabc_off = p.d_ftabc_off;
+  A.n_ftabc = static_cast<int>(p.h_ftabc.size());
+  A.ftabc_phi = p.ftabc_phi;
+  A.tab_smem = 0;
+  for (int k = 0; k < 16; ++k) A.ftabc_lev[k] = p.ftabc_lev[k];
   return A;
 }
 
@@ -1156,7 +1162,17 @@ size_t freq_smem(const Plan& p, int nbuf, int cols = 0) {
   if (cols == 0) cols = p.freq_cols;
   return size_t(p.N_fr) * sizeof(float2) + size_t(nbuf) * cols * p.N_fr * sizeof(float2) +
          size_t(p.n_beta2) * sizeof(int2) +
-         std::max(p.chunks1.size(), p.chunks2.size()) * sizeof(FreqChunk);
+         std::max(p.chunks1.size(), p.chunks2.size()) * sizeof(FreqChunk) + size_t(p.n_beta2) * sizeof(int) + 16;
+}
+
+// Shared memory of a specialised second-order launch: with the compact filter
+// tables staged (A.tab_smem = 1) when two CTAs still fit on an SM, else without.
+size_t ct_smem(const Plan& p, int nbuf, int cols, FreqArgs& A) {
+  constexpr size_t kTwoCtas = 113 * 1024;
+  const size_t base = freq_smem(p, nbuf, cols);
+  const size_t with = base + p.h_ftabc.size() * sizeof(float);
+  A.tab_smem = with <= kTwoCtas ? 1 : 0;
+  return A.tab_smem ? with : base;
 }
 
 // Forward stages.  `full` = false stops after what the adjoint needs
@@ -1183,14 +1199,15 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
     if (full) {
       allow_big_smem<k_freq_fwd<2>>();
       prof_begin(p, JTFS_STAGE_FREQ2_FWD, s);
-      FreqArgs FA2w = FA2;
+      FreqArgs FA2w = FA2, FA2n = FA2;
       FA2w.W = p.freq_cols_wide;
       FA2w.logW = ceil_log2(p.freq_cols_wide);
-      if (!(p.tune_wide && launch_freq_fwd_ct(2, FA2w, p.lF, static_cast<unsigned>(p.tiles2w.size()),
-                                              freq_smem(p, 3, p.freq_cols_wide), s, p.d_tiles2w, nullptr, w.Y2,
-                                              w.V2)) &&
-          !launch_freq_fwd_ct(2, FA2, p.lF, static_cast<unsigned>(p.tiles2.size()), freq_smem(p, 3), s,
-                              p.d_tiles2, nullptr, w.Y2, w.V2))
+      const size_t smem_w = ct_smem(p, 3, p.freq_cols_wide, FA2w);
+      const size_t smem_n = ct_smem(p, 3, p.freq_cols, FA2n);
+      if (!(p.tune_wide && launch_freq_fwd_ct(2, FA2w, p.lF, static_cast<unsigned>(p.tiles2w.size()), smem_w, s,
+                                              p.d_tiles2w, nullptr, w.Y2, w.V2)) &&
+          !launch_freq_fwd_ct(2, FA2n, p.lF, static_cast<unsigned>(p.tiles2.size()), smem_n, s, p.d_tiles2,
+                              nullptr, w.Y2, w.V2))
         k_freq_fwd<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 3), s>>>(
             FA2, p.d_tiles2, nullptr, w.Y2, w.V2);
       prof_end(p, JTFS_STAGE_FREQ2_FWD, s);
@@ -1244,8 +1261,10 @@ int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, 
     JTFS_TRY(check_launch());
     allow_big_smem<k_freq_adj<2>>();
     prof_begin(p, JTFS_STAGE_FREQ2_ADJ, s);
-    if (!launch_freq_adj_ct(2, FA2, p.lF, static_cast<unsigned>(p.tiles2.size()), freq_smem(p, 5), s, p.d_tiles2,
-                            nullptr, w.Y2, w.V2, nullptr, w.dY2))
+    FreqArgs FA2c = FA2;
+    const size_t smem_c = ct_smem(p, 5, p.freq_cols, FA2c);
+    if (!launch_freq_adj_ct(2, FA2c, p.lF, static_cast<unsigned>(p.tiles2.size()), smem_c, s, p.d_tiles2, nullptr,
+                            w.Y2, w.V2, nullptr, w.dY2))
       k_freq_adj<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 5), s>>>(
           FA2, p.d_tiles2, nullptr, w.Y2, w.V2, nullptr, w.dY2);
     prof_end(p, JTFS_STAGE_FREQ2_ADJ, s);

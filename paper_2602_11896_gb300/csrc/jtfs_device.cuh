@@ -102,6 +102,11 @@ struct FreqArgs {
   const int64_t* v2_off;
   const float2* tw;
   int twlog;
+  // compact tables (see Plan::h_ftabc); tab_smem = 1 stages them in shared memory
+  const float* ftabc;
+  const int* ftabc_off;
+  int n_ftabc, ftabc_phi, tab_smem;
+  int ftabc_lev[16];
 };
 
 // Shared-memory layout of the frequential kernels (all in float2 units):
@@ -109,12 +114,16 @@ struct FreqArgs {
 //   bufs  nbuf x [W * N_fr]     interleaved transforms
 //   band  [n_beta2] int2        (lo, hi) of each frequential filter
 //   chk   [n_chunks] FreqChunk
+//   toff  [n_beta2] int         offset of each filter's band in the compact table
+//   tc    [n_ftabc] float       compact table (16-byte aligned), when A.tab_smem
 struct FreqSmem {
   float2* tw;
   float2* buf;
   const float* tab;  // global (read through L1): [n_ftab][N_fr]
   int2* band;
   FreqChunk* chk;
+  int* toff;
+  const float* tc;   // compact table: shared memory if A.tab_smem, else global
 };
 
 __device__ __forceinline__ FreqSmem freq_smem_carve(const FreqArgs& A, float2* sm, int nbuf) {
@@ -125,6 +134,9 @@ __device__ __forceinline__ FreqSmem freq_smem_carve(const FreqArgs& A, float2* s
   S.tab = A.ftab;
   S.band = reinterpret_cast<int2*>(S.buf + nbuf * WN);
   S.chk = reinterpret_cast<FreqChunk*>(S.band + A.n_beta2);
+  S.toff = reinterpret_cast<int*>(S.chk + A.n_chunks);
+  float* tcs = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(S.toff + A.n_beta2) + 15) & ~uintptr_t(15));
+  S.tc = A.tab_smem ? tcs : A.ftabc;
   return S;
 }
 
@@ -136,6 +148,11 @@ __device__ __forceinline__ void freq_stage_tables(const FreqArgs& A, const FreqS
   int* cdst = reinterpret_cast<int*>(S.chk);
   for (int i = threadIdx.x; i < A.n_chunks * static_cast<int>(sizeof(FreqChunk) / sizeof(int)); i += blockDim.x)
     cdst[i] = csrc[i];
+  for (int i = threadIdx.x; i < A.n_beta2; i += blockDim.x) S.toff[i] = __ldg(A.ftabc_off + i);
+  if (A.tab_smem) {
+    float* tcs = const_cast<float*>(S.tc);
+    for (int i = threadIdx.x; i < A.n_ftabc; i += blockDim.x) tcs[i] = __ldg(A.ftabc + i);
+  }
 }
 
 // Columns of the tile into interleaved layout dst[r * W + w], zero-padded to N_fr rows.

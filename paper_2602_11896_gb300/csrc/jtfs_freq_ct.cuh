@@ -162,11 +162,11 @@ __device__ __forceinline__ void ct_fold(const FreqSmem& S, const FreqChunk& ch, 
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (b >= 0) {
       const int2 bd = S.band[b];
-      const float* t = S.tab + b * NFR;
+      const float* t = S.tc + S.toff[b] - bd.x;  // t[sb] = filter at signed bin sb of its band
       const float4* yc = y4 + wp;
       for (int sb = bd.x + ((m - bd.x) & (R - 1)); sb <= bd.y; sb += R) {
         const int q = sb & (NFR - 1);
-        const float g = __ldg(t + q);
+        const float g = t[sb];
         const float4 y = yc[q << LWP];
         acc.x += g * y.x;
         acc.y += g * y.y;
@@ -183,7 +183,7 @@ template <int LOGNFR, int LF, int K, int LC>
 __device__ __forceinline__ void ct_pool_fold(const FreqArgs& A, const FreqSmem& S, const float2* uh, float2* out) {
   constexpr int NFR = 1 << LOGNFR, LR = LOGNFR - K, R = 1 << LR, LRO = LOGNFR - LF, RO = 1 << LRO, LP = LC - 1;
   constexpr float INV = 1.f / R;
-  const float* t = S.tab + A.n_beta2 * NFR;
+  const float* t = S.tc + A.ftabc_phi - A.phiF.lo;  // t[sb] = phi_F at signed bin sb of its band
   const float4* u4 = reinterpret_cast<const float4*>(uh);
   float4* o4 = reinterpret_cast<float4*>(out);
 #pragma unroll 2
@@ -191,7 +191,7 @@ __device__ __forceinline__ void ct_pool_fold(const FreqArgs& A, const FreqSmem& 
     const int fp = i & ((1 << LP) - 1), m = i >> LP;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int sb = A.phiF.lo + ((m - A.phiF.lo) & (RO - 1)); sb <= A.phiF.hi; sb += RO) {
-      const float g = __ldg(t + (sb & (NFR - 1)));
+      const float g = t[sb];
       const float4 v = u4[((sb & (R - 1)) << LP) + fp];
       acc.x += g * v.x;
       acc.y += g * v.y;
@@ -287,13 +287,13 @@ __device__ __forceinline__ void adj_chunk(const FreqArgs& A, const FreqSmem& S, 
   float2* dW = CtFft<false, LRO, LC, 0, LOGNFR>::run(dwb, z, S.tw);
   float2* X = (dW == dwb) ? z : dwb;
   {
-    const float* lev = S.tab + (A.n_beta2 + 1 + K) * NFR;
+    const float* lev = S.tc + A.ftabc_lev[K];
     const float4* dW4 = reinterpret_cast<const float4*>(dW);
     float4* X4 = reinterpret_cast<float4*>(X);
 #pragma unroll 4
     for (int i = threadIdx.x; i < (R << LP); i += kThreads) {
       const int fp = i & ((1 << LP) - 1), m = i >> LP;
-      const float sc = __ldg(lev + m) * INVR;
+      const float sc = lev[m] * INVR;
       const float4 v = dW4[((m & (RO - 1)) << LP) + fp];
       X4[i] = make_float4(v.x * sc, v.y * sc, v.z * sc, v.w * sc);
     }
@@ -327,7 +327,7 @@ __device__ __forceinline__ void adj_chunk(const FreqArgs& A, const FreqSmem& S, 
         const int b = ch.beta[bc];
         const int2 bd = S.band[b];
         if (sgn < bd.x || sgn > bd.y) continue;
-        const float gg = __ldg(S.tab + b * NFR + m);
+        const float gg = S.tc[S.toff[b] + (sgn - bd.x)];
         const float4 v = dZ4[((m & (R - 1)) << LP) + (bc << LWP) + wp];
         acc.x += gg * v.x;
         acc.y += gg * v.y;

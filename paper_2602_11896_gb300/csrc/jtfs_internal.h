@@ -154,6 +154,13 @@ struct Plan {
   // phi_F periodised onto N_fr / 2^k bins (k = 0 .. log2 F).
   std::vector<float> h_ftab;
   int n_ftab = 0;
+  // The same tables restricted to what the specialised kernels read: each
+  // second-order beta over its band [lo, hi] (offset ftabc_off[b]), phi_F over
+  // its band (offset ftabc_phi), and the phi_F level rows (offset ftabc_lev[k]).
+  std::vector<float> h_ftabc;
+  std::vector<int> h_ftabc_off;
+  int ftabc_phi = 0;
+  int ftabc_lev[16] = {};
 
   // Host copies of the device tables.
   std::vector<FiltD> h_psi1, h_psi2, h_beta;  // psi1/psi2 on grid N; beta on N_fr
@@ -177,6 +184,8 @@ struct Plan {
   const FreqChunk* d_chunks1 = nullptr;
   const FreqChunk* d_chunks2 = nullptr;
   const float* d_ftab = nullptr;
+  const float* d_ftabc = nullptr;
+  const int* d_ftabc_off = nullptr;
   const int4* d_pool_tiles = nullptr;
   const int4* d_pool_fwd_tiles[3] = {nullptr, nullptr, nullptr};
   const int* d_pool_tile0[3] = {nullptr, nullptr, nullptr};

@@ -328,6 +328,19 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
         p.h_ftab[size_t(p.n_beta2 + 1 + k) * n + m] = static_cast<float>(acc);
       }
     }
+    p.h_ftabc.clear();
+    p.h_ftabc_off.assign(p.n_beta2, 0);
+    for (int b = 0; b < p.n_beta2; ++b) {
+      p.h_ftabc_off[b] = static_cast<int>(p.h_ftabc.size());
+      for (int sb = p.h_beta[b].lo; sb <= p.h_beta[b].hi; ++sb) p.h_ftabc.push_back(p.h_ftab[size_t(b) * n + (sb & (n - 1))]);
+    }
+    p.ftabc_phi = static_cast<int>(p.h_ftabc.size());
+    for (int sb = p.h_phiF.lo; sb <= p.h_phiF.hi; ++sb)
+      p.h_ftabc.push_back(p.h_ftab[size_t(p.n_beta2) * n + (sb & (n - 1))]);
+    for (int k = 0; k <= p.lF && k < 16; ++k) {
+      p.ftabc_lev[k] = static_cast<int>(p.h_ftabc.size());
+      for (int m = 0; m < (n >> k); ++m) p.h_ftabc.push_back(p.h_ftab[size_t(p.n_beta2 + 1 + k) * n + m]);
+    }
   }
   // Chunks of frequential filters with equal stride level.
   auto make_chunks = [&](int nb, std::vector<FreqChunk>& out) {
@@ -463,6 +476,8 @@ int upload_plan(Plan& p) {
   const size_t o_c1 = put(p.chunks1.data(), p.chunks1.size() * sizeof(FreqChunk));
   const size_t o_c2 = put(p.chunks2.data(), p.chunks2.size() * sizeof(FreqChunk));
   const size_t o_ftab = put(p.h_ftab.data(), p.h_ftab.size() * sizeof(float));
+  const size_t o_ftabc = put(p.h_ftabc.data(), p.h_ftabc.size() * sizeof(float));
+  const size_t o_ftabc_off = put(p.h_ftabc_off.data(), p.h_ftabc_off.size() * sizeof(int));
   const size_t o_pt = put(p.pool_tiles.data(), p.pool_tiles.size() * sizeof(int4));
   size_t o_pft[3], o_pt0[3];
   for (int si = 0; si < 3; ++si) {
@@ -505,6 +520,8 @@ int upload_plan(Plan& p) {
   p.d_chunks1 = reinterpret_cast<const FreqChunk*>(at(o_c1));
   p.d_chunks2 = reinterpret_cast<const FreqChunk*>(at(o_c2));
   p.d_ftab = reinterpret_cast<const float*>(at(o_ftab));
+  p.d_ftabc = reinterpret_cast<const float*>(at(o_ftabc));
+  p.d_ftabc_off = reinterpret_cast<const int*>(at(o_ftabc_off));
   p.d_pool_tiles = reinterpret_cast<const int4*>(at(o_pt));
   for (int si = 0; si < 3; ++si) {
     p.d_pool_fwd_tiles[si] = reinterpret_cast<const int4*>(at(o_pft[si]));
