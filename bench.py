@@ -546,7 +546,7 @@ def main():
     roofline = None
     if flops is not None:
         ach = flops / (stage_ms[dom] / 1e3) / 1e12
-        per_clip = DRAM_BYTES_PER_CLIP.get(dom)
+        per_clip = (DRAM_BYTES_PER_CLIP or {}).get(dom)
         roofline = {"bound": "alu", "kernel": names[dom], "achieved": ach, "peak": FP32_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
                     "traffic": per_clip * wl.batch if per_clip is not None else None,
