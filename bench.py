@@ -41,7 +41,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per clip of one launch of the second-order frequential kernels, from an
 # ncu capture of the 1-clip case of this workload (traffic scales with the clips processed).  Valid for
 # the kernel versions it was taken on; set to None when those kernels change.
-DRAM_BYTES_PER_CLIP = None
+DRAM_BYTES_PER_CLIP = {0: 13.368832e6 + 137.416704e6, 1: 206.388480e6 + 8.455680e6}
 
 
 def parse():
