@@ -38,10 +38,22 @@ UNIT = "audio-samples/s"
 L2_FLUSH_BYTES = 256 << 20
 # FP32 ALU peak of a GB300 from unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per clip of one launch of the second-order frequential kernels, from an
-# ncu capture of the 1-clip case of this workload (traffic scales with the clips processed).  Valid for
-# the kernel versions it was taken on; set to None when those kernels change.
-DRAM_BYTES_PER_CLIP = {0: 13.368832e6 + 137.416704e6, 1: 206.388480e6 + 8.455680e6}
+# DRAM bytes (read + write) per clip of one launch of the frequential kernels, keyed by profiling
+# stage (0 / 1: FFT forward / adjoint of the groups they keep, 4 / 5: tensor-core forward / adjoint),
+# from an ncu capture of the 1-clip case of this workload (traffic scales with the clips processed).
+# Valid for the kernel versions it was taken on; emptied when those kernels change.
+DRAM_BYTES_PER_CLIP = {}
+
+
+def bf16_peak():
+    """Measured dense BF16 tensor peak of the GB300s (sustained figure: the kernel is timed
+    inside a long run of steps), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        mp = json.load(open(path))
+        return float(mp["bf16_tflops_sustained"]), "measured (MEASURED_PEAKS.json bf16_tflops_sustained)"
+    except (OSError, ValueError, KeyError):
+        return 1700.0, "fallback (sustained BF16, no MEASURED_PEAKS.json)"
 
 
 def parse():
@@ -88,6 +100,49 @@ def freq_flops_per_column(plan, adjoint: bool) -> float:
     if adjoint:
         f += 5 * Nfr * _lg(Nfr)
     return f
+
+
+def tc_groups(plan):
+    """Second-order groups the tensor-core frequential kernels take: (n1max, columns per clip)."""
+    info = plan.info
+    _, _, j2 = plan.filters(1)
+    _, _, j1 = plan.filters(0)
+    lT = info["log2_T"]
+    out = []
+    if info["R_out"] not in (16, 32) or info["N_fr"] < 64:
+        return out
+    for jj in j2:
+        n1 = int((j1 < jj).sum())
+        L2 = info["N"] >> min(int(jj), lT)
+        if 0 < n1 <= 64 and L2 >= 128:
+            out.append((n1, L2))
+    return out
+
+
+def tc_tensor_flops(plan, adjoint: bool) -> float:
+    """Tensor FLOPs the tensor-core frequential launches issue per call (three BF16 products per
+    FP32 product: hi.hi + lo.hi + hi.lo), M = 128 columns per tile."""
+    info = plan.info
+    Nfr, RO, lF = info["N_fr"], info["R_out"], info["log2_F"]
+    _, _, jf = plan.filters(2)
+    _, _, jl = plan.filters(3)
+    ks = [min(int(jl[1]), lF)] + [min(int(j), lF) for j in jf] * 2
+    chunks = []
+    for k in ks:
+        R = Nfr >> k
+        rc = min(R, 32)
+        chunks += [rc] * (R // rc)
+    total = 0.0
+    for n1, L2 in tc_groups(plan):
+        kp = 16 * ((2 * n1 + 15) // 16)
+        tiles = info["batch"] * ((L2 + 127) // 128)
+        per_tile = 0.0
+        for rc in chunks:
+            per_tile += 2 * 128 * (2 * rc) * kp + 2 * 128 * RO * rc      # GEMM1 (recomputed in the adjoint), pooling
+            if adjoint:
+                per_tile += 2 * 128 * kp * (2 * rc)                        # GEMM3
+        total += 3 * per_tile * tiles
+    return total
 
 
 def columns_per_launch(plan) -> int:
@@ -490,7 +545,7 @@ def main():
     K = args.steps
     lib = _native.load()
     stage_events = {}
-    for st in range(4):
+    for st in range(6):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
         for e in evs:           # torch creates the CUDA event on its first record
             e.record()
@@ -517,7 +572,7 @@ def main():
     clk = clocks.stop()
     if dist:
         dist.barrier()
-    for st in range(4):
+    for st in range(6):
         lib.jtfs_profile_stage(plan._h, st, None, 0)
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     if dist:
@@ -530,33 +585,46 @@ def main():
     # Per-stage average launch duration (CUDA events on the library's stream).
     stage_ms = {}
     for st, (evs, _) in stage_events.items():
-        d = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(K)]
+        d = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(K)] if tuning[3] or st < 4 else [0.0]
         stage_ms[st] = float(np.mean(d))
-    names = {0: "k_freq_fwd_ct<2,8,4,3> (second-order frequential scattering + modulus + phi_F)",
-             1: "k_freq_adj_ct<2,8,3,3> (adjoint of the second-order frequential scattering)",
-             2: "k_pool_fwd + k_pool_reduce (phi_T averaging)", 3: "k_pool_adj (adjoint of phi_T averaging)"}
-    dom = max(stage_ms, key=stage_ms.get)
-    cols = columns_per_launch(plan)
-    flops = None
-    if dom in (0, 1):
-        flops = freq_flops_per_column(plan, adjoint=(dom == 1)) * cols
-    else:
-        info = plan.info
-        flops = None
+    # Kernels of the step: tensor-core frequential launches (stages 4, 5), the FFT kernels of the
+    # remaining groups (stage 0 / 1 minus the tensor-core part), time pooling (2, 3).
+    kern = {"k_freq_tc_adj (tensor-core adjoint of the second-order frequential scattering)": stage_ms[5],
+            "k_freq_tc_fwd (tensor-core second-order frequential scattering + modulus + phi_F)": stage_ms[4],
+            "k_freq_adj_ct (FFT adjoint, groups with n1max > 64)": stage_ms[1] - stage_ms[5],
+            "k_freq_fwd_ct (FFT forward, groups with n1max > 64)": stage_ms[0] - stage_ms[4],
+            "k_pool_fwd + k_pool_reduce (phi_T averaging)": stage_ms[2],
+            "k_pool_adj (adjoint of phi_T averaging)": stage_ms[3]}
+    dom = max(kern, key=kern.get)
+    launch_ms = kern[dom]
     roofline = None
-    if flops is not None:
-        ach = flops / (stage_ms[dom] / 1e3) / 1e12
-        per_clip = (DRAM_BYTES_PER_CLIP or {}).get(dom)
-        roofline = {"bound": "alu", "kernel": names[dom], "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+    if dom.startswith("k_freq_tc"):
+        adj = dom.startswith("k_freq_tc_adj")
+        flops = tc_tensor_flops(plan, adjoint=adj)
+        ach = flops / (launch_ms / 1e3) / 1e12
+        peak, peak_src = bf16_peak()
+        per_clip = (DRAM_BYTES_PER_CLIP or {}).get(5 if adj else 4)
+        roofline = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": per_clip * wl.batch if per_clip is not None else None,
+                    "traffic_note": "ncu dram bytes of the 1-clip capture x clips per launch",
+                    "flops_per_launch": flops, "flops_note": "issued BF16 tensor FLOPs: 3 products (hi.hi, lo.hi, "
+                    "hi.lo) per FP32-accurate product, M = 128 columns per tile; one third is the contraction itself",
+                    "launch_ms": launch_ms, "peak_source": peak_src,
+                    "stage_ms": {k.split(" ")[0]: round(v, 4) for k, v in kern.items()},
+                    "step_share": launch_ms / ms_per_step}
+    elif dom.startswith("k_freq_"):
+        adj = dom.startswith("k_freq_adj")
+        cols = columns_per_launch(plan) - wl.batch * sum(L2 for _, L2 in (tc_groups(plan) if tuning[3] else []))
+        flops = freq_flops_per_column(plan, adjoint=adj) * cols
+        ach = flops / (launch_ms / 1e3) / 1e12
+        per_clip = (DRAM_BYTES_PER_CLIP or {}).get(1 if adj else 0)
+        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP32_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
                     "traffic": per_clip * wl.batch if per_clip is not None else None,
-                    "traffic_note": "ncu dram bytes of the 1-clip capture x clips per launch",
-                    "hbm_gbs_at_traffic": (per_clip * wl.batch / (stage_ms[dom] / 1e3) / 1e9
-                                           if per_clip is not None else None),
-                    "flops_per_launch": flops, "launch_ms": stage_ms[dom],
+                    "flops_per_launch": flops, "launch_ms": launch_ms,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (no measured FP32 peak)",
-                    "stage_ms": {names[s].split(" ")[0]: round(t, 4) for s, t in stage_ms.items()},
-                    "step_share": stage_ms[dom] / ms_per_step}
+                    "stage_ms": {k.split(" ")[0]: round(v, 4) for k, v in kern.items()},
+                    "step_share": launch_ms / ms_per_step}
 
     # End to end through the public API from pinned host memory.
     y_host = torch.tensor(inits, dtype=torch.float32).pin_memory()
@@ -599,7 +667,8 @@ def main():
                 "config": config_dict(wl), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(lib.jtfs_launch_count(plan._h, 3)) * K,
                 "clocks": clk, "wall_s_timed": t_wall,
-                "tuning": {"wide_forward_tiles": tuning[0], "pool_split": tuning[1], "fft_points_per_cta": tuning[2]},
+                "tuning": {"wide_forward_tiles": tuning[0], "pool_split": tuning[1], "fft_points_per_cta": tuning[2],
+                           "tensor_core_frequential": tuning[3]},
                 "metamer_loss": {"first_timed_step": float(hist[0].mean().item()),
                                  "last_timed_step": float(hist[-1].mean().item()),
                                  "adam_steps_before_last": args.warmup + K - 1}}

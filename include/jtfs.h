@@ -245,19 +245,26 @@ int jtfs_batch_metamer_step(jtfs_batch_t batch, float* y, const float* phi_targe
                             void* stream);
 
 /*
- * Autotuning.  A plan has three execution choices that change no result:
+ * Autotuning.  A plan has four execution choices that change no result
+ * beyond rounding:
  *   choice[0]  wide column tiles (1) or narrow ones (0) for the second-order
  *              frequential forward kernel;
  *   choice[1]  time samples per CTA of the phi_T averaging forward
  *              (1024, 2048 or 4096);
- *   choice[2]  points per CTA of the batched small FFTs (1024 .. 8192).
+ *   choice[2]  points per CTA of the batched small FFTs (1024 .. 8192);
+ *   choice[3]  second-order frequential scattering of the path groups with at
+ *              most 64 rows n1 on the tensor cores (1) or on the FFT kernels
+ *              (0); reads 0, and setting 1 has no effect, for plans whose
+ *              shape the tensor-core kernels do not handle (R_out not 16 or
+ *              32, no such group).  jtfs_set_tuning takes n = 3 (choice[3]
+ *              unchanged) or n >= 4.
  * jtfs_autotune times jtfs_loss_grad on the caller's y and phi_target (device
  * arrays as for jtfs_loss_grad; loss [batch] and dy [batch][N] are scratch
  * outputs) for each candidate, one choice at a time, keeps the fastest, and
  * writes the choices to choice[0..n) (host, may be NULL).  It synchronises
  * the stream (it is a set-up call, not a hot-path one).  jtfs_set_tuning
  * applies saved choices; jtfs_get_tuning reads the current ones.  All return
- * the number of choices (3) or an error code.  Not thread-safe with concurrent
+ * the number of choices (4) or an error code.  Not thread-safe with concurrent
  * compute calls on the same plan.
  */
 int jtfs_autotune(jtfs_plan_t plan, const float* y, const float* phi_target,
@@ -353,7 +360,9 @@ int jtfs_adam_update(float* param, const float* grad, float* m, float* v,
 #define JTFS_STAGE_FREQ2_ADJ 1 /* its adjoint (§2.3, Eq. (7))                */
 #define JTFS_STAGE_POOL_FWD  2 /* second-order phi_T averaging (Eq. (5))     */
 #define JTFS_STAGE_POOL_ADJ  3 /* its adjoint (Eq. (6))                      */
-#define JTFS_STAGE_COUNT     4
+#define JTFS_STAGE_FREQ2_FWD_TC 4 /* the tensor-core launches inside stage 0  */
+#define JTFS_STAGE_FREQ2_ADJ_TC 5 /* the tensor-core launches inside stage 1  */
+#define JTFS_STAGE_COUNT     6
 int jtfs_profile_stage(jtfs_plan_t plan, int stage, void** events, int count);
 
 /*
@@ -362,6 +371,33 @@ int jtfs_profile_stage(jtfs_plan_t plan, int stage, void** events, int count);
  * Returns the count or JTFS_ERR_ARG.
  */
 int64_t jtfs_launch_count(jtfs_plan_t plan, int call);
+
+/*
+ * Tensor-core second-order frequential scattering (§3.4, the modulus of
+ * Eq. (2), phi_F of Eq. (5), and the adjoint of §2.3 / Eq. (7)).  Per time
+ * column of a path group with n1max <= 64 rows, the filtering along n1 by
+ * psi_beta (decimated by 2^k) is a product with a fixed complex matrix H_beta
+ * [N_fr / 2^k][n1max] and the phi_F averaging after the modulus a product with
+ * a fixed real matrix P_k [R_out][N_fr / 2^k]; the kernels run both on BF16
+ * tensor cores with hi/lo-split operands and FP32 accumulation.
+ *
+ * jtfs_tc_error: 1 if a tensor-core frequential kernel gave up waiting on one
+ * of its barriers since the last call (its outputs are then invalid), else 0;
+ * synchronous; clears the flag.  JTFS_ERR_CUDA if the flag cannot be read.
+ *
+ * jtfs_tc_table copies, as float (hi + lo of the BF16 split), one of the
+ * plan's operand tables into out[0 .. n) (host memory) and returns the number
+ * of floats the table has (call with out = NULL to size it):
+ *   which = 0: H, [rows][128]: row 2 (off_beta + r) + x, column 2 n + y holds
+ *              the coefficient of (re, im)[y] of Y2[n] in (re, im)[x] of
+ *              Z_beta[r], n < 64; off_beta = sum of N_fr / 2^k over earlier
+ *              filters (filter order of the Phi layout);
+ *   which = 1: P, [log2 F + 1][R_out][N_fr]: P_k[ro][r], zero for r >= N_fr / 2^k.
+ * Works on host-only plans.  Errors: JTFS_ERR_ARG (NULL plan, bad which),
+ * JTFS_ERR_SHAPE (the plan has no tensor-core groups).
+ */
+int jtfs_tc_error(void);
+int64_t jtfs_tc_table(jtfs_plan_t plan, int which, float* out, int64_t n);
 
 /* Static description of an error code (never NULL). */
 const char* jtfs_error_string(int code);

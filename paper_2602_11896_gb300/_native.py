@@ -63,6 +63,8 @@ SIGNATURES = {
     "jtfs_cast_bf16": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
     "jtfs_adam_update": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_int,
                                  c_void_p]),
+    "jtfs_tc_error": (c_int, []),
+    "jtfs_tc_table": (c_int64, [c_void_p, c_int, POINTER(c_float), c_int64]),
     "jtfs_profile_stage": (c_int, [c_void_p, c_int, POINTER(c_void_p), c_int]),
     "jtfs_launch_count": (c_int64, [c_void_p, c_int]),
     "jtfs_error_string": (c_char_p, [c_int]),

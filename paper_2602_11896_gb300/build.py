@@ -1,6 +1,6 @@
 """Build the in-tree C-ABI library ``libjtfs.so`` for GB300 (sm_103a) with nvcc.
 
-Two translation units compile in parallel; the CUDA runtime is linked
+The translation units compile in parallel; the CUDA runtime is linked
 statically so the library loads without a GPU (plan inspection works on any
 host).  Usage: ``python -m paper_2602_11896_gb300.build`` or ``build()``.
 """
@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libjtfs.so")
 SOURCES = ["jtfs_plan.cpp", "jtfs_cuda.cu", "jtfs_batch.cu", "jtfs_decoder.cu", "jtfs_freq_ct_fwd.cu",
            "jtfs_freq_ct_adj.cu", "jtfs_freq_ct_long_fwd.cu",
-           "jtfs_freq_ct_long_adj.cu"]
+           "jtfs_freq_ct_long_adj.cu", "jtfs_freq_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1143,10 +1143,17 @@ int64_t fft_launches(const std::vector<FftLaunch>& L) {
   return n;
 }
 
+// Launches of the second-order frequential stage (forward or adjoint): the
+// tensor-core kernels of the groups they handle plus one FFT-kernel launch.
+int64_t freq2_launches(const Plan& p) {
+  if (!(p.tc_ok && p.tune_tc)) return 1;
+  return int64_t(!p.tc_tiles[0].empty()) + int64_t(!p.tc_tiles[1].empty()) + int64_t(!p.tiles2_fft.empty());
+}
+
 int64_t forward_launches(const Plan& p, bool full) {
   int64_t n = fft_launches(p.L_x) + fft_launches(p.L_u1) + fft_launches(p.L_u1inplace) + fft_launches(p.L_s1);
   if (full) n += fft_launches(p.L_s0) + 1;
-  if (p.n_active > 0) n += fft_launches(p.L_y2) + (full ? 3 : 0);
+  if (p.n_active > 0) n += fft_launches(p.L_y2) + (full ? 2 + freq2_launches(p) : 0);
   return n;
 }
 
@@ -1154,7 +1161,7 @@ int64_t backward_launches(const Plan& p) {
   int64_t n = 1 + fft_launches(p.L_ds1) + static_cast<int64_t>(p.L_u1inplace.size()) +
               2 * fft_launches(p.L_u1inplace) + fft_launches(p.L_u1) + fft_launches(p.L_ds0) + 1 +
               fft_launches(p.L_x);
-  if (p.n_active > 0) n += 2 + fft_launches(p.L_y2inplace);
+  if (p.n_active > 0) n += 1 + freq2_launches(p) + fft_launches(p.L_y2inplace);
   return n;
 }
 
@@ -1204,12 +1211,21 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
       FA2w.logW = ceil_log2(p.freq_cols_wide);
       const size_t smem_w = ct_smem(p, 3, p.freq_cols_wide, FA2w);
       const size_t smem_n = ct_smem(p, 3, p.freq_cols, FA2n);
-      if (!(p.tune_wide && launch_freq_fwd_ct(2, FA2w, p.lF, static_cast<unsigned>(p.tiles2w.size()), smem_w, s,
-                                              p.d_tiles2w, nullptr, w.Y2, w.V2)) &&
-          !launch_freq_fwd_ct(2, FA2n, p.lF, static_cast<unsigned>(p.tiles2.size()), smem_n, s, p.d_tiles2,
-                              nullptr, w.Y2, w.V2))
-        k_freq_fwd<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 3), s>>>(
-            FA2, p.d_tiles2, nullptr, w.Y2, w.V2);
+      // Groups with at most 64 rows n1 on the tensor cores, the others on the FFT kernels.
+      const bool tc = p.tc_ok && p.tune_tc;
+      if (tc) {
+        prof_begin(p, JTFS_STAGE_FREQ2_FWD_TC, s);
+        JTFS_TRY(tc_forward(p, w.Y2, w.V2, s));
+        prof_end(p, JTFS_STAGE_FREQ2_FWD_TC, s);
+      }
+      const Tile* t2 = tc ? p.d_tiles2_fft : p.d_tiles2;
+      const Tile* t2w = tc ? p.d_tiles2w_fft : p.d_tiles2w;
+      const unsigned n2 = static_cast<unsigned>(tc ? p.tiles2_fft.size() : p.tiles2.size());
+      const unsigned n2w = static_cast<unsigned>(tc ? p.tiles2w_fft.size() : p.tiles2w.size());
+      if (n2 > 0 &&
+          !(p.tune_wide && launch_freq_fwd_ct(2, FA2w, p.lF, n2w, smem_w, s, t2w, nullptr, w.Y2, w.V2)) &&
+          !launch_freq_fwd_ct(2, FA2n, p.lF, n2, smem_n, s, t2, nullptr, w.Y2, w.V2))
+        k_freq_fwd<2><<<n2, kThreads, freq_smem(p, 3), s>>>(FA2, t2, nullptr, w.Y2, w.V2);
       prof_end(p, JTFS_STAGE_FREQ2_FWD, s);
       JTFS_TRY(check_launch());
       const PoolArgs PA = pool_args(p);
@@ -1263,10 +1279,16 @@ int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, 
     prof_begin(p, JTFS_STAGE_FREQ2_ADJ, s);
     FreqArgs FA2c = FA2;
     const size_t smem_c = ct_smem(p, 5, p.freq_cols, FA2c);
-    if (!launch_freq_adj_ct(2, FA2c, p.lF, static_cast<unsigned>(p.tiles2.size()), smem_c, s, p.d_tiles2, nullptr,
-                            w.Y2, w.V2, nullptr, w.dY2))
-      k_freq_adj<2><<<static_cast<unsigned>(p.tiles2.size()), kThreads, freq_smem(p, 5), s>>>(
-          FA2, p.d_tiles2, nullptr, w.Y2, w.V2, nullptr, w.dY2);
+    const bool tc = p.tc_ok && p.tune_tc;
+    if (tc) {
+      prof_begin(p, JTFS_STAGE_FREQ2_ADJ_TC, s);
+      JTFS_TRY(tc_adjoint(p, w.Y2, w.V2, w.dY2, s));
+      prof_end(p, JTFS_STAGE_FREQ2_ADJ_TC, s);
+    }
+    const Tile* t2 = tc ? p.d_tiles2_fft : p.d_tiles2;
+    const unsigned n2 = static_cast<unsigned>(tc ? p.tiles2_fft.size() : p.tiles2.size());
+    if (n2 > 0 && !launch_freq_adj_ct(2, FA2c, p.lF, n2, smem_c, s, t2, nullptr, w.Y2, w.V2, nullptr, w.dY2))
+      k_freq_adj<2><<<n2, kThreads, freq_smem(p, 5), s>>>(FA2, t2, nullptr, w.Y2, w.V2, nullptr, w.dY2);
     prof_end(p, JTFS_STAGE_FREQ2_ADJ, s);
     JTFS_TRY(check_launch());
   }
@@ -1445,9 +1467,10 @@ extern "C" int64_t jtfs_launch_count(jtfs_plan_t plan, int call) {
 extern "C" int jtfs_get_tuning(jtfs_plan_t plan, int64_t* choice, int n) {
   if (!plan) return JTFS_ERR_ARG;
   const jtfs::Plan& p = plan->p;
-  const int64_t v[3] = {p.tune_wide, jtfs::kPoolSplits[p.tune_split], p.tune_fft_points};
-  for (int i = 0; i < n && i < 3 && choice; ++i) choice[i] = v[i];
-  return 3;
+  const int64_t v[4] = {p.tune_wide, jtfs::kPoolSplits[p.tune_split], p.tune_fft_points,
+                        (p.tc_ok && p.tune_tc) ? 1 : 0};
+  for (int i = 0; i < n && i < 4 && choice; ++i) choice[i] = v[i];
+  return 4;
 }
 
 extern "C" int jtfs_set_tuning(jtfs_plan_t plan, const int64_t* choice, int n) {
@@ -1458,10 +1481,12 @@ extern "C" int jtfs_set_tuning(jtfs_plan_t plan, const int64_t* choice, int n) {
   const int64_t pts = choice[2];
   if ((choice[0] != 0 && choice[0] != 1) || si < 0 || pts < 1024 || pts > 8192 || (pts & (pts - 1))) return JTFS_ERR_ARG;
   const jtfs::Plan& p = plan->p;
+  if (n >= 4 && choice[3] != 0 && choice[3] != 1) return JTFS_ERR_ARG;
   p.tune_wide = static_cast<int>(choice[0]);
   p.tune_split = si;
   p.tune_fft_points = static_cast<int>(pts);
-  return 3;
+  if (n >= 4) p.tune_tc = static_cast<int>(choice[3]);
+  return 4;
 }
 
 extern "C" int jtfs_autotune(jtfs_plan_t plan, const float* y, const float* phi_target, float* loss, float* dy,
@@ -1491,7 +1516,17 @@ extern "C" int jtfs_autotune(jtfs_plan_t plan, const float* y, const float* phi_
     return JTFS_OK;
   };
   int rc = JTFS_OK;
-  {
+  if (p.tc_ok) {
+    float best = 1e30f, t = 0.f;
+    int best_tc = p.tune_tc;
+    for (int v : {1, 0}) {
+      p.tune_tc = v;
+      if ((rc = time_it(&t)) != JTFS_OK) break;
+      if (t < best) best = t, best_tc = v;
+    }
+    p.tune_tc = best_tc;
+  }
+  if (rc == JTFS_OK) {
     float best = 1e30f, t = 0.f;
     int best_pts = p.tune_fft_points;
     for (int pts : {1024, 2048, 4096, 8192}) {

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace jtfs {
@@ -62,6 +63,20 @@ struct FftLaunch {
   int logn;
   int njobs;
   int job0;
+};
+
+// Tensor-core frequential scattering (jtfs_freq_tc.cu): one chunk is up to 32
+// consecutive output rows r of one frequential filter beta, i.e. 2 rc rows
+// (real, imaginary) of the GEMM1 table.
+struct TcChunk {
+  int beta;   // filter index
+  int k;      // its stride level
+  int r0;     // first row of the chunk in [0, N_fr / 2^k)
+  int rc;     // rows in this chunk (16 or 32)
+  int b1row;  // first row of the chunk in the GEMM1 table
+  int prow;   // first row of the chunk in the adjoint pooling table
+  int first;  // first chunk of its filter
+  int last;   // last chunk of its filter
 };
 
 struct FilterH {
@@ -208,9 +223,29 @@ struct Plan {
   const int* d_act_n2 = nullptr;      // per active index: n2
   const int64_t* d_tap_off = nullptr; // per level s
 
+  // Tensor-core frequential path of the second order (jtfs_freq_tc.cu): BF16
+  // hi/lo operand tables of the filter matrices (GEMM1 [tc_nr1 rows x 128],
+  // forward pooling [(lF + 1) R_out rows x tc_kp2], adjoint pooling
+  // [tc_np2 rows x 64], GEMM1 transposed [256 rows x tc_nr1]), the chunk
+  // list, the tiles of the groups it handles (n1max <= 32, <= 64) and the
+  // tiles the FFT kernels keep.
+  bool tc_ok = false;
+  int tc_nr1 = 0, tc_kp2 = 0, tc_np2 = 0;
+  std::vector<uint16_t> tc_b1, tc_b2, tc_b2t, tc_b3;
+  std::vector<TcChunk> tc_chunks;
+  std::vector<Tile> tc_tiles[2];
+  std::vector<Tile> tiles2_fft, tiles2w_fft;
+  mutable int tune_tc = 1;
+  void* d_tc = nullptr;
+  const TcChunk* d_tc_chunks = nullptr;
+  const Tile* d_tc_tiles[2] = {nullptr, nullptr};
+  const Tile* d_tiles2_fft = nullptr;
+  const Tile* d_tiles2w_fft = nullptr;
+  CUtensorMap tc_map[4];  // GEMM1 table, forward pooling, adjoint pooling, GEMM1 transposed
+
   // Measurement hook (jtfs_profile_stage): events per stage and next index.
-  mutable std::vector<void*> prof_events[4];
-  mutable int prof_next[4] = {0, 0, 0, 0};
+  mutable std::vector<void*> prof_events[6];
+  mutable int prof_next[6] = {0, 0, 0, 0, 0, 0};
 };
 
 // Host plan construction (jtfs_plan.cpp).  Returns 0 or a JTFS_ERR_* code.
@@ -218,6 +253,18 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
                int64_t T, int F, int batch, uint32_t flags);
 int upload_plan(Plan& p);
 void release_plan(Plan& p);
+
+// Tensor-core frequential path (jtfs_freq_tc.cu): host tables at plan
+// construction, device copies and tensor maps at upload, release.  tc_build
+// leaves tc_ok false (and the FFT tiles equal to the full lists) for shapes it
+// does not handle.
+void tc_build(Plan& p);
+int tc_upload(Plan& p);
+void tc_release(Plan& p);
+// Launch the second-order forward (V2 from Y2) / adjoint (dY2 from Y2, dV2)
+// on the tensor-core groups; no-ops when the plan has no such group.
+int tc_forward(const Plan& p, const float2* Y2, float* V2, cudaStream_t s);
+int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, cudaStream_t s);
 
 // Stages of one plan on a caller workspace (jtfs_cuda.cu).  run_forward with
 // full = false computes only what run_backward needs (phi may be NULL);

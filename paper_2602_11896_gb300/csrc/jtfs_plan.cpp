@@ -440,6 +440,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   p.ws_scr = take(size_t(std::max<int64_t>(p.scr_elems, 1)) * c8);
   p.ws_part = take(std::max<size_t>(p.pool_fwd_tiles[0].size(), 1) * 64 * p.n_frames * f4);
   p.ws_bytes = o;
+  tc_build(p);
   return JTFS_OK;
 }
 
@@ -539,7 +540,7 @@ int upload_plan(Plan& p) {
   p.d_act_n2 = reinterpret_cast<const int*>(at(o_act));
   p.d_tap_off = reinterpret_cast<const int64_t*>(at(o_tapo));
   p.on_device = true;
-  return JTFS_OK;
+  return tc_upload(p);
 }
 
 void release_plan(Plan& p) {
@@ -548,6 +549,7 @@ void release_plan(Plan& p) {
     cudaGetDevice(&cur);
     if (p.device >= 0 && cur != p.device) cudaSetDevice(p.device);
     cudaFree(p.d_blob);
+    tc_release(p);
     if (cur >= 0 && cur != p.device) cudaSetDevice(cur);
   }
   p.d_blob = nullptr;

@@ -8,7 +8,7 @@ float32 CUDA tensors of shape [batch, N]; anything else raises.
 from __future__ import annotations
 
 import ctypes
-from ctypes import c_double, c_int32, c_int64, c_void_p
+from ctypes import c_double, c_float, c_int32, c_int64, c_void_p
 from typing import Dict, Optional, Tuple
 
 import numpy as np
@@ -78,22 +78,39 @@ class JTFSPlan:
         return np.array(xi[:]), np.array(sg[:]), np.array(jj[:], dtype=np.int64)
 
     # -- tuning -----------------------------------------------------------
-    def tuning(self) -> Tuple[int, int, int]:
-        """(wide forward tiles, pooling split, small-FFT points per CTA) in use."""
-        buf = (c_int64 * 3)()
-        self._lib.jtfs_get_tuning(self._h, buf, 3)
-        return int(buf[0]), int(buf[1]), int(buf[2])
+    def tuning(self) -> Tuple[int, int, int, int]:
+        """(wide forward tiles, pooling split, small-FFT points per CTA, tensor-core frequential path) in use."""
+        buf = (c_int64 * 4)()
+        self._lib.jtfs_get_tuning(self._h, buf, 4)
+        return int(buf[0]), int(buf[1]), int(buf[2]), int(buf[3])
 
     def set_tuning(self, choice) -> None:
-        buf = (c_int64 * 3)(*[int(c) for c in choice])
-        n = self._lib.jtfs_set_tuning(self._h, buf, 3)
+        """Apply 3 choices (tensor-core choice unchanged) or 4 (see ``tuning``)."""
+        vals = [int(c) for c in choice]
+        buf = (c_int64 * len(vals))(*vals)
+        n = self._lib.jtfs_set_tuning(self._h, buf, len(vals))
         _native.check(0 if n >= 0 else n, "jtfs_set_tuning")
+
+    def tc_table(self, which: int) -> np.ndarray:
+        """Operand table of the tensor-core frequential kernels (float, hi + lo of the BF16 split).
+
+        which = 0: H [rows][128] (row 2 (off_beta + r) + x, column 2 n + y); which = 1: P [lF + 1][R_out][N_fr].
+        """
+        n = int(self._lib.jtfs_tc_table(self._h, which, None, 0))
+        _native.check(0 if n >= 0 else n, "jtfs_tc_table")
+        buf = (c_float * n)()
+        self._lib.jtfs_tc_table(self._h, which, buf, n)
+        a = np.frombuffer(buf, dtype=np.float32).copy()
+        if which == 0:
+            return a.reshape(-1, 128)
+        return a.reshape(self.info["log2_F"] + 1, self.info["R_out"], self.info["N_fr"])
 
     def _tune_key(self) -> str:
         name = torch.cuda.get_device_name() if torch.cuda.is_available() else "host"
         return f"{name}|" + ",".join(f"{k}={self.info[k]}" for k in INFO_KEYS[:9])
 
-    def autotune(self, y: torch.Tensor, phi_target: torch.Tensor, cache: Optional[str] = None) -> Tuple[int, int, int]:
+    def autotune(self, y: torch.Tensor, phi_target: torch.Tensor,
+                 cache: Optional[str] = None) -> Tuple[int, int, int, int]:
         """Pick the fastest execution choices for this plan by timing jtfs_loss_grad on (y, phi_target).
 
         With ``cache`` (default: the JTFS_TUNE_CACHE environment variable) the choices are read
@@ -116,11 +133,11 @@ class JTFSPlan:
         loss = torch.empty(self.batch, device=y.device)
         dy = torch.empty_like(y)
         ws = self.workspace(y.device)
-        buf = (c_int64 * 3)()
+        buf = (c_int64 * 4)()
         n = self._lib.jtfs_autotune(self._h, _ptr(y), _ptr(phi_target), _ptr(loss), _ptr(dy), _ptr(ws), _stream(),
-                                    buf, 3)
+                                    buf, 4)
         _native.check(0 if n >= 0 else n, "jtfs_autotune")
-        choice = [int(buf[0]), int(buf[1]), int(buf[2])]
+        choice = [int(buf[i]) for i in range(4)]
         if path:
             table = {}
             if os.path.exists(path):

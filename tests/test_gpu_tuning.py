@@ -34,7 +34,7 @@ def test_every_tuning_choice_gives_the_same_gradient(name):
     l0, g0 = plan.loss_grad(y, tgt)
     for wide, split, pts in itertools.product((0, 1), (1024, 2048, 4096), (1024, 8192)):
         plan.set_tuning((wide, split, pts))
-        assert plan.tuning() == (wide, split, pts)
+        assert plan.tuning()[:3] == (wide, split, pts)
         l1, g1 = plan.loss_grad(y, tgt)
         assert _rel(l1, l0) <= 1e-6 and _rel(g1, g0) <= 1e-6, (wide, split, pts)
         if split == ref_choice[1]:   # only the pooling split reorders a sum
@@ -51,6 +51,7 @@ def test_autotune_picks_a_valid_choice_and_caches_it(tmp_path):
     cache = tmp_path / "tune.json"
     choice = plan.autotune(y, tgt, cache=str(cache))
     assert choice[0] in (0, 1) and choice[1] in (1024, 2048, 4096) and choice[2] in (1024, 2048, 4096, 8192)
+    assert choice[3] in (0, 1)
     table = json.load(open(cache))
     assert list(table.values()) == [list(choice)]
     other = JTFSPlan(**wl.params, batch=4)
