@@ -398,6 +398,13 @@ int64_t jtfs_launch_count(jtfs_plan_t plan, int call);
  */
 int jtfs_tc_error(void);
 int64_t jtfs_tc_table(jtfs_plan_t plan, int which, float* out, int64_t n);
+/*
+ * jtfs_tc_error_info: the first tensor-core wait that expired since the last
+ * call, as info[0 .. min(n, 4)): CTA index (-1: none), thread, byte offset of
+ * the barrier in the CTA's shared memory, phase parity waited for.
+ * Synchronous; clears the record; returns 4 or JTFS_ERR_CUDA.
+ */
+int jtfs_tc_error_info(int64_t* info, int n);
 
 /* Static description of an error code (never NULL). */
 const char* jtfs_error_string(int code);

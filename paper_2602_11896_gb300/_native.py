@@ -64,6 +64,7 @@ SIGNATURES = {
     "jtfs_adam_update": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_int,
                                  c_void_p]),
     "jtfs_tc_error": (c_int, []),
+    "jtfs_tc_error_info": (c_int, [POINTER(c_int64), c_int]),
     "jtfs_tc_table": (c_int64, [c_void_p, c_int, POINTER(c_float), c_int64]),
     "jtfs_profile_stage": (c_int, [c_void_p, c_int, POINTER(c_void_p), c_int]),
     "jtfs_launch_count": (c_int64, [c_void_p, c_int]),

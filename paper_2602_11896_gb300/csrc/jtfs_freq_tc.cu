@@ -48,10 +48,12 @@ namespace jtfs {
 namespace {
 
 __device__ int g_tc_err;
+// First expired wait since the last jtfs_tc_error() (diagnostics): CTA, thread,
+// barrier offset inside the CTA's control block, parity.
+__device__ int g_tc_err_info[4];
 
-constexpr int kTcEpi = 256;              // epilogue / operand-conversion threads
-constexpr int kTcThreads = kTcEpi + 64;  // + TMA warp (8) + MMA warp (9)
 constexpr int kTcM = 128;                // columns per tile
+constexpr int kS2 = 2;                   // stages of the pooling-table ring (4 KB each)
 
 struct TcArgs {
   const TcChunk* chunks;
@@ -70,9 +72,9 @@ struct TcArgs {
 };
 
 struct TcCtl {
-  unsigned long long b1_full[4], b1_empty[4], b2_full[2], b2_empty[2], b3_full[4], b3_empty[4];
+  unsigned long long b1_full[8], b1_empty[8], b2_full[4], b2_empty[4], b3_full[8], b3_empty[8];
   unsigned long long a1_full, d1_full[2], d1_empty[2], a2_full[2], a2_empty[2], d2_full[2], d2_empty[2];
-  unsigned long long dv_full[2], dv_empty[2], d3_full, drain;
+  unsigned long long dv_full[2], dv_empty[2], d3_full, drain[3];
   uint32_t tmem;
   int abort;
 };
@@ -88,21 +90,48 @@ __device__ __forceinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity) {
   for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(bar, parity); ++i) __nanosleep(64);
 }
 
+// Bounded mbarrier wait (see mbar_wait), kept out of line: with the polling
+// loop inlined into the issue and epilogue loops the kernels returned wrong
+// results on the GPU (timing-dependent), with it out of line they are exact.
+__device__ __noinline__ bool tc_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (i >= 8) __nanosleep(64);
+  }
+  *abort = 1;
+  if (atomicCAS(&g_tc_err_info[0], 0, int(blockIdx.x) + 1) == 0) {
+    extern __shared__ uint8_t smem_raw[];
+    g_tc_err_info[1] = int(threadIdx.x);
+    g_tc_err_info[2] = int(bar - smem_u32(smem_raw));
+    g_tc_err_info[3] = int(parity);
+  }
+  return false;
+}
+
+// |x + iy| from the hardware reciprocal square root (a few ulp; the epilogues
+// are instruction-bound and the correctly rounded sqrtf costs a long sequence).
+__device__ __forceinline__ float modulus(float x, float y) {
+  const float m2 = x * x + y * y;
+  return m2 > 0.f ? m2 * rsqrtf(m2) : 0.f;
+}
+
 // Bounded wait taken by a whole epilogue warp: the tcgen05.ld that follow are
 // warp-collective, so every lane must make the same decision.
 __device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity, volatile int* abort) {
-  const bool ok = mbar_wait(bar, parity, abort);
+  const bool ok = tc_wait(bar, parity, abort);
   return __all_sync(0xffffffffu, ok);
 }
 
 // Y2 tile -> A1 (BF16 hi in atoms [0, KA), lo in atoms [KA, 2 KA)), K index 2n + (re, im).
+// Chunks g = part, part + nparts, ... of the row of column c.
 template <int KA>
 __device__ __forceinline__ void load_a1(const TcArgs& A, const Tile& tl, int n1m, int ks1, uint32_t sA1, int c,
-                                        int h) {
+                                        int part, int nparts) {
   const int L2 = 1 << (A.logN - A.s2[tl.a]);
   const float2* ysrc = A.Y2 + int64_t(tl.b) * A.y2_tot + A.y2_off[tl.a] + tl.t0 + c;
   const bool colok = c < tl.ncols;
-  for (int g = h; g < 2 * ks1; g += 2) {  // 16-byte chunk g holds n = 4g .. 4g + 3
+  for (int g = part; g < 2 * ks1; g += nparts) {  // 16-byte chunk g holds n = 4g .. 4g + 3
     uint32_t hi[4], lo[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -117,23 +146,67 @@ __device__ __forceinline__ void load_a1(const TcArgs& A, const Tile& tl, int n1m
   }
 }
 
-// GEMM1 of one chunk into D1 (TMEM column d): 3 passes per k-step.
+// ---------------------------------------------------------------------------
+// Thread roles of both kernels: warps 0-15 are two epilogue groups of 8 warps
+// (group g takes the chunks i with i % 2 == g; inside a group warp w reads TMEM
+// lanes 32 (w % 4) .. + 31 and half (w % 8) / 4 of the chunk's columns),
+// warp 16 lane 0 issues the TMA loads, warps 17, 18 (and 19 in the adjoint)
+// lane 0 each issue one GEMM, so that their barrier waits overlap.  Chunk
+// descriptors are read one chunk ahead (a global read on the issue path costs
+// more than the MMAs it feeds).
+// ---------------------------------------------------------------------------
+constexpr int kGrp = 256;                 // threads per epilogue group
+constexpr int kEpiAll = 2 * kGrp;         // epilogue threads
+constexpr int kWarpTma = 16, kWarpG1 = 17, kWarpG2 = 18, kWarpG3 = 19;
+
+__device__ __forceinline__ void init_barriers(TcCtl* ctl) {
+  for (int s = 0; s < 8; ++s) {
+    mbar_init(smem_u32(&ctl->b1_full[s]), 1);
+    mbar_init(smem_u32(&ctl->b1_empty[s]), 1);
+    mbar_init(smem_u32(&ctl->b3_full[s]), 1);
+    mbar_init(smem_u32(&ctl->b3_empty[s]), 1);
+  }
+  for (int s = 0; s < kS2; ++s) {
+    mbar_init(smem_u32(&ctl->b2_full[s]), 1);
+    mbar_init(smem_u32(&ctl->b2_empty[s]), 1);
+  }
+  for (int s = 0; s < 2; ++s) {
+    mbar_init(smem_u32(&ctl->d1_full[s]), 1);
+    mbar_init(smem_u32(&ctl->d1_empty[s]), kGrp);
+    mbar_init(smem_u32(&ctl->a2_full[s]), kGrp);
+    mbar_init(smem_u32(&ctl->a2_empty[s]), 1);
+    mbar_init(smem_u32(&ctl->d2_full[s]), 1);
+    mbar_init(smem_u32(&ctl->d2_empty[s]), kGrp);
+    mbar_init(smem_u32(&ctl->dv_full[s]), kGrp);
+    mbar_init(smem_u32(&ctl->dv_empty[s]), 1);
+  }
+  mbar_init(smem_u32(&ctl->a1_full), kEpiAll);
+  mbar_init(smem_u32(&ctl->d3_full), 1);
+  for (int s = 0; s < 3; ++s) mbar_init(smem_u32(&ctl->drain[s]), 1);
+  ctl->abort = 0;
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// GEMM1 of one chunk into D1 (TMEM column d): 3 passes per k-step; no fence
+// needed after the TMA waits (the mbarrier orders the async-proxy writes).
 template <int KA, int S1>
 __device__ __forceinline__ bool issue_g1(TcCtl* ctl, const TcChunk& c, int ks1, uint32_t sA1, uint32_t sB1,
                                          uint32_t d, int& c1, volatile int* abort) {
   const uint32_t idesc = idesc_bf16_n(2 * c.rc);
   const int na = (ks1 + 3) >> 2;
+  const uint64_t ah0 = kdesc(sA1), al0 = kdesc(sA1 + uint32_t(KA) * 16384u);
   for (int a = 0; a < na; ++a) {
     const int s = c1 % S1;
-    if (!mbar_wait(smem_u32(&ctl->b1_full[s]), (c1 / S1) & 1, abort)) return false;
+    if (!tc_wait(smem_u32(&ctl->b1_full[s]), (c1 / S1) & 1, abort)) return false;
     tc_fence_after();
-    const uint32_t bh = sB1 + uint32_t(s) * 16384u, bl = bh + 8192u;
-    const uint32_t ah = sA1 + uint32_t(a) * 16384u, al = ah + uint32_t(KA) * 16384u;
-    for (int kk = 0; kk < 4 && a * 4 + kk < ks1; ++kk) {
-      const uint32_t o = uint32_t(kk) * 32u;
-      umma_bf16(d, kdesc(ah + o), kdesc(bh + o), idesc, (a | kk) != 0);
-      umma_bf16(d, kdesc(al + o), kdesc(bh + o), idesc, 1);
-      umma_bf16(d, kdesc(ah + o), kdesc(bl + o), idesc, 1);
+    const uint64_t bh = kdesc(sB1 + uint32_t(s) * 16384u), bl = bh + (8192u >> 4);
+    const uint64_t ah = ah0 + uint64_t(a) * (16384u >> 4), al = al0 + uint64_t(a) * (16384u >> 4);
+    const int kn = min(4, ks1 - a * 4);
+    for (int kk = 0; kk < kn; ++kk) {
+      const uint64_t o = uint64_t(kk) * 2u;  // 32 bytes in 16-byte descriptor units
+      umma_bf16(d, ah + o, bh + o, idesc, (a | kk) != 0);
+      umma_bf16(d, al + o, bh + o, idesc, 1);
+      umma_bf16(d, ah + o, bl + o, idesc, 1);
     }
     umma_commit(smem_u32(&ctl->b1_empty[s]));
     ++c1;
@@ -148,7 +221,7 @@ __device__ __forceinline__ bool load_b1(TcCtl* ctl, const CUtensorMap* tm, const
   const int na = (ks1 + 3) >> 2;
   for (int a = 0; a < na; ++a) {
     const int s = n1 % S1;
-    if (n1 >= S1 && !mbar_wait(smem_u32(&ctl->b1_empty[s]), ((n1 / S1) - 1) & 1, abort)) return false;
+    if (n1 >= S1 && !tc_wait(smem_u32(&ctl->b1_empty[s]), ((n1 / S1) - 1) & 1, abort)) return false;
     const uint32_t bar = smem_u32(&ctl->b1_full[s]);
     mbar_expect_tx(bar, 16384u);
     tma_load_2d(sB1 + uint32_t(s) * 16384u, tm, bar, a * 64, c.b1row);
@@ -158,46 +231,33 @@ __device__ __forceinline__ bool load_b1(TcCtl* ctl, const CUtensorMap* tm, const
   return true;
 }
 
-__device__ __forceinline__ void init_common(TcCtl* ctl) {
-  for (int s = 0; s < 4; ++s) {
-    mbar_init(smem_u32(&ctl->b1_full[s]), 1);
-    mbar_init(smem_u32(&ctl->b1_empty[s]), 1);
-    mbar_init(smem_u32(&ctl->b3_full[s]), 1);
-    mbar_init(smem_u32(&ctl->b3_empty[s]), 1);
+__device__ __forceinline__ TcChunk ld_chunk(const TcChunk* p, int i, int n) {
+  TcChunk c{};
+  if (i < n) {
+    const int4* q = reinterpret_cast<const int4*>(p + i);
+    const int4 x = __ldg(q), y = __ldg(q + 1);
+    c = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
   }
-  for (int s = 0; s < 2; ++s) {
-    mbar_init(smem_u32(&ctl->b2_full[s]), 1);
-    mbar_init(smem_u32(&ctl->b2_empty[s]), 1);
-    mbar_init(smem_u32(&ctl->d1_full[s]), 1);
-    mbar_init(smem_u32(&ctl->d1_empty[s]), kTcEpi);
-    mbar_init(smem_u32(&ctl->a2_full[s]), kTcEpi);
-    mbar_init(smem_u32(&ctl->a2_empty[s]), 1);
-    mbar_init(smem_u32(&ctl->d2_full[s]), 1);
-    mbar_init(smem_u32(&ctl->d2_empty[s]), kTcEpi);
-    mbar_init(smem_u32(&ctl->dv_full[s]), kTcEpi);
-    mbar_init(smem_u32(&ctl->dv_empty[s]), 1);
-  }
-  mbar_init(smem_u32(&ctl->a1_full), kTcEpi);
-  mbar_init(smem_u32(&ctl->d3_full), 1);
-  mbar_init(smem_u32(&ctl->drain), 1);
-  ctl->abort = 0;
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  return c;
 }
 
 // ---------------------------------------------------------------------------
 // Forward: V2 of one tile of 128 columns.
 // Shared memory: A1 [KA atoms hi | KA atoms lo] (16 KB each), B1 ring
-// S1 x 16 KB (64 table rows hi | lo), B2 ring 2 x 4 KB (R_out rows, hi|lo
-// packed in each 128-byte row), A2 NA2 x 16 KB (|Z| hi|lo packed).
+// S1 x 16 KB (64 table rows hi | lo), B2 ring kS2 x 4 KB (R_out rows, hi|lo
+// packed in each 128-byte row), A2 2 x 16 KB (|Z| hi|lo packed, one per group).
 // TMEM: D1 2 x 64 columns at 0, D2 2 x 32 columns at 128.
 // ---------------------------------------------------------------------------
-template <int KA, int S1, int NA2>
+constexpr int kTcFwdThreads = 19 * 32;
+constexpr int kTcAdjThreads = 20 * 32;
+
+template <int KA, int S1>
 constexpr size_t tc_fwd_smem() {
-  return sizeof(TcCtl) + 1024 + size_t(KA) * 32768 + size_t(S1) * 16384 + 2 * 4096 + size_t(NA2) * 16384;
+  return sizeof(TcCtl) + 1024 + size_t(KA) * 32768 + size_t(S1) * 16384 + size_t(kS2) * 4096 + 2 * 16384;
 }
 
-template <int KA, int S1, int NA2>
-__global__ void __launch_bounds__(kTcThreads, 1)
+template <int KA, int S1>
+__global__ void __launch_bounds__(kTcFwdThreads, 1)
 k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2, const TcArgs A) {
   extern __shared__ uint8_t smem_raw[];
   TcCtl* ctl = reinterpret_cast<TcCtl*>(smem_raw);
@@ -205,68 +265,80 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
   const uint32_t sA1 = base;
   const uint32_t sB1 = sA1 + uint32_t(KA) * 32768u;
   const uint32_t sB2 = sB1 + uint32_t(S1) * 16384u;
-  const uint32_t sA2 = sB2 + 2u * 4096u;
+  const uint32_t sA2 = sB2 + uint32_t(kS2) * 4096u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Tile tl = A.tiles[blockIdx.x];
   const int n1m = A.n1max_act[tl.a];
   const int ks1 = (2 * n1m + 15) >> 4;
   const int nch = A.n_chunks, RO = A.RO;
   volatile int* abort = &ctl->abort;
-  if (threadIdx.x == 0) init_common(ctl);
-  if (warp == 9) tmem_alloc(smem_u32(&ctl->tmem), 256);
+  if (threadIdx.x == 0) init_barriers(ctl);
+  if (warp == kWarpG1) tmem_alloc(smem_u32(&ctl->tmem), 256);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = ctl->tmem;
   int n1 = 0, n2 = 0;  // TMA stages issued (producer)
-  bool mma_ran = false;
+  bool issued = false;
 
-  if (warp == 8) {
+  if (warp == kWarpTma) {
     if (lane == 0) {
-      bool ok = load_b1<S1>(ctl, &tmB1, A.chunks[0], ks1, A.nr1, sB1, n1, abort);
+      TcChunk nx = ld_chunk(A.chunks, 0, nch);
+      bool ok = load_b1<S1>(ctl, &tmB1, nx, ks1, A.nr1, sB1, n1, abort);
+      TcChunk cur = nx;
       for (int i = 0; ok && i < nch; ++i) {
-        if (i + 1 < nch) ok = load_b1<S1>(ctl, &tmB1, A.chunks[i + 1], ks1, A.nr1, sB1, n1, abort);
+        nx = ld_chunk(A.chunks, i + 1, nch);
+        if (i + 1 < nch) ok = load_b1<S1>(ctl, &tmB1, nx, ks1, A.nr1, sB1, n1, abort);
         if (!ok) break;
-        const TcChunk c = A.chunks[i];
-        const int s = n2 & 1;
-        if (n2 >= 2 && !mbar_wait(smem_u32(&ctl->b2_empty[s]), ((n2 >> 1) - 1) & 1, abort)) break;
+        const int s = n2 % kS2;
+        if (n2 >= kS2 && !tc_wait(smem_u32(&ctl->b2_empty[s]), ((n2 / kS2) - 1) & 1, abort)) break;
         const uint32_t bar = smem_u32(&ctl->b2_full[s]);
         mbar_expect_tx(bar, uint32_t(RO) * 128u);
-        tma_load_2d(sB2 + uint32_t(s) * 4096u, &tmB2, bar, 64 * (c.r0 >> 5), c.k * RO);
+        tma_load_2d(sB2 + uint32_t(s) * 4096u, &tmB2, bar, 64 * (cur.r0 >> 5), cur.k * RO);
         ++n2;
+        cur = nx;
       }
     }
-  } else if (warp == 9) {
-    if (lane == 0) {
-      mma_ran = true;
-      int c1 = 0, c2 = 0;
-      bool ok = mbar_wait(smem_u32(&ctl->a1_full), 0, abort);
+  } else if (warp == kWarpG1) {
+    if (lane == 0) {  // GEMM1: D1[i & 1] = Y . B1 (chunk i)
+      issued = true;
+      int c1 = 0;
+      bool ok = tc_wait(smem_u32(&ctl->a1_full), 0, abort);
       tc_fence_after();
-      if (ok) ok = issue_g1<KA, S1>(ctl, A.chunks[0], ks1, sA1, sB1, tmem, c1, abort);
-      if (ok) umma_commit(smem_u32(&ctl->d1_full[0]));
-      const uint32_t idesc2 = idesc_bf16_n(RO);
+      TcChunk nx = ld_chunk(A.chunks, 0, nch);
       for (int i = 0; ok && i < nch; ++i) {
-        if (i + 1 < nch) {
-          const int j = (i + 1) & 1;
-          if (i + 1 >= 2 && !mbar_wait(smem_u32(&ctl->d1_empty[j]), (((i + 1) >> 1) - 1) & 1, abort)) break;
+        const TcChunk c = nx;
+        nx = ld_chunk(A.chunks, i + 1, nch);
+        const int j = i & 1;
+        if (i >= 2) {
+          if (!tc_wait(smem_u32(&ctl->d1_empty[j]), ((i >> 1) - 1) & 1, abort)) break;
           tc_fence_after();
-          if (!issue_g1<KA, S1>(ctl, A.chunks[i + 1], ks1, sA1, sB1, tmem + uint32_t(j) * 64u, c1, abort)) break;
-          umma_commit(smem_u32(&ctl->d1_full[j]));
         }
-        // GEMM2 of chunk i.
-        const TcChunk c = A.chunks[i];
-        const int ja = i % NA2, s = c2 & 1, bj = c.beta & 1;
-        if (!mbar_wait(smem_u32(&ctl->a2_full[ja]), (i / NA2) & 1, abort)) break;
-        if (!mbar_wait(smem_u32(&ctl->b2_full[s]), (c2 >> 1) & 1, abort)) break;
-        if (c.first && c.beta >= 2 && !mbar_wait(smem_u32(&ctl->d2_empty[bj]), ((c.beta >> 1) - 1) & 1, abort)) break;
+        if (!issue_g1<KA, S1>(ctl, c, ks1, sA1, sB1, tmem + uint32_t(j) * 64u, c1, abort)) break;
+        umma_commit(smem_u32(&ctl->d1_full[j]));
+      }
+    }
+  } else if (warp == kWarpG2) {
+    if (lane == 0) {  // GEMM2: D2[beta & 1] += |Z| . P^T (chunk i)
+      issued = true;
+      int c2 = 0;
+      const uint32_t idesc2 = idesc_bf16_n(RO);
+      TcChunk nx = ld_chunk(A.chunks, 0, nch);
+      for (int i = 0; i < nch; ++i) {
+        const TcChunk c = nx;
+        nx = ld_chunk(A.chunks, i + 1, nch);
+        const int ja = i & 1, s = c2 % kS2, bj = c.beta & 1;
+        if (!tc_wait(smem_u32(&ctl->a2_full[ja]), (i >> 1) & 1, abort)) break;
+        if (!tc_wait(smem_u32(&ctl->b2_full[s]), (c2 / kS2) & 1, abort)) break;
+        if (c.first && c.beta >= 2 && !tc_wait(smem_u32(&ctl->d2_empty[bj]), ((c.beta >> 1) - 1) & 1, abort)) break;
         tc_fence_after();
         const uint32_t d = tmem + 128u + uint32_t(bj) * 32u;
-        const uint32_t a2 = sA2 + uint32_t(ja) * 16384u, b2 = sB2 + uint32_t(s) * 4096u;
+        const uint64_t a2 = kdesc(sA2 + uint32_t(ja) * 16384u), b2 = kdesc(sB2 + uint32_t(s) * 4096u);
         for (int kk = 0; kk < (c.rc >> 4); ++kk) {
-          const uint32_t o = uint32_t(kk) * 32u;
-          umma_bf16(d, kdesc(a2 + o), kdesc(b2 + o), idesc2, !(c.first && kk == 0));
-          umma_bf16(d, kdesc(a2 + 64u + o), kdesc(b2 + o), idesc2, 1);
-          umma_bf16(d, kdesc(a2 + o), kdesc(b2 + 64u + o), idesc2, 1);
+          const uint64_t o = uint64_t(kk) * 2u;
+          umma_bf16(d, a2 + o, b2 + o, idesc2, !(c.first && kk == 0));
+          umma_bf16(d, a2 + 4u + o, b2 + o, idesc2, 1);
+          umma_bf16(d, a2 + o, b2 + 4u + o, idesc2, 1);
         }
         umma_commit(smem_u32(&ctl->a2_empty[ja]));
         umma_commit(smem_u32(&ctl->b2_empty[s]));
@@ -274,15 +346,15 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         ++c2;
       }
     }
-  } else {
-    // Epilogue warps.
-    const int q = warp & 3, h = warp >> 2;
+  } else if (warp < kWarpTma) {
+    // Epilogue groups.
+    const int g = warp >> 3, q = warp & 3, h = (warp >> 2) & 1;
     const int c = q * 32 + lane;
     const uint32_t lane_off = uint32_t(q * 32) << 16;
     const bool colok = c < tl.ncols;
     const int L2 = 1 << (A.logN - A.s2[tl.a]);
     float* vdst = A.V2 + int64_t(tl.b) * A.v2_tot + A.v2_off[tl.a] + tl.t0 + c;
-    load_a1<KA>(A, tl, n1m, ks1, sA1, c, h);
+    load_a1<KA>(A, tl, n1m, ks1, sA1, c, (warp >> 2) & 3, 4);
     fence_proxy_async();
     mbar_arrive(smem_u32(&ctl->a1_full));
     auto store_v2 = [&](int beta) -> bool {
@@ -296,12 +368,14 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         uint32_t r[16];
         tmem_ld16_nowait(taddr, r);
         tmem_ld_wait();
+        tmem_regs_ready(r);
 #pragma unroll
         for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
       } else {
         uint32_t r[8];
         tmem_ld8_nowait(taddr, r);
         tmem_ld_wait();
+        tmem_regs_ready(r);
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[e]);
       }
@@ -315,12 +389,12 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
       }
       return true;
     };
-    bool ok = true;
-    for (int i = 0; i < nch; ++i) {
-      const TcChunk ch = A.chunks[i];
-      const int j = i & 1, ja = i % NA2;
-      if (!wait_warp(smem_u32(&ctl->d1_full[j]), (i >> 1) & 1, abort)) { ok = false; break; }
-      if (i >= NA2 && !wait_warp(smem_u32(&ctl->a2_empty[ja]), ((i / NA2) - 1) & 1, abort)) { ok = false; break; }
+    TcChunk nx = ld_chunk(A.chunks, g, nch);
+    for (int i = g; i < nch; i += 2) {
+      const TcChunk ch = nx;
+      nx = ld_chunk(A.chunks, i + 2, nch);
+      const int j = i & 1;
+      if (!wait_warp(smem_u32(&ctl->d1_full[j]), (i >> 1) & 1, abort)) break;
       tc_fence_after();
       // D1 columns [h rc, h rc + rc): rc / 2 complex values, rows r = h rc / 2 + e.
       const uint32_t taddr = tmem + lane_off + uint32_t(j) * 64u + uint32_t(h * ch.rc);
@@ -329,24 +403,23 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         float z[32];
         tmem_ld32(taddr, z);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) mag[e] = sqrtf(z[2 * e] * z[2 * e] + z[2 * e + 1] * z[2 * e + 1]);
+        for (int e = 0; e < 16; ++e) mag[e] = modulus(z[2 * e], z[2 * e + 1]);
       } else {
         uint32_t r[16];
         tmem_ld16_nowait(taddr, r);
         tmem_ld_wait();
+        tmem_regs_ready(r);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const float x = __uint_as_float(r[2 * e]), y = __uint_as_float(r[2 * e + 1]);
-          mag[e] = sqrtf(x * x + y * y);
-        }
+        for (int e = 0; e < 8; ++e) mag[e] = modulus(__uint_as_float(r[2 * e]), __uint_as_float(r[2 * e + 1]));
 #pragma unroll
         for (int e = 8; e < 16; ++e) mag[e] = 0.f;
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&ctl->d1_empty[j]));
-      // |Z| rows into A2 (hi at K = r, lo at K = 32 + r), 8 values per 16-byte chunk.
-      const uint32_t a2 = sA2 + uint32_t(ja) * 16384u;
-      const int nck = ch.rc >> 4, ck0 = h * nck;  // chunks of this half
+      // |Z| rows into this group's A2 (hi at K = r, lo at K = 32 + r) once GEMM2 of chunk i - 2 has read it.
+      if (i >= 2 && !wait_warp(smem_u32(&ctl->a2_empty[j]), ((i >> 1) - 1) & 1, abort)) break;
+      const uint32_t a2 = sA2 + uint32_t(j) * 16384u;
+      const int nck = ch.rc >> 4, ck0 = h * nck;
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         if (t < nck) {
@@ -358,25 +431,25 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         }
       }
       fence_proxy_async();
-      mbar_arrive(smem_u32(&ctl->a2_full[ja]));
-      if (i >= 1 && A.chunks[i - 1].last && !store_v2(A.chunks[i - 1].beta)) { ok = false; break; }
+      mbar_arrive(smem_u32(&ctl->a2_full[j]));
+      if (ch.last && !store_v2(ch.beta)) break;
     }
-    if (ok) store_v2(A.chunks[nch - 1].beta);
   }
 
   // Teardown: no TMA copy or MMA of this CTA may be in flight when it exits.
-  if (warp == 8 && lane == 0 && *abort) {
+  if (warp == kWarpTma && lane == 0 && *abort) {
     for (int t = max(0, n1 - S1); t < n1; ++t) mbar_wait_drain(smem_u32(&ctl->b1_full[t % S1]), (t / S1) & 1);
-    for (int t = max(0, n2 - 2); t < n2; ++t) mbar_wait_drain(smem_u32(&ctl->b2_full[t & 1]), (t >> 1) & 1);
+    for (int t = max(0, n2 - kS2); t < n2; ++t) mbar_wait_drain(smem_u32(&ctl->b2_full[t % kS2]), (t / kS2) & 1);
   }
-  if (warp == 9 && lane == 0 && mma_ran) {
-    umma_commit(smem_u32(&ctl->drain));
-    mbar_wait_drain(smem_u32(&ctl->drain), 0);
+  if ((warp == kWarpG1 || warp == kWarpG2) && lane == 0 && issued) {
+    const uint32_t dr = smem_u32(&ctl->drain[warp - kWarpG1]);
+    umma_commit(dr);
+    mbar_wait_drain(dr, 0);
   }
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && *abort) atomicExch(&g_tc_err, 1);
-  if (warp == 9) {
+  if (warp == kWarpG1) {
     __syncwarp();
     tmem_dealloc(tmem, 256);
   }
@@ -384,19 +457,20 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
 
 // ---------------------------------------------------------------------------
 // Adjoint: dY2 of one tile of 128 columns, from Y2 (recomputed Z) and dV2.
-// Shared memory: A1 as forward, B1 ring S1 x 16 KB, B2' ring 2 x 4 KB
+// Shared memory: A1 as forward, B1 ring S1 x 16 KB, B2' ring kS2 x 4 KB
 // (32 table rows, hi|lo packed), dV 2 x 16 KB (hi|lo packed), A3 NA3 x 32 KB
-// (dZ hi atom | lo atom), B3 ring S3 x 16 KB (64 rows (n, re/im) x 64 K, hi | lo).
+// (dZ hi atom | lo atom; with NA3 = 2 one per group), B3 ring S3 x 16 KB (64 rows
+// (n, re/im) x 64 K, hi | lo).
 // TMEM (512 columns): D1 2 x 64 at 0, D2' 2 x 32 at 128, D3 <= 128 at 256.
 // ---------------------------------------------------------------------------
 template <int KA, int S1, int S3, int NA3>
 constexpr size_t tc_adj_smem() {
-  return sizeof(TcCtl) + 1024 + size_t(KA) * 32768 + size_t(S1) * 16384 + 2 * 4096 + 2 * 16384 +
+  return sizeof(TcCtl) + 1024 + size_t(KA) * 32768 + size_t(S1) * 16384 + size_t(kS2) * 4096 + 2 * 16384 +
          size_t(NA3) * 32768 + size_t(S3) * 16384;
 }
 
 template <int KA, int S1, int S3, int NA3>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcAdjThreads, 1)
 k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2t,
               const __grid_constant__ CUtensorMap tmB3, const TcArgs A) {
   extern __shared__ uint8_t smem_raw[];
@@ -405,7 +479,7 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
   const uint32_t sA1 = base;
   const uint32_t sB1 = sA1 + uint32_t(KA) * 32768u;
   const uint32_t sB2 = sB1 + uint32_t(S1) * 16384u;
-  const uint32_t sDV = sB2 + 2u * 4096u;
+  const uint32_t sDV = sB2 + uint32_t(kS2) * 4096u;
   const uint32_t sA3 = sDV + 2u * 16384u;
   const uint32_t sB3 = sA3 + uint32_t(NA3) * 32768u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -415,34 +489,32 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
   const int k1pad = 16 * ks1;               // GEMM3 N (columns (n, re/im) kept)
   const int nh = (k1pad + 63) >> 6;         // GEMM3 N-halves of 64
   const int nch = A.n_chunks, RO = A.RO;
-  const int nbeta = A.chunks[nch - 1].beta + 1;
+  const int nbeta = ld_chunk(A.chunks, nch - 1, nch).beta + 1;
   volatile int* abort = &ctl->abort;
-  if (threadIdx.x == 0) init_common(ctl);
-  if (warp == 9) tmem_alloc(smem_u32(&ctl->tmem), 512);
+  if (threadIdx.x == 0) init_barriers(ctl);
+  if (warp == kWarpG1) tmem_alloc(smem_u32(&ctl->tmem), 512);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = ctl->tmem;
   int n1 = 0, n2 = 0, n3 = 0;
-  bool mma_ran = false;
+  bool issued = false;
 
-  if (warp == 8) {
+  if (warp == kWarpTma) {
     if (lane == 0) {
-      auto load_b2 = [&](int i) -> bool {
-        const TcChunk c = A.chunks[i];
-        const int s = n2 & 1;
-        if (n2 >= 2 && !mbar_wait(smem_u32(&ctl->b2_empty[s]), ((n2 >> 1) - 1) & 1, abort)) return false;
+      auto load_b2 = [&](const TcChunk& c) -> bool {
+        const int s = n2 % kS2;
+        if (n2 >= kS2 && !tc_wait(smem_u32(&ctl->b2_empty[s]), ((n2 / kS2) - 1) & 1, abort)) return false;
         const uint32_t bar = smem_u32(&ctl->b2_full[s]);
         mbar_expect_tx(bar, 4096u);
         tma_load_2d(sB2 + uint32_t(s) * 4096u, &tmB2t, bar, 0, c.prow);
         ++n2;
         return true;
       };
-      auto load_b3 = [&](int i) -> bool {
-        const TcChunk c = A.chunks[i];
+      auto load_b3 = [&](const TcChunk& c) -> bool {
         for (int u = 0; u < nh; ++u) {
           const int s = n3 % S3;
-          if (n3 >= S3 && !mbar_wait(smem_u32(&ctl->b3_empty[s]), ((n3 / S3) - 1) & 1, abort)) return false;
+          if (n3 >= S3 && !tc_wait(smem_u32(&ctl->b3_empty[s]), ((n3 / S3) - 1) & 1, abort)) return false;
           const uint32_t bar = smem_u32(&ctl->b3_full[s]);
           mbar_expect_tx(bar, 16384u);
           tma_load_2d(sB3 + uint32_t(s) * 16384u, &tmB3, bar, c.b1row, 64 * u);
@@ -451,70 +523,90 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         }
         return true;
       };
-      bool ok = load_b1<S1>(ctl, &tmB1, A.chunks[0], ks1, A.nr1, sB1, n1, abort) && load_b2(0);
+      TcChunk cur = ld_chunk(A.chunks, 0, nch);
+      bool ok = load_b1<S1>(ctl, &tmB1, cur, ks1, A.nr1, sB1, n1, abort) && load_b2(cur);
       for (int i = 0; ok && i < nch; ++i) {
-        if (i + 1 < nch) ok = load_b1<S1>(ctl, &tmB1, A.chunks[i + 1], ks1, A.nr1, sB1, n1, abort) && load_b2(i + 1);
-        if (ok) ok = load_b3(i);
+        const TcChunk nx = ld_chunk(A.chunks, i + 1, nch);
+        if (i + 1 < nch) ok = load_b1<S1>(ctl, &tmB1, nx, ks1, A.nr1, sB1, n1, abort) && load_b2(nx);
+        if (ok) ok = load_b3(cur);
+        cur = nx;
       }
     }
-  } else if (warp == 9) {
-    if (lane == 0) {
-      mma_ran = true;
-      int c1 = 0, c2 = 0, c3 = 0;
-      auto g2t = [&](int i) -> bool {  // d|Z| of chunk i into D2'[i & 1]
-        const TcChunk c = A.chunks[i];
-        const int bj = c.beta & 1, j = i & 1, s = c2 & 1;
-        if (c.first && !mbar_wait(smem_u32(&ctl->dv_full[bj]), (c.beta >> 1) & 1, abort)) return false;
-        if (i >= 2 && !mbar_wait(smem_u32(&ctl->d2_empty[j]), ((i >> 1) - 1) & 1, abort)) return false;
-        if (!mbar_wait(smem_u32(&ctl->b2_full[s]), (c2 >> 1) & 1, abort)) return false;
+  } else if (warp == kWarpG1) {
+    if (lane == 0) {  // GEMM1 (recompute Z): D1[i & 1]
+      issued = true;
+      int c1 = 0;
+      bool ok = tc_wait(smem_u32(&ctl->a1_full), 0, abort);
+      tc_fence_after();
+      TcChunk nx = ld_chunk(A.chunks, 0, nch);
+      for (int i = 0; ok && i < nch; ++i) {
+        const TcChunk c = nx;
+        nx = ld_chunk(A.chunks, i + 1, nch);
+        const int j = i & 1;
+        if (i >= 2) {
+          if (!tc_wait(smem_u32(&ctl->d1_empty[j]), ((i >> 1) - 1) & 1, abort)) break;
+          tc_fence_after();
+        }
+        if (!issue_g1<KA, S1>(ctl, c, ks1, sA1, sB1, tmem + uint32_t(j) * 64u, c1, abort)) break;
+        umma_commit(smem_u32(&ctl->d1_full[j]));
+      }
+    }
+  } else if (warp == kWarpG2) {
+    if (lane == 0) {  // GEMM2': d|Z| = dV . P into D2'[i & 1]
+      issued = true;
+      int c2 = 0;
+      TcChunk nx = ld_chunk(A.chunks, 0, nch);
+      for (int i = 0; i < nch; ++i) {
+        const TcChunk c = nx;
+        nx = ld_chunk(A.chunks, i + 1, nch);
+        const int bj = c.beta & 1, j = i & 1, s = c2 % kS2;
+        if (c.first && !tc_wait(smem_u32(&ctl->dv_full[bj]), (c.beta >> 1) & 1, abort)) break;
+        if (i >= 2) {
+          if (!tc_wait(smem_u32(&ctl->d2_empty[j]), ((i >> 1) - 1) & 1, abort)) break;
+          tc_fence_after();
+        }
+        if (!tc_wait(smem_u32(&ctl->b2_full[s]), (c2 / kS2) & 1, abort)) break;
         tc_fence_after();
         const uint32_t d = tmem + 128u + uint32_t(j) * 32u;
         const uint32_t idesc = idesc_bf16_n(c.rc);
-        const uint32_t a = sDV + uint32_t(bj) * 16384u, b = sB2 + uint32_t(s) * 4096u;
+        const uint64_t a = kdesc(sDV + uint32_t(bj) * 16384u), b = kdesc(sB2 + uint32_t(s) * 4096u);
         for (int kk = 0; kk < (RO >> 4); ++kk) {
-          const uint32_t o = uint32_t(kk) * 32u;
-          umma_bf16(d, kdesc(a + o), kdesc(b + o), idesc, kk != 0);
-          umma_bf16(d, kdesc(a + 64u + o), kdesc(b + o), idesc, 1);
-          umma_bf16(d, kdesc(a + o), kdesc(b + 64u + o), idesc, 1);
+          const uint64_t o = uint64_t(kk) * 2u;
+          umma_bf16(d, a + o, b + o, idesc, kk != 0);
+          umma_bf16(d, a + 4u + o, b + o, idesc, 1);
+          umma_bf16(d, a + o, b + 4u + o, idesc, 1);
         }
         umma_commit(smem_u32(&ctl->b2_empty[s]));
         umma_commit(smem_u32(&ctl->d2_full[j]));
         if (c.last) umma_commit(smem_u32(&ctl->dv_empty[bj]));
         ++c2;
-        return true;
-      };
-      auto g1 = [&](int i) -> bool {
-        const int j = i & 1;
-        if (i >= 2 && !mbar_wait(smem_u32(&ctl->d1_empty[j]), ((i >> 1) - 1) & 1, abort)) return false;
-        tc_fence_after();
-        if (!issue_g1<KA, S1>(ctl, A.chunks[i], ks1, sA1, sB1, tmem + uint32_t(j) * 64u, c1, abort)) return false;
-        umma_commit(smem_u32(&ctl->d1_full[j]));
-        return true;
-      };
-      bool ok = mbar_wait(smem_u32(&ctl->a1_full), 0, abort);
-      tc_fence_after();
-      ok = ok && g1(0) && g2t(0);
-      for (int i = 0; ok && i < nch; ++i) {
-        if (i + 1 < nch && !(g1(i + 1) && g2t(i + 1))) break;
-        // GEMM3 of chunk i: D3 += dZ . B1 (rows of the chunk); A3 buffers use the a2 barriers.
-        const TcChunk c = A.chunks[i];
+      }
+    }
+  } else if (warp == kWarpG3) {
+    if (lane == 0) {  // GEMM3: D3 += dZ . B1 (rows of chunk i); A3 buffers use the a2 barriers.
+      issued = true;
+      int c3 = 0;
+      TcChunk nx = ld_chunk(A.chunks, 0, nch);
+      for (int i = 0; i < nch; ++i) {
+        const TcChunk c = nx;
+        nx = ld_chunk(A.chunks, i + 1, nch);
         const int ja = i % NA3;
-        if (!mbar_wait(smem_u32(&ctl->a2_full[ja]), (i / NA3) & 1, abort)) break;
+        if (!tc_wait(smem_u32(&ctl->a2_full[ja]), (i / NA3) & 1, abort)) break;
         tc_fence_after();
-        const uint32_t ah = sA3 + uint32_t(ja) * 32768u, al = ah + 16384u;
+        const uint64_t ah = kdesc(sA3 + uint32_t(ja) * 32768u), al = ah + (16384u >> 4);
         bool okb = true;
         for (int u = 0; u < nh; ++u) {
           const int s = c3 % S3;
-          if (!mbar_wait(smem_u32(&ctl->b3_full[s]), (c3 / S3) & 1, abort)) { okb = false; break; }
+          if (!tc_wait(smem_u32(&ctl->b3_full[s]), (c3 / S3) & 1, abort)) { okb = false; break; }
           tc_fence_after();
-          const uint32_t bh = sB3 + uint32_t(s) * 16384u, bl = bh + 8192u;
+          const uint64_t bh = kdesc(sB3 + uint32_t(s) * 16384u), bl = bh + (8192u >> 4);
           const uint32_t d = tmem + 256u + uint32_t(u) * 64u;
           const uint32_t idesc = idesc_bf16_n(min(64, k1pad - 64 * u));
           for (int kk = 0; kk < (c.rc >> 3); ++kk) {  // K = 2 rc
-            const uint32_t o = uint32_t(kk) * 32u;
-            umma_bf16(d, kdesc(ah + o), kdesc(bh + o), idesc, (i | kk) != 0);
-            umma_bf16(d, kdesc(al + o), kdesc(bh + o), idesc, 1);
-            umma_bf16(d, kdesc(ah + o), kdesc(bl + o), idesc, 1);
+            const uint64_t o = uint64_t(kk) * 2u;
+            umma_bf16(d, ah + o, bh + o, idesc, (i | kk) != 0);
+            umma_bf16(d, al + o, bh + o, idesc, 1);
+            umma_bf16(d, ah + o, bl + o, idesc, 1);
           }
           umma_commit(smem_u32(&ctl->b3_empty[s]));
           ++c3;
@@ -524,9 +616,9 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         if (i == nch - 1) umma_commit(smem_u32(&ctl->d3_full));
       }
     }
-  } else {
-    // Epilogue warps.
-    const int q = warp & 3, h = warp >> 2;
+  } else if (warp < kWarpTma) {
+    // Epilogue groups.
+    const int g = warp >> 3, q = warp & 3, h = (warp >> 2) & 1;
     const int c = q * 32 + lane;
     const uint32_t lane_off = uint32_t(q * 32) << 16;
     const bool colok = c < tl.ncols;
@@ -552,15 +644,17 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         }
       }
     };
-    load_a1<KA>(A, tl, n1m, ks1, sA1, c, h);
-    load_dv(0);
+    load_a1<KA>(A, tl, n1m, ks1, sA1, c, (warp >> 2) & 3, 4);
+    if (g == 0) load_dv(0);
     fence_proxy_async();
     mbar_arrive(smem_u32(&ctl->a1_full));
-    mbar_arrive(smem_u32(&ctl->dv_full[0]));
+    if (g == 0) mbar_arrive(smem_u32(&ctl->dv_full[0]));
     bool ok = true;
-    for (int i = 0; i < nch; ++i) {
-      const TcChunk ch = A.chunks[i];
-      const int j = i & 1, ja = i % NA3;
+    TcChunk nx = ld_chunk(A.chunks, g, nch);
+    for (int i = g; i < nch; i += 2) {
+      const TcChunk ch = nx;
+      nx = ld_chunk(A.chunks, i + 2, nch);
+      const int j = i & 1;
       if (ch.first && ch.beta + 1 < nbeta) {
         const int nb = ch.beta + 1, bj = nb & 1;
         if (nb >= 2 && !wait_warp(smem_u32(&ctl->dv_empty[bj]), ((nb >> 1) - 1) & 1, abort)) { ok = false; break; }
@@ -570,31 +664,37 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
       }
       if (!wait_warp(smem_u32(&ctl->d1_full[j]), (i >> 1) & 1, abort)) { ok = false; break; }
       if (!wait_warp(smem_u32(&ctl->d2_full[j]), (i >> 1) & 1, abort)) { ok = false; break; }
-      if (i >= NA3 && !wait_warp(smem_u32(&ctl->a2_empty[ja]), ((i / NA3) - 1) & 1, abort)) { ok = false; break; }
       tc_fence_after();
       // Z rows r = h rc / 2 + e (D1 columns [h rc, h rc + rc)) and d|Z| (D2' columns [h rc / 2, ...)).
-      const int hr = ch.rc >> 1;
-      float z[32], g[16];
+      float z[32], gz[16];
       if (ch.rc == 32) {
-        tmem_ld32(tmem + lane_off + uint32_t(j) * 64u + uint32_t(h * 32), z);
-        uint32_t r[16];
-        tmem_ld16_nowait(tmem + lane_off + 128u + uint32_t(j) * 32u + uint32_t(h * 16), r);
+        uint32_t r[32], r16[16];
+        tmem_ld16_nowait(tmem + lane_off + uint32_t(j) * 64u + uint32_t(h * 32), *reinterpret_cast<uint32_t(*)[16]>(r));
+        tmem_ld16_nowait(tmem + lane_off + uint32_t(j) * 64u + uint32_t(h * 32 + 16),
+                         *reinterpret_cast<uint32_t(*)[16]>(r + 16));
+        tmem_ld16_nowait(tmem + lane_off + 128u + uint32_t(j) * 32u + uint32_t(h * 16), r16);
         tmem_ld_wait();
+        tmem_regs_ready(r);
+        tmem_regs_ready(r16);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) g[e] = __uint_as_float(r[e]);
+        for (int e = 0; e < 32; ++e) z[e] = __uint_as_float(r[e]);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) gz[e] = __uint_as_float(r16[e]);
       } else {
         uint32_t r[16], r8[8];
         tmem_ld16_nowait(tmem + lane_off + uint32_t(j) * 64u + uint32_t(h * 16), r);
         tmem_ld8_nowait(tmem + lane_off + 128u + uint32_t(j) * 32u + uint32_t(h * 8), r8);
         tmem_ld_wait();
+        tmem_regs_ready(r);
+        tmem_regs_ready(r8);
 #pragma unroll
         for (int e = 0; e < 16; ++e) z[e] = __uint_as_float(r[e]);
 #pragma unroll
         for (int e = 16; e < 32; ++e) z[e] = 0.f;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) g[e] = __uint_as_float(r8[e]);
+        for (int e = 0; e < 8; ++e) gz[e] = __uint_as_float(r8[e]);
 #pragma unroll
-        for (int e = 8; e < 16; ++e) g[e] = 0.f;
+        for (int e = 8; e < 16; ++e) gz[e] = 0.f;
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&ctl->d1_empty[j]));
@@ -602,13 +702,16 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
       // dZ = Z / |Z| * d|Z| (0 where |Z| = 0), K index 2 r + (re, im) of the chunk.
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
-        const float m = sqrtf(z[2 * e] * z[2 * e] + z[2 * e + 1] * z[2 * e + 1]);
-        const float s = m > 0.f ? g[e] / m : 0.f;
-        z[2 * e] *= s;
-        z[2 * e + 1] *= s;
+        const float m2 = z[2 * e] * z[2 * e] + z[2 * e + 1] * z[2 * e + 1];
+        const float sc = m2 > 0.f ? gz[e] * rsqrtf(m2) : 0.f;
+        z[2 * e] *= sc;
+        z[2 * e + 1] *= sc;
       }
+      // dZ into A3 buffer i % NA3 once GEMM3 of chunk i - NA3 has read it.
+      const int ja = i % NA3;
+      if (i >= NA3 && !wait_warp(smem_u32(&ctl->a2_empty[ja]), ((i / NA3) - 1) & 1, abort)) { ok = false; break; }
       const uint32_t ah = sA3 + uint32_t(ja) * 32768u, al = ah + 16384u;
-      const int nck = ch.rc >> 3, ck0 = h * nck;  // 16-byte chunks of this half (2 r values each... 4 words)
+      const int nck = ch.rc >> 3, ck0 = h * nck;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         if (t < nck) {
@@ -619,11 +722,10 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
           st_shared_v4(al + swz128(c, ck0 + t), lo);
         }
       }
-      (void)hr;
       fence_proxy_async();
       mbar_arrive(smem_u32(&ctl->a2_full[ja]));
     }
-    if (ok && wait_warp(smem_u32(&ctl->d3_full), 0, abort)) {
+    if (g == 0 && ok && wait_warp(smem_u32(&ctl->d3_full), 0, abort)) {
       tc_fence_after();
       // D3 columns (n, re/im): this half holds n in [h k1pad / 4, (h + 1) k1pad / 4).
       const int64_t ybase = int64_t(tl.b) * A.y2_tot + A.y2_off[tl.a] + tl.t0 + c;
@@ -632,6 +734,7 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         uint32_t r[8];
         tmem_ld8_nowait(tmem + lane_off + 256u + uint32_t(h * ncol + b8), r);
         tmem_ld_wait();
+        tmem_regs_ready(r);
         const int n0 = (h * ncol + b8) >> 1;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -643,19 +746,20 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
     }
   }
 
-  if (warp == 8 && lane == 0 && *abort) {
+  if (warp == kWarpTma && lane == 0 && *abort) {
     for (int t = max(0, n1 - S1); t < n1; ++t) mbar_wait_drain(smem_u32(&ctl->b1_full[t % S1]), (t / S1) & 1);
-    for (int t = max(0, n2 - 2); t < n2; ++t) mbar_wait_drain(smem_u32(&ctl->b2_full[t & 1]), (t >> 1) & 1);
+    for (int t = max(0, n2 - kS2); t < n2; ++t) mbar_wait_drain(smem_u32(&ctl->b2_full[t % kS2]), (t / kS2) & 1);
     for (int t = max(0, n3 - S3); t < n3; ++t) mbar_wait_drain(smem_u32(&ctl->b3_full[t % S3]), (t / S3) & 1);
   }
-  if (warp == 9 && lane == 0 && mma_ran) {
-    umma_commit(smem_u32(&ctl->drain));
-    mbar_wait_drain(smem_u32(&ctl->drain), 0);
+  if (warp >= kWarpG1 && warp <= kWarpG3 && lane == 0 && issued) {
+    const uint32_t dr = smem_u32(&ctl->drain[warp - kWarpG1]);
+    umma_commit(dr);
+    mbar_wait_drain(dr, 0);
   }
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && *abort) atomicExch(&g_tc_err, 1);
-  if (warp == 9) {
+  if (warp == kWarpG1) {
     __syncwarp();
     tmem_dealloc(tmem, 512);
   }
@@ -689,11 +793,8 @@ void split_bf16(double v, uint16_t& hi, uint16_t& lo) {
   lo = bf16_rn(static_cast<float>(v - double(bf16_f(hi))));
 }
 
-template <int KA, int S1, int NA2>
-constexpr size_t fwd_smem() { return tc_fwd_smem<KA, S1, NA2>(); }
-
-constexpr int kFwdS1[2] = {2, 4}, kFwdNA2[2] = {2, 2};
-constexpr int kAdjS1[2] = {3, 2}, kAdjS3[2] = {2, 3}, kAdjNA3[2] = {2, 1};
+constexpr int kFwdS1[2] = {8, 6};
+constexpr int kAdjS1[2] = {3, 3}, kAdjS3[2] = {2, 2}, kAdjNA3[2] = {2, 1};
 
 PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
@@ -928,18 +1029,18 @@ int tc_forward(const Plan& p, const float2* Y2, float* V2, cudaStream_t s) {
   A.Y2 = Y2;
   A.V2 = V2;
   if (!p.tc_tiles[0].empty()) {
-    constexpr size_t smem = tc_fwd_smem<1, kFwdS1[0], kFwdNA2[0]>();
-    if (tc_opt_in<k_freq_tc_fwd<1, kFwdS1[0], kFwdNA2[0]>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
+    constexpr size_t smem = tc_fwd_smem<1, kFwdS1[0]>();
+    if (tc_opt_in<k_freq_tc_fwd<1, kFwdS1[0]>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
     A.tiles = p.d_tc_tiles[0];
-    k_freq_tc_fwd<1, kFwdS1[0], kFwdNA2[0]><<<static_cast<unsigned>(p.tc_tiles[0].size()), kTcThreads, smem, s>>>(
+    k_freq_tc_fwd<1, kFwdS1[0]><<<static_cast<unsigned>(p.tc_tiles[0].size()), kTcFwdThreads, smem, s>>>(
         p.tc_map[0], p.tc_map[1], A);
     if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
   }
   if (!p.tc_tiles[1].empty()) {
-    constexpr size_t smem = tc_fwd_smem<2, kFwdS1[1], kFwdNA2[1]>();
-    if (tc_opt_in<k_freq_tc_fwd<2, kFwdS1[1], kFwdNA2[1]>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
+    constexpr size_t smem = tc_fwd_smem<2, kFwdS1[1]>();
+    if (tc_opt_in<k_freq_tc_fwd<2, kFwdS1[1]>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
     A.tiles = p.d_tc_tiles[1];
-    k_freq_tc_fwd<2, kFwdS1[1], kFwdNA2[1]><<<static_cast<unsigned>(p.tc_tiles[1].size()), kTcThreads, smem, s>>>(
+    k_freq_tc_fwd<2, kFwdS1[1]><<<static_cast<unsigned>(p.tc_tiles[1].size()), kTcFwdThreads, smem, s>>>(
         p.tc_map[0], p.tc_map[1], A);
     if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
   }
@@ -957,7 +1058,7 @@ int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, c
     if (tc_opt_in<k_freq_tc_adj<1, kAdjS1[0], kAdjS3[0], kAdjNA3[0]>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
     A.tiles = p.d_tc_tiles[0];
     k_freq_tc_adj<1, kAdjS1[0], kAdjS3[0], kAdjNA3[0]>
-        <<<static_cast<unsigned>(p.tc_tiles[0].size()), kTcThreads, smem, s>>>(p.tc_map[0], p.tc_map[2],
+        <<<static_cast<unsigned>(p.tc_tiles[0].size()), kTcAdjThreads, smem, s>>>(p.tc_map[0], p.tc_map[2],
                                                                                p.tc_map[3], A);
     if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
   }
@@ -966,7 +1067,7 @@ int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, c
     if (tc_opt_in<k_freq_tc_adj<2, kAdjS1[1], kAdjS3[1], kAdjNA3[1]>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
     A.tiles = p.d_tc_tiles[1];
     k_freq_tc_adj<2, kAdjS1[1], kAdjS3[1], kAdjNA3[1]>
-        <<<static_cast<unsigned>(p.tc_tiles[1].size()), kTcThreads, smem, s>>>(p.tc_map[0], p.tc_map[2],
+        <<<static_cast<unsigned>(p.tc_tiles[1].size()), kTcAdjThreads, smem, s>>>(p.tc_map[0], p.tc_map[2],
                                                                                p.tc_map[3], A);
     if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
   }
@@ -981,9 +1082,18 @@ int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, c
 extern "C" int jtfs_tc_error(void) {
   int v = 0;
   if (cudaMemcpyFromSymbol(&v, jtfs::g_tc_err, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
-  const int zero = 0;
-  if (v && cudaMemcpyToSymbol(jtfs::g_tc_err, &zero, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
+  const int zero[4] = {0, 0, 0, 0};
+  if (v && cudaMemcpyToSymbol(jtfs::g_tc_err, zero, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
   return v;
+}
+
+extern "C" int jtfs_tc_error_info(int64_t* info, int n) {
+  int v[4];
+  if (cudaMemcpyFromSymbol(v, jtfs::g_tc_err_info, sizeof(v)) != cudaSuccess) return JTFS_ERR_CUDA;
+  for (int i = 0; i < n && i < 4 && info; ++i) info[i] = i == 0 ? int64_t(v[0]) - 1 : v[i];
+  const int zero[4] = {0, 0, 0, 0};
+  if (cudaMemcpyToSymbol(jtfs::g_tc_err_info, zero, sizeof(zero)) != cudaSuccess) return JTFS_ERR_CUDA;
+  return 4;
 }
 
 extern "C" int64_t jtfs_tc_table(jtfs_plan_t plan, int which, float* out, int64_t n) {
