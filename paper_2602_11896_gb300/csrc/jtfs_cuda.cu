@@ -738,6 +738,95 @@ k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ part, c
   }
 }
 
+// Forward, split over time, register-blocked for 16-byte shared loads: a CTA
+// of 4 FR threads owns a 64-row x FR-frame tile of one (clip, n2) and the time
+// samples [split * split_len, +split_len); thread (tr = tid % 16, tf = tid / 16)
+// accumulates rows 4 tr .. 4 tr + 3 and frames 4 tf .. 4 tf + 3, reading one
+// float4 of V2 rows and one (warp-broadcast) float4 of taps per time sample.
+// The V2 chunk is read into registers one chunk ahead.  Partials as k_pool_fwd.
+template <int FR>
+__global__ void __launch_bounds__(4 * FR)
+k_pool_fwd2(PoolArgs A, const float* __restrict__ V2, float* __restrict__ part, const int4* __restrict__ tiles,
+            int split_len) {
+  constexpr int NT = 4 * FR;                     // threads
+  constexpr int VPT = (kPoolRows * kPoolK / 4) / NT;  // float4 of V2 per thread per chunk (>= 1)
+  __shared__ __align__(16) float Vs[kPoolK][kPoolRows + 4];
+  __shared__ __align__(16) float Gs[kPoolK][FR];
+  const int4 tl = tiles[blockIdx.x];  // (clip, active n2, row tile, split)
+  const int b = tl.x, a = tl.y, split = tl.w;
+  const int fb = blockIdx.y * FR;
+  const int s = A.s2[a];
+  const int lL = A.logN - s, L = 1 << lL;
+  const int D = 1 << (A.lT - s);
+  const int rows = A.n_beta2 * A.R_out;
+  const int r0 = tl.z * kPoolRows;
+  const int tbeg = split * split_len, tend = min(L, tbeg + split_len);
+  const float* v = V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
+  const float* g = A.taps + A.tap_off[s];
+  const int tr = threadIdx.x & 15, tf = threadIdx.x >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  // V2 chunk loader: float4 q of the chunk = row q / 8, samples 4 (q % 8) .. + 3.
+  float4 pre[VPT];
+  auto load = [&](int t0) {
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+      const int q = threadIdx.x + u * NT;
+      const int rr = q >> 3, tq = (q & 7) * 4;
+      const int r = r0 + rr;
+      pre[u] = (r < rows && t0 + tq < tend)
+                   ? *reinterpret_cast<const float4*>(v + static_cast<int64_t>(r) * L + t0 + tq)
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  load(tbeg);
+  for (int t0 = tbeg; t0 < tend; t0 += kPoolK) {
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+      const int q = threadIdx.x + u * NT;
+      const int rr = q >> 3, tq = (q & 7) * 4;
+      Vs[tq][rr] = pre[u].x;
+      Vs[tq + 1][rr] = pre[u].y;
+      Vs[tq + 2][rr] = pre[u].z;
+      Vs[tq + 3][rr] = pre[u].w;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = threadIdx.x + u * NT;
+      const int tt = i % kPoolK, ff = i / kPoolK;
+      const int f = fb + ff;
+      Gs[tt][ff] = (f < A.n_frames && t0 + tt < tend) ? __ldg(g + ((f * D - (t0 + tt)) & (L - 1))) : 0.f;
+    }
+    __syncthreads();
+    if (t0 + kPoolK < tend) load(t0 + kPoolK);
+#pragma unroll 8
+    for (int tt = 0; tt < kPoolK; ++tt) {
+      const float4 vv = *reinterpret_cast<const float4*>(&Vs[tt][4 * tr]);
+      const float4 gg = *reinterpret_cast<const float4*>(&Gs[tt][4 * tf]);
+      const float vr[4] = {vv.x, vv.y, vv.z, vv.w}, gf[4] = {gg.x, gg.y, gg.z, gg.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(vr[i], gf[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  // partial layout: [tile index][64 rows][n_frames]
+  float* out = part + static_cast<int64_t>(blockIdx.x) * kPoolRows * A.n_frames;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rr = 4 * tr + i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int f = fb + 4 * tf + j;
+      if (f < A.n_frames) out[rr * A.n_frames + f] = acc[i][j];
+    }
+  }
+}
+
 // Phi2[b][a][r][f] = sum over splits (ascending) of the partials.
 __global__ void __launch_bounds__(kThreads)
 k_pool_reduce(PoolArgs A, const float* __restrict__ part, float* __restrict__ phi, const int* __restrict__ tile0,
@@ -827,6 +916,77 @@ k_pool_fwd_band(PoolArgs A, const float* __restrict__ V2, float* __restrict__ ph
 
 // Adjoint: a CTA owns 64 rows x 64 time samples; thread (ty = tid / 16,
 // tx = tid % 16) computes rows ty + 16 i (i < 4) and times tx + 16 j (j < 4).
+// Adjoint, dense groups: dV2[rows x L] = dPhi2[rows x nf] G^T on tiles of 64
+// rows x 128 samples; thread (tr = tid % 16, tt = tid / 16) owns rows
+// 4 tr .. 4 tr + 3 and samples 8 tt .. 8 tt + 7 (one float4 of dPhi2 rows and
+// two of taps per frame), written as float4 pairs.
+__global__ void __launch_bounds__(kThreads)
+k_pool_adj2(PoolArgs A, const float* __restrict__ dphi, float* __restrict__ dV2, const int4* __restrict__ tiles) {
+  __shared__ __align__(16) float Ps[32][kPoolRows + 4];
+  __shared__ __align__(16) float Gs[32][128 + 4];
+  const int4 tl = tiles[blockIdx.x];  // (b, a, row tile, 128-sample tile)
+  const int b = tl.x, a = tl.y;
+  const int s = A.s2[a];
+  const int lL = A.logN - s, L = 1 << lL;
+  const int D = 1 << (A.lT - s);
+  const int rows = A.n_beta2 * A.R_out;
+  const int r0 = tl.z * kPoolRows, t0 = tl.w * 128;
+  const float* dp = dphi + static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a];
+  const float* g = A.taps + A.tap_off[s];
+  const int tr = threadIdx.x & 15, tt = threadIdx.x >> 4;
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  for (int f0 = 0; f0 < A.n_frames; f0 += 32) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {  // 64 rows x 32 frames
+      const int i = threadIdx.x + u * kThreads;
+      const int rr = i >> 5, ff = i & 31;
+      const int r = r0 + rr, f = f0 + ff;
+      Ps[ff][rr] = (r < rows && f < A.n_frames) ? dp[static_cast<int64_t>(r) * A.n_frames + f] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {  // 32 frames x 128 samples
+      const int i = threadIdx.x + u * kThreads;
+      const int ff = i >> 7, ts = i & 127;
+      const int f = f0 + ff, t = t0 + ts;
+      Gs[ff][ts] = (f < A.n_frames && t < L) ? __ldg(g + ((f * D - t) & (L - 1))) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int ff = 0; ff < 32; ++ff) {
+      const float4 pv = *reinterpret_cast<const float4*>(&Ps[ff][4 * tr]);
+      const float4 g0 = *reinterpret_cast<const float4*>(&Gs[ff][8 * tt]);
+      const float4 g1 = *reinterpret_cast<const float4*>(&Gs[ff][8 * tt + 4]);
+      const float pr[4] = {pv.x, pv.y, pv.z, pv.w};
+      const float gt[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(pr[i], gt[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float* out = dV2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
+  const int t = t0 + 8 * tt;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + 4 * tr + i;
+    if (r >= rows || t >= L) continue;
+    float* o = out + static_cast<int64_t>(r) * L + t;
+    if (L >= 8) {  // L is a power of two: t + 8 <= L and 16-byte aligned rows
+      reinterpret_cast<float4*>(o)[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      reinterpret_cast<float4*>(o)[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (t + j < L) o[j] = acc[i][j];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_pool_adj(PoolArgs A, const float* __restrict__ dphi, float* __restrict__ dV2, const int4* __restrict__ tiles) {
   __shared__ float Ps[32][kPoolRows + 1];
@@ -1241,7 +1401,15 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
                                                                                             p.d_pool_band_tiles);
         JTFS_TRY(check_launch());
       }
-      if (grid.x) {
+      if (grid.x && p.n_frames >= 32) {
+        // 16-byte register-blocked kernel: 32, 64 or 128 frames per CTA.
+        const int fr = p.n_frames >= 128 ? 128 : p.n_frames >= 64 ? 64 : 32;
+        const dim3 g2(grid.x, static_cast<unsigned>((p.n_frames + fr - 1) / fr));
+        if (fr == 128) k_pool_fwd2<128><<<g2, 512, 0, s>>>(PA, w.V2, w.part, pt, split_len);
+        else if (fr == 64) k_pool_fwd2<64><<<g2, 256, 0, s>>>(PA, w.V2, w.part, pt, split_len);
+        else k_pool_fwd2<32><<<g2, 128, 0, s>>>(PA, w.V2, w.part, pt, split_len);
+        JTFS_TRY(check_launch());
+      } else if (grid.x) {
         switch (fpt) {
           case 16: k_pool_fwd<16><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
           case 8: k_pool_fwd<8><<<grid, kThreads, 0, s>>>(PA, w.V2, w.part, pt, split_len); break;
@@ -1272,7 +1440,10 @@ int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, 
   if (p.n_active > 0) {
     const PoolArgs PA = pool_args(p);
     prof_begin(p, JTFS_STAGE_POOL_ADJ, s);
-    k_pool_adj<<<static_cast<unsigned>(p.pool_tiles.size()), kThreads, 0, s>>>(PA, dphi, w.V2, p.d_pool_tiles);
+    if (!p.pool_tiles2.empty())
+      k_pool_adj2<<<static_cast<unsigned>(p.pool_tiles2.size()), kThreads, 0, s>>>(PA, dphi, w.V2, p.d_pool_tiles2);
+    if (!p.pool_tiles.empty())
+      k_pool_adj<<<static_cast<unsigned>(p.pool_tiles.size()), kThreads, 0, s>>>(PA, dphi, w.V2, p.d_pool_tiles);
     prof_end(p, JTFS_STAGE_POOL_ADJ, s);
     JTFS_TRY(check_launch());
     allow_big_smem<k_freq_adj<2>>();

@@ -363,16 +363,6 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   make_chunks(p.n_beta1, p.chunks1);
   make_chunks(p.n_beta2, p.chunks2);
   // Tiles of the adjoint time pooling: 64 path-rows x 64 time samples.
-  p.pool_tiles.clear();
-  {
-    const int rows = p.n_beta2 * p.R_out;
-    for (int b = 0; b < B; ++b)
-      for (int a = 0; a < p.n_active; ++a) {
-        const int L = static_cast<int>(N >> p.s2[a]);
-        for (int rt = 0; rt < (rows + 63) / 64; ++rt)
-          for (int tt = 0; tt < (L + 63) / 64; ++tt) p.pool_tiles.push_back(make_int4(b, a, rt, tt));
-      }
-  }
   // Banded pooling where the taps' reach is small against the circle: g_s[d] /
   // g_s[0] = exp(-c (2^s d)^2) (c = 2 pi^2 sigma_T^2) is below 2^-40 once
   // 2^s |d| > sqrt(40 ln 2 / c), so a frame only sees W = floor(that / 2^s) + 1
@@ -388,6 +378,23 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
       const int64_t W = static_cast<int64_t>(std::floor(reach / double(int64_t(1) << s))) + 1;
       if (2 * W + 32 * D <= L / 2 && (63 + 2 * W) / D + 2 <= p.n_frames) p.pool_w[a] = static_cast<int>(W);
     }
+  }
+  // Adjoint tiles: 64 rows x 64 samples for the banded groups, 64 rows x 128
+  // samples for the dense ones.
+  p.pool_tiles.clear();
+  p.pool_tiles2.clear();
+  {
+    const int rows = p.n_beta2 * p.R_out;
+    for (int b = 0; b < B; ++b)
+      for (int a = 0; a < p.n_active; ++a) {
+        const int L = static_cast<int>(N >> p.s2[a]);
+        for (int rt = 0; rt < (rows + 63) / 64; ++rt) {
+          if (p.pool_w[a])
+            for (int tt = 0; tt < (L + 63) / 64; ++tt) p.pool_tiles.push_back(make_int4(b, a, rt, tt));
+          else
+            for (int tt = 0; tt < (L + 127) / 128; ++tt) p.pool_tiles2.push_back(make_int4(b, a, rt, tt));
+        }
+      }
   }
   p.pool_band_tiles.clear();
   {
@@ -480,6 +487,7 @@ int upload_plan(Plan& p) {
   const size_t o_ftabc = put(p.h_ftabc.data(), p.h_ftabc.size() * sizeof(float));
   const size_t o_ftabc_off = put(p.h_ftabc_off.data(), p.h_ftabc_off.size() * sizeof(int));
   const size_t o_pt = put(p.pool_tiles.data(), p.pool_tiles.size() * sizeof(int4));
+  const size_t o_pt2 = put(p.pool_tiles2.data(), p.pool_tiles2.size() * sizeof(int4));
   size_t o_pft[3], o_pt0[3];
   for (int si = 0; si < 3; ++si) {
     o_pft[si] = put(p.pool_fwd_tiles[si].data(), p.pool_fwd_tiles[si].size() * sizeof(int4));
@@ -524,6 +532,7 @@ int upload_plan(Plan& p) {
   p.d_ftabc = reinterpret_cast<const float*>(at(o_ftabc));
   p.d_ftabc_off = reinterpret_cast<const int*>(at(o_ftabc_off));
   p.d_pool_tiles = reinterpret_cast<const int4*>(at(o_pt));
+  p.d_pool_tiles2 = reinterpret_cast<const int4*>(at(o_pt2));
   for (int si = 0; si < 3; ++si) {
     p.d_pool_fwd_tiles[si] = reinterpret_cast<const int4*>(at(o_pft[si]));
     p.d_pool_tile0[si] = reinterpret_cast<const int*>(at(o_pt0[si]));
