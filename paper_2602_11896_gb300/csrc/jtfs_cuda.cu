@@ -738,19 +738,23 @@ k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ part, c
   }
 }
 
-// Forward, split over time, register-blocked for 16-byte shared loads: a CTA
-// of 4 FR threads owns a 64-row x FR-frame tile of one (clip, n2) and the time
-// samples [split * split_len, +split_len); thread (tr = tid % 16, tf = tid / 16)
-// accumulates rows 4 tr .. 4 tr + 3 and frames 4 tf .. 4 tf + 3, reading one
-// float4 of V2 rows and one (warp-broadcast) float4 of taps per time sample.
-// The V2 chunk is read into registers one chunk ahead.  Partials as k_pool_fwd.
+// Forward, split over time, register-blocked: a CTA of 4 FR threads owns a
+// 64-row x FR-frame tile of one (clip, n2) and the time samples
+// [split * split_len, +split_len).  Warp w accumulates frames 8 w .. 8 w + 7
+// and lane l rows 2 l, 2 l + 1: per time sample one float2 of V2 rows and two
+// warp-broadcast float4 of taps feed 16 FMAs.  Shared layouts are swizzled so
+// that neither the transposing stores nor the reads conflict:
+//   Vs[t][2 ((r >> 1) ^ sv(t)) + (r & 1)],  sv(t) = 2 ((t >> 2) & 7)
+//   Gs[t][f ^ (8 (t & 3))]
+// The next chunk's V2 and taps are read into registers while the current one
+// is used.  Partial sums as k_pool_fwd (reduced by k_pool_reduce).
 template <int FR>
 __global__ void __launch_bounds__(4 * FR)
 k_pool_fwd2(PoolArgs A, const float* __restrict__ V2, float* __restrict__ part, const int4* __restrict__ tiles,
             int split_len) {
-  constexpr int NT = 4 * FR;                     // threads
+  constexpr int NT = 4 * FR;                          // threads
   constexpr int VPT = (kPoolRows * kPoolK / 4) / NT;  // float4 of V2 per thread per chunk (>= 1)
-  __shared__ __align__(16) float Vs[kPoolK][kPoolRows + 4];
+  __shared__ __align__(16) float Vs[kPoolK][kPoolRows];
   __shared__ __align__(16) float Gs[kPoolK][FR];
   const int4 tl = tiles[blockIdx.x];  // (clip, active n2, row tile, split)
   const int b = tl.x, a = tl.y, split = tl.w;
@@ -763,15 +767,15 @@ k_pool_fwd2(PoolArgs A, const float* __restrict__ V2, float* __restrict__ part, 
   const int tbeg = split * split_len, tend = min(L, tbeg + split_len);
   const float* v = V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
   const float* g = A.taps + A.tap_off[s];
-  const int tr = threadIdx.x & 15, tf = threadIdx.x >> 4;
-  float acc[4][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float acc[2][8];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  // V2 chunk loader: float4 q of the chunk = row q / 8, samples 4 (q % 8) .. + 3.
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  // V2 chunk: float4 q = row q / 8, samples 4 (q % 8) .. + 3 (coalesced rows).
   float4 pre[VPT];
-  auto load = [&](int t0) {
+  auto load_v = [&](int t0) {
 #pragma unroll
     for (int u = 0; u < VPT; ++u) {
       const int q = threadIdx.x + u * NT;
@@ -782,46 +786,66 @@ k_pool_fwd2(PoolArgs A, const float* __restrict__ V2, float* __restrict__ part, 
                    : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
-  load(tbeg);
+  // Taps: element e = tid + u NT, block e / 32 covers samples 4 (blk % 8) .. + 3
+  // and frames 8 (blk / 8) .. + 7; lane: sample + (lane & 3), frame + (lane >> 2).
+  float gpre[8];
+  auto load_g = [&](int t0) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = threadIdx.x + u * NT, blk = e >> 5, ln = e & 31;
+      const int tt = 4 * (blk & 7) + (ln & 3), ff = 8 * (blk >> 3) + (ln >> 2);
+      const int f = fb + ff;
+      gpre[u] = (f < A.n_frames && t0 + tt < tend) ? __ldg(g + ((f * D - (t0 + tt)) & (L - 1))) : 0.f;
+    }
+  };
+  load_v(tbeg);
+  load_g(tbeg);
   for (int t0 = tbeg; t0 < tend; t0 += kPoolK) {
 #pragma unroll
     for (int u = 0; u < VPT; ++u) {
       const int q = threadIdx.x + u * NT;
       const int rr = q >> 3, tq = (q & 7) * 4;
-      Vs[tq][rr] = pre[u].x;
-      Vs[tq + 1][rr] = pre[u].y;
-      Vs[tq + 2][rr] = pre[u].z;
-      Vs[tq + 3][rr] = pre[u].w;
+      const float x[4] = {pre[u].x, pre[u].y, pre[u].z, pre[u].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int t = tq + e;
+        Vs[t][2 * ((rr >> 1) ^ (2 * ((t >> 2) & 7))) + (rr & 1)] = x[e];
+      }
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int i = threadIdx.x + u * NT;
-      const int tt = i % kPoolK, ff = i / kPoolK;
-      const int f = fb + ff;
-      Gs[tt][ff] = (f < A.n_frames && t0 + tt < tend) ? __ldg(g + ((f * D - (t0 + tt)) & (L - 1))) : 0.f;
+      const int e = threadIdx.x + u * NT, blk = e >> 5, ln = e & 31;
+      const int tt = 4 * (blk & 7) + (ln & 3), ff = 8 * (blk >> 3) + (ln >> 2);
+      Gs[tt][ff ^ (8 * (tt & 3))] = gpre[u];
     }
     __syncthreads();
-    if (t0 + kPoolK < tend) load(t0 + kPoolK);
+    if (t0 + kPoolK < tend) {
+      load_v(t0 + kPoolK);
+      load_g(t0 + kPoolK);
+    }
 #pragma unroll 8
     for (int tt = 0; tt < kPoolK; ++tt) {
-      const float4 vv = *reinterpret_cast<const float4*>(&Vs[tt][4 * tr]);
-      const float4 gg = *reinterpret_cast<const float4*>(&Gs[tt][4 * tf]);
-      const float vr[4] = {vv.x, vv.y, vv.z, vv.w}, gf[4] = {gg.x, gg.y, gg.z, gg.w};
+      const float2 vv = *reinterpret_cast<const float2*>(&Vs[tt][2 * (lane ^ (2 * ((tt >> 2) & 7)))]);
+      const int gc = (8 * warp) ^ (8 * (tt & 3));
+      const float4 g0 = *reinterpret_cast<const float4*>(&Gs[tt][gc]);
+      const float4 g1 = *reinterpret_cast<const float4*>(&Gs[tt][gc + 4]);
+      const float gf[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(vr[i], gf[j], acc[i][j]);
+      for (int j = 0; j < 8; ++j) {
+        acc[0][j] = fmaf(vv.x, gf[j], acc[0][j]);
+        acc[1][j] = fmaf(vv.y, gf[j], acc[1][j]);
+      }
     }
     __syncthreads();
   }
   // partial layout: [tile index][64 rows][n_frames]
   float* out = part + static_cast<int64_t>(blockIdx.x) * kPoolRows * A.n_frames;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int rr = 4 * tr + i;
+  for (int i = 0; i < 2; ++i) {
+    const int rr = 2 * lane + i;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int f = fb + 4 * tf + j;
+    for (int j = 0; j < 8; ++j) {
+      const int f = fb + 8 * warp + j;
       if (f < A.n_frames) out[rr * A.n_frames + f] = acc[i][j];
     }
   }
@@ -917,29 +941,42 @@ k_pool_fwd_band(PoolArgs A, const float* __restrict__ V2, float* __restrict__ ph
 // Adjoint: a CTA owns 64 rows x 64 time samples; thread (ty = tid / 16,
 // tx = tid % 16) computes rows ty + 16 i (i < 4) and times tx + 16 j (j < 4).
 // Adjoint, dense groups: dV2[rows x L] = dPhi2[rows x nf] G^T on tiles of 64
-// rows x 128 samples; thread (tr = tid % 16, tt = tid / 16) owns rows
-// 4 tr .. 4 tr + 3 and samples 8 tt .. 8 tt + 7 (one float4 of dPhi2 rows and
-// two of taps per frame), written as float4 pairs.
+// rows x (kPoolAdjSub x 128) samples: the CTA loads its dPhi2 rows once, then
+// walks its 128-sample sub-tiles, gathering the next sub-tile's taps into
+// registers while it computes the current one.  Thread (tr = tid % 16,
+// tt = tid / 16) owns rows 4 tr .. 4 tr + 3 and samples 8 tt .. 8 tt + 7 of a
+// sub-tile (one float4 of dPhi2 rows and two of taps per frame), written as
+// float4 pairs.  Frames are taken 32 at a time.
+constexpr int kPoolAdjSub = 4;
+
 __global__ void __launch_bounds__(kThreads)
 k_pool_adj2(PoolArgs A, const float* __restrict__ dphi, float* __restrict__ dV2, const int4* __restrict__ tiles) {
   __shared__ __align__(16) float Ps[32][kPoolRows + 4];
   __shared__ __align__(16) float Gs[32][128 + 4];
-  const int4 tl = tiles[blockIdx.x];  // (b, a, row tile, 128-sample tile)
+  const int4 tl = tiles[blockIdx.x];  // (b, a, row tile, group of kPoolAdjSub 128-sample tiles)
   const int b = tl.x, a = tl.y;
   const int s = A.s2[a];
   const int lL = A.logN - s, L = 1 << lL;
   const int D = 1 << (A.lT - s);
   const int rows = A.n_beta2 * A.R_out;
-  const int r0 = tl.z * kPoolRows, t0 = tl.w * 128;
+  const int r0 = tl.z * kPoolRows;
   const float* dp = dphi + static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a];
   const float* g = A.taps + A.tap_off[s];
+  float* out = dV2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
   const int tr = threadIdx.x & 15, tt = threadIdx.x >> 4;
-  float acc[4][8];
+  float gpre[16];
+  auto load_g = [&](int f0, int t0) {  // 32 frames x 128 samples: element i = (frame i / 128, sample i % 128)
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int u = 0; u < 16; ++u) {
+      const int i = threadIdx.x + u * kThreads;
+      const int f = f0 + (i >> 7), t = t0 + (i & 127);
+      gpre[u] = (f < A.n_frames && t < L) ? __ldg(g + ((f * D - t) & (L - 1))) : 0.f;
+    }
+  };
+  const int tbase = tl.w * (kPoolAdjSub * 128);
+  const int nsub = min(kPoolAdjSub, (L - tbase + 127) / 128);
   for (int f0 = 0; f0 < A.n_frames; f0 += 32) {
+    __syncthreads();
 #pragma unroll
     for (int u = 0; u < 8; ++u) {  // 64 rows x 32 frames
       const int i = threadIdx.x + u * kThreads;
@@ -947,42 +984,58 @@ k_pool_adj2(PoolArgs A, const float* __restrict__ dphi, float* __restrict__ dV2,
       const int r = r0 + rr, f = f0 + ff;
       Ps[ff][rr] = (r < rows && f < A.n_frames) ? dp[static_cast<int64_t>(r) * A.n_frames + f] : 0.f;
     }
+    load_g(f0, tbase);
+    for (int sub = 0; sub < nsub; ++sub) {
+      const int t0 = tbase + sub * 128;
+      __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {  // 32 frames x 128 samples
-      const int i = threadIdx.x + u * kThreads;
-      const int ff = i >> 7, ts = i & 127;
-      const int f = f0 + ff, t = t0 + ts;
-      Gs[ff][ts] = (f < A.n_frames && t < L) ? __ldg(g + ((f * D - t) & (L - 1))) : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int ff = 0; ff < 32; ++ff) {
-      const float4 pv = *reinterpret_cast<const float4*>(&Ps[ff][4 * tr]);
-      const float4 g0 = *reinterpret_cast<const float4*>(&Gs[ff][8 * tt]);
-      const float4 g1 = *reinterpret_cast<const float4*>(&Gs[ff][8 * tt + 4]);
-      const float pr[4] = {pv.x, pv.y, pv.z, pv.w};
-      const float gt[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+      for (int u = 0; u < 16; ++u) {
+        const int i = threadIdx.x + u * kThreads;
+        Gs[i >> 7][i & 127] = gpre[u];
+      }
+      __syncthreads();
+      if (sub + 1 < nsub) load_g(f0, t0 + 128);
+      float acc[4][8];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(pr[i], gt[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-  float* out = dV2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
-  const int t = t0 + 8 * tt;
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll 8
+      for (int ff = 0; ff < 32; ++ff) {
+        const float4 pv = *reinterpret_cast<const float4*>(&Ps[ff][4 * tr]);
+        const float4 g0 = *reinterpret_cast<const float4*>(&Gs[ff][8 * tt]);
+        const float4 g1 = *reinterpret_cast<const float4*>(&Gs[ff][8 * tt + 4]);
+        const float pr[4] = {pv.x, pv.y, pv.z, pv.w};
+        const float gt[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = r0 + 4 * tr + i;
-    if (r >= rows || t >= L) continue;
-    float* o = out + static_cast<int64_t>(r) * L + t;
-    if (L >= 8) {  // L is a power of two: t + 8 <= L and 16-byte aligned rows
-      reinterpret_cast<float4*>(o)[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-      reinterpret_cast<float4*>(o)[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
-    } else {
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (t + j < L) o[j] = acc[i][j];
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(pr[i], gt[j], acc[i][j]);
+      }
+      // More than 32 frames: accumulate this frame block into dV2 (first block stores).
+      const int t = t0 + 8 * tt;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = r0 + 4 * tr + i;
+        if (r >= rows || t >= L) continue;
+        float* o = out + static_cast<int64_t>(r) * L + t;
+        if (L >= 8) {  // L is a power of two: t + 8 <= L and 16-byte aligned rows
+          float4* o4 = reinterpret_cast<float4*>(o);
+          float4 x0 = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+          float4 x1 = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+          if (f0 > 0) {
+            const float4 y0 = o4[0], y1 = o4[1];
+            x0 = make_float4(y0.x + x0.x, y0.y + x0.y, y0.z + x0.z, y0.w + x0.w);
+            x1 = make_float4(y1.x + x1.x, y1.y + x1.y, y1.z + x1.z, y1.w + x1.w);
+          }
+          o4[0] = x0;
+          o4[1] = x1;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (t + j < L) o[j] = (f0 > 0 ? o[j] : 0.f) + acc[i][j];
+        }
+      }
     }
   }
 }

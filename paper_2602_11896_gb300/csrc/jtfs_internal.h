@@ -157,7 +157,7 @@ struct Plan {
   int freq_cols_wide = kFreqCols;
   std::vector<FreqChunk> chunks1, chunks2;
   std::vector<int4> pool_tiles;   // adjoint time pooling, banded groups: (clip, active n2, row tile, 64-sample tile)
-  std::vector<int4> pool_tiles2;  // adjoint time pooling, dense groups: (clip, active n2, row tile, 128-sample tile)
+  std::vector<int4> pool_tiles2;  // adjoint time pooling, dense groups: (clip, active n2, row tile, 512-sample tile)
   std::vector<int4> pool_fwd_tiles[3];  // forward time pooling per split: (clip, active n2, row tile, split)
   std::vector<int> pool_tile0[3];       // per split and (clip, active n2): first forward tile
   // Banded time pooling: per active n2 the tap half-width W (level samples)

@@ -379,8 +379,8 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
       if (2 * W + 32 * D <= L / 2 && (63 + 2 * W) / D + 2 <= p.n_frames) p.pool_w[a] = static_cast<int>(W);
     }
   }
-  // Adjoint tiles: 64 rows x 64 samples for the banded groups, 64 rows x 128
-  // samples for the dense ones.
+  // Adjoint tiles: 64 rows x 64 samples for the banded groups, 64 rows x 512
+  // samples (four 128-sample sub-tiles) for the dense ones.
   p.pool_tiles.clear();
   p.pool_tiles2.clear();
   {
@@ -392,7 +392,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
           if (p.pool_w[a])
             for (int tt = 0; tt < (L + 63) / 64; ++tt) p.pool_tiles.push_back(make_int4(b, a, rt, tt));
           else
-            for (int tt = 0; tt < (L + 127) / 128; ++tt) p.pool_tiles2.push_back(make_int4(b, a, rt, tt));
+            for (int tt = 0; tt < (L + 511) / 512; ++tt) p.pool_tiles2.push_back(make_int4(b, a, rt, tt));
         }
       }
   }
