@@ -11,4 +11,7 @@ Modules:
   bruteforce   -- the same definition by direct O(n^2) circular convolution
                   with time-domain filters built by explicit DFT sums; for
                   tiny inputs only.  It pins jtfs_oracle.
+  reconstruct  -- the reconstruction variant of §2.3: coloured-noise
+                  initialisation from the target's S1 and momentum descent
+                  with a bold-driver step size.
 """
