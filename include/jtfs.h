@@ -169,6 +169,67 @@ int metamer_step(jtfs_plan_t plan, float* y, const float* phi_target,
                  float* loss_out, void* workspace, void* stream);
 
 /*
+ * Reconstruction variant of §2.3: the paper starts the descent from coloured
+ * Gaussian noise whose power spectral density follows the target's
+ * first-order scattering S1x(t, lambda), and refines it by momentum updates
+ * whose step size follows the "bold driver" heuristic.
+ *
+ * jtfs_coloured_init -- initial signal of that descent.  With Psi_l the
+ * first-layer filtering of band l decimated to its U1 rate (§3.2), P_l the
+ * phi_T pooling that turns U1 into S1 (Eq. (4)) and ^T real adjoints:
+ *   y~ = sum_l c_l Psi_l^T ( A_l . Psi_l w ),   A_l = 2^(lT-k1) P_l^T S1x(., l),
+ *   y0 = y~ ||x|| / ||y~||   per clip (y0 = 0 where y~ = 0),
+ * c_l = 2^(k1+1) / sqrt(mean over the N bins of psi_hat_l^6) (so band l of y~
+ * has E|Psi_l y~|^2 = A_l^2 for a slowly varying envelope; jtfs_init_gains
+ * returns c_l 2^(lT-k1)).  y~ is linear in w, so y0 is Gaussian given the
+ * target, with local power in band l proportional to S1x^2.
+ *   x        [batch][N] float32 (device): the target clips.
+ *   w_noise  [batch][N] float32 (device): white Gaussian noise drawn by the
+ *            caller (the library draws no random numbers).
+ *   y0       [batch][N] float32 (device), written; may not alias x or w_noise.
+ * All three 16-byte aligned.  Uses the workspace like jtfs_forward; errors
+ * as jtfs_forward.
+ */
+int jtfs_coloured_init(jtfs_plan_t plan, const float* x, const float* w_noise,
+                       float* y0, void* workspace, void* stream);
+
+/* Entries of jtfs_init_gains' table (per first-order filter n1, c_l 2^(lT-k1));
+ * returns the count (N1), writes min(count, n) floats to out if out != NULL
+ * (JTFS_ERR_ARG if n < count).  Host-only plans answer too. */
+int64_t jtfs_init_gains(jtfs_plan_t plan, float* out, int64_t n);
+
+/*
+ * metamer_step_momentum -- one evaluation of the momentum descent of §2.3
+ * with the bold-driver step size, on every clip, in place:
+ *   u_n = m u_{n-1} - mu_n grad E(y_n),   y_{n+1} = y_n + u_n.
+ * Per clip, E(y_n) is compared with E_acc, the loss at the last accepted
+ * point.  E <= E_acc accepts y_n: mu grows by 1.1 (not at the first
+ * evaluation), E_acc = E, g_acc = grad E(y_n), and the momentum step is
+ * taken.  Otherwise (E increased, or is NaN) y_n is rejected: mu halves, y
+ * returns to the accepted point (y_n - u_{n-1}), the momentum is dropped and
+ * the step -mu * g_acc is taken from there.  Every decision is made on the
+ * device, so the call can be captured in a CUDA graph.
+ *   y, u, g_acc  [batch][N] float32 (device), updated in place; u and g_acc
+ *                start at zero.
+ *   state        [batch][4] float32 (device, 16-byte aligned), updated in
+ *                place: (mu, E_acc, 1 if the last evaluation was accepted
+ *                else 0, evaluations so far).  Start with (mu0, +inf, 0, 0);
+ *                §2.3 uses mu0 = 0.1.
+ *   m            momentum in [0, 1) (§2.3: 0.9).
+ *   loss_out     [batch] float32 (device): E at the y given on entry.
+ * Errors as jtfs_forward, plus JTFS_ERR_ARG for m outside [0, 1).
+ */
+int metamer_step_momentum(jtfs_plan_t plan, float* y, const float* phi_target,
+                          float* u, float* g_acc, float* state, float m,
+                          float* loss_out, void* workspace, void* stream);
+
+/* The update of metamer_step_momentum alone, from a loss [batch] and
+ * gradient g [batch][n] already computed (n a power of two). */
+int jtfs_momentum_update(float* y, float* u, float* g_acc, const float* g,
+                         float* state, const float* loss, int batch, int64_t n,
+                         float m, void* stream);
+
+/*
  * jtfs_forward_noalloc -- the forward transform of jtfs_forward, for callers
  * that cannot allocate device memory: code that runs where cudaMalloc is not
  * allowed or not available to it (for example a real-time audio callback

@@ -6,7 +6,7 @@ gradient, computed by hand-written sm_103a CUDA kernels behind the C ABI of
 include/jtfs.h.  This package is the thin PyTorch-side binding.
 """
 
-from .jtfs import JTFSPlan, JTFSBatch, jtfs, INFO_KEYS  # noqa: F401
+from .jtfs import JTFSPlan, JTFSBatch, jtfs, momentum_update, INFO_KEYS  # noqa: F401
 from . import _native  # noqa: F401
 
-__all__ = ["JTFSPlan", "JTFSBatch", "jtfs", "INFO_KEYS"]
+__all__ = ["JTFSPlan", "JTFSBatch", "jtfs", "momentum_update", "INFO_KEYS"]

@@ -23,6 +23,12 @@ SIGNATURES = {
     "jtfs_plan_filters": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_double),
                                   POINTER(c_int32), c_int]),
     "jtfs_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "jtfs_coloured_init": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "jtfs_init_gains": (c_int64, [c_void_p, POINTER(c_float), c_int64]),
+    "metamer_step_momentum": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float,
+                                      c_void_p, c_void_p, c_void_p]),
+    "jtfs_momentum_update": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int64,
+                                     c_float, c_void_p]),
     "jtfs_forward_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "jtfs_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "jtfs_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

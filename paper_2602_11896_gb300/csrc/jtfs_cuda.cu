@@ -263,6 +263,18 @@ struct LdDz {
   }
 };
 
+// Band product of the coloured initialisation (§2.3): g = a * z, with the
+// envelope a the real part of a complex row and z the band-passed noise.
+struct LdLin {
+  const float2* a;
+  const float2* z;
+  __device__ float2 operator()(const Job& jb, int idx, int) const {
+    const float s = a[jb.src + idx].x;
+    const float2 v = z[jb.src + idx];
+    return make_float2(s * v.x, s * v.y);
+  }
+};
+
 struct StC {
   float2* d;
   __device__ void operator()(const Job& jb, int idx, float2 v) const { d[jb.dst + idx] = v; }
@@ -1172,7 +1184,7 @@ k_dX(GradArgs A, int64_t total, const float2* __restrict__ dZ1, const float2* __
     acc.x += g * v.x;
     acc.y += g * v.y;
   }
-  if (s >= A.phiT.lo && s <= A.phiT.hi) {
+  if (dS0h && s >= A.phiT.lo && s <= A.phiT.hi) {
     const float g = fval(A.phiT, s);
     const float2 v = dS0h[static_cast<int64_t>(b) * A.n_frames + (m & (A.n_frames - 1))];
     acc.x += g * v.x;
@@ -1218,6 +1230,90 @@ k_adam(float* __restrict__ y, float* __restrict__ m, float* __restrict__ v, cons
   m[i] = mi;
   v[i] = vi;
   y[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction variant of §2.3: coloured initialisation and momentum
+// descent with the bold-driver step size.
+// ---------------------------------------------------------------------------
+
+// rows[r][t] *= gain[r mod n_rows] over `total` = batch * n_rows * row_len entries.
+__global__ void __launch_bounds__(kThreads)
+k_scale_rows(float* __restrict__ rows, const float* __restrict__ gain, int n_rows, int log_len, int64_t total) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  rows[i] *= gain[static_cast<int>((i >> log_len) % n_rows)];
+}
+
+// Per clip b (one CTA): y[b] *= ||x[b]|| / ||y[b]|| (y[b] = 0 when ||y[b]|| = 0);
+// both squared norms summed in double in a fixed order.
+__global__ void __launch_bounds__(512)
+k_energy_match(const float* __restrict__ x, float* __restrict__ y, int64_t n) {
+  __shared__ double red[2][512];
+  const float* xb = x + static_cast<int64_t>(blockIdx.x) * n;
+  float* yb = y + static_cast<int64_t>(blockIdx.x) * n;
+  double sx = 0.0, sy = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double a = xb[i], b = yb[i];
+    sx += a * a;
+    sy += b * b;
+  }
+  red[0][threadIdx.x] = sx;
+  red[1][threadIdx.x] = sy;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  const float scale = red[1][0] > 0.0 ? static_cast<float>(sqrt(red[0][0] / red[1][0])) : 0.f;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) yb[i] *= scale;
+}
+
+// Bold-driver decision per clip: state[b] = (mu, E_acc, accepted, evaluations).
+// Accept when E <= E_acc (E_acc = +inf before the first evaluation; NaN is
+// rejected): mu grows by 1.1 unless it is the first evaluation, E_acc = E.
+// Otherwise mu halves.
+__global__ void k_bold_decide(float4* __restrict__ state, const float* __restrict__ loss, int batch) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  float4 st = state[b];
+  const float E = loss[b];
+  const bool acc = E <= st.y;
+  if (acc) {
+    if (isfinite(st.y)) st.x *= 1.1f;
+    st.y = E;
+  } else {
+    st.x *= 0.5f;
+  }
+  st.z = acc ? 1.f : 0.f;
+  st.w += 1.f;
+  state[b] = st;
+}
+
+// Momentum update after k_bold_decide (one thread per sample, clip = i >> log_n):
+//   accepted: g_acc = g, u = m u - mu g, y += u;
+//   rejected: y -= u (back to the accepted point), u = -mu g_acc, y += u.
+__global__ void __launch_bounds__(kThreads)
+k_momentum(float* __restrict__ y, float* __restrict__ u, float* __restrict__ g_acc, const float* __restrict__ g,
+           const float4* __restrict__ state, int log_n, int64_t total, float m) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const float4 st = state[i >> log_n];
+  float yi = y[i];
+  float ui;
+  if (st.z != 0.f) {
+    const float gi = g[i];
+    g_acc[i] = gi;
+    ui = m * u[i] - st.x * gi;
+  } else {
+    yi -= u[i];
+    ui = -st.x * g_acc[i];
+  }
+  u[i] = ui;
+  y[i] = yi + ui;
 }
 
 // ---------------------------------------------------------------------------
@@ -1543,6 +1639,61 @@ int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, 
   return JTFS_OK;
 }
 
+// Coloured initialisation (§2.3): y0 = ||x|| y~ / ||y~||,
+// y~ = sum_l c_l Psi_l^T (A_l . Psi_l w), A_l = 2^(lT-k1) P_l^T S1x(., l).
+// The chain is the first-layer part of the adjoint with the envelope in place
+// of dU1 and a linear band product in place of the modulus adjoint.
+int coloured_init_stages(const Plan& p, const float* x, const float* w_noise, float* y0, const Bufs& w,
+                         cudaStream_t s) {
+  // S1 of the target: first layer and phi_T pooling (§3.2, Eq. (4)).
+  JTFS_TRY((run_fft<false>(p, p.L_x, LdReal{x}, StC{w.Xh}, w.scr, s)));
+  JTFS_TRY((run_fft<true>(p, p.L_u1, LdBand{w.Xh, p.d_psi1, FiltD{}}, StC{w.U1h}, w.scr, s)));
+  JTFS_TRY((run_fft<false>(p, p.L_u1inplace, LdMod{w.U1h}, StC{w.U1h}, w.scr, s)));
+  JTFS_TRY((run_fft<true>(p, p.L_s1, LdBand{w.U1h, nullptr, p.h_phiT}, StR{w.S1}, w.scr, s)));
+  // Envelopes c_l A_l at the U1 rate: gains, then the adjoint of the pooling.
+  {
+    const int64_t total = int64_t(p.batch) * p.N1 * p.n_frames;
+    k_scale_rows<<<static_cast<unsigned>((total + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        w.S1, p.d_cinit, p.N1, p.log_frames, total);
+    JTFS_TRY(check_launch());
+  }
+  JTFS_TRY((run_fft<false>(p, p.L_ds1, LdReal{w.S1}, StC{w.dS1h}, w.scr, s)));
+  GradArgs GA = grad_args(p);
+  GradArgs GA1 = GA;
+  GA1.n_active = 0;  // no second-order term
+  for (const FftLaunch& l : p.L_u1inplace) {
+    dim3 grid((1u << l.logn) / kThreads + 1, l.njobs);
+    k_dU1<<<grid, kThreads, 0, s>>>(GA1, p.d_jobs + l.job0, nullptr, w.dS1h, w.U1h);
+    JTFS_TRY(check_launch());
+  }
+  JTFS_TRY((run_fft<true>(p, p.L_u1inplace, LdC{w.U1h}, StC{w.U1h}, w.scr, s)));
+  // Band-passed noise Psi_l w, band products, and the filterbank adjoint.
+  JTFS_TRY((run_fft<false>(p, p.L_x, LdReal{w_noise}, StC{w.Xh}, w.scr, s)));
+  JTFS_TRY((run_fft<true>(p, p.L_u1, LdBand{w.Xh, p.d_psi1, FiltD{}}, StC{w.Zs}, w.scr, s)));
+  JTFS_TRY((run_fft<false>(p, p.L_u1inplace, LdLin{w.U1h, w.Zs}, StC{w.Zs}, w.scr, s)));
+  {
+    const int64_t total = int64_t(p.batch) * p.N;
+    k_dX<<<static_cast<unsigned>((total + kThreads - 1) / kThreads), kThreads, 0, s>>>(GA, total, w.Zs, nullptr,
+                                                                                       w.dXh);
+    JTFS_TRY(check_launch());
+  }
+  JTFS_TRY((run_fft<true>(p, p.L_x, LdC{w.dXh}, StR{y0}, w.scr, s)));
+  k_energy_match<<<p.batch, 512, 0, s>>>(x, y0, p.N);
+  return check_launch();
+}
+
+int momentum_update(float* y, float* u, float* g_acc, const float* g, float* state, const float* loss, int batch,
+                    int64_t n, float m, cudaStream_t s) {
+  k_bold_decide<<<(batch + 127) / 128, 128, 0, s>>>(reinterpret_cast<float4*>(state), loss, batch);
+  JTFS_TRY(check_launch());
+  int log_n = 0;
+  while ((int64_t(1) << log_n) < n) ++log_n;
+  const int64_t total = int64_t(batch) * n;
+  k_momentum<<<static_cast<unsigned>((total + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+      y, u, g_acc, g, reinterpret_cast<const float4*>(state), log_n, total, m);
+  return check_launch();
+}
+
 int check_call(const Plan& p, void* ws) {
   if (!p.on_device) return JTFS_ERR_NODEVICE;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return JTFS_ERR_WORKSPACE;
@@ -1663,6 +1814,46 @@ extern "C" int metamer_step(jtfs_plan_t plan, float* y, const float* phi_target,
   jtfs::k_adam<<<static_cast<unsigned>((n + jtfs::kThreads - 1) / jtfs::kThreads), jtfs::kThreads, 0, s>>>(
       y, adam_m, adam_v, w.dy, n, lr, c1, c2);
   return jtfs::check_launch();
+}
+
+extern "C" int jtfs_coloured_init(jtfs_plan_t plan, const float* x, const float* w_noise, float* y0,
+                                  void* workspace, void* stream) {
+  if (!plan || !x || !w_noise || !y0 || jtfs::misaligned(x) || jtfs::misaligned(w_noise) || jtfs::misaligned(y0))
+    return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  JTFS_TRY(jtfs::check_call(p, workspace));
+  return jtfs::coloured_init_stages(p, x, w_noise, y0, jtfs::bufs(p, workspace), static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int jtfs_momentum_update(float* y, float* u, float* g_acc, const float* g, float* state,
+                                    const float* loss, int batch, int64_t n, float m, void* stream) {
+  if (!y || !u || !g_acc || !g || !state || !loss || batch < 1 || n < 1 || (n & (n - 1)) ||
+      (reinterpret_cast<uintptr_t>(state) & 15) || !(m >= 0.f && m < 1.f))
+    return JTFS_ERR_ARG;
+  return jtfs::momentum_update(y, u, g_acc, g, state, loss, batch, n, m, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int metamer_step_momentum(jtfs_plan_t plan, float* y, const float* phi_target, float* u, float* g_acc,
+                                     float* state, float m, float* loss_out, void* workspace, void* stream) {
+  if (!plan || !y || !phi_target || !u || !g_acc || !state || !loss_out || jtfs::misaligned(u) ||
+      jtfs::misaligned(g_acc) || (reinterpret_cast<uintptr_t>(state) & 15) || !(m >= 0.f && m < 1.f))
+    return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  JTFS_TRY(jtfs::check_call(p, workspace));
+  const Bufs w = jtfs::bufs(p, workspace);
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  JTFS_TRY(jtfs_loss_grad(plan, y, phi_target, loss_out, w.dy, workspace, stream));
+  return jtfs::momentum_update(y, u, g_acc, w.dy, state, loss_out, p.batch, p.N, m, s);
+}
+
+extern "C" int64_t jtfs_init_gains(jtfs_plan_t plan, float* out, int64_t n) {
+  if (!plan) return JTFS_ERR_ARG;
+  const auto& g = plan->p.h_cinit;
+  if (out) {
+    if (n < static_cast<int64_t>(g.size())) return JTFS_ERR_ARG;
+    std::copy(g.begin(), g.end(), out);
+  }
+  return static_cast<int64_t>(g.size());
 }
 
 extern "C" int jtfs_profile_stage(jtfs_plan_t plan, int stage, void** events, int count) {

@@ -182,6 +182,10 @@ struct Plan {
   std::vector<FiltD> h_psi1, h_psi2, h_beta;  // psi1/psi2 on grid N; beta on N_fr
   FiltD h_phiT{}, h_phiF{};                   // phi_T on grid N, phi_F on grid N_fr
   std::vector<float> h_taps;
+  // Per n1: gain of band n1 in the coloured initialisation (§2.3),
+  // 2^(lT+1) / sqrt(mean_m psi_hat(m)^6): c = 2^(k1+1) / sqrt(...) times the
+  // 2^(lT-k1) that makes the adjoint of the phi_T pooling an interpolation.
+  std::vector<float> h_cinit;
 
   // Device side.
   bool on_device = false;
@@ -224,6 +228,7 @@ struct Plan {
   const int* d_k1 = nullptr;          // per n1
   const int* d_act_n2 = nullptr;      // per active index: n2
   const int64_t* d_tap_off = nullptr; // per level s
+  const float* d_cinit = nullptr;     // per n1
 
   // Tensor-core frequential path of the second order (jtfs_freq_tc.cu): BF16
   // hi/lo operand tables of the filter matrices (GEMM1 [tc_nr1 rows x 128],

@@ -164,6 +164,26 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   p.h_psi1.clear();
   for (int n1 = 0; n1 < p.N1; ++n1)
     p.h_psi1.push_back(make_filt(p.psi1[n1].xi, p.psi1[n1].sigma, int(N), p.k1[n1], p.psi1[n1].j, false));
+  // Band gains of the coloured initialisation: mean over the N bins of
+  // psi_hat^6, summed where it exceeds exp(-108) of its peak (6 sigma around
+  // xi, and around 0 where the kappa term is not negligible).
+  p.h_cinit.resize(p.N1);
+  for (int n1 = 0; n1 < p.N1; ++n1) {
+    const double xi = p.psi1[n1].xi, sg = p.psi1[n1].sigma;
+    const double kappa = std::exp(-xi * xi / (2.0 * sg * sg));
+    const int64_t half = N / 2;
+    auto bin = [&](double w) { return std::max<int64_t>(-half, std::min<int64_t>(half - 1, int64_t(std::floor(w * N)))); };
+    int64_t lo = bin(xi - 6.0 * sg), hi = bin(xi + 6.0 * sg) + 1;
+    if (kappa > 1e-8) lo = std::min(lo, bin(-6.0 * sg));
+    double s6 = 0.0;
+    for (int64_t m = lo; m <= hi && m < half; ++m) {
+      const double w = double(m) / double(N);
+      const double v = std::exp(-(w - xi) * (w - xi) / (2.0 * sg * sg)) - kappa * std::exp(-w * w / (2.0 * sg * sg));
+      const double v2 = v * v;
+      s6 += v2 * v2 * v2;
+    }
+    p.h_cinit[n1] = static_cast<float>(std::ldexp(1.0, p.lT + 1) / std::sqrt(s6 / double(N)));
+  }
   p.h_psi2.clear();
   for (int n2 = 0; n2 < p.N2; ++n2)
     p.h_psi2.push_back(make_filt(p.psi2[n2].xi, p.psi2[n2].sigma, int(N),
@@ -504,6 +524,7 @@ int upload_plan(Plan& p) {
   const size_t o_k1 = put(p.k1.data(), p.k1.size() * sizeof(int));
   const size_t o_act = put(act_n2.data(), act_n2.size() * sizeof(int));
   const size_t o_tapo = put(p.tap_off.data(), p.tap_off.size() * sizeof(int64_t));
+  const size_t o_cin = put(p.h_cinit.data(), p.h_cinit.size() * sizeof(float));
 
   if (cudaGetDevice(&p.device) != cudaSuccess) return JTFS_ERR_CUDA;
   void* blob = nullptr;
@@ -548,6 +569,7 @@ int upload_plan(Plan& p) {
   p.d_k1 = reinterpret_cast<const int*>(at(o_k1));
   p.d_act_n2 = reinterpret_cast<const int*>(at(o_act));
   p.d_tap_off = reinterpret_cast<const int64_t*>(at(o_tapo));
+  p.d_cinit = reinterpret_cast<const float*>(at(o_cin));
   p.on_device = true;
   return tc_upload(p);
 }

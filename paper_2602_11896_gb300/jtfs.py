@@ -223,6 +223,68 @@ class JTFSPlan:
                       "metamer_step")
         return loss
 
+    # -- reconstruction variant of §2.3 --------------------------------------
+    def init_gains(self) -> np.ndarray:
+        """Per first-order filter, the band gain of the coloured initialisation times 2^(lT-k1)."""
+        n = int(self._lib.jtfs_init_gains(self._h, None, 0))
+        _native.check(0 if n >= 0 else n, "jtfs_init_gains")
+        buf = (c_float * n)()
+        self._lib.jtfs_init_gains(self._h, buf, n)
+        return np.frombuffer(buf, dtype=np.float32).copy()
+
+    def coloured_init(self, x: torch.Tensor, w_noise: torch.Tensor, out: Optional[torch.Tensor] = None,
+                      workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Coloured Gaussian noise following the target's S1 (jtfs_coloured_init), energy of x."""
+        self._check(x, self.N, "x")
+        self._check(w_noise, self.N, "w_noise")
+        y0 = out if out is not None else torch.empty_like(x)
+        ws = workspace if workspace is not None else self.workspace(x.device)
+        _native.check(self._lib.jtfs_coloured_init(self._h, _ptr(x), _ptr(w_noise), _ptr(y0), _ptr(ws), _stream()),
+                      "jtfs_coloured_init")
+        return y0
+
+    def momentum_state(self, mu0: float = 0.1, device=None) -> Dict[str, torch.Tensor]:
+        """Zero momentum, zero stored gradient and per-clip (mu0, +inf, 0, 0) bold-driver state."""
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        st = torch.zeros(self.batch, 4, device=dev)
+        st[:, 0] = float(mu0)
+        st[:, 1] = float("inf")
+        return {"u": torch.zeros(self.batch, self.N, device=dev), "g_acc": torch.zeros(self.batch, self.N, device=dev),
+                "state": st}
+
+    def metamer_step_momentum(self, y: torch.Tensor, phi_target: torch.Tensor, opt: Dict[str, torch.Tensor],
+                              m: float = 0.9, loss_out: Optional[torch.Tensor] = None,
+                              workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """One momentum / bold-driver evaluation (metamer_step_momentum); ``opt`` from ``momentum_state``."""
+        self._check(y, self.N, "y")
+        self._check(opt["u"], self.N, "u")
+        self._check(opt["g_acc"], self.N, "g_acc")
+        self._check(opt["state"], 4, "state")
+        self._check(phi_target, self.phi_size, "phi_target")
+        loss = loss_out if loss_out is not None else torch.empty(self.batch, device=y.device)
+        ws = workspace if workspace is not None else self.workspace(y.device)
+        _native.check(self._lib.metamer_step_momentum(self._h, _ptr(y), _ptr(phi_target), _ptr(opt["u"]),
+                                                      _ptr(opt["g_acc"]), _ptr(opt["state"]), float(m), _ptr(loss),
+                                                      _ptr(ws), _stream()), "metamer_step_momentum")
+        return loss
+
+
+def momentum_update(y: torch.Tensor, opt: Dict[str, torch.Tensor], grad: torch.Tensor, loss: torch.Tensor,
+                    m: float = 0.9) -> None:
+    """The update of metamer_step_momentum alone (jtfs_momentum_update), from a given loss and gradient."""
+    B, n = y.shape
+    for t, name in ((y, "y"), (opt["u"], "u"), (opt["g_acc"], "g_acc"), (grad, "grad")):
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != (B, n):
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor of shape {(B, n)}")
+    st = opt["state"]
+    if not st.is_cuda or st.dtype != torch.float32 or tuple(st.shape) != (B, 4) or not st.is_contiguous():
+        raise TypeError("state must be a contiguous float32 CUDA tensor of shape (batch, 4)")
+    if not loss.is_cuda or loss.dtype != torch.float32 or loss.numel() != B:
+        raise TypeError("loss must be a float32 CUDA tensor of batch elements")
+    lib = _native.load()
+    _native.check(lib.jtfs_momentum_update(_ptr(y), _ptr(opt["u"]), _ptr(opt["g_acc"]), _ptr(grad), _ptr(st),
+                                           _ptr(loss), B, n, float(m), _stream()), "jtfs_momentum_update")
+
 
 class JTFSBatch:
     """Clips of uneven lengths solved together (jtfs_batch_* in include/jtfs.h).
