@@ -65,11 +65,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip autotuning at set-up")
     ap.add_argument("--workload", default="chirps",
-                    choices=["chirps", "uneven64", "initialiser", "decoder", "long"],
+                    choices=["chirps", "uneven64", "initialiser", "decoder", "long", "reconstruct"],
                     help="chirps: the 8 x 2^16 benchmark (default); uneven64: 64 clips of 2^14..2^18 samples; "
                          "initialiser: 32 tone clips of 2^16 samples from the learned decoder vs white noise; "
                          "decoder: the learned initialiser's training step on the tensor cores; "
-                         "long: 4 clips of 2^20 samples, forward + loss + gradient")
+                         "long: 4 clips of 2^20 samples, forward + loss + gradient; "
+                         "reconstruct: the paper's coloured-noise start and bold-driver momentum against "
+                         "white-noise Adam on the chirp batch, 200 evaluations each")
     ap.add_argument("--batch", type=int, default=0,
                     help="clips per GPU (default: the workload's 8); smaller values only for ncu captures")
     return ap.parse_args()
@@ -352,6 +354,47 @@ def run_initialiser(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reconstruct(args):
+    """The chirp batch (8 x 2^16): the paper's reconstruction of §2.3 (coloured noise following S1x, momentum
+    0.9 with bold-driver step size from 0.1) against white-noise Adam (lr 0.1), and the two crossed arms,
+    200 gradient evaluations each; wall time for each arm to reach the white-noise Adam run's final loss."""
+    from paper_2602_11896_gb300 import JTFSPlan
+    from paper_2602_11896_gb300.reconstruct import compare_reconstruction
+    wl = get_workload(WORKLOAD)
+    plan = JTFSPlan(**wl.params, batch=wl.batch)
+    if not args.no_tune:
+        plan.autotune(torch.tensor(wl.inits(), device="cuda"), plan.forward(torch.tensor(wl.targets(), device="cuda")))
+    x = torch.tensor(wl.targets(), device="cuda")
+    phi_t = plan.forward(x)
+    noise = torch.tensor(wl.inits(), device="cuda")
+    for _ in range(max(args.warmup, 1)):   # warm-up: a short run of every arm
+        compare_reconstruction(plan, x, phi_t, noise, steps=3)
+    steps = 200
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev = compare_reconstruction(plan, x, phi_t, noise, steps=steps)
+    clk = clocks.stop()
+    marks = [0, 9, 24, 49, 99, 149, 199]
+    arms = {k: {"initial_loss": a["initial_loss"], "final_loss": a["final_loss"], "ms": a["ms"],
+                "init_ms": a["init_ms"], "steps_to_target": a["steps_to_target"], "ms_to_target": a["ms_to_target"],
+                "curve_at": {str(i + 1): a["curve"][i] for i in marks},
+                **{k2: a[k2] for k2 in ("rejected", "final_mu") if k2 in a}}
+            for k, a in ev["arms"].items()}
+    paper = ev["arms"]["coloured_momentum"]
+    line = {"metric": "wall time of the paper's reconstruction (coloured init + bold-driver momentum) to the "
+                      "white-noise Adam run's 200-step loss", "unit": "ms",
+            "value": paper["ms_to_target"], "n_gpus": 1, "steps": steps, "warmup": max(args.warmup, 1),
+            "ms_per_step": paper["ms_per_step"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "batch": wl.batch, **wl.params, "sample_rate_hz": wl.sr,
+                       "adam": {"lr": ev["lr"]}, "momentum": {"m": ev["m"], "mu0": ev["mu0"],
+                                                              "bold_driver": [1.1, 0.5]},
+                       "curves": "per-clip running minimum of the loss, summed over the batch",
+                       "l2": "each arm's evaluations timed as one region; inputs and workspace exceed L2"},
+            "target_loss": ev["target_loss"], "arms": arms, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def run_long(args):
     """4 clips of 2^20 samples (polyphonic notes + pink noise at 22.05 kHz; J=14, Q=16, Q2=2, J_fr=6,
     Q_fr=2, T=2^13, F=16): one step = forward, loss against the targets' Phi and the hand-written adjoint
@@ -484,6 +527,12 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the chirps workload"}))
             return
         run_initialiser(args)
+        return
+    if args.workload == "reconstruct":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the chirps workload"}))
+            return
+        run_reconstruct(args)
         return
     if args.workload == "uneven64":
         if args.impl == "reference":

@@ -9,7 +9,7 @@ first-order scattering S1x(t, lambda), and refines it by additive momentum
 updates whose step size follows the "bold driver" heuristic.  The paper gives
 neither construction in formulas; the readings taken here are
 
-  R16 Coloured initialisation.  With the first-layer operators of §3.2,
+  R18 Coloured initialisation.  With the first-layer operators of §3.2,
       Psi_l w = decimate_{k1}(w * psi_l)  (complex, at the U1 rate of band l)
       and the phi_T pooling P_l u = decimate_{lT-k1}(u * phi_T) that turns U1
       into S1 (Eq. (4)), the initial signal is
@@ -26,7 +26,7 @@ neither construction in formulas; the readings taken here are
       w, so y0 is Gaussian given the target; its local power in band l is
       proportional to A_l^2 = S1x^2.  The final scale matches the target's
       energy.
-  R17 Momentum with bold driver (reading of the recursion printed in §2.3,
+  R19 Momentum with bold driver (reading of the recursion printed in §2.3,
       whose u_n appears on both sides and whose sign is ambiguous):
         u_n = m u_{n-1} - mu_n grad E(y_n),  y_{n+1} = y_n + u_n,  m = 0.9,
       mu_0 = 0.1.  At each evaluation, per clip: if E(y_n) <= E_acc (the loss
@@ -48,8 +48,8 @@ import torch
 
 from .jtfs_oracle import C128, F64, Plan, conv_circ, decimate, gauss_hat, morlet_hat, periodise
 
-GROW = 1.1     # bold driver: step-size factor after a decrease (R17)
-SHRINK = 0.5   # bold driver: step-size factor after an increase (R17)
+GROW = 1.1     # bold driver: step-size factor after a decrease (R19)
+SHRINK = 0.5   # bold driver: step-size factor after an increase (R19)
 
 
 # ---------------------------------------------------------------------------
@@ -94,14 +94,14 @@ def pool_T_adjoint(s: torch.Tensor, plan: Plan, n1: int) -> torch.Tensor:
 
 
 def band_gain(plan: Plan, n1: int) -> float:
-    """c_l = 2^(k1+1) / sqrt(mean_m psi_hat_l(m)^6) (R16)."""
+    """c_l = 2^(k1+1) / sqrt(mean_m psi_hat_l(m)^6) (R18)."""
     f = plan.psi1[n1]
     p = morlet_hat(plan.N, f.xi, f.sigma)
     return 2.0 ** (plan.k1[n1] + 1) / math.sqrt(float((p ** 6).mean()))
 
 
 # ---------------------------------------------------------------------------
-# Coloured initialisation (§2.3, R16)
+# Coloured initialisation (§2.3, R18)
 # ---------------------------------------------------------------------------
 
 def first_order(x: torch.Tensor, plan: Plan) -> torch.Tensor:
@@ -111,12 +111,12 @@ def first_order(x: torch.Tensor, plan: Plan) -> torch.Tensor:
 
 
 def envelope(S1: torch.Tensor, plan: Plan, n1: int) -> torch.Tensor:
-    """A_l = 2^(lT-k1) P_l^T S1(., l): the S1 row interpolated to the U1 rate (R16)."""
+    """A_l = 2^(lT-k1) P_l^T S1(., l): the S1 row interpolated to the U1 rate (R18)."""
     return 2.0 ** (plan.lT - plan.k1[n1]) * pool_T_adjoint(S1[:, n1], plan, n1)
 
 
 def coloured_init(x: torch.Tensor, w: torch.Tensor, plan: Plan, raw: bool = False) -> torch.Tensor:
-    """Initial signal y0 [B, N] of the reconstruction (R16) from target x and white noise w.
+    """Initial signal y0 [B, N] of the reconstruction (R18) from target x and white noise w.
 
     With ``raw`` the unscaled y~ is returned (linear in w).
     """
@@ -135,7 +135,7 @@ def coloured_init(x: torch.Tensor, w: torch.Tensor, plan: Plan, raw: bool = Fals
 
 
 # ---------------------------------------------------------------------------
-# Momentum descent with the bold-driver step size (§2.3, R17)
+# Momentum descent with the bold-driver step size (§2.3, R19)
 # ---------------------------------------------------------------------------
 
 def bold_driver_step(y: np.ndarray, u: np.ndarray, g_acc: np.ndarray, mu: np.ndarray, E_acc: np.ndarray,

@@ -158,3 +158,18 @@ def test_momentum_graph_replay_equals_eager():
     yg, lg, sg = run(True)
     assert se[0, 3].item() == sg[0, 3].item() == 4.0
     assert torch.equal(ye, yg) and torch.equal(le, lg) and torch.equal(se, sg)
+
+
+def test_compare_reconstruction_runs_every_arm():
+    """The comparison helper on the tone clip: four arms, finite non-increasing curves, the target reached by Adam."""
+    from paper_2602_11896_gb300.reconstruct import compare_reconstruction
+    wl = get_workload("tones8k_n8192")
+    plan = _plan(wl.params, 1)
+    x = torch.tensor(wl.targets(), device="cuda")
+    ev = compare_reconstruction(plan, x, plan.forward(x), torch.tensor(wl.inits(), device="cuda"), steps=12)
+    assert set(ev["arms"]) == {"white_adam", "coloured_momentum", "coloured_adam", "white_momentum"}
+    for arm in ev["arms"].values():
+        c = np.array(arm["curve"])
+        assert c.shape == (12,) and np.isfinite(c).all() and (np.diff(c) <= 0).all()
+    assert ev["arms"]["white_adam"]["steps_to_target"] == 12
+    assert ev["arms"]["coloured_adam"]["initial_loss"] < ev["arms"]["white_adam"]["initial_loss"]
