@@ -171,5 +171,5 @@ def test_compare_reconstruction_runs_every_arm():
     for arm in ev["arms"].values():
         c = np.array(arm["curve"])
         assert c.shape == (12,) and np.isfinite(c).all() and (np.diff(c) <= 0).all()
-    assert ev["arms"]["white_adam"]["steps_to_target"] == 12
+    assert 1 <= ev["arms"]["white_adam"]["steps_to_target"] <= 12
     assert ev["arms"]["coloured_adam"]["initial_loss"] < ev["arms"]["white_adam"]["initial_loss"]
