@@ -61,6 +61,16 @@ reason in the repository's design notes):
   R15 Clips whose length L is not a power of two: zero-padded on the right
       to the next power of two, Phi computed there, and only the first
       ceil(L/T) frames of each row kept (the crop's adjoint fills zeros).
+  R20 Reflect boundary (the padding "on both sides" of §3.2 as an option):
+      P = ceil(sqrt(ln(1000) / 2) / (pi sigma_min)) samples per side, the
+      half-width beyond which the slowest time envelope exp(-2 pi^2 sigma^2
+      t^2) among psi1, psi2 and phi_T is below 1e-3 of its peak; padded
+      length n = next power of two >= L + 2P; left pad p0 = T floor((n - L) /
+      (2T)) (frames stay on the stride-T grid), the rest on the right; the
+      padding mirrors the clip without repeating its edge samples (x[-t] =
+      x[t], x[L-1+t] = x[L-1-t], repeated with period 2(L-1)); Phi is
+      computed on the padded clip and the ceil(L/T) frames starting at
+      frame p0 / T are kept.
 """
 
 from __future__ import annotations
@@ -414,5 +424,55 @@ def loss_and_grad_uneven(y: torch.Tensor, phi_target: torch.Tensor,
     y = y.detach().to(F64).clone().requires_grad_(True)
     with torch.enable_grad():
         E = ((jtfs_uneven(y, params) - phi_target.to(F64)) ** 2).sum()
+        (g,) = torch.autograd.grad(E, y)
+    return E.detach(), g.detach()
+
+
+# ---------------------------------------------------------------------------
+# Reflect boundary (reading R20): pad on both sides by reflection, compute
+# Phi on the padded clip, keep the frames over the clip (§3.2's padding and
+# unpadding).
+# ---------------------------------------------------------------------------
+
+def reflect_pad_width(params: Dict[str, int]) -> int:
+    """P of R20 from the filterbanks the parameters define (they do not depend on N)."""
+    plan = Plan(**{**params, "N": max(params["T"], 2 ** (params["J"] + 1))})
+    sig = min([f.sigma for f in plan.psi1] + [f.sigma for f in plan.psi2] + [plan.sigma_phiT])
+    return int(math.ceil(math.sqrt(math.log(1000.0) / 2.0) / (math.pi * sig)))
+
+
+def reflect_layout(L: int, params: Dict[str, int]) -> Tuple[int, int, int, int]:
+    """(n, p0, first kept frame, kept frames) of a clip of L samples (R20)."""
+    T = params["T"]
+    n = _next_pow2(L + 2 * reflect_pad_width(params))
+    p0 = T * ((n - L) // (2 * T))
+    return n, p0, p0 // T, -(-L // T)
+
+
+def reflect_index(u: torch.Tensor, L: int) -> torch.Tensor:
+    """Index into a clip of L samples of position u relative to its first sample, mirrored (R20)."""
+    if L == 1:
+        return torch.zeros_like(u)
+    per = 2 * (L - 1)
+    r = torch.remainder(u, per)
+    return torch.where(r < L, r, per - r)
+
+
+def jtfs_reflect(y: torch.Tensor, params: Dict[str, int]) -> torch.Tensor:
+    """Phi of one clip y [L] with the reflect boundary: rows x ceil(L/T) frames, flattened."""
+    L = y.shape[-1]
+    n, p0, f0, nf = reflect_layout(L, params)
+    plan = Plan(**{**params, "N": n})
+    yp = y.reshape(L).to(F64)[reflect_index(torch.arange(n) - p0, L)][None]
+    phi = jtfs(yp, plan)["phi"].reshape(-1, plan.n_frames)
+    return phi[:, f0:f0 + nf].reshape(-1)
+
+
+def loss_and_grad_reflect(y: torch.Tensor, phi_target: torch.Tensor,
+                          params: Dict[str, int]) -> Tuple[torch.Tensor, torch.Tensor]:
+    """E = ||Phi_reflect(y) - target||^2 and dE/dy for one clip."""
+    y = y.detach().to(F64).clone().requires_grad_(True)
+    with torch.enable_grad():
+        E = ((jtfs_reflect(y, params) - phi_target.to(F64)) ** 2).sum()
         (g,) = torch.autograd.grad(E, y)
     return E.detach(), g.detach()
