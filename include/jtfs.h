@@ -276,8 +276,20 @@ int jtfs_forward_noalloc(jtfs_plan_t plan, const float* x, float* phi,
  */
 typedef struct jtfs_batch_s* jtfs_batch_t;
 
-/* Create a ragged batch of `count` clips (1 <= count, 1 <= lengths[b] <= 2^20);
- * other parameters as jtfs_plan.  Errors as jtfs_plan. */
+/*
+ * Create a ragged batch of `count` clips (1 <= count, 1 <= lengths[b] <= 2^20);
+ * other parameters as jtfs_plan.  flags: JTFS_PLAN_HOST_ONLY, and
+ * JTFS_BATCH_REFLECT for the padding "on both sides" of §3.2 in place of
+ * zeros on the right: each clip is mirrored (edge samples not repeated) over
+ * P samples on each side, P = ceil(sqrt(ln(1000)/2) / (pi sigma_min)) with
+ * sigma_min the narrowest Fourier width among the first- and second-order
+ * filters and phi_T (where the slowest time envelope falls below 1e-3),
+ * padded to n = next power of two >= L + 2P with p0 = T floor((n-L)/(2T))
+ * samples on the left; Phi keeps the ceil(L/T) frames from frame p0/T on, and
+ * the gradient sums every mirrored copy back onto its sample.  Padded lengths
+ * must stay <= 2^20 (JTFS_ERR_SHAPE otherwise).  Errors as jtfs_plan.
+ */
+#define JTFS_BATCH_REFLECT 2u
 int jtfs_batch_create(jtfs_batch_t* out, const int64_t* lengths, int count, int J,
                       int Q, int Q2, int J_fr, int Q_fr, int64_t T, int F,
                       uint32_t flags);

@@ -78,6 +78,7 @@ SIGNATURES = {
 }
 
 PLAN_HOST_ONLY = 1
+BATCH_REFLECT = 2
 
 _lib = None
 

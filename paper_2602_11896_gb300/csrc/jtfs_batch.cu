@@ -3,6 +3,12 @@
 // next power of two >= max(L, T) (§3.2's padding, periodic boundary), its Phi
 // computed there and cropped to the first ceil(L/T) frames of every row; the
 // loss runs over the kept frames only, so the crop's adjoint fills zeros.
+// With JTFS_BATCH_REFLECT the padding is on both sides instead (§3.2's
+// padding and unpadding): P samples per side, P where the slowest time
+// envelope exp(-2 pi^2 sigma^2 t^2) of psi1, psi2 and phi_T drops below 1e-3,
+// padded length n = next power of two >= L + 2P, left pad p0 = T floor((n -
+// L) / 2T), mirror extension without repeating the edge samples; the kept
+// frames start at p0 / T and the gradient folds the mirrored samples back.
 // Packed layouts are described in include/jtfs.h.
 #include <cuda_runtime.h>
 
@@ -30,6 +36,11 @@ struct ClipD {
   int64_t dphi;   // its gradient
   int64_t dy;     // gradient w.r.t. the padded row
   int L, N, nf, nf_full, rows, pad;
+  int f0;         // first kept frame
+  int p0;         // left pad (samples)
+  int refl;       // 1: mirror padding on both sides, 0: zeros on the right
+  int pad2;
+  int64_t g;      // gradient w.r.t. the clip's samples (offset in floats)
 };
 
 struct Group {
@@ -40,12 +51,40 @@ struct Group {
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
-// Padded rows from packed samples (zeros beyond L).
+// Index into a clip of L samples of position u relative to its first sample,
+// mirrored without repeating the edge samples (period 2(L-1)).
+__device__ __forceinline__ int mirror(int u, int L) {
+  if (L == 1) return 0;
+  const int per = 2 * (L - 1);
+  int r = u % per;
+  if (r < 0) r += per;
+  return r < L ? r : per - r;
+}
+
+// Padded rows from packed samples: zeros beyond L, or the mirror extension.
 __global__ void __launch_bounds__(kThreadsB) k_gather(const ClipD* __restrict__ clips, const float* __restrict__ y,
                                                      float* __restrict__ ws) {
   const ClipD c = clips[blockIdx.y];
   for (int t = blockIdx.x * kThreadsB + threadIdx.x; t < c.N; t += gridDim.x * kThreadsB)
-    ws[c.ypad + t] = t < c.L ? y[c.so + t] : 0.f;
+    ws[c.ypad + t] = c.refl ? y[c.so + mirror(t - c.p0, c.L)] : (t < c.L ? y[c.so + t] : 0.f);
+}
+
+// Adjoint of the mirror extension: sample t of a reflect clip collects every
+// padded position that copies it (positions p0 + t + k per, and p0 - t + k per
+// for 0 < t < L-1), summed in ascending order; written over the padded row,
+// which the backward pass no longer reads.
+__global__ void __launch_bounds__(kThreadsB) k_fold(const ClipD* __restrict__ clips, float* ws) {
+  const ClipD c = clips[blockIdx.y];
+  if (!c.refl) return;
+  const float* d = ws + c.dy;
+  const int per = c.L == 1 ? 1 : 2 * (c.L - 1);
+  for (int t = blockIdx.x * kThreadsB + threadIdx.x; t < c.L; t += gridDim.x * kThreadsB) {
+    float acc = 0.f;
+    for (int s = ((c.p0 + t) % per + per) % per; s < c.N; s += per) acc += d[s];
+    if (t > 0 && t < c.L - 1)
+      for (int s = ((c.p0 - t) % per + per) % per; s < c.N; s += per) acc += d[s];
+    ws[c.g + t] = acc;
+  }
 }
 
 // Loss over the kept frames, dPhi = 2 (Phi - target) there and 0 on cropped
@@ -59,8 +98,8 @@ __global__ void __launch_bounds__(512) k_masked_loss(const ClipD* __restrict__ c
   for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
     const int r = static_cast<int>(i / c.nf_full), f = static_cast<int>(i % c.nf_full);
     float d = 0.f;
-    if (f < c.nf) {
-      d = ws[c.phi + i] - tgt[c.po + static_cast<int64_t>(r) * c.nf + f];
+    if (f >= c.f0 && f < c.f0 + c.nf) {
+      d = ws[c.phi + i] - tgt[c.po + static_cast<int64_t>(r) * c.nf + (f - c.f0)];
       acc += static_cast<double>(d) * d;
     }
     ws[c.dphi + i] = 2.f * d;
@@ -81,7 +120,7 @@ __global__ void __launch_bounds__(kThreadsB) k_crop(const ClipD* __restrict__ cl
   const int64_t total = static_cast<int64_t>(c.rows) * c.nf;
   for (int64_t i = blockIdx.x * kThreadsB + threadIdx.x; i < total; i += static_cast<int64_t>(gridDim.x) * kThreadsB) {
     const int64_t r = i / c.nf, f = i % c.nf;
-    phi[c.po + i] = ws[c.phi + r * c.nf_full + f];
+    phi[c.po + i] = ws[c.phi + r * c.nf_full + c.f0 + f];
   }
 }
 
@@ -97,7 +136,7 @@ __global__ void __launch_bounds__(kThreadsB) k_adam_packed(const ClipD* __restri
   const float c2 = 1.f / (1.f - powf(0.999f, static_cast<float>(t_step)));
   for (int t = blockIdx.x * kThreadsB + threadIdx.x; t < c.L; t += gridDim.x * kThreadsB) {
     const int64_t i = c.so + t;
-    const float g = ws[c.dy + t];
+    const float g = ws[c.g + t];
     const float mi = 0.9f * m[i] + 0.1f * g;
     const float vi = 0.999f * v[i] + 0.001f * g * g;
     m[i] = mi;
@@ -137,19 +176,38 @@ extern "C" int jtfs_batch_create(jtfs_batch_t* out, const int64_t* lengths, int 
   if (!out || !lengths || count < 1) return JTFS_ERR_ARG;
   *out = nullptr;
   if (T < 2 || (T & (T - 1))) return JTFS_ERR_SHAPE;
+  const bool refl = (flags & JTFS_BATCH_REFLECT) != 0;
+  flags &= ~JTFS_BATCH_REFLECT;
   jtfs_batch_s* b = new (std::nothrow) jtfs_batch_s();
   if (!b) return JTFS_ERR_NOMEM;
   int rc = JTFS_OK;
   try {
+    // Mirror pad width from the filterbanks (independent of the length).
+    int64_t P = 0;
+    if (refl) {
+      jtfs::Plan probe;
+      const int64_t n_probe = std::max<int64_t>({T, int64_t(1) << std::min(J + 1, 20), 16});
+      rc = jtfs::build_plan(probe, n_probe, J, Q, Q2, J_fr, Q_fr, T, F, 1, JTFS_PLAN_HOST_ONLY);
+      if (rc == JTFS_OK) {
+        double sig = probe.phiT.sigma;
+        for (const auto& f : probe.psi1) sig = std::min(sig, f.sigma);
+        for (const auto& f : probe.psi2) sig = std::min(sig, f.sigma);
+        P = static_cast<int64_t>(std::ceil(std::sqrt(std::log(1000.0) / 2.0) / (M_PI * sig)));
+      }
+    }
     std::map<int64_t, std::vector<int>> by_n;
-    for (int i = 0; i < count; ++i) {
+    for (int i = 0; i < count && rc == JTFS_OK; ++i) {
       const int64_t L = lengths[i];
       if (L < 1 || L > (int64_t(1) << 20)) {
         rc = JTFS_ERR_SHAPE;
         break;
       }
       int64_t n = 1;
-      while (n < std::max<int64_t>(L, T)) n <<= 1;
+      while (n < std::max<int64_t>(refl ? L + 2 * P : L, T)) n <<= 1;
+      if (n > (int64_t(1) << 20)) {
+        rc = JTFS_ERR_SHAPE;
+        break;
+      }
       by_n[n].push_back(i);
       b->lengths.push_back(L);
     }
@@ -166,15 +224,15 @@ extern "C" int jtfs_batch_create(jtfs_batch_t* out, const int64_t* lengths, int 
           rc = jtfs::upload_plan(g.plan);
           if (rc != JTFS_OK) break;
         }
-        const size_t B = g.clips.size(), N = static_cast<size_t>(kv.first), P = static_cast<size_t>(g.plan.phi_size);
+        const size_t B = g.clips.size(), N = static_cast<size_t>(kv.first), Pz = static_cast<size_t>(g.plan.phi_size);
         g.ws_off = off;
         off = jtfs::align256(off + g.plan.ws_bytes);
         g.ypad_off = off;
         off = jtfs::align256(off + B * N * sizeof(float));
         g.phi_off = off;
-        off = jtfs::align256(off + B * P * sizeof(float));
+        off = jtfs::align256(off + B * Pz * sizeof(float));
         g.dphi_off = off;
-        off = jtfs::align256(off + B * P * sizeof(float));
+        off = jtfs::align256(off + B * Pz * sizeof(float));
         g.dy_off = off;
         off = jtfs::align256(off + B * N * sizeof(float));
         for (size_t k = 0; k < B; ++k) {
@@ -183,11 +241,15 @@ extern "C" int jtfs_batch_create(jtfs_batch_t* out, const int64_t* lengths, int 
           c.N = static_cast<int>(N);
           c.nf_full = g.plan.n_frames;
           c.nf = static_cast<int>((c.L + T - 1) / T);
-          c.rows = static_cast<int>(P / g.plan.n_frames);
+          c.rows = static_cast<int>(Pz / g.plan.n_frames);
+          c.refl = refl ? 1 : 0;
+          c.p0 = refl ? static_cast<int>(T * ((static_cast<int64_t>(N) - c.L) / (2 * T))) : 0;
+          c.f0 = static_cast<int>(c.p0 / T);
           c.ypad = static_cast<int64_t>(g.ypad_off / sizeof(float) + k * N);
-          c.phi = static_cast<int64_t>(g.phi_off / sizeof(float) + k * P);
-          c.dphi = static_cast<int64_t>(g.dphi_off / sizeof(float) + k * P);
+          c.phi = static_cast<int64_t>(g.phi_off / sizeof(float) + k * Pz);
+          c.dphi = static_cast<int64_t>(g.dphi_off / sizeof(float) + k * Pz);
           c.dy = static_cast<int64_t>(g.dy_off / sizeof(float) + k * N);
+          c.g = refl ? c.ypad : c.dy;
         }
         b->max_blocks_x = std::max<int>(b->max_blocks_x, static_cast<int>((N + 255) / 256));
       }
@@ -294,6 +356,9 @@ extern "C" int jtfs_batch_metamer_step(jtfs_batch_t batch, float* y, const float
                             reinterpret_cast<float*>(base + g.dy_off), base + g.ws_off, s);
     if (rc != JTFS_OK) return rc;
   }
+  jtfs::k_fold<<<dim3(std::min(batch->max_blocks_x, 1024), count), jtfs::kThreadsB, 0, s>>>(
+      batch->d_clips, reinterpret_cast<float*>(base));
+  if (launched() != JTFS_OK) return JTFS_ERR_CUDA;
   jtfs::k_adam_packed<<<dim3(std::min(batch->max_blocks_x, 1024), count), jtfs::kThreadsB, 0, s>>>(
       batch->d_clips, reinterpret_cast<const float*>(base), y, adam_m, adam_v, step, lr);
   if (launched() != JTFS_OK) return JTFS_ERR_CUDA;

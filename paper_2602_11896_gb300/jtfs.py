@@ -290,20 +290,26 @@ class JTFSBatch:
     """Clips of uneven lengths solved together (jtfs_batch_* in include/jtfs.h).
 
     Each clip is zero-padded to the next power of two >= max(L, T) and its Phi
-    cropped to ceil(L/T) frames per row.  Samples and Phi are packed:
-    ``sample_offsets`` / ``phi_offsets`` give each clip's slice.
+    cropped to ceil(L/T) frames per row; with ``boundary="reflect"`` it is
+    mirrored on both sides instead and the frames over the clip are kept (see
+    jtfs_batch_create).  Samples and Phi are packed: ``sample_offsets`` /
+    ``phi_offsets`` give each clip's slice.
     """
 
     def __init__(self, lengths, J: int, Q: int, Q2: int, J_fr: int, Q_fr: int, T: int, F: int,
-                 host_only: bool = False):
+                 host_only: bool = False, boundary: str = "zero"):
+        if boundary not in ("zero", "reflect"):
+            raise ValueError("boundary must be 'zero' or 'reflect'")
         lib = _native.load()
         if not host_only and not torch.cuda.is_available():
             raise RuntimeError("JTFSBatch needs a CUDA device (or host_only=True for inspection)")
         lens = [int(v) for v in lengths]
         arr = (c_int64 * len(lens))(*lens)
         h = c_void_p()
-        _native.check(lib.jtfs_batch_create(ctypes.byref(h), arr, len(lens), J, Q, Q2, J_fr, Q_fr, T, F,
-                                            _native.PLAN_HOST_ONLY if host_only else 0), "jtfs_batch_create")
+        flags = (_native.PLAN_HOST_ONLY if host_only else 0) | (_native.BATCH_REFLECT if boundary == "reflect" else 0)
+        _native.check(lib.jtfs_batch_create(ctypes.byref(h), arr, len(lens), J, Q, Q2, J_fr, Q_fr, T, F, flags),
+                      "jtfs_batch_create")
+        self.boundary = boundary
         self._h, self._lib = h, lib
         so = (c_int64 * (len(lens) + 1))()
         po = (c_int64 * (len(lens) + 1))()

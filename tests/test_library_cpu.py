@@ -103,3 +103,18 @@ def test_python_api_refuses_cpu_tensors():
     plan = JTFSPlan(**PARAMS[0], host_only=True)
     with pytest.raises(TypeError):
         plan.forward(torch.zeros(1, 256))
+
+
+def test_reflect_batch_layout_matches_oracle():
+    """Host-only reflect batch: per-clip Phi sizes equal the oracle's cropped reflect layout (R20)."""
+    import torch
+    from oracle import jtfs_oracle as O
+    from paper_2602_11896_gb300 import JTFSBatch
+    params = dict(J=4, Q=4, Q2=1, J_fr=2, Q_fr=1, T=16, F=2)
+    lengths = [1, 37, 200, 256, 4000]
+    b = JTFSBatch(lengths, **params, host_only=True, boundary="reflect")
+    for i, L in enumerate(lengths):
+        want = O.jtfs_reflect(torch.zeros(L, dtype=torch.float64), params).numel()
+        assert b.phi_offsets[i + 1] - b.phi_offsets[i] == want
+    with pytest.raises(RuntimeError):
+        JTFSBatch([2 ** 20], **params, host_only=True, boundary="reflect")
