@@ -75,12 +75,16 @@ def jtfs_bruteforce(x: np.ndarray, plan: Plan, keep: bool = False) -> Dict[str, 
     phiT = idft_explicit(_morlet(N, 0.0, plan.sigma_phiT))
     phiF = idft_explicit(_morlet(Nfr, 0.0, plan.sigma_phiF))
 
-    S0 = circ_conv(x.astype(np.complex128), phiT).real[:, :: 2 ** lT]
+    # Unpooled variants (reading R21): plan.average_local / plan.average_local_fr.
+    S0 = circ_conv(x.astype(np.complex128), phiT).real[:, :: 2 ** lT] if plan.average_local else x.copy()
 
     U1: List[np.ndarray] = []
-    for f, k1 in zip(plan.psi1, plan.k1):
+    U1_2: List[np.ndarray] = []
+    for n1, f in enumerate(plan.psi1):
         h = idft_explicit(_morlet(N, f.xi, f.sigma))
-        U1.append(np.abs(circ_conv(x.astype(np.complex128), h)[:, :: 2 ** k1]))
+        full = circ_conv(x.astype(np.complex128), h)
+        U1.append(np.abs(full[:, :: 2 ** plan.k1[n1]]))
+        U1_2.append(np.abs(full[:, :: 2 ** (plan.k1[n1] if plan.average_local else f.j)]))
 
     S1 = np.stack([
         circ_conv(U1[n1].astype(np.complex128), level(phiT, k1)).real[:, :: 2 ** (lT - k1)]
@@ -90,23 +94,25 @@ def jtfs_bruteforce(x: np.ndarray, plan: Plan, keep: bool = False) -> Dict[str, 
         """|Z *_n1 psi_beta| decimated, then *_n1 phi_F decimated; Z [B, N_fr, L]."""
         hb = idft_explicit(_morlet(Nfr, xi_b, sig_b))
         y = _along(Z, 1, lambda a: circ_conv(a, hb))[:, :: 2 ** k_b, :]
-        u = np.abs(y).astype(np.complex128)
-        v = _along(u, 1, lambda a: circ_conv(a, level(phiF, k_b))).real
+        u = np.abs(y)
+        if not plan.average_local_fr:
+            return u
+        v = _along(u.astype(np.complex128), 1, lambda a: circ_conv(a, level(phiF, k_b))).real
         return v[:, :: 2 ** (lF - k_b), :]
 
     S1p = np.zeros((B, Nfr, S1.shape[2]), dtype=np.complex128)
     S1p[:, : plan.N1] = S1
-    Phi1 = np.stack([freq_path(S1p, *b) for b in plan.beta_first], axis=1)
+    Phi1 = np.concatenate([freq_path(S1p, *b) for b in plan.beta_first], axis=1)
 
     blocks = []
     for n2 in plan.active:
         f2 = plan.psi2[n2]
-        s2 = min(f2.j, lT)
+        s2 = min(f2.j, lT) if plan.average_local else f2.j
         h2 = idft_explicit(_morlet(N, f2.xi, f2.sigma))
         rows = []
         for n1 in range(plan.n1_max[n2]):
-            k1 = plan.k1[n1]
-            rows.append(circ_conv(U1[n1].astype(np.complex128), level(h2, k1))[:, :: 2 ** (s2 - k1)])
+            k1 = plan.k1[n1] if plan.average_local else plan.psi1[n1].j
+            rows.append(circ_conv(U1_2[n1].astype(np.complex128), level(h2, k1))[:, :: 2 ** (s2 - k1)])
         Y2 = np.stack(rows, axis=1)
         Y2p = np.zeros((B, Nfr, Y2.shape[2]), dtype=np.complex128)
         Y2p[:, : Y2.shape[1]] = Y2
@@ -114,16 +120,16 @@ def jtfs_bruteforce(x: np.ndarray, plan: Plan, keep: bool = False) -> Dict[str, 
         for xi_b, sig_b, k_b in plan.beta_second:
             hb = idft_explicit(_morlet(Nfr, xi_b, sig_b))
             y = _along(Y2p, 1, lambda a: circ_conv(a, hb))[:, :: 2 ** k_b, :]
-            u = np.abs(y).astype(np.complex128)
-            a = circ_conv(u, level(phiT, s2)).real[:, :, :: 2 ** (lT - s2)]   # *_t phi_T
-            a = a.astype(np.complex128)
-            v = _along(a, 1, lambda z: circ_conv(z, level(phiF, k_b))).real[:, :: 2 ** (lF - k_b), :]
-            per_beta.append(v)
-        blocks.append(np.stack(per_beta, axis=1))
+            a = np.abs(y)
+            if plan.average_local:
+                a = circ_conv(a.astype(np.complex128), level(phiT, s2)).real[:, :, :: 2 ** (lT - s2)]   # *_t phi_T
+            if plan.average_local_fr:
+                a = _along(a.astype(np.complex128), 1,
+                           lambda z: circ_conv(z, level(phiF, k_b))).real[:, :: 2 ** (lF - k_b), :]
+            per_beta.append(a)
+        blocks.append(np.concatenate(per_beta, axis=1))
 
-    parts = [S0, Phi1.reshape(B, -1)]
-    if blocks:
-        parts.append(np.stack(blocks, axis=1).reshape(B, -1))
+    parts = [S0, Phi1.reshape(B, -1)] + [blk.reshape(B, -1) for blk in blocks]
     out = {"phi": np.concatenate(parts, axis=1)}
     if keep:
         out.update(S0=S0, U1=U1, S1=S1, Phi1=Phi1)

@@ -61,6 +61,16 @@ reason in the repository's design notes):
   R15 Clips whose length L is not a power of two: zero-padded on the right
       to the next power of two, Phi computed there, and only the first
       ceil(L/T) frames of each row kept (the crop's adjoint fills zeros).
+  R21 Unpooled outputs (average_local / average_local_fr of §3.3-§3.5 set
+      to False).  average_local = False: the zeroth-order output is U0 = x
+      at full rate; the rows U1 that feed the second order are taken at
+      stride k1 = j1 and the second order at total stride j2 (k2 = j2 - k1,
+      §3.3), with no phi_T averaging of |Y2_fr|; the first order keeps S1 at
+      stride T (the main algorithm scatters S1 along n1, which needs one
+      time grid).  average_local_fr = False: frequential stride k = j_fr for
+      every beta (phi_F included, §3.4) and no phi_F averaging: each beta
+      yields N_fr / 2^k rows of |Y_fr|.  Outputs are concatenated in the
+      path order of R12, rows per beta, then frames.
   R20 Reflect boundary (the padding "on both sides" of §3.2 as an option):
       P = ceil(sqrt(ln(1000) / 2) / (pi sigma_min)) samples per side, the
       half-width beyond which the slowest time envelope exp(-2 pi^2 sigma^2
@@ -148,6 +158,8 @@ class Plan:
     Q_fr: int
     T: int
     F: int
+    average_local: bool = True
+    average_local_fr: bool = True
     psi1: List[Filter] = field(init=False)
     psi2: List[Filter] = field(init=False)
     psi_fr: List[Filter] = field(init=False)
@@ -176,20 +188,34 @@ class Plan:
         self.n1_max = [sum(1 for f1 in self.psi1 if f1.j < f2.j) for f2 in self.psi2]
         self.active = [n2 for n2 in range(len(self.psi2)) if self.n1_max[n2] > 0]
         # Frequential filter sets (reading R10): (xi, sigma, k_fr); xi = 0 is phi_F.
-        phi = (0.0, self.sigma_phiF, min(self.j_phiF, self.lF))
-        plus = [(f.xi, f.sigma, min(f.j, self.lF)) for f in self.psi_fr]
-        minus = [(-f.xi, f.sigma, min(f.j, self.lF)) for f in self.psi_fr]
+        # Frequential strides capped at log2 F unless the output is unpooled (R21).
+        kcap = (lambda j: min(j, self.lF)) if self.average_local_fr else (lambda j: j)
+        phi = (0.0, self.sigma_phiF, kcap(self.j_phiF))
+        plus = [(f.xi, f.sigma, kcap(f.j)) for f in self.psi_fr]
+        minus = [(-f.xi, f.sigma, kcap(f.j)) for f in self.psi_fr]
         self.beta_first = [phi] + plus
         self.beta_second = [phi] + plus + minus
         self.R_out = self.N_fr >> self.lF
         self.n_frames = self.N >> self.lT
+        # Time strides of the rows feeding the second order and of the second order (R7, R21).
+        self.k1_2 = [min(f.j, self.lT) if self.average_local else f.j for f in self.psi1]
+        self.s2 = [min(f.j, self.lT) if self.average_local else f.j for f in self.psi2]
+
+    def rows(self, beta: Tuple[float, float, int]) -> int:
+        """Rows n1 of one frequential path: R_out pooled, else N_fr / 2^k (R21)."""
+        return self.R_out if self.average_local_fr else self.N_fr >> beta[2]
+
+    def frames2(self, n2: int) -> int:
+        """Time frames of the second-order paths of n2: N/T pooled, else N / 2^j2 (R21)."""
+        return self.n_frames if self.average_local else self.N >> self.s2[n2]
 
     @property
     def phi_size(self) -> int:
-        """Floats per clip in the flat Phi vector (reading R12)."""
-        per_path = self.R_out * self.n_frames
-        return (self.n_frames + len(self.beta_first) * per_path
-                + len(self.active) * len(self.beta_second) * per_path)
+        """Floats per clip in the flat Phi vector (readings R12, R21)."""
+        s0 = self.n_frames if self.average_local else self.N
+        first = sum(self.rows(b) for b in self.beta_first) * self.n_frames
+        second = sum(sum(self.rows(b) for b in self.beta_second) * self.frames2(n2) for n2 in self.active)
+        return s0 + first + second
 
 
 # ---------------------------------------------------------------------------
@@ -284,14 +310,19 @@ def jtfs(x: torch.Tensor, plan: Plan, keep: bool = False,
     phiT = gauss_hat(N, plan.sigma_phiT)
     phiF = gauss_hat(plan.N_fr, plan.sigma_phiF)
 
-    # Zeroth order: x * phi_T at stride T (first yield of the main algorithm).
-    S0 = decimate(torch.fft.ifft(X * phiT, dim=-1).real, lT, -1)
+    # Zeroth order: x * phi_T at stride T (first yield of the main algorithm), or x itself (R21).
+    if plan.average_local:
+        S0 = decimate(torch.fft.ifft(X * phiT, dim=-1).real, lT, -1)
+    else:
+        S0 = x.to(F64)
 
-    # First layer (§3.2): U1 = |x * psi_n1| at stride 2^k1.
-    U1 = []
-    for f, k1 in zip(plan.psi1, plan.k1):
+    # First layer (§3.2): U1 = |x * psi_n1| at stride 2^k1; the second order reads
+    # its rows at stride 2^k1_2 (equal to k1 unless unpooled in time, R21).
+    U1, U1_2 = [], []
+    for f, k1, k12 in zip(plan.psi1, plan.k1, plan.k1_2):
         z = torch.fft.ifft(X * morlet_hat(N, f.xi, f.sigma), dim=-1)
         U1.append(decimate(z, k1, -1).abs())
+        U1_2.append(U1[-1] if k12 == k1 else decimate(z, k12, -1).abs())
 
     # First-order time averaging, S_1 of the main algorithm (§3.5), Eq. (4)'s phi_T.
     S1 = torch.stack([
@@ -299,22 +330,31 @@ def jtfs(x: torch.Tensor, plan: Plan, keep: bool = False,
         for n1, k1 in enumerate(plan.k1)], dim=1)                         # [B, N1, N/T]
 
     # First-order frequential scattering (spinned=False, §3.4) then phi_F averaging.
+    def pool_F(u: torch.Tensor, k_b: int) -> torch.Tensor:
+        """*_n1 phi_F decimated to 2^lF (Eq. (5)), or the rows as they are (unpooled, R21)."""
+        if not plan.average_local_fr:
+            return u
+        return decimate(conv_circ(u, periodise(phiF, k_b), 1), lF - k_b, 1).real
+
+    def join(blocks: List[torch.Tensor]) -> torch.Tensor:
+        """[B, paths, R_out, frames] when every path has R_out rows, else rows concatenated."""
+        return torch.stack(blocks, 1) if plan.average_local_fr else torch.cat(blocks, 1)
+
     S1p = pad_rows(S1, plan.N_fr, 1)
     phi1 = []
     for xi_b, sig_b, k_b in plan.beta_first:
         yfr = decimate(conv_circ(S1p, freq_filter_hat(plan.N_fr, xi_b, sig_b), 1), k_b, 1)
-        v = decimate(conv_circ(yfr.abs(), periodise(phiF, k_b), 1), lF - k_b, 1).real
-        phi1.append(v)
-    Phi1 = torch.stack(phi1, 1)                                          # [B, 1+K, R_out, N/T]
+        phi1.append(pool_F(yfr.abs(), k_b))
+    Phi1 = join(phi1)                                                    # [B, 1+K, R_out, N/T]
 
     def second_order_block(U1_rows: List[torch.Tensor], n2: int) -> Tuple[torch.Tensor, torch.Tensor]:
         f2 = plan.psi2[n2]
-        s2 = min(f2.j, lT)
+        s2 = plan.s2[n2]
         psi2 = morlet_hat(N, f2.xi, f2.sigma)
         # Second layer, time variable (§3.3): rows n1 with j1 < j2, stacked.
         rows = []
         for n1 in range(plan.n1_max[n2]):
-            k1 = plan.k1[n1]
+            k1 = plan.k1_2[n1]
             rows.append(decimate(conv_circ(U1_rows[n1], periodise(psi2, k1), -1), s2 - k1, -1))
         Y2 = torch.stack(rows, 1)                                        # [B, n1_max, N/2^s2]
         # Second layer, frequency variable (§3.4, spinned=True), modulus, Eq. (5).
@@ -323,13 +363,13 @@ def jtfs(x: torch.Tensor, plan: Plan, keep: bool = False,
         for xi_b, sig_b, k_b in plan.beta_second:
             yfr = decimate(conv_circ(Y2p, freq_filter_hat(plan.N_fr, xi_b, sig_b), 1), k_b, 1)
             u2 = yfr.abs()
-            a = decimate(conv_circ(u2, periodise(phiT, s2), 2), lT - s2, 2).real      # *_t phi_T
-            v = decimate(conv_circ(a, periodise(phiF, k_b), 1), lF - k_b, 1).real     # *_n1 phi_F
-            blocks.append(v)
-        return torch.stack(blocks, 1), Y2                                # [B, 1+2K, R_out, N/T]
+            if plan.average_local:
+                u2 = decimate(conv_circ(u2, periodise(phiT, s2), 2), lT - s2, 2).real     # *_t phi_T
+            blocks.append(pool_F(u2, k_b))                                           # *_n1 phi_F
+        return join(blocks), Y2                                          # [B, 1+2K, R_out, N/T]
 
     if active is not None:
-        sel = {int(a): second_order_block(U1, plan.active[int(a)])[0] for a in active}
+        sel = {int(a): second_order_block(U1_2, plan.active[int(a)])[0] for a in active}
         return {"S0": S0, "Phi1": Phi1, "Phi2_sel": sel}
 
     phi2, Y2s = [], []
@@ -337,20 +377,19 @@ def jtfs(x: torch.Tensor, plan: Plan, keep: bool = False,
         if checkpoint_blocks and torch.is_grad_enabled():
             from torch.utils.checkpoint import checkpoint
             blk = checkpoint(lambda *rows, _n2=n2: second_order_block(list(rows), _n2)[0],
-                             *U1[:plan.n1_max[n2]], use_reentrant=False)
+                             *U1_2[:plan.n1_max[n2]], use_reentrant=False)
         else:
-            blk, Y2 = second_order_block(U1, n2)
+            blk, Y2 = second_order_block(U1_2, n2)
             if keep:
                 Y2s.append(Y2)
         phi2.append(blk)
 
-    parts = [S0, Phi1.reshape(B, -1)]
-    if phi2:
-        parts.append(torch.stack(phi2, 1).reshape(B, -1))
+    parts = [S0, Phi1.reshape(B, -1)] + [blk.reshape(B, -1) for blk in phi2]
     out = {"phi": torch.cat(parts, 1)}
     if keep:
+        pooled = plan.average_local and plan.average_local_fr
         out.update(S0=S0, U1=U1, S1=S1, Phi1=Phi1, Y2=Y2s,
-                   Phi2=torch.stack(phi2, 1) if phi2 else None)
+                   Phi2=(torch.stack(phi2, 1) if phi2 else None) if pooled else phi2)
     return out
 
 
@@ -358,15 +397,15 @@ def phi_blocks(phi: torch.Tensor, plan: Plan) -> Dict[str, torch.Tensor]:
     """Split a flat [B, phi_size] Phi into S0, first-order and per-n2 blocks."""
     B = phi.shape[0]
     nf = plan.n_frames
-    per_path = plan.R_out * nf
     o = 0
-    out = {"S0": phi[:, o:o + nf]}
-    o += nf
-    n = len(plan.beta_first) * per_path
+    n = nf if plan.average_local else plan.N
+    out = {"S0": phi[:, o:o + n]}
+    o += n
+    n = sum(plan.rows(b) for b in plan.beta_first) * nf
     out["first"] = phi[:, o:o + n]
     o += n
     for n2 in plan.active:
-        n = len(plan.beta_second) * per_path
+        n = sum(plan.rows(b) for b in plan.beta_second) * plan.frames2(n2)
         out[f"n2={n2}"] = phi[:, o:o + n]
         o += n
     assert o == phi.shape[1] == plan.phi_size and B == phi.shape[0]
