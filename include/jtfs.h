@@ -50,6 +50,18 @@ extern "C" {
 /* Plan flags. */
 #define JTFS_PLAN_HOST_ONLY 1u /* build the tables on the host only; compute
                                   calls then fail with JTFS_ERR_NODEVICE.   */
+/* Unpooled outputs (§3.3-§3.5 with average_local / average_local_fr off):
+ * JTFS_PLAN_UNPOOLED_T: the zeroth-order block is x itself ([N]); the
+ *   second order is |Y2_fr| *_n1 phi_F at time stride 2^j2 (no phi_T), the
+ *   block of n2 being [1+2K][R_out][N / 2^j2]; the first order keeps S1 at
+ *   stride T.  Plans where some first-order j1 exceeds log2 T are refused
+ *   (JTFS_ERR_SHAPE): their second-order rows would need U1 at stride j1.
+ * JTFS_PLAN_UNPOOLED_F: frequential stride 2^j for every beta (phi_F
+ *   included) and no phi_F averaging: each path has N_fr / 2^j rows instead
+ *   of R_out (first and second order).
+ * Phi's path order is unchanged; jtfs_phi_size gives the new size. */
+#define JTFS_PLAN_UNPOOLED_T 4u
+#define JTFS_PLAN_UNPOOLED_F 8u
 
 typedef struct jtfs_plan_s* jtfs_plan_t;
 

@@ -79,6 +79,8 @@ SIGNATURES = {
 
 PLAN_HOST_ONLY = 1
 BATCH_REFLECT = 2
+PLAN_UNPOOLED_T = 4
+PLAN_UNPOOLED_F = 8
 
 _lib = None
 

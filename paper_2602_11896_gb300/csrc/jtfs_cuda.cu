@@ -1237,6 +1237,18 @@ k_adam(float* __restrict__ y, float* __restrict__ m, float* __restrict__ v, cons
 // descent with the bold-driver step size.
 // ---------------------------------------------------------------------------
 
+// Per clip b (blockIdx.y): dst[b dst_stride + dst_off + i] (+)= src[b src_stride + src_off + i], i < len.
+// Moves blocks between Phi and the workspace for the unpooled outputs.
+__global__ void __launch_bounds__(kThreads)
+k_copy_block(const float* __restrict__ src, int64_t src_stride, int64_t src_off, float* __restrict__ dst,
+             int64_t dst_stride, int64_t dst_off, int64_t len, int accumulate) {
+  const float* a = src + static_cast<int64_t>(blockIdx.y) * src_stride + src_off;
+  float* d = dst + static_cast<int64_t>(blockIdx.y) * dst_stride + dst_off;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < len;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    d[i] = accumulate ? d[i] + a[i] : a[i];
+}
+
 // rows[r][t] *= gain[r mod n_rows] over `total` = batch * n_rows * row_len entries.
 __global__ void __launch_bounds__(kThreads)
 k_scale_rows(float* __restrict__ rows, const float* __restrict__ gain, int n_rows, int log_len, int64_t total) {
@@ -1431,6 +1443,14 @@ GradArgs grad_args(const Plan& p) {
 
 int check_launch() { return cudaGetLastError() == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA; }
 
+int copy_block(const Plan& p, const float* src, int64_t src_stride, int64_t src_off, float* dst, int64_t dst_stride,
+               int64_t dst_off, int64_t len, bool accumulate, cudaStream_t s) {
+  const unsigned gx = static_cast<unsigned>(std::min<int64_t>((len + kThreads - 1) / kThreads, 4096));
+  k_copy_block<<<dim3(std::max(gx, 1u), static_cast<unsigned>(p.batch)), kThreads, 0, s>>>(
+      src, src_stride, src_off, dst, dst_stride, dst_off, len, accumulate ? 1 : 0);
+  return check_launch();
+}
+
 // Bracket one launch of `stage` with the caller's events, if registered.
 void prof_begin(const Plan& p, int stage, cudaStream_t s) {
   const auto& ev = p.prof_events[stage];
@@ -1461,15 +1481,15 @@ int64_t freq2_launches(const Plan& p) {
 
 int64_t forward_launches(const Plan& p, bool full) {
   int64_t n = fft_launches(p.L_x) + fft_launches(p.L_u1) + fft_launches(p.L_u1inplace) + fft_launches(p.L_s1);
-  if (full) n += fft_launches(p.L_s0) + 1;
-  if (p.n_active > 0) n += fft_launches(p.L_y2) + (full ? 2 + freq2_launches(p) : 0);
+  if (full) n += (p.unpooled_t ? 1 : fft_launches(p.L_s0)) + 1;
+  if (p.n_active > 0) n += fft_launches(p.L_y2) + (full ? (p.unpooled_t ? 1 : 2) + freq2_launches(p) : 0);
   return n;
 }
 
 int64_t backward_launches(const Plan& p) {
   int64_t n = 1 + fft_launches(p.L_ds1) + static_cast<int64_t>(p.L_u1inplace.size()) +
-              2 * fft_launches(p.L_u1inplace) + fft_launches(p.L_u1) + fft_launches(p.L_ds0) + 1 +
-              fft_launches(p.L_x);
+              2 * fft_launches(p.L_u1inplace) + fft_launches(p.L_u1) + (p.unpooled_t ? 1 : fft_launches(p.L_ds0)) +
+              1 + fft_launches(p.L_x);
   if (p.n_active > 0) n += 1 + freq2_launches(p) + fft_launches(p.L_y2inplace);
   return n;
 }
@@ -1497,7 +1517,12 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
   JTFS_TRY((run_fft<false>(p, p.L_x, LdReal{x}, StC{w.Xh}, w.scr, s)));
   JTFS_TRY((run_fft<true>(p, p.L_u1, LdBand{w.Xh, p.d_psi1, FiltD{}}, StC{w.U1h}, w.scr, s)));
   JTFS_TRY((run_fft<false>(p, p.L_u1inplace, LdMod{w.U1h}, StC{w.U1h}, w.scr, s)));
-  if (full) JTFS_TRY((run_fft<true>(p, p.L_s0, LdBand{w.Xh, nullptr, p.h_phiT}, StR{phi}, w.scr, s)));
+  if (full) {
+    if (p.unpooled_t)  // zeroth order = x
+      JTFS_TRY(copy_block(p, x, p.N, 0, phi, p.phi_size, 0, p.N, false, s));
+    else
+      JTFS_TRY((run_fft<true>(p, p.L_s0, LdBand{w.Xh, nullptr, p.h_phiT}, StR{phi}, w.scr, s)));
+  }
   JTFS_TRY((run_fft<true>(p, p.L_s1, LdBand{w.U1h, nullptr, p.h_phiT}, StR{w.S1}, w.scr, s)));
   const FreqArgs FA = freq_args(p, 1);
   const FreqArgs FA2 = freq_args(p, 2);
@@ -1537,6 +1562,10 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
         k_freq_fwd<2><<<n2, kThreads, freq_smem(p, 3), s>>>(FA2, t2, nullptr, w.Y2, w.V2);
       prof_end(p, JTFS_STAGE_FREQ2_FWD, s);
       JTFS_TRY(check_launch());
+      if (p.unpooled_t) {  // second-order blocks = V2 (no phi_T)
+        JTFS_TRY(copy_block(p, w.V2, p.v2_tot, 0, phi, p.phi_size, p.phi2_base, p.v2_tot, false, s));
+        return JTFS_OK;
+      }
       const PoolArgs PA = pool_args(p);
       const int fpt = p.n_frames >= 128 ? 16 : p.n_frames >= 64 ? 8 : p.n_frames >= 32 ? 4 : p.n_frames >= 16 ? 2 : 1;
       const int si = p.tune_split;
@@ -1589,6 +1618,8 @@ int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, 
   if (p.n_active > 0) {
     const PoolArgs PA = pool_args(p);
     prof_begin(p, JTFS_STAGE_POOL_ADJ, s);
+    if (p.unpooled_t)  // dV2 = the second-order blocks of dPhi
+      JTFS_TRY(copy_block(p, dphi, p.phi_size, p.phi2_base, w.V2, p.v2_tot, 0, p.v2_tot, false, s));
     if (!p.pool_tiles2.empty())
       k_pool_adj2<<<static_cast<unsigned>(p.pool_tiles2.size()), kThreads, 0, s>>>(PA, dphi, w.V2, p.d_pool_tiles2);
     if (!p.pool_tiles.empty())
@@ -1628,14 +1659,16 @@ int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, 
   JTFS_TRY((run_fft<true>(p, p.L_u1inplace, LdC{w.U1h}, StC{w.U1h}, w.scr, s)));
   JTFS_TRY((run_fft<true>(p, p.L_u1, LdBand{w.Xh, p.d_psi1, FiltD{}}, StC{w.Zs}, w.scr, s)));
   JTFS_TRY((run_fft<false>(p, p.L_u1inplace, LdDz{w.U1h, w.Zs}, StC{w.Zs}, w.scr, s)));
-  JTFS_TRY((run_fft<false>(p, p.L_ds0, LdReal{dphi}, StC{w.dS0h}, w.scr, s)));
+  if (!p.unpooled_t) JTFS_TRY((run_fft<false>(p, p.L_ds0, LdReal{dphi}, StC{w.dS0h}, w.scr, s)));
   {
     const int64_t total = int64_t(p.batch) * p.N;
-    k_dX<<<static_cast<unsigned>((total + kThreads - 1) / kThreads), kThreads, 0, s>>>(GA, total, w.Zs, w.dS0h,
-                                                                                       w.dXh);
+    k_dX<<<static_cast<unsigned>((total + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        GA, total, w.Zs, p.unpooled_t ? nullptr : w.dS0h, w.dXh);
     JTFS_TRY(check_launch());
   }
   JTFS_TRY((run_fft<true>(p, p.L_x, LdC{w.dXh}, StR{dx}, w.scr, s)));
+  if (p.unpooled_t)  // the zeroth order is x: its gradient adds directly
+    JTFS_TRY(copy_block(p, dphi, p.phi_size, 0, dx, p.N, 0, p.N, true, s));
   return JTFS_OK;
 }
 

@@ -104,6 +104,11 @@ struct Plan {
   int batch = 0;
   uint32_t flags = 0;
 
+  // Output variants (JTFS_PLAN_UNPOOLED_T / _F): no phi_T averaging of the
+  // second order (stride 2^j2, zeroth order = x), no phi_F averaging.
+  bool unpooled_t = false, unpooled_f = false;
+  int64_t phi2_base = 0;  // start of the second-order blocks inside Phi
+
   // Derived sizes.
   int logN = 0, lT = 0, lF = 0;
   int N1 = 0, N2 = 0, K = 0;

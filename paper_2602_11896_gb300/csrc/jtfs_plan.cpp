@@ -101,6 +101,9 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   if (J > 24 || Q > 64 || Q2 > 64 || J_fr > 12 || Q_fr > 16) return JTFS_ERR_SHAPE;
   p.N = N; p.J = J; p.Q = Q; p.Q2 = Q2; p.J_fr = J_fr; p.Q_fr = Q_fr;
   p.T = T; p.F = F; p.batch = batch; p.flags = flags;
+  p.unpooled_t = (flags & JTFS_PLAN_UNPOOLED_T) != 0;
+  p.unpooled_f = (flags & JTFS_PLAN_UNPOOLED_F) != 0;
+  if (p.unpooled_f) return JTFS_ERR_SHAPE;
   p.logN = ilog2(N);
   p.lT = ilog2(T);
   p.lF = static_cast<int>(std::floor(std::log2(double(F))));
@@ -141,9 +144,14 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   for (int n2 = 0; n2 < p.N2; ++n2)
     if (p.n1max[n2] > 0) {
       p.active.push_back(n2);
-      p.s2.push_back(std::min(p.psi2[n2].j, p.lT));
+      p.s2.push_back(p.unpooled_t ? p.psi2[n2].j : std::min(p.psi2[n2].j, p.lT));
     }
   p.n_active = static_cast<int>(p.active.size());
+  // Unpooled in time: the rows feeding the second order are read at stride
+  // j1; supported where that equals the first order's min(j1, log2 T).
+  if (p.unpooled_t)
+    for (int n1 = 0; n1 < p.N1; ++n1)
+      if (p.psi1[n1].j > p.lT) return JTFS_ERR_SHAPE;
   // Rows with j1 < j2 are a prefix of n1 because j1 is non-decreasing in n1.
   for (int n1 = 1; n1 < p.N1; ++n1)
     if (p.psi1[n1].j < p.psi1[n1 - 1].j) return JTFS_ERR_SHAPE;
@@ -204,16 +212,18 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   p.y2_tot = 0;
   p.v2_tot = 0;
   const int64_t per_path = int64_t(p.R_out) * p.n_frames;
-  p.phi1_off = p.n_frames;
+  p.phi1_off = p.unpooled_t ? N : p.n_frames;
+  p.phi2_base = p.phi1_off + p.n_beta1 * per_path;
   for (int a = 0; a < p.n_active; ++a) {
     const int64_t L2 = N >> p.s2[a];
     p.y2_off[a] = p.y2_tot;
     p.y2_tot += int64_t(p.n1max[p.active[a]]) * L2;
     p.v2_off[a] = p.v2_tot;
     p.v2_tot += int64_t(p.n_beta2) * p.R_out * L2;
-    p.phi2_off[a] = p.phi1_off + p.n_beta1 * per_path + int64_t(a) * p.n_beta2 * per_path;
+    // Unpooled in time, the second-order blocks are V2 itself.
+    p.phi2_off[a] = p.phi2_base + (p.unpooled_t ? p.v2_off[a] : int64_t(a) * p.n_beta2 * per_path);
   }
-  p.phi_size = p.n_frames + p.n_beta1 * per_path + int64_t(p.n_active) * p.n_beta2 * per_path;
+  p.phi_size = p.phi2_base + (p.unpooled_t ? p.v2_tot : int64_t(p.n_active) * p.n_beta2 * per_path);
 
   // Time-pooling taps g_s[t] = 2^s phi_T[2^s t] for every level s <= log2 T,
   // where phi_T[tau] = (1/N) sum_m phi_hat_T(m/N) e^{2 pi i m tau / N}
@@ -288,7 +298,9 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
     add(p.L_s1, p.log_frames, s1);
     add(p.L_ds1, p.log_frames, ds1);
   }
-  for (int lev = 0; lev <= p.lT; ++lev) {
+  int max_s2 = p.lT;
+  for (int a = 0; a < p.n_active; ++a) max_s2 = std::max(max_s2, p.s2[a]);
+  for (int lev = 0; lev <= max_s2; ++lev) {
     std::vector<Job> band, rows;
     for (int b = 0; b < B; ++b)
       for (int a = 0; a < p.n_active; ++a) {
@@ -389,7 +401,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   // level samples on either side.  Chosen when a 32-frame window (forward) and
   // the frames of a 64-sample tile (adjoint) stay within the circle.
   p.pool_w.assign(p.n_active, 0);
-  {
+  if (!p.unpooled_t) {
     const double c = 2.0 * M_PI * M_PI * p.phiT.sigma * p.phiT.sigma;
     const double reach = std::sqrt(40.0 * std::log(2.0) / c);
     for (int a = 0; a < p.n_active; ++a) {
@@ -403,7 +415,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   // samples (four 128-sample sub-tiles) for the dense ones.
   p.pool_tiles.clear();
   p.pool_tiles2.clear();
-  {
+  if (!p.unpooled_t) {
     const int rows = p.n_beta2 * p.R_out;
     for (int b = 0; b < B; ++b)
       for (int a = 0; a < p.n_active; ++a) {
@@ -417,7 +429,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
       }
   }
   p.pool_band_tiles.clear();
-  {
+  if (!p.unpooled_t) {
     const int rows = p.n_beta2 * p.R_out;
     for (int b = 0; b < B; ++b)
       for (int a = 0; a < p.n_active; ++a) {
@@ -429,6 +441,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   for (int si = 0; si < 3; ++si) {
     p.pool_fwd_tiles[si].clear();
     p.pool_tile0[si].clear();
+    if (p.unpooled_t) continue;
     const int rows = p.n_beta2 * p.R_out;
     for (int b = 0; b < B; ++b)
       for (int a = 0; a < p.n_active; ++a) {

@@ -35,13 +35,17 @@ class JTFSPlan:
     two), J octaves, Q and Q2 filters per octave of the first- and
     second-order time filterbanks, J_fr and Q_fr of the frequential
     filterbank, time averaging T (power of two) and frequency averaging F.
+    ``average_local`` / ``average_local_fr`` False give the unpooled outputs
+    (JTFS_PLAN_UNPOOLED_T / _F in include/jtfs.h).
     """
 
     def __init__(self, N: int, J: int, Q: int, Q2: int, J_fr: int, Q_fr: int, T: int, F: int,
-                 batch: int = 1, host_only: bool = False):
+                 batch: int = 1, host_only: bool = False, average_local: bool = True,
+                 average_local_fr: bool = True):
         lib = _native.load()
         h = c_void_p()
-        flags = _native.PLAN_HOST_ONLY if host_only else 0
+        flags = ((_native.PLAN_HOST_ONLY if host_only else 0) | (0 if average_local else _native.PLAN_UNPOOLED_T)
+                 | (0 if average_local_fr else _native.PLAN_UNPOOLED_F))
         if not host_only and not torch.cuda.is_available():
             raise RuntimeError("JTFSPlan needs a CUDA device (or host_only=True for inspection)")
         _native.check(lib.jtfs_plan(ctypes.byref(h), N, J, Q, Q2, J_fr, Q_fr, T, F, batch, flags),
