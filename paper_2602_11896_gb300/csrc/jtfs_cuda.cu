@@ -515,6 +515,22 @@ k_freq_fwd(FreqArgs A, const Tile* __restrict__ tiles, const float* __restrict__
       }
     }
     __syncthreads();
+    if (A.unpooled_f) {  // |Y_fr| rows as they are: no phi_F
+      for (int i = threadIdx.x; i < (1 << (lR + lc)); i += blockDim.x) {
+        const int f = i & ((1 << lc) - 1), row = i >> lc;
+        const int bc = f >> A.logW, w = f & (W - 1);
+        if (bc < ch.n && w < tl.ncols) {
+          const int b = ch.beta[bc];
+          const int64_t r = A.row_off[b] + row;
+          if (MODE == 1)
+            out[static_cast<int64_t>(tl.b) * A.phi_size + A.phi1_off + r * A.n_frames + tl.t0 + w] = z[i].x;
+          else
+            out[static_cast<int64_t>(tl.b) * A.v2_tot + A.v2_off[tl.a] + r * stride + tl.t0 + w] = z[i].x;
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     float2* zo = (z == f1) ? f2 : f1;
     float2* uh = cta_fft_il<false>(z, zo, lR, lc, S.tw, A.logNfr);
     float2* g = (uh == f1) ? f2 : f1;
@@ -575,6 +591,27 @@ k_freq_adj(FreqArgs A, const Tile* __restrict__ tiles, const float* S1, const fl
     float2* z = cta_fft_il<true>(f1, f2, lR, lc, S.tw, A.logNfr);
     float2* dwb = (z == f1) ? f2 : f1;
     for (int i = threadIdx.x; i < (R << lc); i += blockDim.x) zb[i] = z[i];
+    float2* du;
+    float2* other;
+    if (A.unpooled_f) {  // no phi_F: the output gradient is d|Y_fr| itself
+      for (int i = threadIdx.x; i < (R << lc); i += blockDim.x) {
+        const int f = i & (cnt - 1), row = i >> lc;
+        const int bc = f >> A.logW, w = f & (W - 1);
+        float v = 0.f;
+        if (bc < ch.n && w < tl.ncols) {
+          const int b = ch.beta[bc];
+          const int64_t r = A.row_off[b] + row;
+          if (MODE == 1)
+            v = dout[static_cast<int64_t>(tl.b) * A.phi_size + A.phi1_off + r * A.n_frames + tl.t0 + w];
+          else
+            v = dout[static_cast<int64_t>(tl.b) * A.v2_tot + A.v2_off[tl.a] + r * stride + tl.t0 + w];
+        }
+        dwb[i] = make_float2(v, 0.f);
+      }
+      __syncthreads();
+      du = dwb;
+      other = z;
+    } else {
     // dw: the output gradient of the chunk, interleaved [row][f].
     for (int i = threadIdx.x; i < (Ro << lc); i += blockDim.x) {
       const int f = i & (cnt - 1), row = i >> lc;
@@ -608,7 +645,9 @@ k_freq_adj(FreqArgs A, const Tile* __restrict__ tiles, const float* S1, const fl
       }
     }
     __syncthreads();
-    float2* du = cta_fft_il<true>(X, dW, lR, lc, S.tw, A.logNfr);
+    du = cta_fft_il<true>(X, dW, lR, lc, S.tw, A.logNfr);
+    other = (du == X) ? dW : X;
+    }
     // dz = Re(du) z / |z|  (0 where z = 0)
     for (int i = threadIdx.x; i < (R << lc); i += kThreads) {
       const float gr = du[i].x;
@@ -617,7 +656,6 @@ k_freq_adj(FreqArgs A, const Tile* __restrict__ tiles, const float* S1, const fl
       du[i] = mg > 0.f ? make_float2(gr * v.x / mg, gr * v.y / mg) : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    float2* other = (du == X) ? dW : X;
     float2* dZ = cta_fft_il<false>(du, other, lR, lc, S.tw, A.logNfr);
     // D[m][w] += (1/N_fr) sum_beta psi_beta(s(m)) dZ_beta[m mod R][w]
     {
@@ -668,6 +706,7 @@ k_freq_adj(FreqArgs A, const Tile* __restrict__ tiles, const float* S1, const fl
 // ---------------------------------------------------------------------------
 struct PoolArgs {
   int logN, lT, n_frames, R_out, n_beta2, n_active;
+  int rows2;  // rows of one second-order block (n_beta2 R_out when pooled along n1)
   int64_t phi_size, v2_tot;
   const int* s2;
   const int64_t* v2_off;
@@ -702,7 +741,7 @@ k_pool_fwd(PoolArgs A, const float* __restrict__ V2, float* __restrict__ part, c
   const int s = A.s2[a];
   const int lL = A.logN - s, L = 1 << lL;
   const int D = 1 << (A.lT - s);
-  const int rows = A.n_beta2 * A.R_out;
+  const int rows = A.rows2;
   const int r0 = tl.z * kPoolRows;
   const int tbeg = split * split_len, tend = min(L, tbeg + split_len);
   const float* v = V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
@@ -774,7 +813,7 @@ k_pool_fwd2(PoolArgs A, const float* __restrict__ V2, float* __restrict__ part, 
   const int s = A.s2[a];
   const int lL = A.logN - s, L = 1 << lL;
   const int D = 1 << (A.lT - s);
-  const int rows = A.n_beta2 * A.R_out;
+  const int rows = A.rows2;
   const int r0 = tl.z * kPoolRows;
   const int tbeg = split * split_len, tend = min(L, tbeg + split_len);
   const float* v = V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
@@ -869,7 +908,7 @@ k_pool_reduce(PoolArgs A, const float* __restrict__ part, float* __restrict__ ph
               int split_len, int64_t total) {
   const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= total) return;
-  const int rows = A.n_beta2 * A.R_out;
+  const int rows = A.rows2;
   const int64_t per_a = static_cast<int64_t>(rows) * A.n_frames;
   const int64_t ba = idx / per_a;
   const int rf = static_cast<int>(idx % per_a);
@@ -902,7 +941,7 @@ k_pool_fwd_band(PoolArgs A, const float* __restrict__ V2, float* __restrict__ ph
   const int lL = A.logN - s, L = 1 << lL;
   const int D = 1 << (A.lT - s);
   const int W = A.pool_w[a];
-  const int rows = A.n_beta2 * A.R_out;
+  const int rows = A.rows2;
   const int r0 = tl.z * kPoolRows;
   const int tbeg = f0 * D - W, tend = (f0 + 8 * FPT - 1) * D + W + 1;
   const float* v = V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
@@ -970,7 +1009,7 @@ k_pool_adj2(PoolArgs A, const float* __restrict__ dphi, float* __restrict__ dV2,
   const int s = A.s2[a];
   const int lL = A.logN - s, L = 1 << lL;
   const int D = 1 << (A.lT - s);
-  const int rows = A.n_beta2 * A.R_out;
+  const int rows = A.rows2;
   const int r0 = tl.z * kPoolRows;
   const float* dp = dphi + static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a];
   const float* g = A.taps + A.tap_off[s];
@@ -1061,7 +1100,7 @@ k_pool_adj(PoolArgs A, const float* __restrict__ dphi, float* __restrict__ dV2, 
   const int s = A.s2[a];
   const int lL = A.logN - s, L = 1 << lL;
   const int D = 1 << (A.lT - s);
-  const int rows = A.n_beta2 * A.R_out;
+  const int rows = A.rows2;
   const int r0 = tl.z * kPoolRows, t0 = tl.w * kPoolT;
   const float* dp = dphi + static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a];
   const float* g = A.taps + A.tap_off[s];
@@ -1394,6 +1433,8 @@ FreqArgs freq_args(const Plan& p, int mode) {
   A.ftabc_phi = p.ftabc_phi;
   A.tab_smem = 0;
   for (int k = 0; k < 16; ++k) A.ftabc_lev[k] = p.ftabc_lev[k];
+  A.unpooled_f = p.unpooled_f ? 1 : 0;
+  A.row_off = p.d_row_off;
   return A;
 }
 
@@ -1404,6 +1445,7 @@ PoolArgs pool_args(const Plan& p) {
   A.n_frames = p.n_frames;
   A.R_out = p.R_out;
   A.n_beta2 = p.n_beta2;
+  A.rows2 = p.rows2;
   A.n_active = p.n_active;
   A.phi_size = p.phi_size;
   A.v2_tot = p.v2_tot;
@@ -1527,8 +1569,8 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
   const FreqArgs FA = freq_args(p, 1);
   const FreqArgs FA2 = freq_args(p, 2);
   if (full) {
-    if (!launch_freq_fwd_ct(1, FA, p.lF, static_cast<unsigned>(p.tiles1.size()), freq_smem(p, 3), s, p.d_tiles1,
-                            w.S1, nullptr, phi)) {
+    if (p.unpooled_f || !launch_freq_fwd_ct(1, FA, p.lF, static_cast<unsigned>(p.tiles1.size()), freq_smem(p, 3), s,
+                                            p.d_tiles1, w.S1, nullptr, phi)) {
       allow_big_smem<k_freq_fwd<1>>();
       k_freq_fwd<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 3), s>>>(
           FA, p.d_tiles1, w.S1, nullptr, phi);
@@ -1557,8 +1599,9 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
       const unsigned n2 = static_cast<unsigned>(tc ? p.tiles2_fft.size() : p.tiles2.size());
       const unsigned n2w = static_cast<unsigned>(tc ? p.tiles2w_fft.size() : p.tiles2w.size());
       if (n2 > 0 &&
-          !(p.tune_wide && launch_freq_fwd_ct(2, FA2w, p.lF, n2w, smem_w, s, t2w, nullptr, w.Y2, w.V2)) &&
-          !launch_freq_fwd_ct(2, FA2n, p.lF, n2, smem_n, s, t2, nullptr, w.Y2, w.V2))
+          (p.unpooled_f ||
+           (!(p.tune_wide && launch_freq_fwd_ct(2, FA2w, p.lF, n2w, smem_w, s, t2w, nullptr, w.Y2, w.V2)) &&
+            !launch_freq_fwd_ct(2, FA2n, p.lF, n2, smem_n, s, t2, nullptr, w.Y2, w.V2))))
         k_freq_fwd<2><<<n2, kThreads, freq_smem(p, 3), s>>>(FA2, t2, nullptr, w.Y2, w.V2);
       prof_end(p, JTFS_STAGE_FREQ2_FWD, s);
       JTFS_TRY(check_launch());
@@ -1598,7 +1641,7 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
         JTFS_TRY(check_launch());
       }
       if (grid.x) {
-        const int64_t total = int64_t(p.batch) * p.n_active * p.n_beta2 * p.R_out * p.n_frames;
+        const int64_t total = int64_t(p.batch) * p.n_active * p.rows2 * p.n_frames;
         k_pool_reduce<<<static_cast<unsigned>((total + kThreads - 1) / kThreads), kThreads, 0, s>>>(
             PA, w.part, phi, p.d_pool_tile0[si], split_len, total);
       }
@@ -1638,14 +1681,15 @@ int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, 
     }
     const Tile* t2 = tc ? p.d_tiles2_fft : p.d_tiles2;
     const unsigned n2 = static_cast<unsigned>(tc ? p.tiles2_fft.size() : p.tiles2.size());
-    if (n2 > 0 && !launch_freq_adj_ct(2, FA2c, p.lF, n2, smem_c, s, t2, nullptr, w.Y2, w.V2, nullptr, w.dY2))
+    if (n2 > 0 &&
+        (p.unpooled_f || !launch_freq_adj_ct(2, FA2c, p.lF, n2, smem_c, s, t2, nullptr, w.Y2, w.V2, nullptr, w.dY2)))
       k_freq_adj<2><<<n2, kThreads, freq_smem(p, 5), s>>>(FA2, t2, nullptr, w.Y2, w.V2, nullptr, w.dY2);
     prof_end(p, JTFS_STAGE_FREQ2_ADJ, s);
     JTFS_TRY(check_launch());
   }
   allow_big_smem<k_freq_adj<1>>();
-  if (!launch_freq_adj_ct(1, FA, p.lF, static_cast<unsigned>(p.tiles1.size()), freq_smem(p, 5), s, p.d_tiles1, w.S1,
-                          nullptr, dphi, w.S1, nullptr))
+  if (p.unpooled_f || !launch_freq_adj_ct(1, FA, p.lF, static_cast<unsigned>(p.tiles1.size()), freq_smem(p, 5), s,
+                                          p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr))
     k_freq_adj<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 5), s>>>(
         FA, p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr);
   JTFS_TRY(check_launch());

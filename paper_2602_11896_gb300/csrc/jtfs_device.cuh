@@ -107,6 +107,9 @@ struct FreqArgs {
   const int* ftabc_off;
   int n_ftabc, ftabc_phi, tab_smem;
   int ftabc_lev[16];
+  // Unpooled along n1 (no phi_F): each path's |Y_fr| rows start at row_off[beta].
+  int unpooled_f;
+  const int* row_off;
 };
 
 // Shared-memory layout of the frequential kernels (all in float2 units):

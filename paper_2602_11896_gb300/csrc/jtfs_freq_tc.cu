@@ -860,6 +860,7 @@ void tc_build(Plan& p) {
   p.tiles2w_fft = p.tiles2w;
   const int RO = p.R_out, NF = p.N_fr;
   if (p.n_active == 0 || (RO != 16 && RO != 32) || NF < 64 || NF > 1024) return;
+  if (p.unpooled_f) return;  // the GEMM tables include the phi_F averaging
   std::vector<int> ka(p.n_active, 0);
   bool any = false;
   for (int a = 0; a < p.n_active; ++a) {

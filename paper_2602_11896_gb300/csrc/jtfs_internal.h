@@ -108,6 +108,12 @@ struct Plan {
   // second order (stride 2^j2, zeroth order = x), no phi_F averaging.
   bool unpooled_t = false, unpooled_f = false;
   int64_t phi2_base = 0;  // start of the second-order blocks inside Phi
+  // Rows n1 of each frequential path, as offsets: path beta (second-order
+  // order: phi_F, +xi, -xi; the first order uses the first 1 + K) starts at
+  // row_off[beta] of its block; R_out per path unless unpooled along n1.
+  std::vector<int> row_off;
+  int rows1 = 0, rows2 = 0;  // rows of the first-order block, of one second-order block
+  const int* d_row_off = nullptr;
 
   // Derived sizes.
   int logN = 0, lT = 0, lF = 0;

@@ -103,7 +103,6 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   p.T = T; p.F = F; p.batch = batch; p.flags = flags;
   p.unpooled_t = (flags & JTFS_PLAN_UNPOOLED_T) != 0;
   p.unpooled_f = (flags & JTFS_PLAN_UNPOOLED_F) != 0;
-  if (p.unpooled_f) return JTFS_ERR_SHAPE;
   p.logN = ilog2(N);
   p.lT = ilog2(T);
   p.lF = static_cast<int>(std::floor(std::log2(double(F))));
@@ -160,15 +159,23 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   p.h_beta.clear();
   p.beta_k.clear();
   {
-    const int kphi = std::min(p.phiF.j, p.lF);
+    // Frequential strides capped at floor(log2 F), or 2^j when unpooled along n1.
+    const int kphi = p.unpooled_f ? p.phiF.j : std::min(p.phiF.j, p.lF);
+    if (kphi > p.logNfr - 1) return JTFS_ERR_SHAPE;  // at least two rows per path
     p.h_beta.push_back(make_filt(0.0, p.phiF.sigma, p.N_fr, kphi, p.phiF.j, true));
     for (int s = 0; s < 2; ++s)
       for (auto& f : p.psifr) {
-        const int k = std::min(f.j, p.lF);
+        const int k = p.unpooled_f ? f.j : std::min(f.j, p.lF);
+        if (k > p.logNfr - 1) return JTFS_ERR_SHAPE;
         p.h_beta.push_back(make_filt(s == 0 ? f.xi : -f.xi, f.sigma, p.N_fr, k, f.j, false));
       }
     for (auto& f : p.h_beta) p.beta_k.push_back(f.k);
   }
+  p.row_off.assign(p.n_beta2 + 1, 0);
+  for (int b = 0; b < p.n_beta2; ++b)
+    p.row_off[b + 1] = p.row_off[b] + (p.unpooled_f ? (p.N_fr >> p.beta_k[b]) : p.R_out);
+  p.rows1 = p.row_off[p.n_beta1];
+  p.rows2 = p.row_off[p.n_beta2];
   p.h_psi1.clear();
   for (int n1 = 0; n1 < p.N1; ++n1)
     p.h_psi1.push_back(make_filt(p.psi1[n1].xi, p.psi1[n1].sigma, int(N), p.k1[n1], p.psi1[n1].j, false));
@@ -211,19 +218,18 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   p.phi2_off.resize(p.n_active);
   p.y2_tot = 0;
   p.v2_tot = 0;
-  const int64_t per_path = int64_t(p.R_out) * p.n_frames;
   p.phi1_off = p.unpooled_t ? N : p.n_frames;
-  p.phi2_base = p.phi1_off + p.n_beta1 * per_path;
+  p.phi2_base = p.phi1_off + int64_t(p.rows1) * p.n_frames;
   for (int a = 0; a < p.n_active; ++a) {
     const int64_t L2 = N >> p.s2[a];
     p.y2_off[a] = p.y2_tot;
     p.y2_tot += int64_t(p.n1max[p.active[a]]) * L2;
     p.v2_off[a] = p.v2_tot;
-    p.v2_tot += int64_t(p.n_beta2) * p.R_out * L2;
+    p.v2_tot += int64_t(p.rows2) * L2;
     // Unpooled in time, the second-order blocks are V2 itself.
-    p.phi2_off[a] = p.phi2_base + (p.unpooled_t ? p.v2_off[a] : int64_t(a) * p.n_beta2 * per_path);
+    p.phi2_off[a] = p.phi2_base + (p.unpooled_t ? p.v2_off[a] : int64_t(a) * p.rows2 * p.n_frames);
   }
-  p.phi_size = p.phi2_base + (p.unpooled_t ? p.v2_tot : int64_t(p.n_active) * p.n_beta2 * per_path);
+  p.phi_size = p.phi2_base + (p.unpooled_t ? p.v2_tot : int64_t(p.n_active) * p.rows2 * p.n_frames);
 
   // Time-pooling taps g_s[t] = 2^s phi_T[2^s t] for every level s <= log2 T,
   // where phi_T[tau] = (1/N) sum_m phi_hat_T(m/N) e^{2 pi i m tau / N}
@@ -375,9 +381,11 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
     }
   }
   // Chunks of frequential filters with equal stride level.
+  int kmax = p.lF;
+  for (int b = 0; b < p.n_beta2; ++b) kmax = std::max(kmax, p.beta_k[b]);
   auto make_chunks = [&](int nb, std::vector<FreqChunk>& out) {
     out.clear();
-    for (int k = 0; k <= p.lF; ++k) {
+    for (int k = 0; k <= kmax; ++k) {
       const int cap = std::min(16, 1 << k);
       FreqChunk c{};
       c.k = k;
@@ -416,7 +424,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   p.pool_tiles.clear();
   p.pool_tiles2.clear();
   if (!p.unpooled_t) {
-    const int rows = p.n_beta2 * p.R_out;
+    const int rows = p.rows2;
     for (int b = 0; b < B; ++b)
       for (int a = 0; a < p.n_active; ++a) {
         const int L = static_cast<int>(N >> p.s2[a]);
@@ -430,7 +438,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   }
   p.pool_band_tiles.clear();
   if (!p.unpooled_t) {
-    const int rows = p.n_beta2 * p.R_out;
+    const int rows = p.rows2;
     for (int b = 0; b < B; ++b)
       for (int a = 0; a < p.n_active; ++a) {
         if (!p.pool_w[a]) continue;
@@ -442,7 +450,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
     p.pool_fwd_tiles[si].clear();
     p.pool_tile0[si].clear();
     if (p.unpooled_t) continue;
-    const int rows = p.n_beta2 * p.R_out;
+    const int rows = p.rows2;
     for (int b = 0; b < B; ++b)
       for (int a = 0; a < p.n_active; ++a) {
         const int L = static_cast<int>(N >> p.s2[a]);
@@ -538,6 +546,7 @@ int upload_plan(Plan& p) {
   const size_t o_act = put(act_n2.data(), act_n2.size() * sizeof(int));
   const size_t o_tapo = put(p.tap_off.data(), p.tap_off.size() * sizeof(int64_t));
   const size_t o_cin = put(p.h_cinit.data(), p.h_cinit.size() * sizeof(float));
+  const size_t o_roff = put(p.row_off.data(), p.row_off.size() * sizeof(int));
 
   if (cudaGetDevice(&p.device) != cudaSuccess) return JTFS_ERR_CUDA;
   void* blob = nullptr;
@@ -583,6 +592,7 @@ int upload_plan(Plan& p) {
   p.d_act_n2 = reinterpret_cast<const int*>(at(o_act));
   p.d_tap_off = reinterpret_cast<const int64_t*>(at(o_tapo));
   p.d_cinit = reinterpret_cast<const float*>(at(o_cin));
+  p.d_row_off = reinterpret_cast<const int*>(at(o_roff));
   p.on_device = true;
   return tc_upload(p);
 }

@@ -16,10 +16,10 @@ TOL = 1e-4
 
 CASES = {
     "tiny_n256": dict(N=256, J=4, Q=4, Q2=1, J_fr=2, Q_fr=1, T=16, F=2),
-    "tiny_n512_q3": dict(N=512, J=5, Q=3, Q2=2, J_fr=2, Q_fr=2, T=32, F=3),
+    "tiny_n512_q3": dict(N=512, J=5, Q=3, Q2=2, J_fr=2, Q_fr=2, T=32, F=3),    # phi_F stride 2 > log2 F
     "tones8k_n8192": dict(N=2 ** 13, J=6, Q=8, Q2=1, J_fr=3, Q_fr=1, T=64, F=4),
 }
-MODES = {"time": (False, True)}
+MODES = {"time": (False, True), "freq": (True, False), "both": (False, False)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -76,3 +76,20 @@ def test_time_unpooled_refuses_rows_beyond_the_time_stride():
     from paper_2602_11896_gb300 import JTFSPlan
     with pytest.raises(RuntimeError):
         JTFSPlan(N=256, J=5, Q=2, Q2=1, J_fr=2, Q_fr=1, T=8, F=4, average_local=False)
+
+
+def test_freq_unpooled_chirp_batch_sampled():
+    """The chirp plan (8 x 2^16) unpooled along n1: one sampled clip's first-order block and two
+    second-order blocks against the oracle (the generic frequential kernels at full size)."""
+    from workloads import get_workload
+    wl = get_workload("chirps22k_b8_n65536")
+    plan, op = _plans(wl.params, (True, False), 2)
+    x = _inputs(op.N, 2, 51)
+    phi = plan.forward(torch.tensor(x, device="cuda")).cpu().numpy()
+    sel = [0, len(op.active) - 1]
+    ref = O.jtfs(torch.tensor(x[1:2]), op, active=sel)
+    g = O.phi_blocks(torch.tensor(phi[1:2], dtype=torch.float64), op)
+    assert _rel(g["S0"], ref["S0"]) <= TOL
+    assert _rel(g["first"], ref["Phi1"].reshape(1, -1)) <= TOL
+    for a in sel:
+        assert _rel(g[f"n2={op.active[a]}"], ref["Phi2_sel"][a].reshape(1, -1)) <= TOL, a
