@@ -73,6 +73,9 @@ def parse():
                          "reconstruct: the paper's coloured-noise start and bold-driver momentum against "
                          "white-noise Adam on the chirp batch, 200 evaluations each; "
                          "reflect: the chirp batch with mirror padding on both sides")
+    ap.add_argument("--unpooled", default="none", choices=list(VARIANTS),
+                    help="chirps workload only: unpooled outputs (average_local / average_local_fr off): "
+                         "time, freq or both")
     ap.add_argument("--batch", type=int, default=0,
                     help="clips per GPU (default: the workload's 8); smaller values only for ncu captures")
     return ap.parse_args()
@@ -89,17 +92,19 @@ def _lg(n):
 def freq_flops_per_column(plan, adjoint: bool) -> float:
     info = plan.info
     Nfr, Rout, lF = info["N_fr"], info["R_out"], info["log2_F"]
+    pooled = getattr(plan, "average_local_fr", True)
+    cap = (lambda j: min(int(j), lF)) if pooled else int
     _, _, jf = plan.filters(2)
     _, _, jl = plan.filters(3)
-    ks = [min(int(jl[1]), lF)] + [min(int(j), lF) for j in jf] * 2
+    ks = [cap(jl[1])] + [cap(j) for j in jf] * 2
     f = 5 * Nfr * _lg(Nfr)
     for k in ks:
         R = Nfr >> k
+        pool = 2.5 * R * _lg(R) + 2 * R + 2.5 * Rout * _lg(Rout) if pooled else 0.0   # phi_F and its adjoint
         if not adjoint:
-            f += 2 * Nfr + 5 * R * _lg(R) + 3 * R + 2.5 * R * _lg(R) + 2 * R + 2.5 * Rout * _lg(Rout)
+            f += 2 * Nfr + 5 * R * _lg(R) + 3 * R + pool
         else:
-            f += (2 * Nfr + 5 * R * _lg(R) + 2.5 * Rout * _lg(Rout) + 2 * R + 2.5 * R * _lg(R)
-                  + 6 * R + 5 * R * _lg(R) + 2 * Nfr)
+            f += 2 * Nfr + 5 * R * _lg(R) + pool + 6 * R + 5 * R * _lg(R) + 2 * Nfr
     if adjoint:
         f += 5 * Nfr * _lg(Nfr)
     return f
@@ -220,9 +225,19 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # Reference arm: the FP64 oracle on the host cores.
 # ---------------------------------------------------------------------------
+# Output variant of the chirp step (--unpooled): average_local, average_local_fr.
+VARIANTS = {"none": (True, True), "time": (False, True), "freq": (True, False), "both": (False, False)}
+VARIANT = {"name": "none"}
+
+
+def variant_kw():
+    al, alf = VARIANTS[VARIANT["name"]]
+    return dict(average_local=al, average_local_fr=alf)
+
+
 def oracle_clip_seconds(wl, clip: int):
     from oracle import jtfs_oracle as O
-    ref = O.Plan(**wl.params)
+    ref = O.Plan(**wl.params, **variant_kw())
     y = torch.tensor(wl.inits()[clip:clip + 1], dtype=torch.float64)
     tgt = O.jtfs(torch.tensor(wl.targets()[clip:clip + 1], dtype=torch.float64), ref)["phi"]
     t0 = time.perf_counter()
@@ -233,7 +248,7 @@ def oracle_clip_seconds(wl, clip: int):
 def run_reference(args, wl):
     from oracle import jtfs_oracle as O
     small = get_workload("tones8k_n8192")
-    sp = O.Plan(**small.params)
+    sp = O.Plan(**small.params, **variant_kw())
     ys = torch.tensor(small.inits(), dtype=torch.float64)
     ts = O.jtfs(torch.tensor(small.targets(), dtype=torch.float64), sp)["phi"]
     for _ in range(args.warmup):
@@ -256,11 +271,17 @@ def run_reference(args, wl):
 
 
 def config_dict(wl):
-    return {"workload": wl.name, "batch": wl.batch, "N": wl.N, "J": wl.J, "Q": wl.Q, "Q2": wl.Q2,
-            "J_fr": wl.J_fr, "Q_fr": wl.Q_fr, "T": wl.T, "F": wl.F, "sample_rate_hz": wl.sr,
-            "step": "metamer_step: JTFS forward + loss + hand-written adjoint + Adam (lr 0.1)",
-            "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written between timed steps (outside the events)",
-            "parallelism": "replicas (independent clips per GPU)"}
+    cfg = {"workload": wl.name, "batch": wl.batch, "N": wl.N, "J": wl.J, "Q": wl.Q, "Q2": wl.Q2,
+           "J_fr": wl.J_fr, "Q_fr": wl.Q_fr, "T": wl.T, "F": wl.F, "sample_rate_hz": wl.sr,
+           "step": "metamer_step: JTFS forward + loss + hand-written adjoint + Adam (lr 0.1)",
+           "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written between timed steps (outside the events)",
+           "parallelism": "replicas (independent clips per GPU)"}
+    if VARIANT["name"] != "none":
+        cfg["workload"] = f"{wl.name}_unpooled_{VARIANT['name']}"
+        cfg["outputs"] = {"time": "second order at stride 2^j2 without phi_T, zeroth order = x",
+                          "freq": "frequential stride 2^j without phi_F",
+                          "both": "no phi_T on the second order and no phi_F"}[VARIANT["name"]]
+    return cfg
 
 
 # ---------------------------------------------------------------------------
@@ -559,6 +580,7 @@ def run_decoder(args):
 
 def main():
     args = parse()
+    VARIANT["name"] = args.unpooled
     if args.workload == "long":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the chirps workload"}))
@@ -617,7 +639,7 @@ def main():
                                  init_seeds=wl.init_seeds[:args.batch])
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    plan = JTFSPlan(**wl.params, batch=wl.batch)
+    plan = JTFSPlan(**wl.params, batch=wl.batch, **variant_kw())
     seed_off = 1000 * rank
     targets = wl.targets() if rank == 0 else None
     if rank != 0:
@@ -707,7 +729,7 @@ def main():
         flops = tc_tensor_flops(plan, adjoint=adj)
         ach = flops / (launch_ms / 1e3) / 1e12
         peak, peak_src = bf16_peak()
-        per_clip = (DRAM_BYTES_PER_CLIP or {}).get(5 if adj else 4)
+        per_clip = (DRAM_BYTES_PER_CLIP or {}).get(5 if adj else 4) if VARIANT["name"] == "none" else None
         roofline = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": per_clip * wl.batch if per_clip is not None else None,
                     "traffic_note": "ncu dram bytes of the 1-clip capture x clips per launch",
@@ -721,7 +743,7 @@ def main():
         cols = columns_per_launch(plan) - wl.batch * sum(L2 for _, L2 in (tc_groups(plan) if tuning[3] else []))
         flops = freq_flops_per_column(plan, adjoint=adj) * cols
         ach = flops / (launch_ms / 1e3) / 1e12
-        per_clip = (DRAM_BYTES_PER_CLIP or {}).get(1 if adj else 0)
+        per_clip = (DRAM_BYTES_PER_CLIP or {}).get(1 if adj else 0) if VARIANT["name"] == "none" else None
         roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP32_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
                     "traffic": per_clip * wl.batch if per_clip is not None else None,

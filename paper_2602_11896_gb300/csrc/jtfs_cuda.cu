@@ -1258,6 +1258,47 @@ k_loss(const float* __restrict__ phi, const float* __restrict__ tgt, float* __re
   if (threadIdx.x == 0) loss[b] = static_cast<float>(red[0]);
 }
 
+// Large Phi: the same loss over `parts` CTAs per clip.  Part j of clip b
+// sums entries [j chunk, (j+1) chunk) into part_sum[b][j] (double, fixed
+// order); k_loss_sum then adds the parts of each clip in a fixed order.
+__global__ void __launch_bounds__(512)
+k_loss_part(const float* __restrict__ phi, const float* __restrict__ tgt, float* __restrict__ dphi,
+            double* __restrict__ part_sum, int64_t size, int64_t chunk) {
+  __shared__ double red[512];
+  const int b = blockIdx.y;
+  const int64_t lo = static_cast<int64_t>(blockIdx.x) * chunk, hi = min(size, lo + chunk);
+  const float* p = phi + static_cast<int64_t>(b) * size;
+  const float* t = tgt + static_cast<int64_t>(b) * size;
+  double acc = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const float d = p[i] - t[i];
+    if (dphi) dphi[static_cast<int64_t>(b) * size + i] = 2.f * d;
+    acc += static_cast<double>(d) * d;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part_sum[static_cast<int64_t>(b) * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(256)
+k_loss_sum(const double* __restrict__ part_sum, float* __restrict__ loss, int parts) {
+  __shared__ double red[256];
+  const double* ps = part_sum + static_cast<int64_t>(blockIdx.x) * parts;
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < parts; j += blockDim.x) acc += ps[j];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[blockIdx.x] = static_cast<float>(red[0]);
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_adam(float* __restrict__ y, float* __restrict__ m, float* __restrict__ v, const float* __restrict__ g,
        int64_t n, float lr, float c1, float c2) {
@@ -1373,6 +1414,7 @@ k_momentum(float* __restrict__ y, float* __restrict__ u, float* __restrict__ g_a
 struct Bufs {
   float2 *Xh, *U1h, *Zs, *dS1h, *Y2, *dY2, *dXh, *dS0h, *scr;
   float *S1, *V2, *phi, *dphi, *dy, *part;
+  double* lossp;
 };
 
 Bufs bufs(const Plan& p, void* ws) {
@@ -1393,6 +1435,7 @@ Bufs bufs(const Plan& p, void* ws) {
   w.dy = reinterpret_cast<float*>(c + p.ws_dy);
   w.scr = reinterpret_cast<float2*>(c + p.ws_scr);
   w.part = reinterpret_cast<float*>(c + p.ws_part);
+  w.lossp = reinterpret_cast<double*>(c + p.ws_lossp);
   return w;
 }
 
@@ -1869,7 +1912,15 @@ extern "C" int jtfs_loss_grad(jtfs_plan_t plan, const float* y, const float* phi
   const Bufs w = jtfs::bufs(p, workspace);
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   JTFS_TRY(jtfs::forward_stages(p, y, w.phi, w, true, s));
-  jtfs::k_loss<<<p.batch, 512, 0, s>>>(w.phi, phi_target, dy ? w.dphi : nullptr, loss, p.phi_size);
+  if (p.loss_parts <= 1) {
+    jtfs::k_loss<<<p.batch, 512, 0, s>>>(w.phi, phi_target, dy ? w.dphi : nullptr, loss, p.phi_size);
+  } else {
+    const int64_t chunk = (p.phi_size + p.loss_parts - 1) / p.loss_parts;
+    jtfs::k_loss_part<<<dim3(p.loss_parts, p.batch), 512, 0, s>>>(w.phi, phi_target, dy ? w.dphi : nullptr,
+                                                                  w.lossp, p.phi_size, chunk);
+    JTFS_TRY(jtfs::check_launch());
+    jtfs::k_loss_sum<<<p.batch, 256, 0, s>>>(w.lossp, loss, p.loss_parts);
+  }
   JTFS_TRY(jtfs::check_launch());
   if (!dy) return JTFS_OK;
   return jtfs::backward_stages(p, w.dphi, dy, w, s);
@@ -1947,8 +1998,8 @@ extern "C" int64_t jtfs_launch_count(jtfs_plan_t plan, int call) {
   switch (call) {
     case 0: return jtfs::forward_launches(p, true);
     case 1: return jtfs::forward_launches(p, false) + jtfs::backward_launches(p);
-    case 2: return jtfs::forward_launches(p, true) + 1 + jtfs::backward_launches(p);
-    case 3: return jtfs::forward_launches(p, true) + 2 + jtfs::backward_launches(p);
+    case 2: return jtfs::forward_launches(p, true) + (p.loss_parts > 1 ? 2 : 1) + jtfs::backward_launches(p);
+    case 3: return jtfs::forward_launches(p, true) + (p.loss_parts > 1 ? 3 : 2) + jtfs::backward_launches(p);
     default: return JTFS_ERR_ARG;
   }
 }

@@ -148,7 +148,8 @@ struct Plan {
   // Workspace layout (byte offsets).
   size_t ws_Xh = 0, ws_U1h = 0, ws_Zs = 0, ws_S1 = 0, ws_dS1h = 0, ws_Y2 = 0,
          ws_dY2 = 0, ws_V2 = 0, ws_phi = 0, ws_dphi = 0, ws_scr = 0,
-         ws_dXh = 0, ws_dS0h = 0, ws_dy = 0, ws_part = 0, ws_bytes = 0;
+         ws_dXh = 0, ws_dS0h = 0, ws_dy = 0, ws_part = 0, ws_lossp = 0, ws_bytes = 0;
+  int loss_parts = 1;  // CTAs per clip of the loss reduction (large Phi: several)
   int64_t scr_elems = 0;  // four-step scratch, complex elements
 
   // Launch descriptions.

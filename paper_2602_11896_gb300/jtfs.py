@@ -53,6 +53,8 @@ class JTFSPlan:
         self._h = h
         self._lib = lib
         self.host_only = host_only
+        self.average_local = average_local
+        self.average_local_fr = average_local_fr
         buf = (c_int64 * len(INFO_KEYS))()
         n = lib.jtfs_plan_info(h, buf, len(INFO_KEYS))
         if n < len(INFO_KEYS):
