@@ -1573,8 +1573,7 @@ int64_t forward_launches(const Plan& p, bool full) {
 
 int64_t backward_launches(const Plan& p) {
   int64_t n = 1 + fft_launches(p.L_ds1) + static_cast<int64_t>(p.L_u1inplace.size()) +
-              2 * fft_launches(p.L_u1inplace) + fft_launches(p.L_u1) + (p.unpooled_t ? 1 : fft_launches(p.L_ds0)) +
-              1 + fft_launches(p.L_x);
+              2 * fft_launches(p.L_u1inplace) + (p.unpooled_t ? 1 : fft_launches(p.L_ds0)) + 1 + fft_launches(p.L_x);
   if (p.n_active > 0) n += 1 + freq2_launches(p) + fft_launches(p.L_y2inplace);
   return n;
 }
@@ -1599,9 +1598,11 @@ size_t ct_smem(const Plan& p, int nbuf, int cols, FreqArgs& A) {
 // Forward stages.  `full` = false stops after what the adjoint needs
 // (Xhat, U1hat, S1, Y2) and skips writing Phi.
 int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, bool full, cudaStream_t s) {
+  // The band signals x * psi_n1 (decimated) stay in Zs for the adjoint's
+  // modulus derivative; U1h receives the FFT of their modulus.
   JTFS_TRY((run_fft<false>(p, p.L_x, LdReal{x}, StC{w.Xh}, w.scr, s)));
-  JTFS_TRY((run_fft<true>(p, p.L_u1, LdBand{w.Xh, p.d_psi1, FiltD{}}, StC{w.U1h}, w.scr, s)));
-  JTFS_TRY((run_fft<false>(p, p.L_u1inplace, LdMod{w.U1h}, StC{w.U1h}, w.scr, s)));
+  JTFS_TRY((run_fft<true>(p, p.L_u1, LdBand{w.Xh, p.d_psi1, FiltD{}}, StC{w.Zs}, w.scr, s)));
+  JTFS_TRY((run_fft<false>(p, p.L_u1inplace, LdMod{w.Zs}, StC{w.U1h}, w.scr, s)));
   if (full) {
     if (p.unpooled_t)  // zeroth order = x
       JTFS_TRY(copy_block(p, x, p.N, 0, phi, p.phi_size, 0, p.N, false, s));
@@ -1696,7 +1697,7 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
 }
 
 // Backward stages from dphi (device, [batch][phi_size]) to dx.  Requires
-// forward_stages(full or not) to have filled Xh, U1h, S1 and Y2.
+// forward_stages(full or not) to have filled Zs, U1h, S1 and Y2.
 int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, cudaStream_t s) {
   const FreqArgs FA = freq_args(p, 1);
   const FreqArgs FA2 = freq_args(p, 2);
@@ -1744,7 +1745,6 @@ int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, 
     JTFS_TRY(check_launch());
   }
   JTFS_TRY((run_fft<true>(p, p.L_u1inplace, LdC{w.U1h}, StC{w.U1h}, w.scr, s)));
-  JTFS_TRY((run_fft<true>(p, p.L_u1, LdBand{w.Xh, p.d_psi1, FiltD{}}, StC{w.Zs}, w.scr, s)));
   JTFS_TRY((run_fft<false>(p, p.L_u1inplace, LdDz{w.U1h, w.Zs}, StC{w.Zs}, w.scr, s)));
   if (!p.unpooled_t) JTFS_TRY((run_fft<false>(p, p.L_ds0, LdReal{dphi}, StC{w.dS0h}, w.scr, s)));
   {

@@ -487,9 +487,9 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   p.ws_dy = take(size_t(B) * N * f4);
   p.ws_scr = take(size_t(std::max<int64_t>(p.scr_elems, 1)) * c8);
   p.ws_part = take(std::max<size_t>(p.pool_fwd_tiles[0].size(), 1) * 64 * p.n_frames * f4);
-  // Loss reduction: one CTA per clip up to 2^20 Phi entries, else one per 2^18 (at most 1024).
-  p.loss_parts = p.phi_size <= (int64_t(1) << 20)
-                     ? 1 : static_cast<int>(std::min<int64_t>(1024, (p.phi_size + (1 << 18) - 1) >> 18));
+  // Loss reduction: one CTA per clip up to 2^15 Phi entries, else one per 2^13 (at most 1024).
+  p.loss_parts = p.phi_size <= (int64_t(1) << 15)
+                     ? 1 : static_cast<int>(std::min<int64_t>(1024, (p.phi_size + (1 << 13) - 1) >> 13));
   p.ws_lossp = take(size_t(B) * p.loss_parts * sizeof(double));
   p.ws_bytes = o;
   tc_build(p);
