@@ -159,7 +159,7 @@ constexpr int kGrp = 256;                 // threads per epilogue group
 constexpr int kEpiAll = 2 * kGrp;         // epilogue threads
 constexpr int kWarpTma = 16, kWarpG1 = 17, kWarpG2 = 18, kWarpG3 = 19;
 
-__device__ __forceinline__ void init_barriers(TcCtl* ctl) {
+__device__ __forceinline__ void init_barriers(TcCtl* ctl, int n_epi) {
   for (int s = 0; s < 8; ++s) {
     mbar_init(smem_u32(&ctl->b1_full[s]), 1);
     mbar_init(smem_u32(&ctl->b1_empty[s]), 1);
@@ -180,7 +180,7 @@ __device__ __forceinline__ void init_barriers(TcCtl* ctl) {
     mbar_init(smem_u32(&ctl->dv_full[s]), kGrp);
     mbar_init(smem_u32(&ctl->dv_empty[s]), 1);
   }
-  mbar_init(smem_u32(&ctl->a1_full), kEpiAll);
+  mbar_init(smem_u32(&ctl->a1_full), n_epi);
   mbar_init(smem_u32(&ctl->d3_full), 1);
   for (int s = 0; s < 3; ++s) mbar_init(smem_u32(&ctl->drain[s]), 1);
   ctl->abort = 0;
@@ -248,7 +248,11 @@ __device__ __forceinline__ TcChunk ld_chunk(const TcChunk* p, int i, int n) {
 // packed in each 128-byte row), A2 2 x 16 KB (|Z| hi|lo packed, one per group).
 // TMEM: D1 2 x 64 columns at 0, D2 2 x 32 columns at 128.
 // ---------------------------------------------------------------------------
-constexpr int kTcFwdThreads = 19 * 32;
+// Forward threads with NG epilogue groups: 8 NG epilogue warps, then the TMA
+// warp and the two issuing warps.  NG = 1 runs two CTAs per SM (two
+// independent hand-off chains per SM instead of two groups in one CTA).
+template <int NG>
+constexpr int tc_fwd_threads() { return (8 * NG + 3) * 32; }
 constexpr int kTcAdjThreads = 20 * 32;
 
 template <int KA, int S1>
@@ -256,9 +260,10 @@ constexpr size_t tc_fwd_smem() {
   return sizeof(TcCtl) + 1024 + size_t(KA) * 32768 + size_t(S1) * 16384 + size_t(kS2) * 4096 + 2 * 16384;
 }
 
-template <int KA, int S1>
-__global__ void __launch_bounds__(kTcFwdThreads, 1)
+template <int KA, int S1, int NG>
+__global__ void __launch_bounds__(tc_fwd_threads<NG>(), NG == 1 ? 2 : 1)
 k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2, const TcArgs A) {
+  constexpr int wTma = 8 * NG, wG1 = wTma + 1, wG2 = wTma + 2;
   extern __shared__ uint8_t smem_raw[];
   TcCtl* ctl = reinterpret_cast<TcCtl*>(smem_raw);
   const uint32_t base = (smem_u32(smem_raw) + sizeof(TcCtl) + 1023u) & ~1023u;
@@ -272,8 +277,8 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
   const int ks1 = (2 * n1m + 15) >> 4;
   const int nch = A.n_chunks, RO = A.RO;
   volatile int* abort = &ctl->abort;
-  if (threadIdx.x == 0) init_barriers(ctl);
-  if (warp == kWarpG1) tmem_alloc(smem_u32(&ctl->tmem), 256);
+  if (threadIdx.x == 0) init_barriers(ctl, kGrp * NG);
+  if (warp == wG1) tmem_alloc(smem_u32(&ctl->tmem), 256);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -281,7 +286,7 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
   int n1 = 0, n2 = 0;  // TMA stages issued (producer)
   bool issued = false;
 
-  if (warp == kWarpTma) {
+  if (warp == wTma) {
     if (lane == 0) {
       TcChunk nx = ld_chunk(A.chunks, 0, nch);
       bool ok = load_b1<S1>(ctl, &tmB1, nx, ks1, A.nr1, sB1, n1, abort);
@@ -299,7 +304,7 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         cur = nx;
       }
     }
-  } else if (warp == kWarpG1) {
+  } else if (warp == wG1) {
     if (lane == 0) {  // GEMM1: D1[i & 1] = Y . B1 (chunk i)
       issued = true;
       int c1 = 0;
@@ -318,7 +323,7 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         umma_commit(smem_u32(&ctl->d1_full[j]));
       }
     }
-  } else if (warp == kWarpG2) {
+  } else if (warp == wG2) {
     if (lane == 0) {  // GEMM2: D2[beta & 1] += |Z| . P^T (chunk i)
       issued = true;
       int c2 = 0;
@@ -346,7 +351,7 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         ++c2;
       }
     }
-  } else if (warp < kWarpTma) {
+  } else if (warp < wTma) {
     // Epilogue groups.
     const int g = warp >> 3, q = warp & 3, h = (warp >> 2) & 1;
     const int c = q * 32 + lane;
@@ -354,7 +359,7 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
     const bool colok = c < tl.ncols;
     const int L2 = 1 << (A.logN - A.s2[tl.a]);
     float* vdst = A.V2 + int64_t(tl.b) * A.v2_tot + A.v2_off[tl.a] + tl.t0 + c;
-    load_a1<KA>(A, tl, n1m, ks1, sA1, c, (warp >> 2) & 3, 4);
+    load_a1<KA>(A, tl, n1m, ks1, sA1, c, (warp >> 2) & (2 * NG - 1), 2 * NG);
     fence_proxy_async();
     mbar_arrive(smem_u32(&ctl->a1_full));
     auto store_v2 = [&](int beta) -> bool {
@@ -390,9 +395,9 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
       return true;
     };
     TcChunk nx = ld_chunk(A.chunks, g, nch);
-    for (int i = g; i < nch; i += 2) {
+    for (int i = g; i < nch; i += NG) {
       const TcChunk ch = nx;
-      nx = ld_chunk(A.chunks, i + 2, nch);
+      nx = ld_chunk(A.chunks, i + NG, nch);
       const int j = i & 1;
       if (!wait_warp(smem_u32(&ctl->d1_full[j]), (i >> 1) & 1, abort)) break;
       tc_fence_after();
@@ -437,19 +442,19 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
   }
 
   // Teardown: no TMA copy or MMA of this CTA may be in flight when it exits.
-  if (warp == kWarpTma && lane == 0 && *abort) {
+  if (warp == wTma && lane == 0 && *abort) {
     for (int t = max(0, n1 - S1); t < n1; ++t) mbar_wait_drain(smem_u32(&ctl->b1_full[t % S1]), (t / S1) & 1);
     for (int t = max(0, n2 - kS2); t < n2; ++t) mbar_wait_drain(smem_u32(&ctl->b2_full[t % kS2]), (t / kS2) & 1);
   }
-  if ((warp == kWarpG1 || warp == kWarpG2) && lane == 0 && issued) {
-    const uint32_t dr = smem_u32(&ctl->drain[warp - kWarpG1]);
+  if ((warp == wG1 || warp == wG2) && lane == 0 && issued) {
+    const uint32_t dr = smem_u32(&ctl->drain[warp - wG1]);
     umma_commit(dr);
     mbar_wait_drain(dr, 0);
   }
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && *abort) atomicExch(&g_tc_err, 1);
-  if (warp == kWarpG1) {
+  if (warp == wG1) {
     __syncwarp();
     tmem_dealloc(tmem, 256);
   }
@@ -491,7 +496,7 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
   const int nch = A.n_chunks, RO = A.RO;
   const int nbeta = ld_chunk(A.chunks, nch - 1, nch).beta + 1;
   volatile int* abort = &ctl->abort;
-  if (threadIdx.x == 0) init_barriers(ctl);
+  if (threadIdx.x == 0) init_barriers(ctl, kEpiAll);
   if (warp == kWarpG1) tmem_alloc(smem_u32(&ctl->tmem), 512);
   tc_fence_before();
   __syncthreads();
@@ -793,7 +798,7 @@ void split_bf16(double v, uint16_t& hi, uint16_t& lo) {
   lo = bf16_rn(static_cast<float>(v - double(bf16_f(hi))));
 }
 
-constexpr int kFwdS1[2] = {8, 6};
+constexpr int kFwdS1[2] = {2, 6};  // n1max <= 32: two CTAs per SM, so a 2-stage table ring
 constexpr int kAdjS1[2] = {3, 3}, kAdjS3[2] = {2, 2}, kAdjNA3[2] = {2, 1};
 
 PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
@@ -1031,17 +1036,18 @@ int tc_forward(const Plan& p, const float2* Y2, float* V2, cudaStream_t s) {
   A.V2 = V2;
   if (!p.tc_tiles[0].empty()) {
     constexpr size_t smem = tc_fwd_smem<1, kFwdS1[0]>();
-    if (tc_opt_in<k_freq_tc_fwd<1, kFwdS1[0]>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
+    static_assert(2 * (smem + 1024) <= 228 * 1024, "two forward CTAs per SM");
+    if (tc_opt_in<k_freq_tc_fwd<1, kFwdS1[0], 1>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
     A.tiles = p.d_tc_tiles[0];
-    k_freq_tc_fwd<1, kFwdS1[0]><<<static_cast<unsigned>(p.tc_tiles[0].size()), kTcFwdThreads, smem, s>>>(
+    k_freq_tc_fwd<1, kFwdS1[0], 1><<<static_cast<unsigned>(p.tc_tiles[0].size()), tc_fwd_threads<1>(), smem, s>>>(
         p.tc_map[0], p.tc_map[1], A);
     if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
   }
   if (!p.tc_tiles[1].empty()) {
     constexpr size_t smem = tc_fwd_smem<2, kFwdS1[1]>();
-    if (tc_opt_in<k_freq_tc_fwd<2, kFwdS1[1]>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
+    if (tc_opt_in<k_freq_tc_fwd<2, kFwdS1[1], 2>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
     A.tiles = p.d_tc_tiles[1];
-    k_freq_tc_fwd<2, kFwdS1[1]><<<static_cast<unsigned>(p.tc_tiles[1].size()), kTcFwdThreads, smem, s>>>(
+    k_freq_tc_fwd<2, kFwdS1[1], 2><<<static_cast<unsigned>(p.tc_tiles[1].size()), tc_fwd_threads<2>(), smem, s>>>(
         p.tc_map[0], p.tc_map[1], A);
     if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
   }
