@@ -42,7 +42,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # stage (0 / 1: FFT forward / adjoint of the groups they keep, 4 / 5: tensor-core forward / adjoint),
 # from an ncu capture of the 1-clip case of this workload (traffic scales with the clips processed).
 # Valid for the kernel versions it was taken on; emptied when those kernels change.
-DRAM_BYTES_PER_CLIP = {}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one clip's launches of each stage (the tensor-core
+# frequential forward = 4 and adjoint = 5, both kernels of a stage summed), from the capture summarised in
+# profiles/top_kernels_chirps22k_b1_n65536.md; the traffic of a launch grows with the clips it processes.
+DRAM_BYTES_PER_CLIP = {4: 102.31936e6, 5: 213.347328e6}
 
 
 def bf16_peak():
