@@ -238,6 +238,27 @@ def variant_kw():
     return dict(average_local=al, average_local_fr=alf)
 
 
+def rank_inputs(wl, rank: int):
+    """(targets, initial iterates) [batch][N] of one rank: rank 0 runs the workload's own seeds, rank r
+    the same recipe with seeds offset by 1000 r (independent clips per GPU: weak scaling, no collective)."""
+    import dataclasses
+    off = 1000 * rank
+    w = dataclasses.replace(wl, target_seeds=[s + off for s in wl.target_seeds],
+                            init_seeds=[s + off for s in wl.init_seeds])
+    return w.targets(), w.inits()
+
+
+def job_throughput(ms_local: float, world: int, clips_per_rank: int, N: int, steps: int, dist=None, device=None):
+    """(slowest rank's ms for `steps` steps, whole-job audio-samples/s): every rank processed
+    clips_per_rank x N samples per step; the job's time is the maximum over ranks."""
+    ms = ms_local
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * clips_per_rank * N * steps / (ms / 1e3)
+
+
 def oracle_clip_seconds(wl, clip: int):
     from oracle import jtfs_oracle as O
     ref = O.Plan(**wl.params, **variant_kw())
@@ -643,14 +664,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     plan = JTFSPlan(**wl.params, batch=wl.batch, **variant_kw())
-    seed_off = 1000 * rank
-    targets = wl.targets() if rank == 0 else None
-    if rank != 0:
-        from workloads import signals
-        targets = np.stack([signals.chirp_am_mix(wl.N, wl.sr, s + seed_off) for s in wl.target_seeds])
-        inits = np.stack([signals.white_noise(wl.N, s + seed_off) for s in wl.init_seeds])
-    else:
-        inits = wl.inits()
+    targets, inits = rank_inputs(wl, rank)
     x = torch.tensor(targets, device=dev)
     y0 = torch.tensor(inits, device=dev)
     phi_t = plan.forward(x)
@@ -703,13 +717,9 @@ def main():
         dist.barrier()
     for st in range(6):
         lib.jtfs_profile_stage(plan._h, st, None, 0)
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = job_throughput(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, wl.batch, wl.N, K,
+                               dist if dist else None, dev)
     ms_per_step = ms / K
-    value = world * wl.batch * wl.N * K / (ms / 1e3)
 
     # Per-stage average launch duration (CUDA events on the library's stream).
     stage_ms = {}
@@ -777,8 +787,8 @@ def main():
         yo_host.copy_(y_dev, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / Ke
-    e2e = {"value": world * wl.batch * wl.N / (e2e_ms / 1e3), "unit": UNIT,
+    e2e_ms, e2e_value = job_throughput(e0.elapsed_time(e1) / Ke, world, wl.batch, wl.N, 1, dist if dist else None, dev)
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(y_host.numel() * 4 + t_host.numel() * 4),
            "d2h_bytes_per_step": int(l_host.numel() * 4 + yo_host.numel() * 4), "ms_per_step": e2e_ms}
 

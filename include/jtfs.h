@@ -299,7 +299,9 @@ typedef struct jtfs_batch_s* jtfs_batch_t;
  * padded to n = next power of two >= L + 2P with p0 = T floor((n-L)/(2T))
  * samples on the left; Phi keeps the ceil(L/T) frames from frame p0/T on, and
  * the gradient sums every mirrored copy back onto its sample.  Padded lengths
- * must stay <= 2^20 (JTFS_ERR_SHAPE otherwise).  Errors as jtfs_plan.
+ * must stay <= 2^20 (JTFS_ERR_SHAPE otherwise).  The unpooled flags are
+ * refused (JTFS_ERR_ARG): the crop indexes Phi as rows x frames.  Errors as
+ * jtfs_plan.
  */
 #define JTFS_BATCH_REFLECT 2u
 int jtfs_batch_create(jtfs_batch_t* out, const int64_t* lengths, int count, int J,

@@ -176,6 +176,8 @@ extern "C" int jtfs_batch_create(jtfs_batch_t* out, const int64_t* lengths, int 
   if (!out || !lengths || count < 1) return JTFS_ERR_ARG;
   *out = nullptr;
   if (T < 2 || (T & (T - 1))) return JTFS_ERR_SHAPE;
+  // The crop and the masked loss index Phi as rows x frames: unpooled layouts are not batched.
+  if (flags & (JTFS_PLAN_UNPOOLED_T | JTFS_PLAN_UNPOOLED_F)) return JTFS_ERR_ARG;
   const bool refl = (flags & JTFS_BATCH_REFLECT) != 0;
   flags &= ~JTFS_BATCH_REFLECT;
   jtfs_batch_s* b = new (std::nothrow) jtfs_batch_s();

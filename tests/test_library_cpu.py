@@ -118,3 +118,13 @@ def test_reflect_batch_layout_matches_oracle():
         assert b.phi_offsets[i + 1] - b.phi_offsets[i] == want
     with pytest.raises(RuntimeError):
         JTFSBatch([2 ** 20], **params, host_only=True, boundary="reflect")
+
+
+def test_batch_refuses_unpooled_flags():
+    """Ragged batches crop Phi as rows x frames, so the unpooled layouts are refused."""
+    lib = _native.load()
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int64 * 2)(300, 500)
+    for flag in (_native.PLAN_UNPOOLED_T, _native.PLAN_UNPOOLED_F):
+        rc = lib.jtfs_batch_create(ctypes.byref(h), arr, 2, 4, 4, 1, 2, 1, 16, 2, _native.PLAN_HOST_ONLY | flag)
+        assert rc == -1 and not h.value
