@@ -25,28 +25,25 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank_main(rank, world, port, out):
+def _rank_main(rank, world, port, out_dir):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         ms_local = [120.0, 150.0][rank]                       # rank 1 is the slower one
         ms, value = bench.job_throughput(ms_local, world, 8, 65536, 10, dist)
         dist.barrier()
-        out[rank] = (ms, value)
+        np.save(os.path.join(out_dir, f"rank{rank}.npy"), np.array([ms, value]))
     finally:
         dist.destroy_process_group()
 
 
-def test_job_throughput_is_max_over_two_gloo_ranks():
+def test_job_throughput_is_max_over_two_gloo_ranks(tmp_path):
     world = 2
-    with mp.Manager() as mgr:
-        out = mgr.dict()
-        mp.spawn(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
-        res = dict(out)
+    mp.spawn(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
     want_ms = 150.0
     want = world * 8 * 65536 * 10 / (want_ms / 1e3)
     for rank in range(world):
-        ms, value = res[rank]
+        ms, value = np.load(tmp_path / f"rank{rank}.npy")
         assert ms == want_ms
         assert value == pytest.approx(want, rel=1e-12)
 
