@@ -807,7 +807,7 @@ def main():
                 "gpu_launches": int(lib.jtfs_launch_count(plan._h, 3)) * K,
                 "clocks": clk, "wall_s_timed": t_wall,
                 "tuning": {"wide_forward_tiles": tuning[0], "pool_split": tuning[1], "fft_points_per_cta": tuning[2],
-                           "tensor_core_frequential": tuning[3]},
+                           "tensor_core_frequential": tuning[3], "tensor_core_pooling": tuning[4]},
                 "metamer_loss": {"first_timed_step": float(hist[0].mean().item()),
                                  "last_timed_step": float(hist[-1].mean().item()),
                                  "adam_steps_before_last": args.warmup + K - 1}}

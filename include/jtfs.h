@@ -332,7 +332,7 @@ int jtfs_batch_metamer_step(jtfs_batch_t batch, float* y, const float* phi_targe
                             void* stream);
 
 /*
- * Autotuning.  A plan has four execution choices that change no result
+ * Autotuning.  A plan has five execution choices that change no result
  * beyond rounding:
  *   choice[0]  wide column tiles (1) or narrow ones (0) for the second-order
  *              frequential forward kernel;
@@ -343,15 +343,18 @@ int jtfs_batch_metamer_step(jtfs_batch_t batch, float* y, const float* phi_targe
  *              most 64 rows n1 on the tensor cores (1) or on the FFT kernels
  *              (0); reads 0, and setting 1 has no effect, for plans whose
  *              shape the tensor-core kernels do not handle (R_out not 16 or
- *              32, no such group).  jtfs_set_tuning takes n = 3 (choice[3]
- *              unchanged) or n >= 4.
+ *              32, no such group);
+ *   choice[4]  time pooling of the second order (dense groups) on the tensor
+ *              cores (1) or on the FMA kernels (0); reads 0 for plans whose
+ *              frame count (N / T) is not 32, 64 or 128.
+ * jtfs_set_tuning takes n = 3, 4 or 5 (later choices unchanged).
  * jtfs_autotune times jtfs_loss_grad on the caller's y and phi_target (device
  * arrays as for jtfs_loss_grad; loss [batch] and dy [batch][N] are scratch
  * outputs) for each candidate, one choice at a time, keeps the fastest, and
  * writes the choices to choice[0..n) (host, may be NULL).  It synchronises
  * the stream (it is a set-up call, not a hot-path one).  jtfs_set_tuning
  * applies saved choices; jtfs_get_tuning reads the current ones.  All return
- * the number of choices (4) or an error code.  Not thread-safe with concurrent
+ * the number of choices (5) or an error code.  Not thread-safe with concurrent
  * compute calls on the same plan.
  */
 int jtfs_autotune(jtfs_plan_t plan, const float* y, const float* phi_target,

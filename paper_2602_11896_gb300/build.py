@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libjtfs.so")
 SOURCES = ["jtfs_plan.cpp", "jtfs_cuda.cu", "jtfs_batch.cu", "jtfs_decoder.cu", "jtfs_freq_ct_fwd.cu",
            "jtfs_freq_ct_adj.cu", "jtfs_freq_ct_long_fwd.cu",
-           "jtfs_freq_ct_long_adj.cu", "jtfs_freq_tc.cu"]
+           "jtfs_freq_ct_long_adj.cu", "jtfs_freq_tc.cu", "jtfs_pool_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

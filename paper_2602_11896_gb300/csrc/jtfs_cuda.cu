@@ -1666,7 +1666,10 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
                                                                                             p.d_pool_band_tiles);
         JTFS_TRY(check_launch());
       }
-      if (grid.x && p.n_frames >= 32) {
+      if (grid.x && p.tune_pool_tc && pool_tc_supported(p)) {
+        // Tensor cores: 128 rows x all frames per CTA, partials into the same slots.
+        JTFS_TRY(pool_tc_forward(p, w.V2, w.part, si, s));
+      } else if (grid.x && p.n_frames >= 32) {
         // 16-byte register-blocked kernel: 32, 64 or 128 frames per CTA.
         const int fr = p.n_frames >= 128 ? 128 : p.n_frames >= 64 ? 64 : 32;
         const dim3 g2(grid.x, static_cast<unsigned>((p.n_frames + fr - 1) / fr));
@@ -2010,10 +2013,10 @@ extern "C" int64_t jtfs_launch_count(jtfs_plan_t plan, int call) {
 extern "C" int jtfs_get_tuning(jtfs_plan_t plan, int64_t* choice, int n) {
   if (!plan) return JTFS_ERR_ARG;
   const jtfs::Plan& p = plan->p;
-  const int64_t v[4] = {p.tune_wide, jtfs::kPoolSplits[p.tune_split], p.tune_fft_points,
-                        (p.tc_ok && p.tune_tc) ? 1 : 0};
-  for (int i = 0; i < n && i < 4 && choice; ++i) choice[i] = v[i];
-  return 4;
+  const int64_t v[5] = {p.tune_wide, jtfs::kPoolSplits[p.tune_split], p.tune_fft_points,
+                        (p.tc_ok && p.tune_tc) ? 1 : 0, (p.tune_pool_tc && jtfs::pool_tc_supported(p)) ? 1 : 0};
+  for (int i = 0; i < n && i < 5 && choice; ++i) choice[i] = v[i];
+  return 5;
 }
 
 extern "C" int jtfs_set_tuning(jtfs_plan_t plan, const int64_t* choice, int n) {
@@ -2025,11 +2028,13 @@ extern "C" int jtfs_set_tuning(jtfs_plan_t plan, const int64_t* choice, int n) {
   if ((choice[0] != 0 && choice[0] != 1) || si < 0 || pts < 1024 || pts > 8192 || (pts & (pts - 1))) return JTFS_ERR_ARG;
   const jtfs::Plan& p = plan->p;
   if (n >= 4 && choice[3] != 0 && choice[3] != 1) return JTFS_ERR_ARG;
+  if (n >= 5 && choice[4] != 0 && choice[4] != 1) return JTFS_ERR_ARG;
   p.tune_wide = static_cast<int>(choice[0]);
   p.tune_split = si;
   p.tune_fft_points = static_cast<int>(pts);
   if (n >= 4) p.tune_tc = static_cast<int>(choice[3]);
-  return 4;
+  if (n >= 5) p.tune_pool_tc = static_cast<int>(choice[4]);
+  return 5;
 }
 
 extern "C" int jtfs_autotune(jtfs_plan_t plan, const float* y, const float* phi_target, float* loss, float* dy,
@@ -2068,6 +2073,16 @@ extern "C" int jtfs_autotune(jtfs_plan_t plan, const float* y, const float* phi_
       if (t < best) best = t, best_tc = v;
     }
     p.tune_tc = best_tc;
+  }
+  if (rc == JTFS_OK && jtfs::pool_tc_supported(p)) {
+    float best = 1e30f, t = 0.f;
+    int best_v = p.tune_pool_tc;
+    for (int v : {1, 0}) {
+      p.tune_pool_tc = v;
+      if ((rc = time_it(&t)) != JTFS_OK) break;
+      if (t < best) best = t, best_v = v;
+    }
+    p.tune_pool_tc = best_v;
   }
   if (rc == JTFS_OK) {
     float best = 1e30f, t = 0.f;

@@ -1091,7 +1091,9 @@ extern "C" int jtfs_tc_error(void) {
   if (cudaMemcpyFromSymbol(&v, jtfs::g_tc_err, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
   const int zero[4] = {0, 0, 0, 0};
   if (v && cudaMemcpyToSymbol(jtfs::g_tc_err, zero, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
-  return v;
+  const int vp = jtfs::pool_tc_error();
+  if (vp < 0) return vp;
+  return v | vp;
 }
 
 extern "C" int jtfs_tc_error_info(int64_t* info, int n) {

@@ -172,6 +172,9 @@ struct Plan {
   std::vector<int4> pool_tiles2;  // adjoint time pooling, dense groups: (clip, active n2, row tile, 512-sample tile)
   std::vector<int4> pool_fwd_tiles[3];  // forward time pooling per split: (clip, active n2, row tile, split)
   std::vector<int> pool_tile0[3];       // per split and (clip, active n2): first forward tile
+  std::vector<int4> pool_tc_tiles[3];   // tensor-core forward pooling per split: (clip, active n2, even 64-row tile, split)
+  const int4* d_pool_tc_tiles[3] = {nullptr, nullptr, nullptr};
+  mutable int tune_pool_tc = 1;         // time pooling forward on the tensor cores where supported
   // Banded time pooling: per active n2 the tap half-width W (level samples)
   // beyond which g_s is below 2^-40 g_s[0], or 0 where the dense product is
   // used; forward tiles of the banded levels: (clip, active n2, row tile, 32-frame block).
@@ -272,6 +275,14 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
                int64_t T, int F, int batch, uint32_t flags);
 int upload_plan(Plan& p);
 void release_plan(Plan& p);
+
+// Tensor-core time pooling of the second order (jtfs_pool_tc.cu): whether the
+// plan's frame count has a kernel (32, 64 or 128 frames), the forward
+// launch (partials in the slots of k_pool_reduce), and its expired-wait flag
+// (read and cleared).
+bool pool_tc_supported(const Plan& p);
+int pool_tc_forward(const Plan& p, const float* V2, float* part, int si, cudaStream_t s);
+int pool_tc_error();
 
 // Tensor-core frequential path (jtfs_freq_tc.cu): host tables at plan
 // construction, device copies and tensor maps at upload, release.  tc_build

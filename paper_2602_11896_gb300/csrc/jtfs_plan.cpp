@@ -449,6 +449,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   for (int si = 0; si < 3; ++si) {
     p.pool_fwd_tiles[si].clear();
     p.pool_tile0[si].clear();
+    p.pool_tc_tiles[si].clear();
     if (p.unpooled_t) continue;
     const int rows = p.rows2;
     for (int b = 0; b < B; ++b)
@@ -458,7 +459,10 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
         p.pool_tile0[si].push_back(static_cast<int>(p.pool_fwd_tiles[si].size()));
         if (p.pool_w[a]) continue;
         for (int rt = 0; rt < (rows + 63) / 64; ++rt)
-          for (int sp = 0; sp < nsplit; ++sp) p.pool_fwd_tiles[si].push_back(make_int4(b, a, rt, sp));
+          for (int sp = 0; sp < nsplit; ++sp) {
+            p.pool_fwd_tiles[si].push_back(make_int4(b, a, rt, sp));
+            if ((rt & 1) == 0) p.pool_tc_tiles[si].push_back(make_int4(b, a, rt, sp));  // 128 rows: tiles rt, rt + 1
+          }
       }
   }
 
@@ -533,10 +537,11 @@ int upload_plan(Plan& p) {
   const size_t o_ftabc_off = put(p.h_ftabc_off.data(), p.h_ftabc_off.size() * sizeof(int));
   const size_t o_pt = put(p.pool_tiles.data(), p.pool_tiles.size() * sizeof(int4));
   const size_t o_pt2 = put(p.pool_tiles2.data(), p.pool_tiles2.size() * sizeof(int4));
-  size_t o_pft[3], o_pt0[3];
+  size_t o_pft[3], o_pt0[3], o_ptc[3];
   for (int si = 0; si < 3; ++si) {
     o_pft[si] = put(p.pool_fwd_tiles[si].data(), p.pool_fwd_tiles[si].size() * sizeof(int4));
     o_pt0[si] = put(p.pool_tile0[si].data(), p.pool_tile0[si].size() * sizeof(int));
+    o_ptc[si] = put(p.pool_tc_tiles[si].data(), p.pool_tc_tiles[si].size() * sizeof(int4));
   }
   const size_t o_s2 = put(p.s2.data(), p.s2.size() * sizeof(int));
   const size_t o_pw = put(p.pool_w.data(), p.pool_w.size() * sizeof(int));
@@ -583,6 +588,7 @@ int upload_plan(Plan& p) {
   for (int si = 0; si < 3; ++si) {
     p.d_pool_fwd_tiles[si] = reinterpret_cast<const int4*>(at(o_pft[si]));
     p.d_pool_tile0[si] = reinterpret_cast<const int*>(at(o_pt0[si]));
+    p.d_pool_tc_tiles[si] = reinterpret_cast<const int4*>(at(o_ptc[si]));
   }
   p.d_s2 = reinterpret_cast<const int*>(at(o_s2));
   p.d_pool_w = reinterpret_cast<const int*>(at(o_pw));

@@ -1,0 +1,283 @@
+// Time averaging of the second-order paths on the 5th-generation tensor cores
+// (the phi_T average of Eq. (5), at stride T).
+//
+// For one clip and one path group (n2) of level s (rows at stride 2^s, L =
+// N / 2^s samples), every pooled row is
+//   Phi2[r][f] = sum_t V2[r][t] g_s[(f D - t) mod L],   D = 2^(log2 T - s),
+// with g_s the phi_T taps at level s.  All rows share the tap matrix
+// G[f][t] = g_s[(f D - t) mod L], so a tile of 128 rows is the GEMM
+//   D[128 x F] = V[128 x K] . G^T[K x F]         (F = N / T frames, K = time)
+// over a split of the time axis, written as partial sums into the slots of the
+// fixed-order reduction (k_pool_reduce) that the FMA kernels also use.
+// FP32 accuracy from BF16 operands: each operand is split v = hi + lo and each
+// product is hi.hi + lo.hi + hi.lo (three MMAs into one FP32 accumulator).
+//
+// One CTA per (clip, group, 128 rows, time split), 160 threads: warps 0-3 turn
+// 64-sample blocks of V2 (thread = row, the next block's loads in flight while
+// the current one is converted) and of the taps into BF16 hi/lo operand tiles
+// (128-byte swizzle, two shared-memory stages) and then read the accumulator
+// (warp w: TMEM lanes 32w .. 32w + 31); warp 4 lane 0 issues tcgen05.mma.
+// Every wait is bounded: an expired wait stops the CTA (MMAs completed, TMEM
+// freed) and raises a flag read through jtfs_tc_error().
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "jtfs.h"
+#include "jtfs_internal.h"
+#include "jtfs_umma.cuh"
+
+namespace jtfs {
+namespace {
+
+__device__ int g_pt_err;
+
+constexpr int kPtThreads = 160;
+constexpr int kPtRows = 128;  // rows per tile (MMA M)
+constexpr int kPtK = 64;      // samples per operand block (one 128-byte swizzle atom of BF16)
+
+struct PtArgs {
+  const float* V2;
+  float* part;
+  const int4* tiles;      // (clip, active group, first 64-row slot, split)
+  const int* tile0;       // first partial slot of each (clip, group)
+  const int* s2;
+  const int64_t* v2_off;
+  const float* taps;
+  const int64_t* tap_off;
+  int64_t v2_tot;
+  int logN, lT, n_frames, rows, n_active, split_len;
+};
+
+struct PtCtl {
+  unsigned long long full[2], empty[2], done;
+  uint32_t tmem;
+  int abort;
+};
+
+__device__ __noinline__ bool pt_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (i >= 8) __nanosleep(64);
+  }
+  *abort = 1;
+  return false;
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, const uint32_t (&v)[4]) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+               : "memory");
+}
+
+template <int F>
+constexpr size_t pt_smem() {
+  return sizeof(PtCtl) + 1024 + 2 * (2 * 16384 + 2 * size_t(F) * 128);
+}
+
+template <int F>
+__global__ void __launch_bounds__(kPtThreads)
+k_pool_tc_fwd(const PtArgs A) {
+  extern __shared__ uint8_t smem_raw[];
+  PtCtl* ctl = reinterpret_cast<PtCtl*>(smem_raw);
+  constexpr uint32_t kA = 16384u, kB = uint32_t(F) * 128u, kStage = 2 * kA + 2 * kB;
+  const uint32_t base = (smem_u32(smem_raw) + sizeof(PtCtl) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  const int4 tl = A.tiles[blockIdx.x];
+  const int b = tl.x, a = tl.y, slot = tl.z, sp = tl.w;
+  const int s = A.s2[a], lL = A.logN - s, L = 1 << lL, D = 1 << (A.lT - s);
+  const int tbeg = sp * A.split_len, tend = min(L, tbeg + A.split_len);
+  const int nkb = (tend - tbeg + kPtK - 1) / kPtK;
+  const int nsplit = (L + A.split_len - 1) / A.split_len;
+  const int r0 = slot * 64;
+  volatile int* abort = &ctl->abort;
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&ctl->full[i]), 128);
+      mbar_init(smem_u32(&ctl->empty[i]), 1);
+    }
+    mbar_init(smem_u32(&ctl->done), 1);
+    ctl->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 4) tmem_alloc(smem_u32(&ctl->tmem), F < 32 ? 32 : F);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem;
+  bool issued = false;
+
+  if (warp < 4) {
+    // Producer: thread = row r0 + tid of the tile.
+    const int r = r0 + tid;
+    const bool rowok = r < A.rows;
+    const float* vrow = A.V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a] + static_cast<int64_t>(rowok ? r : 0) * L;
+    const float* g = A.taps + A.tap_off[s];
+    const bool vec = L >= kPtK;  // whole 64-sample blocks inside the row: 16-byte loads
+    float4 nxt[16];
+    auto load_v = [&](int t0) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int t = t0 + 4 * c;
+        if (!rowok || t >= tend) {
+          nxt[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else if (vec) {
+          nxt[c] = __ldg(reinterpret_cast<const float4*>(vrow + t));
+        } else {
+          nxt[c] = make_float4(vrow[t], t + 1 < tend ? vrow[t + 1] : 0.f, t + 2 < tend ? vrow[t + 2] : 0.f,
+                               t + 3 < tend ? vrow[t + 3] : 0.f);
+        }
+      }
+    };
+    load_v(tbeg);
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int st = kb & 1;
+      const int t0 = tbeg + kb * kPtK;
+      float4 cur[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) cur[c] = nxt[c];
+      if (kb + 1 < nkb) load_v(t0 + kPtK);
+      if (kb >= 2 && !pt_wait(smem_u32(&ctl->empty[st]), ((kb >> 1) - 1) & 1, abort)) break;
+      const uint32_t sA = base + uint32_t(st) * kStage, sAl = sA + kA, sB = sA + 2 * kA, sBl = sB + kB;
+#pragma unroll
+      for (int ch = 0; ch < 8; ++ch) {  // 8 samples per 16-byte chunk
+        const float4 p = cur[2 * ch], q = cur[2 * ch + 1];
+        uint32_t hi[4], lo[4];
+        split2(p.x, p.y, hi[0], lo[0]);
+        split2(p.z, p.w, hi[1], lo[1]);
+        split2(q.x, q.y, hi[2], lo[2]);
+        split2(q.z, q.w, hi[3], lo[3]);
+        st_shared_v4(sA + swz128(tid, ch), hi);
+        st_shared_v4(sAl + swz128(tid, ch), lo);
+      }
+      // Taps: row f, samples t0 .. t0 + 63 of G[f][t] = g[(f D - t) mod L].
+      for (int q = tid; q < F * 8; q += 128) {
+        const int f = q >> 3, ch = q & 7;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int t = t0 + 8 * ch + e;
+          v[e] = (f < A.n_frames && t < tend) ? __ldg(g + ((f * D - t) & (L - 1))) : 0.f;
+        }
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split2(v[2 * e], v[2 * e + 1], hi[e], lo[e]);
+        st_shared_v4(sB + swz128(f, ch), hi);
+        st_shared_v4(sBl + swz128(f, ch), lo);
+      }
+      fence_proxy_async();
+      mbar_arrive(smem_u32(&ctl->full[st]));
+    }
+  } else if (warp == 4 && lane == 0) {
+    issued = true;
+    const uint32_t idesc = idesc_bf16_n(F);
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int st = kb & 1;
+      if (!pt_wait(smem_u32(&ctl->full[st]), (kb >> 1) & 1, abort)) break;
+      tc_fence_after();
+      const uint32_t sA = base + uint32_t(st) * kStage;
+      const uint64_t ah = sdesc(sA, 16, 1024), al = sdesc(sA + kA, 16, 1024);
+      const uint64_t bh = sdesc(sA + 2 * kA, 16, 1024), bl = sdesc(sA + 2 * kA + kB, 16, 1024);
+#pragma unroll
+      for (int kk = 0; kk < kPtK / 16; ++kk) {
+        const uint64_t o = uint64_t(kk) * 2u;  // 32 bytes in 16-byte descriptor units
+        umma_bf16(tmem, ah + o, bh + o, idesc, (kb | kk) != 0);
+        umma_bf16(tmem, al + o, bh + o, idesc, 1);
+        umma_bf16(tmem, ah + o, bl + o, idesc, 1);
+      }
+      umma_commit(smem_u32(&ctl->empty[st]));
+    }
+    umma_commit(smem_u32(&ctl->done));  // completes once every issued MMA has completed
+  }
+
+  if (warp < 4) {
+    const bool ok = pt_wait(smem_u32(&ctl->done), 0, abort);
+    const bool all = __all_sync(0xffffffffu, ok) && !*abort;
+    tc_fence_after();
+    if (all) {
+      const int r = r0 + tid;
+      const int64_t ba = static_cast<int64_t>(b) * A.n_active + a;
+      const int64_t t = A.tile0[ba] + static_cast<int64_t>(r >> 6) * nsplit + sp;
+      float* out = A.part + (t * 64 + (r & 63)) * A.n_frames;
+#pragma unroll
+      for (int j = 0; j < (F + 31) / 32; ++j) {
+        float v[32];
+        tmem_ld32(tmem + (uint32_t(warp * 32) << 16) + uint32_t(32 * j), v);
+        if (r < A.rows) {
+#pragma unroll
+          for (int e = 0; e < 32; ++e)
+            if (32 * j + e < A.n_frames) out[32 * j + e] = v[e];
+        }
+      }
+    }
+  }
+  if (warp == 4 && lane == 0 && issued && *abort) {
+    // The done commit above already covers every issued MMA; wait for it before freeing TMEM.
+    for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(smem_u32(&ctl->done), 0); ++i) __nanosleep(64);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && *abort) atomicExch(&g_pt_err, 1);
+  if (warp == 4) {
+    __syncwarp();
+    tmem_dealloc(tmem, F < 32 ? 32 : F);
+  }
+}
+
+template <auto Kernel>
+cudaError_t pt_opt_in(size_t smem) {
+  return cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+}
+
+template <int F>
+int launch_pt(const PtArgs& A, unsigned grid, cudaStream_t s) {
+  constexpr size_t smem = pt_smem<F>();
+  if (pt_opt_in<k_pool_tc_fwd<F>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
+  k_pool_tc_fwd<F><<<grid, kPtThreads, smem, s>>>(A);
+  return cudaGetLastError() == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA;
+}
+
+}  // namespace
+
+bool pool_tc_supported(const Plan& p) {
+  return p.n_frames == 32 || p.n_frames == 64 || p.n_frames == 128;
+}
+
+int pool_tc_forward(const Plan& p, const float* V2, float* part, int si, cudaStream_t s) {
+  if (p.pool_tc_tiles[si].empty()) return JTFS_OK;
+  PtArgs A{};
+  A.V2 = V2;
+  A.part = part;
+  A.tiles = p.d_pool_tc_tiles[si];
+  A.tile0 = p.d_pool_tile0[si];
+  A.s2 = p.d_s2;
+  A.v2_off = p.d_v2_off;
+  A.taps = p.d_taps;
+  A.tap_off = p.d_tap_off;
+  A.v2_tot = p.v2_tot;
+  A.logN = p.logN;
+  A.lT = p.lT;
+  A.n_frames = p.n_frames;
+  A.rows = p.rows2;
+  A.n_active = p.n_active;
+  A.split_len = kPoolSplits[si];
+  const unsigned grid = static_cast<unsigned>(p.pool_tc_tiles[si].size());
+  switch (p.n_frames) {
+    case 32: return launch_pt<32>(A, grid, s);
+    case 64: return launch_pt<64>(A, grid, s);
+    case 128: return launch_pt<128>(A, grid, s);
+    default: return JTFS_ERR_SHAPE;
+  }
+}
+
+int pool_tc_error() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_pt_err, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
+  const int zero = 0;
+  if (v && cudaMemcpyToSymbol(g_pt_err, &zero, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
+  return v;
+}
+
+}  // namespace jtfs

@@ -84,14 +84,15 @@ class JTFSPlan:
         return np.array(xi[:]), np.array(sg[:]), np.array(jj[:], dtype=np.int64)
 
     # -- tuning -----------------------------------------------------------
-    def tuning(self) -> Tuple[int, int, int, int]:
-        """(wide forward tiles, pooling split, small-FFT points per CTA, tensor-core frequential path) in use."""
-        buf = (c_int64 * 4)()
-        self._lib.jtfs_get_tuning(self._h, buf, 4)
-        return int(buf[0]), int(buf[1]), int(buf[2]), int(buf[3])
+    def tuning(self) -> Tuple[int, int, int, int, int]:
+        """(wide forward tiles, pooling split, small-FFT points per CTA, tensor-core frequential path,
+        tensor-core time pooling) in use."""
+        buf = (c_int64 * 5)()
+        self._lib.jtfs_get_tuning(self._h, buf, 5)
+        return tuple(int(buf[i]) for i in range(5))
 
     def set_tuning(self, choice) -> None:
-        """Apply 3 choices (tensor-core choice unchanged) or 4 (see ``tuning``)."""
+        """Apply 3, 4 or 5 choices (see ``tuning``); choices not given are unchanged."""
         vals = [int(c) for c in choice]
         buf = (c_int64 * len(vals))(*vals)
         n = self._lib.jtfs_set_tuning(self._h, buf, len(vals))
@@ -116,7 +117,7 @@ class JTFSPlan:
         return f"{name}|" + ",".join(f"{k}={self.info[k]}" for k in INFO_KEYS[:9])
 
     def autotune(self, y: torch.Tensor, phi_target: torch.Tensor,
-                 cache: Optional[str] = None) -> Tuple[int, int, int, int]:
+                 cache: Optional[str] = None) -> Tuple[int, ...]:
         """Pick the fastest execution choices for this plan by timing jtfs_loss_grad on (y, phi_target).
 
         With ``cache`` (default: the JTFS_TUNE_CACHE environment variable) the choices are read
@@ -139,11 +140,11 @@ class JTFSPlan:
         loss = torch.empty(self.batch, device=y.device)
         dy = torch.empty_like(y)
         ws = self.workspace(y.device)
-        buf = (c_int64 * 4)()
+        buf = (c_int64 * 5)()
         n = self._lib.jtfs_autotune(self._h, _ptr(y), _ptr(phi_target), _ptr(loss), _ptr(dy), _ptr(ws), _stream(),
-                                    buf, 4)
+                                    buf, 5)
         _native.check(0 if n >= 0 else n, "jtfs_autotune")
-        choice = [int(buf[i]) for i in range(4)]
+        choice = [int(buf[i]) for i in range(5)]
         if path:
             table = {}
             if os.path.exists(path):

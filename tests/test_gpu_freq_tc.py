@@ -72,3 +72,53 @@ def test_tensor_core_path_repeats_bit_for_bit():
     l0, g0 = plan.loss_grad(y, tgt)
     l1, g1 = plan.loss_grad(y, tgt)
     assert torch.equal(l0, l1) and torch.equal(g0, g1)
+
+
+POOL_CASES = {
+    "chirps22k_b8_n65536": None,                                             # 32 frames
+    "frames64_n16384": dict(N=2 ** 14, J=8, Q=8, Q2=1, J_fr=3, Q_fr=1, T=256, F=4),    # 64 frames
+}
+
+
+@pytest.mark.parametrize("name", list(POOL_CASES))
+def test_tensor_core_pooling_matches_fma_pooling(name):
+    """Time pooling of the dense groups on the tensor cores (BF16 hi/lo split) against the FMA kernels:
+    every second-order block within 2e-5, the rest bit-identical, loss and gradient within 2e-5, no
+    expired wait, and the tensor-core result repeatable bit for bit."""
+    from paper_2602_11896_gb300 import JTFSPlan, _native
+    lib = _native.load()
+    params = POOL_CASES[name] or get_workload(name).params
+    B = 2
+    plan = JTFSPlan(**params, batch=B)
+    base = list(plan.tuning())
+    assert base[4] == 1, "tensor-core pooling should be the default for this frame count"
+    N = params["N"]
+    x = torch.tensor(np.stack([signals.white_noise(N, 51 + b) for b in range(B)]), device="cuda")
+    y = torch.tensor(np.stack([signals.white_noise(N, 61 + b) for b in range(B)]), device="cuda")
+    res = {}
+    for v in (0, 1):
+        plan.set_tuning(base[:4] + [v])
+        assert plan.tuning()[4] == v
+        phi = plan.forward(x).clone()
+        loss, g = plan.loss_grad(y, phi.flip(0).contiguous())
+        res[v] = (phi, loss.clone(), g.clone())
+    again = plan.forward(x)
+    torch.cuda.synchronize()
+    assert lib.jtfs_tc_error() == 0
+    assert torch.equal(again, res[1][0])
+    plan.set_tuning(base)
+    info = plan.info
+    nf, R, K = info["n_frames"], info["R_out"], info["K"]
+    pp = R * nf
+    off2 = nf + (K + 1) * pp
+    p0, p1 = res[0][0], res[1][0]
+    assert torch.equal(p1[:, :off2], p0[:, :off2])
+    worst = 0.0
+    for a in range(info["n_active"]):
+        for b in range(2 * K + 1):
+            o = off2 + (a * (2 * K + 1) + b) * pp
+            d = (p1[:, o:o + pp].double() - p0[:, o:o + pp].double()).norm() / p0[:, o:o + pp].double().norm()
+            worst = max(worst, float(d))
+    assert worst <= 2e-5, worst
+    assert _rel(res[1][1], res[0][1]) <= 2e-5
+    assert _rel(res[1][2], res[0][2]) <= 2e-5

@@ -202,3 +202,16 @@ def test_chirps_workload_full_size_sampled_clip():
                            checkpoint_blocks=True)
     assert _rel(loss[b:b + 1].cpu().numpy(), E.numpy()) <= TOL
     assert _rel(dy[b].cpu().numpy(), g[0].numpy()) <= TOL
+
+
+def test_forward_parity_64_frames_tensor_core_pooling():
+    """A plan with 64 frames (tensor-core time pooling of its dense groups) against the oracle."""
+    params = dict(N=2 ** 14, J=8, Q=8, Q2=1, J_fr=3, Q_fr=1, T=256, F=4)
+    plan = _plan(params, 1)
+    assert plan.tuning()[4] == 1
+    x = _inputs(params["N"], 1, 71)
+    phi = plan.forward(torch.tensor(x, device="cuda")).cpu().numpy()
+    ref_plan = O.Plan(**params)
+    ref = O.jtfs(torch.tensor(x), ref_plan)["phi"].numpy()
+    for k, e in _block_errors(phi, ref, ref_plan).items():
+        assert e <= TOL, (k, e)
