@@ -12,11 +12,12 @@
 // FP32 accuracy from BF16 operands: each operand is split v = hi + lo and each
 // product is hi.hi + lo.hi + hi.lo (three MMAs into one FP32 accumulator).
 //
-// One CTA per (clip, group, 128 rows, time split), 160 threads: warps 0-3 turn
-// 64-sample blocks of V2 (thread = row, the next block's loads in flight while
-// the current one is converted) and of the taps into BF16 hi/lo operand tiles
-// (128-byte swizzle, two shared-memory stages) and then read the accumulator
-// (warp w: TMEM lanes 32w .. 32w + 31); warp 4 lane 0 issues tcgen05.mma.
+// One CTA per (clip, group, 128 rows, time split), 288 threads: warps 0-7 turn
+// 64-sample blocks of V2 (two threads per row, 32 samples each, the next
+// block's loads in flight while the current one is converted) and of the taps
+// into BF16 hi/lo operand tiles (128-byte swizzle, two shared-memory stages)
+// and then read the accumulator (warp w: TMEM lanes 32 (w % 4) .. + 31, half
+// w / 4 of the frames); warp 8 lane 0 issues tcgen05.mma.
 // Every wait is bounded: an expired wait stops the CTA (MMAs completed, TMEM
 // freed) and raises a flag read through jtfs_tc_error().
 #include <cuda.h>
@@ -34,7 +35,9 @@ namespace {
 
 __device__ int g_pt_err;
 
-constexpr int kPtThreads = 160;
+constexpr int kPtThreads = 288;
+constexpr int kPtProd = 256;  // producer / epilogue threads (warps 0-7)
+constexpr int kPtWarpMma = 8;
 constexpr int kPtRows = 128;  // rows per tile (MMA M)
 constexpr int kPtK = 64;      // samples per operand block (one 128-byte swizzle atom of BF16)
 
@@ -95,32 +98,33 @@ k_pool_tc_fwd(const PtArgs A) {
   volatile int* abort = &ctl->abort;
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
-      mbar_init(smem_u32(&ctl->full[i]), 128);
+      mbar_init(smem_u32(&ctl->full[i]), kPtProd);
       mbar_init(smem_u32(&ctl->empty[i]), 1);
     }
     mbar_init(smem_u32(&ctl->done), 1);
     ctl->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 4) tmem_alloc(smem_u32(&ctl->tmem), F < 32 ? 32 : F);
+  if (warp == kPtWarpMma) tmem_alloc(smem_u32(&ctl->tmem), F < 32 ? 32 : F);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = ctl->tmem;
   bool issued = false;
 
-  if (warp < 4) {
-    // Producer: thread = row r0 + tid of the tile.
-    const int r = r0 + tid;
+  if (warp < kPtWarpMma) {
+    // Producer: thread pair per row r0 + tid / 2; thread tid % 2 takes samples 32 (tid % 2) .. + 31.
+    const int rr = tid >> 1, half = tid & 1;
+    const int r = r0 + rr;
     const bool rowok = r < A.rows;
     const float* vrow = A.V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a] + static_cast<int64_t>(rowok ? r : 0) * L;
     const float* g = A.taps + A.tap_off[s];
     const bool vec = L >= kPtK;  // whole 64-sample blocks inside the row: 16-byte loads
-    float4 nxt[16];
+    float4 nxt[8];
     auto load_v = [&](int t0) {
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int t = t0 + 4 * c;
+      for (int c = 0; c < 8; ++c) {
+        const int t = t0 + 32 * half + 4 * c;
         if (!rowok || t >= tend) {
           nxt[c] = make_float4(0.f, 0.f, 0.f, 0.f);
         } else if (vec) {
@@ -135,25 +139,26 @@ k_pool_tc_fwd(const PtArgs A) {
     for (int kb = 0; kb < nkb; ++kb) {
       const int st = kb & 1;
       const int t0 = tbeg + kb * kPtK;
-      float4 cur[16];
+      float4 cur[8];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) cur[c] = nxt[c];
+      for (int c = 0; c < 8; ++c) cur[c] = nxt[c];
       if (kb + 1 < nkb) load_v(t0 + kPtK);
       if (kb >= 2 && !pt_wait(smem_u32(&ctl->empty[st]), ((kb >> 1) - 1) & 1, abort)) break;
       const uint32_t sA = base + uint32_t(st) * kStage, sAl = sA + kA, sB = sA + 2 * kA, sBl = sB + kB;
 #pragma unroll
-      for (int ch = 0; ch < 8; ++ch) {  // 8 samples per 16-byte chunk
-        const float4 p = cur[2 * ch], q = cur[2 * ch + 1];
+      for (int c = 0; c < 4; ++c) {  // 8 samples per 16-byte chunk
+        const int ch = 4 * half + c;
+        const float4 p = cur[2 * c], q = cur[2 * c + 1];
         uint32_t hi[4], lo[4];
         split2(p.x, p.y, hi[0], lo[0]);
         split2(p.z, p.w, hi[1], lo[1]);
         split2(q.x, q.y, hi[2], lo[2]);
         split2(q.z, q.w, hi[3], lo[3]);
-        st_shared_v4(sA + swz128(tid, ch), hi);
-        st_shared_v4(sAl + swz128(tid, ch), lo);
+        st_shared_v4(sA + swz128(rr, ch), hi);
+        st_shared_v4(sAl + swz128(rr, ch), lo);
       }
       // Taps: row f, samples t0 .. t0 + 63 of G[f][t] = g[(f D - t) mod L].
-      for (int q = tid; q < F * 8; q += 128) {
+      for (int q = tid; q < F * 8; q += kPtProd) {
         const int f = q >> 3, ch = q & 7;
         float v[8];
 #pragma unroll
@@ -170,7 +175,7 @@ k_pool_tc_fwd(const PtArgs A) {
       fence_proxy_async();
       mbar_arrive(smem_u32(&ctl->full[st]));
     }
-  } else if (warp == 4 && lane == 0) {
+  } else if (warp == kPtWarpMma && lane == 0) {
     issued = true;
     const uint32_t idesc = idesc_bf16_n(F);
     for (int kb = 0; kb < nkb; ++kb) {
@@ -192,35 +197,52 @@ k_pool_tc_fwd(const PtArgs A) {
     umma_commit(smem_u32(&ctl->done));  // completes once every issued MMA has completed
   }
 
-  if (warp < 4) {
+  if (warp < kPtWarpMma) {
     const bool ok = pt_wait(smem_u32(&ctl->done), 0, abort);
     const bool all = __all_sync(0xffffffffu, ok) && !*abort;
     tc_fence_after();
     if (all) {
-      const int r = r0 + tid;
+      // Warp w: rows 32 (w % 4) + lane of the tile (its TMEM lanes), frames [w / 4 * F / 2, + F / 2).
+      constexpr int FH = F / 2;
+      const int q4 = warp & 3, fh = warp >> 2;
+      const int r = r0 + 32 * q4 + lane;
       const int64_t ba = static_cast<int64_t>(b) * A.n_active + a;
       const int64_t t = A.tile0[ba] + static_cast<int64_t>(r >> 6) * nsplit + sp;
-      float* out = A.part + (t * 64 + (r & 63)) * A.n_frames;
-#pragma unroll
-      for (int j = 0; j < (F + 31) / 32; ++j) {
-        float v[32];
-        tmem_ld32(tmem + (uint32_t(warp * 32) << 16) + uint32_t(32 * j), v);
+      float4* out = reinterpret_cast<float4*>(A.part + (t * 64 + (r & 63)) * A.n_frames + fh * FH);
+      const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(fh * FH);
+      if (FH == 16) {
+        uint32_t v[16];
+        tmem_ld16_nowait(taddr, v);
+        tmem_ld_wait();
+        tmem_regs_ready(v);
         if (r < A.rows) {
 #pragma unroll
-          for (int e = 0; e < 32; ++e)
-            if (32 * j + e < A.n_frames) out[32 * j + e] = v[e];
+          for (int e = 0; e < 4; ++e)
+            out[e] = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                                 __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < FH / 32; ++j) {
+          float v[32];
+          tmem_ld32(taddr + uint32_t(32 * j), v);
+          if (r < A.rows) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              out[8 * j + e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+          }
         }
       }
     }
   }
-  if (warp == 4 && lane == 0 && issued && *abort) {
+  if (warp == kPtWarpMma && lane == 0 && issued && *abort) {
     // The done commit above already covers every issued MMA; wait for it before freeing TMEM.
     for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(smem_u32(&ctl->done), 0); ++i) __nanosleep(64);
   }
   tc_fence_before();
   __syncthreads();
   if (tid == 0 && *abort) atomicExch(&g_pt_err, 1);
-  if (warp == 4) {
+  if (warp == kPtWarpMma) {
     __syncwarp();
     tmem_dealloc(tmem, F < 32 ? 32 : F);
   }
