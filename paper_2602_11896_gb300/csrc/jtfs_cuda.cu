@@ -1710,8 +1710,13 @@ int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, 
     prof_begin(p, JTFS_STAGE_POOL_ADJ, s);
     if (p.unpooled_t)  // dV2 = the second-order blocks of dPhi
       JTFS_TRY(copy_block(p, dphi, p.phi_size, p.phi2_base, w.V2, p.v2_tot, 0, p.v2_tot, false, s));
-    if (!p.pool_tiles2.empty())
-      k_pool_adj2<<<static_cast<unsigned>(p.pool_tiles2.size()), kThreads, 0, s>>>(PA, dphi, w.V2, p.d_pool_tiles2);
+    if (!p.pool_tiles2.empty()) {
+      if (p.tune_pool_tc && pool_tc_supported(p))  // dense groups on the tensor cores
+        JTFS_TRY(pool_tc_adjoint(p, dphi, w.V2, s));
+      else
+        k_pool_adj2<<<static_cast<unsigned>(p.pool_tiles2.size()), kThreads, 0, s>>>(PA, dphi, w.V2,
+                                                                                     p.d_pool_tiles2);
+    }
     if (!p.pool_tiles.empty())
       k_pool_adj<<<static_cast<unsigned>(p.pool_tiles.size()), kThreads, 0, s>>>(PA, dphi, w.V2, p.d_pool_tiles);
     prof_end(p, JTFS_STAGE_POOL_ADJ, s);

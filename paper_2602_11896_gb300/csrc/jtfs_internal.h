@@ -173,6 +173,8 @@ struct Plan {
   std::vector<int4> pool_fwd_tiles[3];  // forward time pooling per split: (clip, active n2, row tile, split)
   std::vector<int> pool_tile0[3];       // per split and (clip, active n2): first forward tile
   std::vector<int4> pool_tc_tiles[3];   // tensor-core forward pooling per split: (clip, active n2, even 64-row tile, split)
+  std::vector<int4> pool_tc_adj_tiles;  // tensor-core adjoint pooling: (clip, active n2, even 64-row tile, 1024-sample block)
+  const int4* d_pool_tc_adj_tiles = nullptr;
   const int4* d_pool_tc_tiles[3] = {nullptr, nullptr, nullptr};
   mutable int tune_pool_tc = 1;         // time pooling forward on the tensor cores where supported
   // Banded time pooling: per active n2 the tap half-width W (level samples)
@@ -282,6 +284,7 @@ void release_plan(Plan& p);
 // (read and cleared).
 bool pool_tc_supported(const Plan& p);
 int pool_tc_forward(const Plan& p, const float* V2, float* part, int si, cudaStream_t s);
+int pool_tc_adjoint(const Plan& p, const float* dphi, float* dV2, cudaStream_t s);
 int pool_tc_error();
 
 // Tensor-core frequential path (jtfs_freq_tc.cu): host tables at plan

@@ -436,6 +436,17 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
         }
       }
   }
+  // Tensor-core adjoint pooling of the dense groups: 128 rows x 1024 samples per CTA.
+  p.pool_tc_adj_tiles.clear();
+  if (!p.unpooled_t) {
+    for (int b = 0; b < B; ++b)
+      for (int a = 0; a < p.n_active; ++a) {
+        if (p.pool_w[a]) continue;
+        const int L = static_cast<int>(N >> p.s2[a]);
+        for (int rt = 0; rt < (p.rows2 + 63) / 64; rt += 2)
+          for (int tb = 0; tb < (L + 1023) / 1024; ++tb) p.pool_tc_adj_tiles.push_back(make_int4(b, a, rt, tb));
+      }
+  }
   p.pool_band_tiles.clear();
   if (!p.unpooled_t) {
     const int rows = p.rows2;
@@ -543,6 +554,7 @@ int upload_plan(Plan& p) {
     o_pt0[si] = put(p.pool_tile0[si].data(), p.pool_tile0[si].size() * sizeof(int));
     o_ptc[si] = put(p.pool_tc_tiles[si].data(), p.pool_tc_tiles[si].size() * sizeof(int4));
   }
+  const size_t o_pta = put(p.pool_tc_adj_tiles.data(), p.pool_tc_adj_tiles.size() * sizeof(int4));
   const size_t o_s2 = put(p.s2.data(), p.s2.size() * sizeof(int));
   const size_t o_pw = put(p.pool_w.data(), p.pool_w.size() * sizeof(int));
   const size_t o_pbt = put(p.pool_band_tiles.data(), p.pool_band_tiles.size() * sizeof(int4));
@@ -589,6 +601,7 @@ int upload_plan(Plan& p) {
     p.d_pool_fwd_tiles[si] = reinterpret_cast<const int4*>(at(o_pft[si]));
     p.d_pool_tile0[si] = reinterpret_cast<const int*>(at(o_pt0[si]));
     p.d_pool_tc_tiles[si] = reinterpret_cast<const int4*>(at(o_ptc[si]));
+    if (si == 2) p.d_pool_tc_adj_tiles = reinterpret_cast<const int4*>(at(o_pta));
   }
   p.d_s2 = reinterpret_cast<const int*>(at(o_s2));
   p.d_pool_w = reinterpret_cast<const int*>(at(o_pw));

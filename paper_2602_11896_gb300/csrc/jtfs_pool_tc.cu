@@ -248,6 +248,192 @@ k_pool_tc_fwd(const PtArgs A) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint: dV2[r][t] = sum_f dPhi2[r][f] G[f][t] for 128 rows and a block of
+// kPtTb samples: D[128 x 128] = dPhi [128 x F] . G [F x 128] per 128-sample
+// block (MMA N = 128), K = F frames.  Operand rows (K-major, 128-byte swizzle):
+// F = 32 packs hi (K 0..31) and lo into one 128-byte row; F = 64, 128 use F / 64
+// atoms of hi then as many of lo.  The dPhi tile is split once; each block's
+// tap tile G^T[t][f] = g[(f D - t) mod L] is built by the same 8 warps, which
+// then store the finished block (TMEM double-buffered, 2 x 128 columns).
+// ---------------------------------------------------------------------------
+constexpr int kPtTb = 1024;   // samples per adjoint CTA (8 blocks of 128)
+
+struct PaCtl {
+  unsigned long long a_full, b_full[2], d_full[2], d_empty[2], done;
+  uint32_t tmem;
+  int abort;
+};
+
+template <int F>
+__host__ __device__ constexpr uint32_t pa_tile() { return F == 32 ? 16384u : uint32_t(F / 64) * 2u * 16384u; }  // 128 rows, hi + lo
+
+template <int F>
+constexpr size_t pa_smem() { return sizeof(PaCtl) + 1024 + 3 * size_t(pa_tile<F>()); }
+
+// Byte offsets of K-step kk (16 K) inside a hi + lo operand tile.
+template <int F>
+__device__ __forceinline__ uint32_t pa_hi(int kk) {
+  return F == 32 ? uint32_t(kk) * 32u : uint32_t(kk >> 2) * 16384u + uint32_t(kk & 3) * 32u;
+}
+template <int F>
+__device__ __forceinline__ uint32_t pa_lo(int kk) {
+  return F == 32 ? 64u + uint32_t(kk) * 32u : uint32_t(F / 64) * 16384u + pa_hi<F>(kk);
+}
+// Shared-memory byte address of the 16-byte chunk holding K = 8 c .. 8 c + 7 of row `row`, hi or lo.
+template <int F>
+__device__ __forceinline__ uint32_t pa_chunk(uint32_t tile, int row, int c, bool lo) {
+  if (F == 32) return tile + swz128(row, c + (lo ? 4 : 0));
+  return tile + (lo ? uint32_t(F / 64) * 16384u : 0u) + uint32_t(c >> 3) * 16384u + swz128(row, c & 7);
+}
+
+template <int F>
+__global__ void __launch_bounds__(kPtThreads)
+k_pool_tc_adj(const PtArgs A, const float* __restrict__ dphi, int64_t phi_size, const int64_t* __restrict__ phi2_off,
+              float* __restrict__ dV2) {
+  extern __shared__ uint8_t smem_raw[];
+  PaCtl* ctl = reinterpret_cast<PaCtl*>(smem_raw);
+  constexpr uint32_t kT = pa_tile<F>();
+  const uint32_t base = (smem_u32(smem_raw) + sizeof(PaCtl) + 1023u) & ~1023u;
+  const uint32_t sA = base, sB0 = base + kT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  const int4 tl = A.tiles[blockIdx.x];  // (clip, active group, first 64-row slot, block of kPtTb samples)
+  const int b = tl.x, a = tl.y, r0 = tl.z * 64, tb0 = tl.w * kPtTb;
+  const int s = A.s2[a], L = 1 << (A.logN - s), D = 1 << (A.lT - s);
+  const int nblk = (min(L - tb0, kPtTb) + 127) / 128;
+  volatile int* abort = &ctl->abort;
+  if (tid == 0) {
+    mbar_init(smem_u32(&ctl->a_full), kPtProd);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&ctl->b_full[i]), kPtProd);
+      mbar_init(smem_u32(&ctl->d_full[i]), 1);
+      mbar_init(smem_u32(&ctl->d_empty[i]), kPtProd);
+    }
+    mbar_init(smem_u32(&ctl->done), 1);
+    ctl->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kPtWarpMma) tmem_alloc(smem_u32(&ctl->tmem), 256);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem;
+  bool issued = false;
+
+  if (warp < kPtWarpMma) {
+    const float* g = A.taps + A.tap_off[s];
+    // Tap tile of block j: row t (0..127) = sample tb0 + 128 j + t, K = frame f.
+    auto build_b = [&](int j) {
+      const uint32_t tile = sB0 + uint32_t(j & 1) * kT;
+      const int tj = tb0 + 128 * j;
+      for (int q = tid; q < 128 * (F / 8); q += kPtProd) {
+        const int row = q / (F / 8), c = q % (F / 8);
+        const int t = tj + row;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int f = 8 * c + e;
+          v[e] = (t < L && f < A.n_frames) ? __ldg(g + ((f * D - t) & (L - 1))) : 0.f;
+        }
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split2(v[2 * e], v[2 * e + 1], hi[e], lo[e]);
+        st_shared_v4(pa_chunk<F>(tile, row, c, false), hi);
+        st_shared_v4(pa_chunk<F>(tile, row, c, true), lo);
+      }
+      fence_proxy_async();
+      mbar_arrive(smem_u32(&ctl->b_full[j & 1]));
+    };
+    // dPhi tile: row r0 + q / (F / 8), frames 8 (q % (F / 8)) .. + 7.
+    const float* dp = dphi + static_cast<int64_t>(b) * phi_size + phi2_off[a];
+    for (int q = tid; q < 128 * (F / 8); q += kPtProd) {
+      const int row = q / (F / 8), c = q % (F / 8);
+      const int r = r0 + row;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
+      if (r < A.rows) {
+        const float4* src = reinterpret_cast<const float4*>(dp + static_cast<int64_t>(r) * A.n_frames + 8 * c);
+        x = __ldg(src);
+        y = __ldg(src + 1);
+      }
+      uint32_t hi[4], lo[4];
+      split2(x.x, x.y, hi[0], lo[0]);
+      split2(x.z, x.w, hi[1], lo[1]);
+      split2(y.x, y.y, hi[2], lo[2]);
+      split2(y.z, y.w, hi[3], lo[3]);
+      st_shared_v4(pa_chunk<F>(sA, row, c, false), hi);
+      st_shared_v4(pa_chunk<F>(sA, row, c, true), lo);
+    }
+    fence_proxy_async();
+    mbar_arrive(smem_u32(&ctl->a_full));
+    build_b(0);
+    if (nblk > 1) build_b(1);
+    // Epilogue of block j: warp w stores rows 32 (w % 4) + lane, samples 64 (w / 4) .. + 63 of the block.
+    const int q4 = warp & 3, hh = warp >> 2;
+    const int r = r0 + 32 * q4 + lane;
+    float* orow = dV2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a] + static_cast<int64_t>(r < A.rows ? r : 0) * L;
+    for (int j = 0; j < nblk; ++j) {
+      const int jb = j & 1;
+      const bool ok = pt_wait(smem_u32(&ctl->d_full[jb]), (j >> 1) & 1, abort);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      const int t = tb0 + 128 * j + 64 * hh;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float v[32];
+        tmem_ld32(tmem + (uint32_t(q4 * 32) << 16) + uint32_t(jb * 128 + 64 * hh + 32 * h), v);
+        if (r < A.rows) {
+          const int tt = t + 32 * h;
+          if (tt + 32 <= L) {
+            float4* o = reinterpret_cast<float4*>(orow + tt);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+              if (tt + e < L) orow[tt + e] = v[e];
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&ctl->d_empty[jb]));
+      // Block j + 2 reuses tap stage jb: its MMAs (block j) have completed (d_full above).
+      if (j + 2 < nblk) build_b(j + 2);
+    }
+  } else if (warp == kPtWarpMma && lane == 0) {
+    issued = true;
+    const uint32_t idesc = idesc_bf16_n(128);
+    bool ok = pt_wait(smem_u32(&ctl->a_full), 0, abort);
+    tc_fence_after();
+    for (int j = 0; ok && j < nblk; ++j) {
+      const int jb = j & 1;
+      if (!pt_wait(smem_u32(&ctl->b_full[jb]), (j >> 1) & 1, abort)) break;
+      if (j >= 2 && !pt_wait(smem_u32(&ctl->d_empty[jb]), ((j >> 1) - 1) & 1, abort)) break;
+      tc_fence_after();
+      const uint32_t sB = sB0 + uint32_t(jb) * kT;
+      const uint32_t d = tmem + uint32_t(jb) * 128u;
+#pragma unroll
+      for (int kk = 0; kk < F / 16; ++kk) {
+        const uint64_t ah = sdesc(sA + pa_hi<F>(kk), 16, 1024), al = sdesc(sA + pa_lo<F>(kk), 16, 1024);
+        const uint64_t bh = sdesc(sB + pa_hi<F>(kk), 16, 1024), bl = sdesc(sB + pa_lo<F>(kk), 16, 1024);
+        umma_bf16(d, ah, bh, idesc, kk != 0);
+        umma_bf16(d, al, bh, idesc, 1);
+        umma_bf16(d, ah, bl, idesc, 1);
+      }
+      umma_commit(smem_u32(&ctl->d_full[jb]));
+    }
+    umma_commit(smem_u32(&ctl->done));  // completes once every issued MMA has completed
+    // TMEM is freed below: wait for that completion (bounded), also after an abort.
+    for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(smem_u32(&ctl->done), 0); ++i) __nanosleep(64);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && *abort) atomicExch(&g_pt_err, 1);
+  if (warp == kPtWarpMma) {
+    __syncwarp();
+    tmem_dealloc(tmem, 256);
+  }
+}
+
 template <auto Kernel>
 cudaError_t pt_opt_in(size_t smem) {
   return cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -261,7 +447,39 @@ int launch_pt(const PtArgs& A, unsigned grid, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA;
 }
 
+template <int F>
+int launch_pa(const PtArgs& A, const float* dphi, int64_t phi_size, const int64_t* phi2_off, float* dV2,
+              unsigned grid, cudaStream_t s) {
+  constexpr size_t smem = pa_smem<F>();
+  if (pt_opt_in<k_pool_tc_adj<F>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
+  k_pool_tc_adj<F><<<grid, kPtThreads, smem, s>>>(A, dphi, phi_size, phi2_off, dV2);
+  return cudaGetLastError() == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA;
+}
+
 }  // namespace
+
+int pool_tc_adjoint(const Plan& p, const float* dphi, float* dV2, cudaStream_t s) {
+  if (p.pool_tc_adj_tiles.empty()) return JTFS_OK;
+  PtArgs A{};
+  A.tiles = p.d_pool_tc_adj_tiles;
+  A.s2 = p.d_s2;
+  A.v2_off = p.d_v2_off;
+  A.taps = p.d_taps;
+  A.tap_off = p.d_tap_off;
+  A.v2_tot = p.v2_tot;
+  A.logN = p.logN;
+  A.lT = p.lT;
+  A.n_frames = p.n_frames;
+  A.rows = p.rows2;
+  A.n_active = p.n_active;
+  const unsigned grid = static_cast<unsigned>(p.pool_tc_adj_tiles.size());
+  switch (p.n_frames) {
+    case 32: return launch_pa<32>(A, dphi, p.phi_size, p.d_phi2_off, dV2, grid, s);
+    case 64: return launch_pa<64>(A, dphi, p.phi_size, p.d_phi2_off, dV2, grid, s);
+    case 128: return launch_pa<128>(A, dphi, p.phi_size, p.d_phi2_off, dV2, grid, s);
+    default: return JTFS_ERR_SHAPE;
+  }
+}
 
 bool pool_tc_supported(const Plan& p) {
   return p.n_frames == 32 || p.n_frames == 64 || p.n_frames == 128;

@@ -215,3 +215,17 @@ def test_forward_parity_64_frames_tensor_core_pooling():
     ref = O.jtfs(torch.tensor(x), ref_plan)["phi"].numpy()
     for k, e in _block_errors(phi, ref, ref_plan).items():
         assert e <= TOL, (k, e)
+
+
+def test_gradient_parity_64_frames_tensor_core_pooling():
+    """The same 64-frame plan: loss and gradient (tensor-core adjoint pooling) against the oracle."""
+    params = dict(N=2 ** 14, J=8, Q=8, Q2=1, J_fr=3, Q_fr=1, T=256, F=4)
+    plan = _plan(params, 1)
+    assert plan.tuning()[4] == 1
+    ref_plan = O.Plan(**params)
+    y = _inputs(params["N"], 1, 81)
+    tgt = O.jtfs(torch.tensor(_inputs(params["N"], 1, 91)), ref_plan)["phi"]
+    loss, dy = plan.loss_grad(torch.tensor(y, device="cuda"), tgt.float().cuda())
+    E, g = O.loss_and_grad(torch.tensor(y), tgt, ref_plan)
+    assert _rel(loss.cpu().numpy(), E.numpy()) <= TOL
+    assert _rel(dy.cpu().numpy(), g.numpy()) <= TOL
