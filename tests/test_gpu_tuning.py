@@ -22,12 +22,18 @@ def _rel(a, b):
     return float((a.double() - b.double()).norm() / b.double().norm())
 
 
+@pytest.mark.parametrize("pool_tc", [0, 1])
 @pytest.mark.parametrize("name", ["tones8k_n8192", "chirps22k_b8_n65536"])
-def test_every_tuning_choice_gives_the_same_gradient(name):
+def test_every_tuning_choice_gives_the_same_gradient(name, pool_tc):
+    """Only the pooling split reorders a sum.  The FMA pooling accumulates in FP32 (differences ~1e-7);
+    the tensor-core pooling accumulates each split's BF16 hi/lo products inside the MMA, so moving the
+    split boundaries changes the result at ~1e-6 (tolerance 1e-5, ten times below the parity bound)."""
     from paper_2602_11896_gb300 import JTFSPlan
     wl = get_workload(name)
     B = 2
     plan = JTFSPlan(**wl.params, batch=B)
+    plan.set_tuning(list(plan.tuning()[:4]) + [pool_tc])
+    tol = 1e-5 if plan.tuning()[4] else 1e-6
     y = torch.tensor(np.stack([signals.white_noise(wl.N, 7 + b) for b in range(B)]), device="cuda")
     tgt = plan.forward(torch.tensor(np.stack([signals.white_noise(wl.N, 17 + b) for b in range(B)]), device="cuda"))
     ref_choice = plan.tuning()
@@ -36,7 +42,7 @@ def test_every_tuning_choice_gives_the_same_gradient(name):
         plan.set_tuning((wide, split, pts))
         assert plan.tuning()[:3] == (wide, split, pts)
         l1, g1 = plan.loss_grad(y, tgt)
-        assert _rel(l1, l0) <= 1e-6 and _rel(g1, g0) <= 1e-6, (wide, split, pts)
+        assert _rel(l1, l0) <= tol and _rel(g1, g0) <= tol, (wide, split, pts)
         if split == ref_choice[1]:   # only the pooling split reorders a sum
             assert torch.equal(l1, l0) and torch.equal(g1, g0), (wide, split, pts)
     plan.set_tuning(ref_choice)
