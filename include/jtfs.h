@@ -111,6 +111,24 @@ int jtfs_plan_destroy(jtfs_plan_t plan);
  */
 int64_t jtfs_phi_size(jtfs_plan_t plan);
 
+/*
+ * Path metadata, one entry per path of Phi in its order (§3.5's yields):
+ *   order     0 zeroth order (S0, or x itself unpooled in time), 1 first-order
+ *             frequential path (|S1 * psi_beta| * phi_F), 2 second-order path;
+ *   n2        second-order time filter index (order 2), else -1;
+ *   beta_idx  frequential filter: 0 phi_F, 1..K +xi_n, K+1..2K -xi_n (order 1
+ *             uses 0..K), -1 for order 0;
+ *   spin      sign of the frequential centre frequency (0 for phi_F and order 0);
+ *   offset    first float of the path's block inside one clip's Phi; the block
+ *             is rows x frames and ends where the next path starts (the last
+ *             one at jtfs_phi_size).
+ * Arrays (host, any may be NULL) need as many entries as the return value:
+ * the number of paths, 1 + (1 + K) + n_active (1 + 2K).  Host-only plans answer
+ * too.  Errors: JTFS_ERR_ARG for a NULL plan.
+ */
+int jtfs_path_meta(jtfs_plan_t plan, int32_t* order, int32_t* n2, int32_t* beta_idx,
+                   int32_t* spin, int64_t* offset);
+
 /* Bytes of device workspace one compute call needs (0 if plan is NULL). */
 size_t jtfs_workspace_bytes(jtfs_plan_t plan);
 
@@ -304,6 +322,10 @@ typedef struct jtfs_batch_s* jtfs_batch_t;
  * jtfs_plan.
  */
 #define JTFS_BATCH_REFLECT 2u
+/* The same call under the name of a plan for clips of uneven lengths. */
+int jtfs_plan_ragged(jtfs_batch_t* out, const int64_t* lengths, int count, int J,
+                     int Q, int Q2, int J_fr, int Q_fr, int64_t T, int F,
+                     uint32_t flags);
 int jtfs_batch_create(jtfs_batch_t* out, const int64_t* lengths, int count, int J,
                       int Q, int Q2, int J_fr, int Q_fr, int64_t T, int F,
                       uint32_t flags);

@@ -19,6 +19,10 @@ SIGNATURES = {
     "jtfs_plan_destroy": (c_int, [c_void_p]),
     "jtfs_phi_size": (c_int64, [c_void_p]),
     "jtfs_workspace_bytes": (c_size_t, [c_void_p]),
+    "jtfs_path_meta": (c_int, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32), POINTER(c_int32),
+                               POINTER(c_int64)]),
+    "jtfs_plan_ragged": (c_int, [POINTER(c_void_p), POINTER(c_int64), c_int, c_int, c_int, c_int, c_int,
+                                 c_int, c_int64, c_int, c_uint32]),
     "jtfs_plan_info": (c_int, [c_void_p, POINTER(c_int64), c_int]),
     "jtfs_plan_filters": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_double),
                                   POINTER(c_int32), c_int]),

@@ -284,6 +284,11 @@ extern "C" int jtfs_batch_create(jtfs_batch_t* out, const int64_t* lengths, int 
   return JTFS_OK;
 }
 
+extern "C" int jtfs_plan_ragged(jtfs_batch_t* out, const int64_t* lengths, int count, int J, int Q, int Q2,
+                                int J_fr, int Q_fr, int64_t T, int F, uint32_t flags) {
+  return jtfs_batch_create(out, lengths, count, J, Q, Q2, J_fr, Q_fr, T, F, flags);
+}
+
 extern "C" int jtfs_batch_destroy(jtfs_batch_t batch) {
   destroy_batch(batch);
   return JTFS_OK;

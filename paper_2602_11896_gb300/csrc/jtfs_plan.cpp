@@ -676,6 +676,29 @@ extern "C" size_t jtfs_workspace_bytes(jtfs_plan_t plan) {
   return plan ? plan->p.ws_bytes : 0;
 }
 
+extern "C" int jtfs_path_meta(jtfs_plan_t plan, int32_t* order, int32_t* n2, int32_t* beta_idx, int32_t* spin,
+                              int64_t* offset) {
+  if (!plan) return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  int k = 0;
+  auto put = [&](int o, int nn, int bi, int sp, int64_t off) {
+    if (order) order[k] = o;
+    if (n2) n2[k] = nn;
+    if (beta_idx) beta_idx[k] = bi;
+    if (spin) spin[k] = sp;
+    if (offset) offset[k] = off;
+    ++k;
+  };
+  auto spin_of = [&](int b) { return b == 0 ? 0 : (b <= p.K ? 1 : -1); };
+  put(0, -1, -1, 0, 0);  // zeroth order
+  for (int b = 0; b < p.n_beta1; ++b) put(1, -1, b, spin_of(b), p.phi1_off + int64_t(p.row_off[b]) * p.n_frames);
+  for (int a = 0; a < p.n_active; ++a) {
+    const int64_t frames = p.unpooled_t ? (int64_t(p.N) >> p.s2[a]) : p.n_frames;
+    for (int b = 0; b < p.n_beta2; ++b) put(2, p.active[a], b, spin_of(b), p.phi2_off[a] + p.row_off[b] * frames);
+  }
+  return k;
+}
+
 extern "C" int jtfs_plan_info(jtfs_plan_t plan, int64_t* info, int count) {
   if (!plan || (count > 0 && !info)) return JTFS_ERR_ARG;
   const jtfs::Plan& p = plan->p;

@@ -83,6 +83,18 @@ class JTFSPlan:
         self._lib.jtfs_plan_filters(self._h, which, xi, sg, jj, n)
         return np.array(xi[:]), np.array(sg[:]), np.array(jj[:], dtype=np.int64)
 
+    def path_meta(self) -> Dict[str, np.ndarray]:
+        """Per path of Phi, in order: order (0, 1, 2), n2, beta_idx, spin and offset (see jtfs_path_meta)."""
+        n = int(self._lib.jtfs_path_meta(self._h, None, None, None, None, None))
+        _native.check(0 if n >= 0 else n, "jtfs_path_meta")
+        arrs = [(c_int32 * n)() for _ in range(4)]
+        off = (c_int64 * n)()
+        self._lib.jtfs_path_meta(self._h, *arrs, off)
+        keys = ("order", "n2", "beta_idx", "spin")
+        out = {k: np.array(a[:], dtype=np.int64) for k, a in zip(keys, arrs)}
+        out["offset"] = np.array(off[:], dtype=np.int64)
+        return out
+
     # -- tuning -----------------------------------------------------------
     def tuning(self) -> Tuple[int, int, int, int, int]:
         """(wide forward tiles, pooling split, small-FFT points per CTA, tensor-core frequential path,

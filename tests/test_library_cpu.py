@@ -128,3 +128,43 @@ def test_batch_refuses_unpooled_flags():
     for flag in (_native.PLAN_UNPOOLED_T, _native.PLAN_UNPOOLED_F):
         rc = lib.jtfs_batch_create(ctypes.byref(h), arr, 2, 4, 4, 1, 2, 1, 16, 2, _native.PLAN_HOST_ONLY | flag)
         assert rc == -1 and not h.value
+
+
+@pytest.mark.parametrize("variant", [(True, True), (False, True), (True, False), (False, False)])
+@pytest.mark.parametrize("name", ["tones8k_n8192", "chirps22k_b8_n65536"])
+def test_path_meta_matches_oracle_layout(name, variant):
+    """Per-path metadata (host-only plans) against the oracle's Phi layout and frequential filter sets."""
+    from paper_2602_11896_gb300 import JTFSPlan
+    from workloads import get_workload
+    wl = get_workload(name)
+    kw = dict(average_local=variant[0], average_local_fr=variant[1])
+    plan = JTFSPlan(**wl.params, host_only=True, **kw)
+    op = O.Plan(**wl.params, **kw)
+    m = plan.path_meta()
+    K1, K2 = len(op.beta_first), len(op.beta_second)
+    n = 1 + K1 + len(op.active) * K2
+    assert all(len(v) == n for v in m.values())
+    assert m["order"].tolist() == [0] + [1] * K1 + [2] * (len(op.active) * K2)
+    assert m["n2"].tolist() == [-1] * (1 + K1) + [n2 for n2 in op.active for _ in range(K2)]
+    assert m["beta_idx"].tolist() == [-1] + list(range(K1)) + list(range(K2)) * len(op.active)
+    signs = [int(np.sign(b[0])) for b in op.beta_second]
+    assert m["spin"].tolist() == [0] + signs[:K1] + signs * len(op.active)
+    # offsets: increasing, path sizes = rows x frames of the oracle's layout, blocks where phi_blocks puts them
+    sizes = [op.N if not op.average_local else op.n_frames]
+    sizes += [op.rows(b) * op.n_frames for b in op.beta_first]
+    sizes += [op.rows(b) * op.frames2(n2) for n2 in op.active for b in op.beta_second]
+    ends = np.cumsum(sizes)
+    assert m["offset"].tolist() == [0] + ends[:-1].tolist()
+    assert ends[-1] == op.phi_size == plan.phi_size
+
+
+def test_plan_ragged_is_the_ragged_batch():
+    lib = _native.load()
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int64 * 3)(300, 512, 100)
+    assert lib.jtfs_plan_ragged(ctypes.byref(h), arr, 3, 4, 4, 1, 2, 1, 16, 2, _native.PLAN_HOST_ONLY) == 0
+    so = (ctypes.c_int64 * 4)()
+    po = (ctypes.c_int64 * 4)()
+    assert lib.jtfs_batch_layout(h, so, po) == 3
+    assert list(so) == [0, 300, 812, 912]
+    lib.jtfs_batch_destroy(h)
