@@ -40,6 +40,7 @@ constexpr int kPtProd = 256;  // producer / epilogue threads (warps 0-7)
 constexpr int kPtWarpMma = 8;
 constexpr int kPtRows = 128;  // rows per tile (MMA M)
 constexpr int kPtK = 64;      // samples per operand block (one 128-byte swizzle atom of BF16)
+static_assert(kPtProd == 2 * kPtRows, "two producer threads per tile row");
 
 struct PtArgs {
   const float* V2;
