@@ -177,3 +177,32 @@ def test_bold_driver_clips_are_independent_and_nan_rejects():
     np.testing.assert_allclose(out["y"][1], [3.0 - 0.1 - 0.2, 4.0 + 0.1 - 0.2])
     np.testing.assert_allclose(out["g_acc"][1], [2.0, 2.0])
     np.testing.assert_allclose(out["y"][2], [5.0 - 1.0 - 0.4, 6.0 - 1.0 - 0.4])
+
+
+def test_bold_driver_accepted_loss_never_increases_on_the_jtfs_loss():
+    """Behaviour on the real loss (tone clip, mu0 = 300, steps that overshoot): the loss at the accepted
+    point never increases, every increase is rejected with the step size halved, and y returns to the
+    accepted point before stepping again (the next evaluation's loss is below the rejected one)."""
+    wl = get_workload("tones8k_n8192")
+    op = O.Plan(**wl.params)
+    tgt = O.jtfs(torch.tensor(wl.targets(), dtype=F64), op)["phi"]
+    y = wl.inits().astype(np.float64)
+    u = np.zeros_like(y)
+    g_acc = np.zeros_like(y)
+    mu = np.array([300.0])
+    E_acc = np.array([np.inf])
+    history = []
+    for _ in range(8):
+        E, g = O.loss_and_grad(torch.tensor(y), tgt, op)
+        out = R.bold_driver_step(y, u, g_acc, mu, E_acc, E.numpy(), g.numpy())
+        history.append((float(E[0]), bool(out["accepted"][0]), float(mu[0]), float(out["mu"][0]),
+                        float(E_acc[0]), float(out["E_acc"][0])))
+        y, u, g_acc, mu, E_acc = out["y"], out["u"], out["g_acc"], out["mu"], out["E_acc"]
+    accepted = [h[1] for h in history]
+    assert True in accepted[1:] and False in accepted
+    for E, acc, mu_in, mu_out, ea_in, ea_out in history:
+        assert ea_out <= ea_in
+        if acc:
+            assert E <= ea_in and ea_out == E
+        else:
+            assert E > ea_in and ea_out == ea_in and mu_out == 0.5 * mu_in
