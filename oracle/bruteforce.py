@@ -13,8 +13,15 @@ alias or a wrong decimation phase in either one shows up as a mismatch:
   "levels[k]", §3.2-§3.3), not a periodised spectrum;
 * every convolution is the direct sum y[t] = sum_s x[s] h[(t - s) mod n].
 
-Filter construction (Eq. (1), §3.1) and the schedule follow the same
-readings as ``jtfs_oracle`` and are retyped here on purpose.
+* the multirate schedule is derived here from the filters' (xi, sigma)
+  alone: the subsampling j of a filter (reading R2: the largest k >= 0 with
+  2^k (xi + 3 sigma) <= 1/2) by counting doublings, the strides k1, s2, k_fr,
+  the second-order row sets (j1 < j2), N_fr and R_out, so that a misreading
+  of the schedule in ``jtfs_oracle`` shows up here too.
+
+Only the filterbank values (xi, sigma of every filter, pinned separately by
+the closed-form counts and progressions of §3.1) and the configuration are
+taken from the oracle's ``Plan``.
 """
 
 from __future__ import annotations
@@ -67,13 +74,57 @@ def _along(a: np.ndarray, axis: int, fn) -> np.ndarray:
     return np.moveaxis(fn(np.moveaxis(a, axis, -1)), -1, axis)
 
 
+def subsampling(xi: float, sigma: float) -> int:
+    """Reading R2 by counting: double the band edge xi + 3 sigma while it stays <= 1/2."""
+    edge, k = xi + 3.0 * sigma, 0
+    while 2.0 * edge <= 0.5:
+        edge *= 2.0
+        k += 1
+    return k
+
+
+def _log2_floor(v: int) -> int:
+    k = 0
+    while (2 << k) <= v:
+        k += 1
+    return k
+
+
+def schedule(plan: Plan) -> Dict:
+    """Strides and row sets of the multirate schedule (readings R2, R3, R7, R8, R10, R21)."""
+    lT, lF = _log2_floor(plan.T), _log2_floor(plan.F)
+    j1 = [subsampling(f.xi, f.sigma) for f in plan.psi1]
+    j2 = [subsampling(f.xi, f.sigma) for f in plan.psi2]
+    jfr = [subsampling(f.xi, f.sigma) for f in plan.psi_fr]
+    sig_phiF = 0.1 / plan.F
+    jphiF = subsampling(0.0, sig_phiF)
+    nfr = 1
+    while nfr < len(plan.psi1) + 2 ** (plan.J_fr + 1):
+        nfr *= 2
+    kfr = (lambda j: min(j, lF)) if plan.average_local_fr else (lambda j: j)
+    phi = (0.0, sig_phiF, kfr(jphiF))
+    plus = [(f.xi, f.sigma, kfr(j)) for f, j in zip(plan.psi_fr, jfr)]
+    minus = [(-f.xi, f.sigma, kfr(j)) for f, j in zip(plan.psi_fr, jfr)]
+    rows2 = [[n1 for n1 in range(len(j1)) if j1[n1] < jj] for jj in j2]
+    return {
+        "lT": lT, "lF": lF, "N_fr": nfr, "sigma_phiT": 0.1 / plan.T, "sigma_phiF": sig_phiF,
+        "j1": j1, "j2": j2,
+        "k1": [min(j, lT) for j in j1],                                     # first order (R7)
+        "k1_2": [min(j, lT) if plan.average_local else j for j in j1],     # rows feeding the second order
+        "s2": [min(j, lT) if plan.average_local else j for j in j2],       # second order total stride
+        "rows2": rows2, "active": [n2 for n2, r in enumerate(rows2) if r],
+        "beta_first": [phi] + plus, "beta_second": [phi] + plus + minus,
+    }
+
+
 def jtfs_bruteforce(x: np.ndarray, plan: Plan, keep: bool = False) -> Dict[str, np.ndarray]:
     """Phi of x [N] or [B, N] by direct convolution; returns {'phi': [B, size]}."""
     x = np.atleast_2d(np.asarray(x, dtype=np.float64))
     B, N = x.shape
-    lT, lF, Nfr = plan.lT, plan.lF, plan.N_fr
-    phiT = idft_explicit(_morlet(N, 0.0, plan.sigma_phiT))
-    phiF = idft_explicit(_morlet(Nfr, 0.0, plan.sigma_phiF))
+    sch = schedule(plan)
+    lT, lF, Nfr = sch["lT"], sch["lF"], sch["N_fr"]
+    phiT = idft_explicit(_morlet(N, 0.0, sch["sigma_phiT"]))
+    phiF = idft_explicit(_morlet(Nfr, 0.0, sch["sigma_phiF"]))
 
     # Unpooled variants (reading R21): plan.average_local / plan.average_local_fr.
     S0 = circ_conv(x.astype(np.complex128), phiT).real[:, :: 2 ** lT] if plan.average_local else x.copy()
@@ -83,12 +134,12 @@ def jtfs_bruteforce(x: np.ndarray, plan: Plan, keep: bool = False) -> Dict[str, 
     for n1, f in enumerate(plan.psi1):
         h = idft_explicit(_morlet(N, f.xi, f.sigma))
         full = circ_conv(x.astype(np.complex128), h)
-        U1.append(np.abs(full[:, :: 2 ** plan.k1[n1]]))
-        U1_2.append(np.abs(full[:, :: 2 ** (plan.k1[n1] if plan.average_local else f.j)]))
+        U1.append(np.abs(full[:, :: 2 ** sch["k1"][n1]]))
+        U1_2.append(np.abs(full[:, :: 2 ** sch["k1_2"][n1]]))
 
     S1 = np.stack([
         circ_conv(U1[n1].astype(np.complex128), level(phiT, k1)).real[:, :: 2 ** (lT - k1)]
-        for n1, k1 in enumerate(plan.k1)], axis=1)                     # [B, N1, N/T]
+        for n1, k1 in enumerate(sch["k1"])], axis=1)                   # [B, N1, N/T]
 
     def freq_path(Z: np.ndarray, xi_b: float, sig_b: float, k_b: int) -> np.ndarray:
         """|Z *_n1 psi_beta| decimated, then *_n1 phi_F decimated; Z [B, N_fr, L]."""
@@ -101,23 +152,23 @@ def jtfs_bruteforce(x: np.ndarray, plan: Plan, keep: bool = False) -> Dict[str, 
         return v[:, :: 2 ** (lF - k_b), :]
 
     S1p = np.zeros((B, Nfr, S1.shape[2]), dtype=np.complex128)
-    S1p[:, : plan.N1] = S1
-    Phi1 = np.concatenate([freq_path(S1p, *b) for b in plan.beta_first], axis=1)
+    S1p[:, : len(plan.psi1)] = S1
+    Phi1 = np.concatenate([freq_path(S1p, *b) for b in sch["beta_first"]], axis=1)
 
     blocks = []
-    for n2 in plan.active:
+    for n2 in sch["active"]:
         f2 = plan.psi2[n2]
-        s2 = min(f2.j, lT) if plan.average_local else f2.j
+        s2 = sch["s2"][n2]
         h2 = idft_explicit(_morlet(N, f2.xi, f2.sigma))
         rows = []
-        for n1 in range(plan.n1_max[n2]):
-            k1 = plan.k1[n1] if plan.average_local else plan.psi1[n1].j
+        for n1 in sch["rows2"][n2]:
+            k1 = sch["k1_2"][n1]
             rows.append(circ_conv(U1_2[n1].astype(np.complex128), level(h2, k1))[:, :: 2 ** (s2 - k1)])
         Y2 = np.stack(rows, axis=1)
         Y2p = np.zeros((B, Nfr, Y2.shape[2]), dtype=np.complex128)
         Y2p[:, : Y2.shape[1]] = Y2
         per_beta = []
-        for xi_b, sig_b, k_b in plan.beta_second:
+        for xi_b, sig_b, k_b in sch["beta_second"]:
             hb = idft_explicit(_morlet(Nfr, xi_b, sig_b))
             y = _along(Y2p, 1, lambda a: circ_conv(a, hb))[:, :: 2 ** k_b, :]
             a = np.abs(y)

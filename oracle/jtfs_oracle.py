@@ -102,32 +102,40 @@ C128 = torch.complex128
 # ---------------------------------------------------------------------------
 
 def morlet_filterbank(J: int, Q: int) -> List[Tuple[float, float]]:
-    """(xi, sigma) pairs of the §3.1 generator, in the order it yields them.
+    """(xi, sigma) of the filterbank §3.1 generates, highest centre frequency first.
 
-    Start at xi = max(1/(1 + 2^(3/Q)), 0.35) with the bandwidth that keeps
-    quality factor Q at an overlap of r_psi between neighbours; divide xi and
-    sigma by 2^(1/Q) while sigma stays above sigma_min * 2^(1/Q), where
-    sigma_min = sigma0 / 2^J (the "elbow"); then emit Q-1 constant-bandwidth
-    filters whose xi decreases arithmetically by elbow_xi / Q.
+    Written from what the generator computes, not from its loop:
+
+    * Constant-Q part.  The first centre frequency is xi_0 = max(1/(1 + 2^(3/Q)),
+      0.35).  Neighbours sit a factor f = 2^(-1/Q) apart, and the width is the
+      one at which a filter and its lower neighbour (width scaled by f too)
+      have both fallen to r_psi where they meet:
+          xi_0 - c sigma_0 = f (xi_0 + c sigma_0),   c = sqrt(2 ln(1/r_psi)),
+      so sigma_0 = (1 - f) / (1 + f) * xi_0 / c.  Filter k has
+      (xi_0 f^k, sigma_0 f^k); k runs from 0 to K, K being the number of
+      k >= 0 whose width sigma_0 f^k still exceeds sigma_min / f, with
+      sigma_min = sigma_0' / 2^J the elbow width (sigma_0' = 0.1 of §3.1).
+    * Constant-bandwidth part.  Below the elbow xi_e = xi_0 f^K, Q - 1 filters
+      of width sigma_min at xi_e (1 - m/Q), m = 1 .. Q - 1.
+    * If sigma_0 <= sigma_min there is no constant-Q part and xi_e = sigma_0
+      (the generator's literal branch, reading of §3.1).
     """
-    xi = max(1.0 / (1.0 + math.pow(2.0, 3.0 / Q)), 0.35)
-    factor = 1.0 / math.pow(2.0, 1.0 / Q)
-    sigma = (1.0 - factor) / (1.0 + factor) * xi / math.sqrt(2.0 * math.log(1.0 / R_PSI))
+    f = math.pow(2.0, -1.0 / Q)
+    xi0 = max(1.0 / (1.0 + math.pow(2.0, 3.0 / Q)), 0.35)
+    c = math.sqrt(2.0 * math.log(1.0 / R_PSI))
+    sigma0 = (1.0 - f) / (1.0 + f) * xi0 / c
     sigma_min = SIGMA0 / 2 ** J
-    out: List[Tuple[float, float]] = []
-    if sigma <= sigma_min:
-        xi = sigma
+    if sigma0 <= sigma_min:
+        constant_q: List[Tuple[float, float]] = []
+        xi_elbow = sigma0
     else:
-        out.append((xi, sigma))
-        while sigma > sigma_min * math.pow(2.0, 1.0 / Q):
-            xi /= math.pow(2.0, 1.0 / Q)
-            sigma /= math.pow(2.0, 1.0 / Q)
-            out.append((xi, sigma))
-    elbow_xi = xi
-    for _ in range(Q - 1):
-        xi -= 1.0 / Q * elbow_xi
-        out.append((xi, sigma_min))
-    return out
+        K = 0
+        while sigma0 * math.pow(f, K) > sigma_min / f:
+            K += 1
+        constant_q = [(xi0 * math.pow(f, k), sigma0 * math.pow(f, k)) for k in range(K + 1)]
+        xi_elbow = constant_q[-1][0]
+    constant_bw = [(xi_elbow * (1.0 - m / Q), sigma_min) for m in range(1, Q)]
+    return constant_q + constant_bw
 
 
 def max_subsampling(xi: float, sigma: float) -> int:
@@ -178,6 +186,7 @@ class Plan:
         self.psi_fr = [Filter(x, s, max_subsampling(x, s)) for x, s in morlet_filterbank(self.J_fr, self.Q_fr)]
         self.sigma_phiT = SIGMA0 / self.T
         self.sigma_phiF = SIGMA0 / self.F
+        self.j_phiT = max_subsampling(0.0, self.sigma_phiT)
         self.j_phiF = max_subsampling(0.0, self.sigma_phiF)
         self.N1 = len(self.psi1)
         self.K = len(self.psi_fr)

@@ -73,6 +73,74 @@ def test_phi_sizes_of_named_workloads():
     assert p2.phi_size == gold["chirps22k_b8_n65536"]
 
 
+# --------------------------------------------------------------------------- subsampling j (reading R2)
+
+SUBS = os.path.join(os.path.dirname(__file__), "golden", "subsampling_j.json")
+
+
+def _subsampling_mismatches():
+    """Differences between the oracle's schedule and the hand-derived tables (empty when they agree)."""
+    gold = json.load(open(SUBS))["configs"]
+    bad = []
+    for name, g in gold.items():
+        p = O.Plan(**g["params"])
+        for key, fb in (("psi1", p.psi1), ("psi2", p.psi2), ("psi_fr", p.psi_fr)):
+            if [f.j for f in fb] != [e["j"] for e in g[key]]:
+                bad.append((name, key))
+        if p.j_phiT != g["phi_T"]["j"] or p.j_phiT != p.lT:
+            bad.append((name, "phi_T"))
+        if p.j_phiF != g["phi_F"]["j"]:
+            bad.append((name, "phi_F"))
+        if p.n1_max != g["n1_max"]:
+            bad.append((name, "n1_max"))
+    return bad
+
+
+def test_subsampling_matches_hand_derived_tables():
+    """Every filter's j, j(phi_T) = log2 T and the row counts n1_max of the tone and chirp plans equal
+    the tables derived in 50-digit arithmetic from the closed forms (tests/golden/subsampling_j.json)."""
+    assert _subsampling_mismatches() == []
+    gold = json.load(open(SUBS))["configs"]
+    from oracle.bruteforce import schedule
+    for g in gold.values():
+        p = O.Plan(**g["params"])
+        for key, fb in (("psi1", p.psi1), ("psi2", p.psi2), ("psi_fr", p.psi_fr)):
+            for f, e in zip(fb, g[key]):      # the restated filterbank against the closed form
+                assert abs(f.xi - e["xi"]) <= 1e-14 and abs(f.sigma - e["sigma"]) <= 1e-14
+        sch = schedule(p)                     # the brute force's own schedule
+        assert sch["j1"] == [e["j"] for e in g["psi1"]] and sch["j2"] == [e["j"] for e in g["psi2"]]
+        assert [len(r) for r in sch["rows2"]] == g["n1_max"]
+
+
+def test_phi_T_subsampling_is_log2_T():
+    """phi_T of width 0.1 / T (reading R3) has j = log2 T: 3 x 0.1 lies in (1/4, 1/2]."""
+    for lT in range(0, 16):
+        T = 2 ** lT
+        assert O.max_subsampling(0.0, 0.1 / T) == lT
+        assert O.Plan(N=max(T, 16), J=2, Q=1, Q2=1, J_fr=1, Q_fr=1, T=T, F=1).j_phiT == lT
+
+
+@pytest.mark.parametrize("plant", ["xi_plus_2_sigma", "round"])
+def test_pins_catch_wrong_subsampling(monkeypatch, plant):
+    """Plant a misreading of R2 in the oracle: the hand-derived tables and the brute force (which derives
+    its own schedule) must both disagree."""
+    p0 = O.Plan(**TINY[1])
+    x = np.random.default_rng(13).standard_normal((1, p0.N))
+
+    def two_sigma(xi, sigma):
+        return max(0, int(math.floor(math.log2(0.5 / (xi + 2.0 * sigma)))))
+
+    def rounded(xi, sigma):
+        return max(0, int(round(math.log2(0.5 / (xi + 3.0 * sigma)))))
+
+    monkeypatch.setattr(O, "max_subsampling", two_sigma if plant == "xi_plus_2_sigma" else rounded)
+    assert _subsampling_mismatches() != []
+    p = O.Plan(**TINY[1])
+    a = O.jtfs(torch.tensor(x), p)["phi"].numpy()
+    b = jtfs_bruteforce(x, p)["phi"]
+    assert a.shape != b.shape or _rel(a, b) > 1e-3
+
+
 # --------------------------------------------------------------------------- filters (Eq. 1)
 
 def test_morlet_zero_mean_and_peak():
