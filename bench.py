@@ -294,6 +294,13 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def device_status(what: str) -> None:
+    """Fail the run if, since the last check, a tensor-core kernel gave up on a barrier (its outputs, and
+    so the timed work, are invalid) or a loss was NaN / Inf (jtfs_status; synchronises the stream)."""
+    from paper_2602_11896_gb300 import _native
+    _native.check_status(what, torch.cuda.current_stream().cuda_stream)
+
+
 def config_dict(wl):
     cfg = {"workload": wl.name, "batch": wl.batch, "N": wl.N, "J": wl.J, "Q": wl.Q, "Q2": wl.Q2,
            "J_fr": wl.J_fr, "Q_fr": wl.Q_fr, "T": wl.T, "F": wl.F, "sample_rate_hz": wl.sr,
@@ -348,6 +355,7 @@ def run_uneven(args):
         e1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
+    device_status("timed steps")
     lat = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
     total = sum(lengths)
     line = {"metric": "batched uneven metamer step audio-samples/s", "value": total / (lat.mean() / 1e3),
@@ -399,6 +407,7 @@ def run_reflect(args):
         e1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
+    device_status("timed steps")
     lat = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
     total = sum(lengths)
     line = {"metric": "JTFS fwd+bwd audio-samples/s (reflect boundary)", "value": total / (lat.mean() / 1e3),
@@ -515,6 +524,7 @@ def run_long(args):
         e1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
+    device_status("timed steps")
     ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
     peak = torch.cuda.max_memory_allocated()
     line = {"metric": METRIC, "value": wl.batch * wl.N / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": K,
@@ -713,6 +723,7 @@ def main():
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
+    device_status("timed steps")
     if dist:
         dist.barrier()
     for st in range(6):
@@ -787,6 +798,7 @@ def main():
         yo_host.copy_(y_dev, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
+    device_status("end-to-end steps")
     e2e_ms, e2e_value = job_throughput(e0.elapsed_time(e1) / Ke, world, wl.batch, wl.N, 1, dist if dist else None, dev)
     e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(y_host.numel() * 4 + t_host.numel() * 4),

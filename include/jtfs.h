@@ -25,6 +25,12 @@
  *   on entry is ignored; calls sharing one workspace must not overlap in time.
  * - A plan is immutable after creation and may be shared by several streams
  *   provided each uses its own workspace.
+ * - Device-side errors: a kernel cannot return a code, so the two failures
+ *   only a running kernel sees -- a non-finite loss (JTFS_ERR_NONFINITE) and a
+ *   tensor-core barrier wait that ran out (JTFS_ERR_TIMEOUT) -- set a status
+ *   word in device memory, and jtfs_status() (a synchronising call) returns
+ *   and clears it.  Call it after a run of compute calls, e.g. once per
+ *   descent, before trusting their results.
  */
 #ifndef JTFS_H
 #define JTFS_H
@@ -46,6 +52,11 @@ extern "C" {
 #define JTFS_ERR_NODEVICE  -6  /* plan was created host-only                */
 #define JTFS_ERR_TOOBIG    -7  /* plan needs more scratch than the fixed
                                   array of jtfs_forward_noalloc holds       */
+#define JTFS_ERR_NONFINITE -8  /* a loss evaluated since the last
+                                  jtfs_status was NaN or infinite           */
+#define JTFS_ERR_TIMEOUT   -9  /* a tensor-core kernel gave up waiting on one
+                                  of its barriers since the last jtfs_status;
+                                  the outputs of that call are invalid      */
 
 /* Plan flags. */
 #define JTFS_PLAN_HOST_ONLY 1u /* build the tables on the host only; compute
@@ -197,6 +208,21 @@ int jtfs_loss_grad(jtfs_plan_t plan, const float* y, const float* phi_target,
 int metamer_step(jtfs_plan_t plan, float* y, const float* phi_target,
                  float* adam_m, float* adam_v, int step, float lr,
                  float* loss_out, void* workspace, void* stream);
+
+/*
+ * metamer_step_counted -- metamer_step with the 1-based Adam step index read
+ * from device memory (`step`, one int32) and incremented there by the call,
+ * so that one recorded call replays as successive steps from a CUDA graph
+ * (the §2.3 descent repeated with no host involvement).  The bias
+ * corrections are computed on the device in double from that index, as
+ * metamer_step computes them on the host, so the iterates of the two calls
+ * agree.  Arguments and errors
+ * otherwise as metamer_step (step must hold >= 1; it is not checked on the
+ * host).
+ */
+int metamer_step_counted(jtfs_plan_t plan, float* y, const float* phi_target,
+                         float* adam_m, float* adam_v, int32_t* step, float lr,
+                         float* loss_out, void* workspace, void* stream);
 
 /*
  * Reconstruction variant of §2.3: the paper starts the descent from coloured
@@ -517,6 +543,35 @@ int64_t jtfs_tc_table(jtfs_plan_t plan, int which, float* out, int64_t n);
  * Synchronous; clears the record; returns 4 or JTFS_ERR_CUDA.
  */
 int jtfs_tc_error_info(int64_t* info, int n);
+
+/*
+ * jtfs_status -- the device-side status of every call enqueued on this
+ * device since the previous jtfs_status: synchronises `stream` (void* as
+ * elsewhere), then reads and clears the status word.
+ *   JTFS_ERR_TIMEOUT    a tensor-core kernel (frequential scattering, time
+ *                       pooling or decoder layer) gave up on a barrier wait;
+ *                       the call that launched it produced invalid outputs.
+ *   JTFS_ERR_NONFINITE  a loss (jtfs_loss_grad, metamer_step*, the batch
+ *                       step) was NaN or infinite: §2.3's loss is finite for
+ *                       finite inputs, so y or the target held NaN / Inf.
+ *   JTFS_OK             neither.
+ * TIMEOUT is reported in preference to NONFINITE.  The word is per device,
+ * not per stream: a call on another stream that has not finished may set it
+ * later.  Also clears what jtfs_tc_error / jtfs_decoder_error report.
+ * JTFS_ERR_CUDA if the stream or the word cannot be read.
+ */
+int jtfs_status(void* stream);
+
+/*
+ * jtfs_set_wait_limit -- for tests of the error path: the number of polls
+ * every later bounded barrier wait of the tensor-core kernels makes before
+ * giving up (polls >= 0; 0 makes every such wait give up at once), or the
+ * default bound (about 0.3 s) again for polls < 0.  Waits that drain copies
+ * and MMAs before a CTA exits keep their full bound, so a kernel that gives
+ * up still leaves no copy or MMA in flight.  Synchronous; affects every plan
+ * on the current device.  Returns JTFS_OK or JTFS_ERR_CUDA.
+ */
+int jtfs_set_wait_limit(int64_t polls);
 
 /* Static description of an error code (never NULL). */
 const char* jtfs_error_string(int code);

@@ -79,7 +79,14 @@ SIGNATURES = {
     "jtfs_profile_stage": (c_int, [c_void_p, c_int, POINTER(c_void_p), c_int]),
     "jtfs_launch_count": (c_int64, [c_void_p, c_int]),
     "jtfs_error_string": (c_char_p, [c_int]),
+    "metamer_step_counted": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float,
+                                     c_void_p, c_void_p, c_void_p]),
+    "jtfs_status": (c_int, [c_void_p]),
+    "jtfs_set_wait_limit": (c_int, [c_int64]),
 }
+
+ERR_NONFINITE = -8
+ERR_TIMEOUT = -9
 
 PLAN_HOST_ONLY = 1
 BATCH_REFLECT = 2
@@ -110,6 +117,29 @@ def error_string(code: int) -> str:
     return load().jtfs_error_string(code).decode()
 
 
+class DeviceStatusError(RuntimeError):
+    """A failure only a running kernel could see (jtfs_status): ``code`` is JTFS_ERR_TIMEOUT or
+    JTFS_ERR_NONFINITE."""
+
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {error_string(code)} ({code})")
+        self.code = code
+
+
 def check(code: int, what: str) -> None:
     if code != 0:
         raise RuntimeError(f"{what} failed: {error_string(code)} ({code})")
+
+
+def status(stream: int = 0) -> int:
+    """jtfs_status on a raw cudaStream_t handle (synchronises it): 0, ERR_TIMEOUT or ERR_NONFINITE."""
+    return int(load().jtfs_status(c_void_p(stream)))
+
+
+def check_status(what: str, stream: int = 0) -> None:
+    """Raise DeviceStatusError if a kernel gave up on a barrier or a loss was non-finite since the
+    last check (synchronises the stream)."""
+    code = status(stream)
+    if code in (ERR_TIMEOUT, ERR_NONFINITE):
+        raise DeviceStatusError(code, what)
+    check(code, what)

@@ -87,6 +87,9 @@ __global__ void __launch_bounds__(kThreadsB) k_fold(const ClipD* __restrict__ cl
   }
 }
 
+// Set by k_masked_loss when a clip's loss is NaN or infinite (jtfs_status).
+__device__ int g_batch_nonfinite;
+
 // Loss over the kept frames, dPhi = 2 (Phi - target) there and 0 on cropped
 // frames; one block per clip, fixed-order reduction.
 __global__ void __launch_bounds__(512) k_masked_loss(const ClipD* __restrict__ clips, const float* __restrict__ tgt,
@@ -110,7 +113,10 @@ __global__ void __launch_bounds__(512) k_masked_loss(const ClipD* __restrict__ c
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) loss[blockIdx.x] = static_cast<float>(red[0]);
+  if (threadIdx.x == 0) {
+    loss[blockIdx.x] = static_cast<float>(red[0]);
+    if (!isfinite(red[0])) atomicOr(&g_batch_nonfinite, 1);
+  }
 }
 
 // Cropped Phi, packed.
@@ -148,6 +154,15 @@ __global__ void __launch_bounds__(kThreadsB) k_adam_packed(const ClipD* __restri
 __global__ void k_step_increment(int* step) { *step += 1; }
 
 }  // namespace
+
+int batch_nonfinite_take() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_batch_nonfinite, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
+  const int zero = 0;
+  if (v && cudaMemcpyToSymbol(g_batch_nonfinite, &zero, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
+  return v;
+}
+
 }  // namespace jtfs
 
 struct jtfs_batch_s {

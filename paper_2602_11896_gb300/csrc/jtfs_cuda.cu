@@ -1234,8 +1234,11 @@ k_dX(GradArgs A, int64_t total, const float2* __restrict__ dZ1, const float2* __
 
 // ---------------------------------------------------------------------------
 // Loss E_b = sum (phi - target)^2 and dphi = 2 (phi - target); fixed-order
-// block reduction (deterministic).
+// block reduction (deterministic).  A NaN or infinite E_b sets g_nonfinite,
+// which jtfs_status reports.
 // ---------------------------------------------------------------------------
+__device__ int g_nonfinite;
+
 __global__ void __launch_bounds__(512)
 k_loss(const float* __restrict__ phi, const float* __restrict__ tgt, float* __restrict__ dphi,
        float* __restrict__ loss, int64_t size) {
@@ -1255,7 +1258,10 @@ k_loss(const float* __restrict__ phi, const float* __restrict__ tgt, float* __re
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) loss[b] = static_cast<float>(red[0]);
+  if (threadIdx.x == 0) {
+    loss[b] = static_cast<float>(red[0]);
+    if (!isfinite(red[0])) atomicOr(&g_nonfinite, 1);
+  }
 }
 
 // Large Phi: the same loss over `parts` CTAs per clip.  Part j of clip b
@@ -1296,7 +1302,10 @@ k_loss_sum(const double* __restrict__ part_sum, float* __restrict__ loss, int pa
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) loss[blockIdx.x] = static_cast<float>(red[0]);
+  if (threadIdx.x == 0) {
+    loss[blockIdx.x] = static_cast<float>(red[0]);
+    if (!isfinite(red[0])) atomicOr(&g_nonfinite, 1);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -1311,6 +1320,32 @@ k_adam(float* __restrict__ y, float* __restrict__ m, float* __restrict__ v, cons
   v[i] = vi;
   y[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
 }
+
+// Adam with the 1-based step index read from device memory (graph replay).
+// The bias corrections are computed once per block in double, as metamer_step
+// computes them on the host, so both give the same iterates.
+__global__ void __launch_bounds__(kThreads)
+k_adam_counted(float* __restrict__ y, float* __restrict__ m, float* __restrict__ v, const float* __restrict__ g,
+               int64_t n, float lr, const int* __restrict__ step) {
+  __shared__ float corr[2];
+  if (threadIdx.x == 0) {
+    const double t = static_cast<double>(*step);
+    corr[0] = static_cast<float>(1.0 / (1.0 - pow(0.9, t)));
+    corr[1] = static_cast<float>(1.0 / (1.0 - pow(0.999, t)));
+  }
+  __syncthreads();
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float c1 = corr[0], c2 = corr[1];
+  const float gi = g[i];
+  const float mi = 0.9f * m[i] + 0.1f * gi;
+  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  y[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+}
+
+__global__ void k_step_next(int* step) { *step += 1; }
 
 // ---------------------------------------------------------------------------
 // Reconstruction variant of §2.3: coloured initialisation and momentum
@@ -1950,6 +1985,46 @@ extern "C" int metamer_step(jtfs_plan_t plan, float* y, const float* phi_target,
   jtfs::k_adam<<<static_cast<unsigned>((n + jtfs::kThreads - 1) / jtfs::kThreads), jtfs::kThreads, 0, s>>>(
       y, adam_m, adam_v, w.dy, n, lr, c1, c2);
   return jtfs::check_launch();
+}
+
+extern "C" int metamer_step_counted(jtfs_plan_t plan, float* y, const float* phi_target, float* adam_m,
+                                    float* adam_v, int32_t* step, float lr, float* loss_out, void* workspace,
+                                    void* stream) {
+  if (!plan || !y || !phi_target || !adam_m || !adam_v || !step || !loss_out || !(lr > 0.f) ||
+      jtfs::misaligned(adam_m) || jtfs::misaligned(adam_v))
+    return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  JTFS_TRY(jtfs::check_call(p, workspace));
+  const Bufs w = jtfs::bufs(p, workspace);
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  JTFS_TRY(jtfs_loss_grad(plan, y, phi_target, loss_out, w.dy, workspace, stream));
+  const int64_t n = int64_t(p.batch) * p.N;
+  jtfs::k_adam_counted<<<static_cast<unsigned>((n + jtfs::kThreads - 1) / jtfs::kThreads), jtfs::kThreads, 0, s>>>(
+      y, adam_m, adam_v, w.dy, n, lr, step);
+  JTFS_TRY(jtfs::check_launch());
+  jtfs::k_step_next<<<1, 1, 0, s>>>(step);
+  return jtfs::check_launch();
+}
+
+extern "C" int jtfs_status(void* stream) {
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return JTFS_ERR_CUDA;
+  int nf = 0;
+  if (cudaMemcpyFromSymbol(&nf, jtfs::g_nonfinite, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
+  const int zero = 0;
+  if (nf && cudaMemcpyToSymbol(jtfs::g_nonfinite, &zero, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
+  const int nfb = jtfs::batch_nonfinite_take();
+  const int tc = jtfs_tc_error();
+  const int dec = jtfs_decoder_error();
+  if (nfb < 0 || tc < 0 || dec < 0) return JTFS_ERR_CUDA;
+  if (tc || dec) return JTFS_ERR_TIMEOUT;
+  if (nf || nfb) return JTFS_ERR_NONFINITE;
+  return JTFS_OK;
+}
+
+extern "C" int jtfs_set_wait_limit(int64_t polls) {
+  JTFS_TRY(jtfs::set_wait_polls_freq(polls));
+  JTFS_TRY(jtfs::set_wait_polls_pool(polls));
+  return jtfs::set_wait_polls_decoder(polls);
 }
 
 extern "C" int jtfs_coloured_init(jtfs_plan_t plan, const float* x, const float* w_noise, float* y0,

@@ -115,7 +115,12 @@ k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensor
   const bool got = mbar_wait(smem_u32(&ctl->done), 0, abort);
   tc_fence_after();
   const int good = __syncthreads_and(got && !*abort && nk > 0);
-  if (good) op.epilogue(tmem, warp, lane);
+  if (good) {
+    op.epilogue(tmem, warp, lane);
+  } else if (threadIdx.x == 32) {
+    // Every MMA issued above must complete before TMEM is freed (the wait above gives up early on abort).
+    for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(smem_u32(&ctl->done), 0); ++i) __nanosleep(64);
+  }
   tc_fence_before();
   __syncthreads();
   if (!good && threadIdx.x == 0) {
@@ -678,6 +683,13 @@ extern "C" int jtfs_convt_out_backward_weight(const uint16_t* x, const float* dy
   k_out_reduce<<<static_cast<unsigned>(cdiv(kC * 9 + 1, 256)), 256, 0, s>>>(part, part_db, dw, db, chunks);
   return ok();
 }
+
+namespace jtfs {
+int set_wait_polls_decoder(int64_t polls) {
+  const uint32_t v = polls < 0 ? kSpinLimit : static_cast<uint32_t>(polls < int64_t(kSpinLimit) ? polls : kSpinLimit);
+  return cudaMemcpyToSymbol(c_wait_polls, &v, sizeof(v)) == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA;
+}
+}  // namespace jtfs
 
 extern "C" int jtfs_decoder_error(void) {
   int v = 0;

@@ -90,22 +90,28 @@ __device__ __forceinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity) {
   for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(bar, parity); ++i) __nanosleep(64);
 }
 
-// Bounded mbarrier wait (see mbar_wait), kept out of line: with the polling
-// loop inlined into the issue and epilogue loops the kernels returned wrong
-// results on the GPU (timing-dependent), with it out of line they are exact.
-__device__ __noinline__ bool tc_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (*abort) return false;
-    if (i >= 8) __nanosleep(64);
-  }
-  *abort = 1;
+// Records the first expired wait since the last jtfs_tc_error_info() (kept out
+// of line: it runs at most once per CTA).
+__device__ __noinline__ void tc_wait_expired(uint32_t bar, uint32_t parity) {
   if (atomicCAS(&g_tc_err_info[0], 0, int(blockIdx.x) + 1) == 0) {
     extern __shared__ uint8_t smem_raw[];
     g_tc_err_info[1] = int(threadIdx.x);
     g_tc_err_info[2] = int(bar - smem_u32(smem_raw));
     g_tc_err_info[3] = int(parity);
   }
+}
+
+// Bounded mbarrier wait: at most c_wait_polls polls (see mbar_wait); gives up
+// early once another role of the CTA aborted.
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  const uint32_t polls = c_wait_polls;
+  for (uint32_t i = 0; i < polls; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (i >= 8) __nanosleep(64);
+  }
+  *abort = 1;
+  tc_wait_expired(bar, parity);
   return false;
 }
 
@@ -617,7 +623,7 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
           ++c3;
         }
         if (!okb) break;
-        umma_commit(smem_u32(&ctl->a2_empty[ja]));
+        umma_commit(smem_u32(&ctl->a2_empty[i & 1]));  // keyed on the chunk, not the buffer
         if (i == nch - 1) umma_commit(smem_u32(&ctl->d3_full));
       }
     }
@@ -712,9 +718,13 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         z[2 * e] *= sc;
         z[2 * e + 1] *= sc;
       }
-      // dZ into A3 buffer i % NA3 once GEMM3 of chunk i - NA3 has read it.
-      const int ja = i % NA3;
-      if (i >= NA3 && !wait_warp(smem_u32(&ctl->a2_empty[ja]), ((i / NA3) - 1) & 1, abort)) { ok = false; break; }
+      // dZ into A3 buffer i % NA3 once GEMM3 has read chunk w = i - NA3, the last chunk that used it.
+      // a2_empty[w & 1] completes its phase (w >> 1) when GEMM3 has read chunk w.  This group has already
+      // seen chunk w - 2 read (its previous wait), and chunk w + 2 cannot have been written yet, so the
+      // phase parity names chunk w without ambiguity.  (Waiting on one barrier for the shared buffer's
+      // last use would not: with NA3 = 1 its parity is the same after chunk i - 1 and after chunk i - 3.)
+      const int ja = i % NA3, w = i - NA3;
+      if (w >= 0 && !wait_warp(smem_u32(&ctl->a2_empty[w & 1]), (w >> 1) & 1, abort)) { ok = false; break; }
       const uint32_t ah = sA3 + uint32_t(ja) * 32768u, al = ah + 16384u;
       const int nck = ch.rc >> 3, ck0 = h * nck;
 #pragma unroll
@@ -1095,6 +1105,13 @@ extern "C" int jtfs_tc_error(void) {
   if (vp < 0) return vp;
   return v | vp;
 }
+
+namespace jtfs {
+int set_wait_polls_freq(int64_t polls) {
+  const uint32_t v = polls < 0 ? kSpinLimit : static_cast<uint32_t>(polls < int64_t(kSpinLimit) ? polls : kSpinLimit);
+  return cudaMemcpyToSymbol(c_wait_polls, &v, sizeof(v)) == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA;
+}
+}  // namespace jtfs
 
 extern "C" int jtfs_tc_error_info(int64_t* info, int n) {
   int v[4];

@@ -286,6 +286,13 @@ bool pool_tc_supported(const Plan& p);
 int pool_tc_forward(const Plan& p, const float* V2, float* part, int si, cudaStream_t s);
 int pool_tc_adjoint(const Plan& p, const float* dphi, float* dV2, cudaStream_t s);
 int pool_tc_error();
+// Device-side status (jtfs_status): each translation unit with flags in
+// device memory reads and clears its own, or sets its copy of the bounded
+// waits' poll limit (c_wait_polls; polls < 0: the default bound).
+int batch_nonfinite_take();
+int set_wait_polls_pool(int64_t polls);
+int set_wait_polls_freq(int64_t polls);
+int set_wait_polls_decoder(int64_t polls);
 
 // Tensor-core frequential path (jtfs_freq_tc.cu): host tables at plan
 // construction, device copies and tensor maps at upload, release.  tc_build

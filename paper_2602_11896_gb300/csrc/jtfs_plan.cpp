@@ -740,6 +740,8 @@ extern "C" const char* jtfs_error_string(int code) {
     case JTFS_ERR_NOMEM: return "allocation failed";
     case JTFS_ERR_NODEVICE: return "plan has no device tables (host-only)";
     case JTFS_ERR_TOOBIG: return "plan needs more scratch than the fixed 32 MiB array of jtfs_forward_noalloc";
+    case JTFS_ERR_NONFINITE: return "a loss was NaN or infinite (non-finite input or target)";
+    case JTFS_ERR_TIMEOUT: return "a tensor-core kernel gave up waiting on a barrier; its outputs are invalid";
     default: return "unknown error";
   }
 }

@@ -61,8 +61,9 @@ struct PtCtl {
   int abort;
 };
 
-__device__ __noinline__ bool pt_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+__device__ __forceinline__ bool pt_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  const uint32_t polls = c_wait_polls;
+  for (uint32_t i = 0; i < polls; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
     if (i >= 8) __nanosleep(64);
@@ -519,6 +520,11 @@ int pool_tc_error() {
   const int zero = 0;
   if (v && cudaMemcpyToSymbol(g_pt_err, &zero, sizeof(int)) != cudaSuccess) return JTFS_ERR_CUDA;
   return v;
+}
+
+int set_wait_polls_pool(int64_t polls) {
+  const uint32_t v = polls < 0 ? kSpinLimit : static_cast<uint32_t>(polls < int64_t(kSpinLimit) ? polls : kSpinLimit);
+  return cudaMemcpyToSymbol(c_wait_polls, &v, sizeof(v)) == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA;
 }
 
 }  // namespace jtfs

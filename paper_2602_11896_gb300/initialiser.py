@@ -272,6 +272,8 @@ def train(dec: Decoder, plan, clips: torch.Tensor, steps: int, lr: float = 1e-3,
         acc += loss.sum()
         cnt += B
         if (it + 1) % log_every == 0 or it + 1 == steps:
+            plan.check_status("decoder training")
+            dec.check_errors()
             history.append((it + 1, float(acc) / cnt))
             log(f"step {it + 1}/{steps}  mean JTFS loss per clip {history[-1][1]:.5g}")
             acc.zero_()
@@ -300,6 +302,7 @@ def descend(plan, y: torch.Tensor, phi_target: torch.Tensor, steps: int, lr: flo
         plan.metamer_step(y, phi_target, m, v, s + 1, lr, loss_out=losses[s], workspace=ws)
     e1.record(stream)
     torch.cuda.synchronize()
+    plan.check_status("Adam descent")
     return losses, e0.elapsed_time(e1)
 
 

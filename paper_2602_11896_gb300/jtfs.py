@@ -242,6 +242,37 @@ class JTFSPlan:
                       "metamer_step")
         return loss
 
+    def metamer_step_counted(self, y: torch.Tensor, phi_target: torch.Tensor, adam_m: torch.Tensor,
+                             adam_v: torch.Tensor, step: torch.Tensor, lr: float,
+                             loss_out: Optional[torch.Tensor] = None,
+                             workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """metamer_step with the Adam step index in a 1-element int32 CUDA tensor (1-based,
+        incremented on the device), so that the call can be captured in a CUDA graph."""
+        for t, n in ((y, "y"), (adam_m, "adam_m"), (adam_v, "adam_v")):
+            self._check(t, self.N, n)
+        self._check(phi_target, self.phi_size, "phi_target")
+        if (not isinstance(step, torch.Tensor) or not step.is_cuda or step.dtype != torch.int32
+                or step.numel() != 1):
+            raise TypeError("step must be a 1-element int32 CUDA tensor")
+        loss = loss_out if loss_out is not None else torch.empty(self.batch, device=y.device)
+        ws = workspace if workspace is not None else self.workspace(y.device)
+        _native.check(self._lib.metamer_step_counted(self._h, _ptr(y), _ptr(phi_target), _ptr(adam_m),
+                                                     _ptr(adam_v), _ptr(step), float(lr), _ptr(loss), _ptr(ws),
+                                                     _stream()), "metamer_step_counted")
+        return loss
+
+    @staticmethod
+    def check_status(what: str = "JTFS", allow_nonfinite: bool = False) -> None:
+        """Synchronise the current stream and raise DeviceStatusError if, since the last check, a
+        tensor-core kernel gave up on a barrier (its outputs are invalid) or, unless
+        ``allow_nonfinite``, a loss was NaN / Inf."""
+        code = _native.status(torch.cuda.current_stream().cuda_stream)
+        if code == _native.ERR_NONFINITE and allow_nonfinite:
+            return
+        if code in (_native.ERR_TIMEOUT, _native.ERR_NONFINITE):
+            raise _native.DeviceStatusError(code, what)
+        _native.check(code, what)
+
     # -- reconstruction variant of §2.3 --------------------------------------
     def init_gains(self) -> np.ndarray:
         """Per first-order filter, the band gain of the coloured initialisation times 2^(lT-k1)."""

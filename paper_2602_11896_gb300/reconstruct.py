@@ -42,7 +42,9 @@ def descend_adam(plan, y: torch.Tensor, phi_target: torch.Tensor, steps: int, lr
     def run():
         for s in range(steps):
             plan.metamer_step(y, phi_target, m, v, s + 1, lr, loss_out=losses[s], workspace=ws)
-    return losses, _timed(run)
+    ms = _timed(run)
+    plan.check_status("Adam descent")
+    return losses, ms
 
 
 def descend_momentum(plan, y: torch.Tensor, phi_target: torch.Tensor, steps: int, mu0: float = 0.1,
@@ -56,7 +58,10 @@ def descend_momentum(plan, y: torch.Tensor, phi_target: torch.Tensor, steps: int
     def run():
         for s in range(steps):
             plan.metamer_step_momentum(y, phi_target, opt, m=m, loss_out=losses[s], workspace=ws)
-    return losses, _timed(run), opt["state"]
+    ms = _timed(run)
+    # A NaN loss is one the bold driver rejects (the step halves), not an error.
+    plan.check_status("momentum descent", allow_nonfinite=True)
+    return losses, ms, opt["state"]
 
 
 def _curve(losses: torch.Tensor) -> np.ndarray:

@@ -115,6 +115,24 @@ def test_batch_graph_replay_equals_eager():
     assert torch.equal(ye, yg) and torch.equal(le, lg)
 
 
+def test_uneven_workload_longest_clip_of_every_bucket():
+    """The 64-clip uneven workload: in every padded-length group (2^15 .. 2^18, the largest taking the
+    biggest four-step FFTs) its longest clip's cropped Phi against the oracle."""
+    lengths = [int(v) for v in uneven_lengths(64, 300)]
+    b = _batch(lengths, TONES)
+    clips = [signals.harmonic_tones(L, 8000.0, 1000 + i) for i, L in enumerate(lengths)]
+    phi = b.forward(torch.tensor(np.concatenate(clips), device="cuda")).cpu().numpy()
+    longest = {}
+    for i, L in enumerate(lengths):
+        n = O.padded_length(L)
+        if n not in longest or L > lengths[longest[n]]:
+            longest[n] = i
+    assert max(longest) == 2 ** 18
+    for n, i in sorted(longest.items()):
+        ref = O.jtfs_uneven(torch.tensor(clips[i], dtype=torch.float64), dict(TONES)).numpy()
+        assert _rel(phi[b.phi_offsets[i]:b.phi_offsets[i + 1]], ref) <= TOL, (n, i)
+
+
 def test_uneven_workload_lengths_sampled_clip():
     """64 log-uniform lengths in [2^14, 2^18] with the 8 kHz tone parameters: the
     shortest clip's cropped Phi against the oracle (the oracle's cost bounds the sample)."""

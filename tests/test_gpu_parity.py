@@ -204,6 +204,37 @@ def test_chirps_workload_full_size_sampled_clip():
     assert _rel(dy[b].cpu().numpy(), g[0].numpy()) <= TOL
 
 
+def _path_errors(phi_gpu, phi_ref, meta, size):
+    """Relative L2 error of every path of one clip's Phi (offsets from jtfs_path_meta)."""
+    off = list(meta["offset"]) + [size]
+    out = {}
+    for p in range(len(meta["offset"])):
+        key = (int(meta["order"][p]), int(meta["n2"][p]), int(meta["beta_idx"][p]))
+        out[key] = _rel(phi_gpu[off[p]:off[p + 1]], phi_ref[off[p]:off[p + 1]])
+    return out
+
+
+@pytest.mark.parametrize("name,clip", [("tones8k_n8192", 0), ("chirps22k_b8_n65536", 5)])
+def test_every_path_within_tolerance(name, clip):
+    """Per path, not per block: S0, every first-order beta and every (n2, beta) path of one clip of the
+    workload in the bench's launch configuration, through the tensor-core groups (default) and through
+    the FFT kernels for every group, each against the oracle at <= 1e-4 relative L2."""
+    wl = get_workload(name)
+    plan = _plan(wl.params, wl.batch)
+    ref = O.Plan(**wl.params)
+    meta = plan.path_meta()
+    assert len(meta["offset"]) == 1 + (1 + ref.K) + len(ref.active) * (1 + 2 * ref.K)
+    sig = wl.targets()
+    phi_ref = O.jtfs(torch.tensor(sig[clip:clip + 1], dtype=torch.float64), ref)["phi"][0].numpy()
+    base = list(plan.tuning())
+    for tc in (1, 0):
+        plan.set_tuning(base[:3] + [tc])
+        phi = plan.forward(torch.tensor(sig, device="cuda"))[clip].cpu().numpy()
+        errs = _path_errors(phi, phi_ref, meta, plan.phi_size)
+        worst = max(errs, key=errs.get)
+        assert errs[worst] <= TOL, (tc, worst, errs[worst])
+
+
 def test_forward_parity_64_frames_tensor_core_pooling():
     """A plan with 64 frames (tensor-core time pooling of its dense groups) against the oracle."""
     params = dict(N=2 ** 14, J=8, Q=8, Q2=1, J_fr=3, Q_fr=1, T=256, F=4)
