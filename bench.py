@@ -156,6 +156,25 @@ def tc_tensor_flops(plan, adjoint: bool) -> float:
     return total
 
 
+def compulsory_bytes_per_clip(plan) -> float:
+    """HBM bytes a fused forward + loss + adjoint cannot avoid, per clip: x read twice, U1 written and read
+    once (it is recomputed, not stored, for the adjoint), dU1 written and read, Phi written, the target Phi
+    read, dy written (FP32).  Y2 and the un-pooled second order are not counted: a fused design keeps them
+    on chip."""
+    info = plan.info
+    N, lT = info["N"], info["log2_T"]
+    _, _, j1 = plan.filters(0)
+    u1 = sum(N >> min(int(j), lT) for j in j1)
+    return 4.0 * (2 * N + 2 * u1 + 2 * u1 + 2 * plan.phi_size + N)
+
+
+def hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
 def columns_per_launch(plan) -> int:
     """Time columns the second-order frequential kernels process per launch."""
     info = plan.info
@@ -749,17 +768,33 @@ def main():
     launch_ms = kern[dom]
     roofline = None
     if dom.startswith("k_freq_tc"):
+        # The method's own work in these kernels is the FFT-count FLOPs of the frequential step (the
+        # algorithmic count of the scope table: 5 n log2 n per complex FFT ...) on the columns of the groups
+        # they take; they run it as dense BF16 GEMMs on the tensor cores, which is reported beside it as
+        # useful dense FLOPs (one product per FP32-accurate product) and as issued FLOPs (three).
         adj = dom.startswith("k_freq_tc_adj")
-        flops = tc_tensor_flops(plan, adjoint=adj)
+        cols = wl.batch * sum(L2 for _, L2 in tc_groups(plan))
+        flops = freq_flops_per_column(plan, adjoint=adj) * cols
         ach = flops / (launch_ms / 1e3) / 1e12
+        issued = tc_tensor_flops(plan, adjoint=adj)
+        t_ach = issued / (launch_ms / 1e3) / 1e12
         peak, peak_src = bf16_peak()
         per_clip = (DRAM_BYTES_PER_CLIP or {}).get(5 if adj else 4) if VARIANT["name"] == "none" else None
-        roofline = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": per_clip * wl.batch if per_clip is not None else None,
+        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP32_PEAK_TFLOPS,
+                    "traffic": per_clip * wl.batch if per_clip is not None else None,
                     "traffic_note": "ncu dram bytes of the 1-clip capture x clips per launch",
-                    "flops_per_launch": flops, "flops_note": "issued BF16 tensor FLOPs: 3 products (hi.hi, lo.hi, "
-                    "hi.lo) per FP32-accurate product, M = 128 columns per tile; one third is the contraction itself",
-                    "launch_ms": launch_ms, "peak_source": peak_src,
+                    "flops_per_launch": flops,
+                    "flops_note": "algorithmic FFT-count FLOPs of the frequential step (5 n log2 n per complex "
+                                  "FFT, 2 per filter product, 3 per modulus, 6 per modulus adjoint) on the "
+                                  f"{cols} tensor-core columns of one launch",
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (no measured FP32 peak)",
+                    "tensor": {"useful_flops_per_launch": issued / 3, "achieved": t_ach / 3, "peak": peak,
+                               "frac": t_ach / 3 / peak, "issued_flops_per_launch": issued,
+                               "issued_achieved": t_ach, "issued_frac": t_ach / peak, "peak_source": peak_src,
+                               "note": "dense BF16 GEMM formulation (M = 128 columns per tile); each FP32-accurate "
+                                       "product is three BF16 products (hi.hi + lo.hi + hi.lo)"},
+                    "launch_ms": launch_ms,
                     "stage_ms": {k.split(" ")[0]: round(v, 4) for k, v in kern.items()},
                     "step_share": launch_ms / ms_per_step}
     elif dom.startswith("k_freq_"):
@@ -775,6 +810,17 @@ def main():
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (no measured FP32 peak)",
                     "stage_ms": {k.split(" ")[0]: round(v, 4) for k, v in kern.items()},
                     "step_share": launch_ms / ms_per_step}
+
+    # Step-level HBM roofline: the compulsory bytes of a fused step against the measured copy bandwidth.
+    if roofline is not None:
+        cb = compulsory_bytes_per_clip(plan) * wl.batch
+        hp, hsrc = hbm_peak()
+        gbs = cb / (ms_per_step / 1e3) / 1e9
+        roofline["step_hbm"] = {"compulsory_bytes_per_step": cb, "achieved_gbs": gbs, "peak_gbs": hp,
+                                "frac": gbs / hp, "peak_source": hsrc,
+                                "note": "x twice, U1 and dU1 written and read, Phi, target Phi, dy; the fused path "
+                                        "does thousands of FLOPs per compulsory byte, so it is compute-bound and "
+                                        "this fraction is small by design"}
 
     # End to end through the public API from pinned host memory.
     y_host = torch.tensor(inits, dtype=torch.float32).pin_memory()
@@ -819,7 +865,8 @@ def main():
                 "gpu_launches": int(lib.jtfs_launch_count(plan._h, 3)) * K,
                 "clocks": clk, "wall_s_timed": t_wall,
                 "tuning": {"wide_forward_tiles": tuning[0], "pool_split": tuning[1], "fft_points_per_cta": tuning[2],
-                           "tensor_core_frequential": tuning[3], "tensor_core_pooling": tuning[4]},
+                           "tensor_core_frequential": tuning[3], "tensor_core_pooling": tuning[4],
+                           "time_fft_engine": tuning[5] if len(tuning) > 5 else None},
                 "metamer_loss": {"first_timed_step": float(hist[0].mean().item()),
                                  "last_timed_step": float(hist[-1].mean().item()),
                                  "adam_steps_before_last": args.warmup + K - 1}}

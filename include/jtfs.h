@@ -380,7 +380,7 @@ int jtfs_batch_metamer_step(jtfs_batch_t batch, float* y, const float* phi_targe
                             void* stream);
 
 /*
- * Autotuning.  A plan has five execution choices that change no result
+ * Autotuning.  A plan has six execution choices that change no result
  * beyond rounding:
  *   choice[0]  wide column tiles (1) or narrow ones (0) for the second-order
  *              frequential forward kernel;
@@ -395,14 +395,19 @@ int jtfs_batch_metamer_step(jtfs_batch_t batch, float* y, const float* phi_targe
  *   choice[4]  time pooling of the second order (dense groups) on the tensor
  *              cores (1) or on the FMA kernels (0); reads 0 for plans whose
  *              frame count (N / T) is not 32, 64 or 128.
- * jtfs_set_tuning takes n = 3, 4 or 5 (later choices unchanged).
+ *   choice[5]  time-axis FFTs of the first and second layers (§3.2-§3.3) on
+ *              the in-place radix-16 engine (1: every size up to 2^13 of a
+ *              stage in one launch, 2^14 .. 2^16 on clusters of 2-8 CTAs
+ *              exchanging through distributed shared memory) or on the
+ *              batched / four-step kernels (0, which choice[2] tunes).
+ * jtfs_set_tuning takes n = 3 .. 6 (later choices unchanged).
  * jtfs_autotune times jtfs_loss_grad on the caller's y and phi_target (device
  * arrays as for jtfs_loss_grad; loss [batch] and dy [batch][N] are scratch
  * outputs) for each candidate, one choice at a time, keeps the fastest, and
  * writes the choices to choice[0..n) (host, may be NULL).  It synchronises
  * the stream (it is a set-up call, not a hot-path one).  jtfs_set_tuning
  * applies saved choices; jtfs_get_tuning reads the current ones.  All return
- * the number of choices (5) or an error code.  Not thread-safe with concurrent
+ * the number of choices (6) or an error code.  Not thread-safe with concurrent
  * compute calls on the same plan.
  */
 int jtfs_autotune(jtfs_plan_t plan, const float* y, const float* phi_target,

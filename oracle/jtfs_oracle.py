@@ -402,6 +402,51 @@ def jtfs(x: torch.Tensor, plan: Plan, keep: bool = False,
     return out
 
 
+def second_order_frames(x: torch.Tensor, plan: Plan, a: int, frames: Sequence[int],
+                        tail: float = 1e-13) -> torch.Tensor:
+    """Second-order paths of active group ``a`` at the pooled frames ``frames`` only:
+    [B, 1+2K, R_out, len(frames)], for clips too long for the whole transform (the
+    un-pooled second order of a 2^20-sample clip is hundreds of GB).
+
+    The same steps as ``jtfs`` for that group -- U1 rows with j1 < j2 (§3.2), Y2
+    (§3.3), frequential filtering, modulus, phi_F (§3.4, Eq. (5)) -- with the
+    phi_T average of Eq. (5) written as the sum it is at the kept frames:
+        Phi[f] = sum_t g[(f D - t) mod L] u[t],   g = ifft(levels[s2] of phi_T),
+    D = 2^(lT - s2), L = N / 2^s2, over the columns t where |g| exceeds ``tail``
+    times its peak (the Gaussian's taps beyond are below it); only those columns
+    are scattered along n1.  Pooled in time only (average_local and
+    average_local_fr on).
+    """
+    if x.dim() == 1:
+        x = x[None]
+    assert plan.average_local and plan.average_local_fr
+    B, N = x.shape
+    n2 = plan.active[int(a)]
+    f2 = plan.psi2[n2]
+    s2, lT = plan.s2[n2], plan.lT
+    L, D = N >> s2, 1 << (lT - s2)
+    X = torch.fft.fft(x.to(C128), dim=-1)
+    psi2 = morlet_hat(N, f2.xi, f2.sigma)
+    rows = []
+    for n1 in range(plan.n1_max[n2]):
+        f, k1 = plan.psi1[n1], plan.k1_2[n1]
+        u1 = decimate(torch.fft.ifft(X * morlet_hat(N, f.xi, f.sigma), dim=-1), k1, -1).abs()
+        rows.append(decimate(conv_circ(u1, periodise(psi2, k1), -1), s2 - k1, -1))
+    Y2 = torch.stack(rows, 1)                                            # [B, n1_max, L]
+    g = torch.fft.ifft(periodise(gauss_hat(N, plan.sigma_phiT), s2).to(C128)).real
+    lag = torch.nonzero(g.abs() > tail * g.abs().max()).flatten()        # lags (f D - t) mod L kept
+    cols = torch.unique(torch.cat([(int(fr) * D - lag) % L for fr in frames]))
+    Yc = pad_rows(Y2[:, :, cols], plan.N_fr, 1)                           # the columns that matter
+    G = torch.stack([g[(int(fr) * D - cols) % L] for fr in frames], 1)   # [columns, frames]
+    phiF = gauss_hat(plan.N_fr, plan.sigma_phiF)
+    out = []
+    for xi_b, sig_b, k_b in plan.beta_second:
+        u = decimate(conv_circ(Yc, freq_filter_hat(plan.N_fr, xi_b, sig_b), 1), k_b, 1).abs()
+        v = u @ G.to(u.dtype)                                             # *_t phi_T at the frames
+        out.append(decimate(conv_circ(v.to(C128), periodise(phiF, k_b), 1), plan.lF - k_b, 1).real)
+    return torch.stack(out, 1)
+
+
 def phi_blocks(phi: torch.Tensor, plan: Plan) -> Dict[str, torch.Tensor]:
     """Split a flat [B, phi_size] Phi into S0, first-order and per-n2 blocks."""
     B = phi.shape[0]

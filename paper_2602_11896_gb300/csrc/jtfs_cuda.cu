@@ -284,6 +284,14 @@ struct StR {  // real part
   __device__ void operator()(const Job& jb, int idx, float2 v) const { d[jb.dst + idx] = v.x; }
 };
 
+}  // namespace
+}  // namespace jtfs
+
+#include "jtfs_tfft.cuh"
+
+namespace jtfs {
+namespace {
+
 // ---------------------------------------------------------------------------
 // Batched FFT kernels.
 // ---------------------------------------------------------------------------
@@ -366,17 +374,22 @@ k_fft4_pass2(St st, const Job* __restrict__ jobs, int logn, int la, const float2
 template <auto Kernel>
 void allow_big_smem() {
   static const cudaError_t once = [] {
-    const cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    // Static shared memory counts against the same per-block limit.
+    cudaFuncAttributes fa{};
+    int stat = 0;
+    if (cudaFuncGetAttributes(&fa, Kernel) == cudaSuccess) stat = static_cast<int>(fa.sharedSizeBytes);
+    const cudaError_t e =
+        cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem - stat);
     cudaGetLastError();  // do not leave a sticky error for the next launch check
     return e;
   }();
   (void)once;
 }
 
+// One launch of the batched / four-step kernels.
 template <bool INV, class Ld, class St>
-int run_fft(const Plan& p, const std::vector<FftLaunch>& L, const Ld& ld, const St& st, float2* scr,
-            cudaStream_t s) {
-  for (const FftLaunch& l : L) {
+int run_fft_launch(const Plan& p, const FftLaunch& l, const Ld& ld, const St& st, float2* scr, cudaStream_t s) {
+  {
     const Job* jobs = p.d_jobs + l.job0;
     if (l.logn <= kSmallLogMax) {
       const int n = 1 << l.logn;
@@ -411,6 +424,72 @@ int run_fft(const Plan& p, const std::vector<FftLaunch>& L, const Ld& ld, const 
       }
     }
     if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
+  }
+  return JTFS_OK;
+}
+
+// Transforms of one stage on the time-axis FFT engine (jtfs_tfft.cuh): every
+// size up to 2^13 in one launch of k_tfft, each size 2^14 .. 2^16 in one
+// cluster launch, larger ones on the four-step kernels.
+template <bool INV, class Ld, class St>
+int run_tfft(const Plan& p, const std::vector<FftLaunch>& L, const Ld& ld, const St& st, float2* scr,
+             cudaStream_t s) {
+  // One launch per run of consecutive items (the plan gives every stage a single run).
+  int i0 = -1, i1 = -1;
+  auto flush = [&]() -> int {
+    if (i1 <= i0) return JTFS_OK;
+    allow_big_smem<k_tfft<INV, Ld, St>>();
+    k_tfft<INV, Ld, St><<<static_cast<unsigned>(i1 - i0), kTfThreads, kTfSmem, s>>>(ld, st, p.d_jobs,
+                                                                                  p.d_tf_items + i0);
+    return cudaGetLastError() == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA;
+  };
+  for (const FftLaunch& l : L) {
+    if (l.logn > kTfLogP || l.n_items == 0) continue;
+    if (l.item0 != i1) {
+      const int rc = flush();
+      if (rc != JTFS_OK) return rc;
+      i0 = l.item0;
+    }
+    i1 = l.item0 + l.n_items;
+  }
+  {
+    const int rc = flush();
+    if (rc != JTFS_OK) return rc;
+  }
+  for (const FftLaunch& l : L) {
+    if (l.logn <= kTfLogP) continue;
+    if (l.logn > kTfLogP + 3) {
+      const int rc = run_fft_launch<INV>(p, l, ld, st, scr, s);
+      if (rc != JTFS_OK) return rc;
+      continue;
+    }
+    allow_big_smem<k_tfft_cluster<INV, Ld, St>>();
+    const unsigned C = 1u << (l.logn - kTfLogP);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(static_cast<unsigned>(l.njobs) * C);
+    cfg.blockDim = dim3(kTfThreads);
+    cfg.dynamicSmemBytes = kTfSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_tfft_cluster<INV, Ld, St>, ld, st, p.d_jobs, l.job0, l.logn) != cudaSuccess)
+      return JTFS_ERR_CUDA;
+  }
+  return JTFS_OK;
+}
+
+template <bool INV, class Ld, class St>
+int run_fft(const Plan& p, const std::vector<FftLaunch>& L, const Ld& ld, const St& st, float2* scr,
+            cudaStream_t s) {
+  if (p.tune_tfft) return run_tfft<INV>(p, L, ld, st, scr, s);
+  for (const FftLaunch& l : L) {
+    const int rc = run_fft_launch<INV>(p, l, ld, st, scr, s);
+    if (rc != JTFS_OK) return rc;
   }
   return JTFS_OK;
 }
@@ -1586,9 +1665,19 @@ void prof_end(const Plan& p, int stage, cudaStream_t s) {
   }
 }
 
-int64_t fft_launches(const std::vector<FftLaunch>& L) {
+int64_t fft_launches(const Plan& p, const std::vector<FftLaunch>& L) {
   int64_t n = 0;
-  for (const FftLaunch& l : L) n += l.logn <= kSmallLogMax ? 1 : 2;
+  int end = -1;
+  for (const FftLaunch& l : L) {
+    if (p.tune_tfft && l.logn <= kTfLogP) {
+      if (l.n_items > 0 && l.item0 != end) ++n;   // a new run of items: one more launch
+      if (l.n_items > 0) end = l.item0 + l.n_items;
+    } else if (p.tune_tfft && l.logn <= kTfLogP + 3) {
+      n += 1;
+    } else {
+      n += l.logn <= kSmallLogMax ? 1 : 2;
+    }
+  }
   return n;
 }
 
@@ -1600,16 +1689,16 @@ int64_t freq2_launches(const Plan& p) {
 }
 
 int64_t forward_launches(const Plan& p, bool full) {
-  int64_t n = fft_launches(p.L_x) + fft_launches(p.L_u1) + fft_launches(p.L_u1inplace) + fft_launches(p.L_s1);
-  if (full) n += (p.unpooled_t ? 1 : fft_launches(p.L_s0)) + 1;
-  if (p.n_active > 0) n += fft_launches(p.L_y2) + (full ? (p.unpooled_t ? 1 : 2) + freq2_launches(p) : 0);
+  int64_t n = fft_launches(p, p.L_x) + fft_launches(p, p.L_u1) + fft_launches(p, p.L_u1inplace) + fft_launches(p, p.L_s1);
+  if (full) n += (p.unpooled_t ? 1 : fft_launches(p, p.L_s0)) + 1;
+  if (p.n_active > 0) n += fft_launches(p, p.L_y2) + (full ? (p.unpooled_t ? 1 : 2) + freq2_launches(p) : 0);
   return n;
 }
 
 int64_t backward_launches(const Plan& p) {
-  int64_t n = 1 + fft_launches(p.L_ds1) + static_cast<int64_t>(p.L_u1inplace.size()) +
-              2 * fft_launches(p.L_u1inplace) + (p.unpooled_t ? 1 : fft_launches(p.L_ds0)) + 1 + fft_launches(p.L_x);
-  if (p.n_active > 0) n += 1 + freq2_launches(p) + fft_launches(p.L_y2inplace);
+  int64_t n = 1 + fft_launches(p, p.L_ds1) + static_cast<int64_t>(p.L_u1inplace.size()) +
+              2 * fft_launches(p, p.L_u1inplace) + (p.unpooled_t ? 1 : fft_launches(p, p.L_ds0)) + 1 + fft_launches(p, p.L_x);
+  if (p.n_active > 0) n += 1 + freq2_launches(p) + fft_launches(p, p.L_y2inplace);
   return n;
 }
 
@@ -2093,10 +2182,11 @@ extern "C" int64_t jtfs_launch_count(jtfs_plan_t plan, int call) {
 extern "C" int jtfs_get_tuning(jtfs_plan_t plan, int64_t* choice, int n) {
   if (!plan) return JTFS_ERR_ARG;
   const jtfs::Plan& p = plan->p;
-  const int64_t v[5] = {p.tune_wide, jtfs::kPoolSplits[p.tune_split], p.tune_fft_points,
-                        (p.tc_ok && p.tune_tc) ? 1 : 0, (p.tune_pool_tc && jtfs::pool_tc_supported(p)) ? 1 : 0};
-  for (int i = 0; i < n && i < 5 && choice; ++i) choice[i] = v[i];
-  return 5;
+  const int64_t v[6] = {p.tune_wide, jtfs::kPoolSplits[p.tune_split], p.tune_fft_points,
+                        (p.tc_ok && p.tune_tc) ? 1 : 0, (p.tune_pool_tc && jtfs::pool_tc_supported(p)) ? 1 : 0,
+                        p.tune_tfft};
+  for (int i = 0; i < n && i < 6 && choice; ++i) choice[i] = v[i];
+  return 6;
 }
 
 extern "C" int jtfs_set_tuning(jtfs_plan_t plan, const int64_t* choice, int n) {
@@ -2109,12 +2199,14 @@ extern "C" int jtfs_set_tuning(jtfs_plan_t plan, const int64_t* choice, int n) {
   const jtfs::Plan& p = plan->p;
   if (n >= 4 && choice[3] != 0 && choice[3] != 1) return JTFS_ERR_ARG;
   if (n >= 5 && choice[4] != 0 && choice[4] != 1) return JTFS_ERR_ARG;
+  if (n >= 6 && choice[5] != 0 && choice[5] != 1) return JTFS_ERR_ARG;
   p.tune_wide = static_cast<int>(choice[0]);
   p.tune_split = si;
   p.tune_fft_points = static_cast<int>(pts);
   if (n >= 4) p.tune_tc = static_cast<int>(choice[3]);
   if (n >= 5) p.tune_pool_tc = static_cast<int>(choice[4]);
-  return 5;
+  if (n >= 6) p.tune_tfft = static_cast<int>(choice[5]);
+  return 6;
 }
 
 extern "C" int jtfs_autotune(jtfs_plan_t plan, const float* y, const float* phi_target, float* loss, float* dy,
@@ -2154,6 +2246,16 @@ extern "C" int jtfs_autotune(jtfs_plan_t plan, const float* y, const float* phi_
     }
     p.tune_tc = best_tc;
   }
+  if (rc == JTFS_OK) {
+    float best = 1e30f, t = 0.f;
+    int best_v = p.tune_tfft;
+    for (int v : {1, 0}) {
+      p.tune_tfft = v;
+      if ((rc = time_it(&t)) != JTFS_OK) break;
+      if (t < best) best = t, best_v = v;
+    }
+    p.tune_tfft = best_v;
+  }
   if (rc == JTFS_OK && jtfs::pool_tc_supported(p)) {
     float best = 1e30f, t = 0.f;
     int best_v = p.tune_pool_tc;
@@ -2164,7 +2266,7 @@ extern "C" int jtfs_autotune(jtfs_plan_t plan, const float* y, const float* phi_
     }
     p.tune_pool_tc = best_v;
   }
-  if (rc == JTFS_OK) {
+  if (rc == JTFS_OK && !p.tune_tfft) {
     float best = 1e30f, t = 0.f;
     int best_pts = p.tune_fft_points;
     for (int pts : {1024, 2048, 4096, 8192}) {

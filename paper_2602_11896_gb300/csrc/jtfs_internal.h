@@ -63,6 +63,8 @@ struct FftLaunch {
   int logn;
   int njobs;
   int job0;
+  int item0;    // this launch's CTAs in the merged small-transform launch of its stage (logn <= 13)
+  int n_items;
 };
 
 // Tensor-core frequential scattering (jtfs_freq_tc.cu): one chunk is up to 32
@@ -234,6 +236,12 @@ struct Plan {
   mutable int tune_wide = 1;
   mutable int tune_split = 1;
   mutable int tune_fft_points = 4096;
+  // Time-axis FFT engine (jtfs_tfft.cuh, tuning choice 6): 1 = in-place
+  // radix-16 CTA transforms with all sizes <= 2^13 of a stage in one launch
+  // and 2^14..2^16 on CTA clusters; 0 = the batched / four-step kernels.
+  mutable int tune_tfft = 1;
+  std::vector<int4> tf_items;          // (first job, jobs, log2 n, 0) per CTA
+  const int4* d_tf_items = nullptr;
   const int* d_s2 = nullptr;          // per active index
   const int* d_pool_w = nullptr;      // per active index
   const int4* d_pool_band_tiles = nullptr;

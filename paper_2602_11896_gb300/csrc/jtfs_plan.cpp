@@ -265,7 +265,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   p.jobs.clear();
   auto add = [&](std::vector<FftLaunch>& L, int logn, const std::vector<Job>& js) {
     if (js.empty()) return;
-    L.push_back({logn, static_cast<int>(js.size()), static_cast<int>(p.jobs.size())});
+    L.push_back({logn, static_cast<int>(js.size()), static_cast<int>(p.jobs.size()), 0, 0});
     p.jobs.insert(p.jobs.end(), js.begin(), js.end());
   };
   const int B = batch;
@@ -322,6 +322,22 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
     add(p.L_y2, p.logN - lev, band);
     add(p.L_y2inplace, p.logN - lev, rows);
   }
+
+  // Items of the time-axis FFT engine's merged launches: for every stage, its launches of up to
+  // 2^13 points get consecutive items (as many jobs per CTA as 2^13 points and 256 jobs allow), so
+  // one launch over the stage's item range runs all of them.
+  p.tf_items.clear();
+  for (auto* L : {&p.L_x, &p.L_u1, &p.L_u1inplace, &p.L_s0, &p.L_s1, &p.L_y2, &p.L_y2inplace, &p.L_ds1,
+                  &p.L_ds0})
+    for (FftLaunch& l : *L) {
+      l.item0 = static_cast<int>(p.tf_items.size());
+      l.n_items = 0;
+      if (l.logn > 13) continue;
+      const int per = std::min(256, 1 << (13 - l.logn));
+      for (int j = 0; j < l.njobs; j += per)
+        p.tf_items.push_back(make_int4(l.job0 + j, std::min(per, l.njobs - j), l.logn, 0));
+      l.n_items = static_cast<int>(p.tf_items.size()) - l.item0;
+    }
 
   // Frequential tiles.
   p.freq_cols = std::max(2, std::min(kFreqCols, 2048 / p.N_fr));  // >= 2: kernels pair columns
@@ -538,6 +554,7 @@ int upload_plan(Plan& p) {
   const size_t o_beta = put(p.h_beta.data(), p.h_beta.size() * sizeof(FiltD));
   const size_t o_taps = put(p.h_taps.data(), p.h_taps.size() * sizeof(float));
   const size_t o_jobs = put(p.jobs.data(), p.jobs.size() * sizeof(Job));
+  const size_t o_tfi = put(p.tf_items.data(), p.tf_items.size() * sizeof(int4));
   const size_t o_t1 = put(p.tiles1.data(), p.tiles1.size() * sizeof(Tile));
   const size_t o_t2 = put(p.tiles2.data(), p.tiles2.size() * sizeof(Tile));
   const size_t o_t2w = put(p.tiles2w.data(), p.tiles2w.size() * sizeof(Tile));
@@ -587,6 +604,7 @@ int upload_plan(Plan& p) {
   p.d_beta = reinterpret_cast<const FiltD*>(at(o_beta));
   p.d_taps = reinterpret_cast<const float*>(at(o_taps));
   p.d_jobs = reinterpret_cast<const Job*>(at(o_jobs));
+  p.d_tf_items = reinterpret_cast<const int4*>(at(o_tfi));
   p.d_tiles1 = reinterpret_cast<const Tile*>(at(o_t1));
   p.d_tiles2 = reinterpret_cast<const Tile*>(at(o_t2));
   p.d_tiles2w = reinterpret_cast<const Tile*>(at(o_t2w));

@@ -96,15 +96,15 @@ class JTFSPlan:
         return out
 
     # -- tuning -----------------------------------------------------------
-    def tuning(self) -> Tuple[int, int, int, int, int]:
+    def tuning(self) -> Tuple[int, int, int, int, int, int]:
         """(wide forward tiles, pooling split, small-FFT points per CTA, tensor-core frequential path,
-        tensor-core time pooling) in use."""
-        buf = (c_int64 * 5)()
-        self._lib.jtfs_get_tuning(self._h, buf, 5)
-        return tuple(int(buf[i]) for i in range(5))
+        tensor-core time pooling, radix-16 / cluster time-axis FFT engine) in use."""
+        buf = (c_int64 * 6)()
+        self._lib.jtfs_get_tuning(self._h, buf, 6)
+        return tuple(int(buf[i]) for i in range(6))
 
     def set_tuning(self, choice) -> None:
-        """Apply 3, 4 or 5 choices (see ``tuning``); choices not given are unchanged."""
+        """Apply 3 to 6 choices (see ``tuning``); choices not given are unchanged."""
         vals = [int(c) for c in choice]
         buf = (c_int64 * len(vals))(*vals)
         n = self._lib.jtfs_set_tuning(self._h, buf, len(vals))
@@ -152,11 +152,11 @@ class JTFSPlan:
         loss = torch.empty(self.batch, device=y.device)
         dy = torch.empty_like(y)
         ws = self.workspace(y.device)
-        buf = (c_int64 * 5)()
+        buf = (c_int64 * 6)()
         n = self._lib.jtfs_autotune(self._h, _ptr(y), _ptr(phi_target), _ptr(loss), _ptr(dy), _ptr(ws), _stream(),
-                                    buf, 5)
+                                    buf, 6)
         _native.check(0 if n >= 0 else n, "jtfs_autotune")
-        choice = [int(buf[i]) for i in range(5)]
+        choice = [int(buf[i]) for i in range(6)]
         if path:
             table = {}
             if os.path.exists(path):

@@ -3,7 +3,8 @@
 The oracle cannot evaluate the whole transform at 2^20 in test time, so:
 * the same filterbanks at reduced N (2^15 forward, 2^14 gradient) against the oracle, every Phi block;
 * at full size, in the launch configuration of the long-signal benchmark: S0, every first-order row and
-  two sampled second-order paths of one clip against the oracle, and the shift-by-T property on another.
+  two sampled second-order paths of one clip against the oracle, every path of the finest second-order
+  level at two frames (the oracle evaluated at those frames only), and the shift-by-T property.
 """
 
 import numpy as np
@@ -105,6 +106,25 @@ def test_full_size_sampled_paths_against_oracle(full):
     assert _rel(got["Phi1"], ref["Phi1"][0]) <= TOL
     for a in sample:
         assert _rel(got[a], ref["Phi2_sel"][a][0]) <= TOL, a
+
+
+def test_full_size_finest_level_against_oracle(full):
+    """The finest second-order level of the 4 x 2^20 plan (the most time columns, the largest FFTs of
+    Y2) at full size: every path of clip 0 at frames 0 (its phi_T window wraps around the circle) and 77,
+    against the oracle evaluated at those frames only."""
+    plan, x, phi, _, _, _ = full
+    ref_plan = O.Plan(**WL.params)
+    s2 = [min(ref_plan.psi2[n2].j, ref_plan.lT) for n2 in ref_plan.active]
+    a = int(np.argmin(s2))
+    frames = [0, 77]
+    ref = O.second_order_frames(torch.tensor(x[:1], dtype=torch.float64), ref_plan, a, frames)[0].numpy()
+    off = ref_plan.n_frames * (1 + (1 + ref_plan.K) * ref_plan.R_out)
+    paths = 1 + 2 * ref_plan.K
+    off += a * paths * ref_plan.R_out * ref_plan.n_frames
+    blk = phi[0, off:off + paths * ref_plan.R_out * ref_plan.n_frames].cpu().numpy()
+    got = blk.reshape(paths, ref_plan.R_out, ref_plan.n_frames)[..., frames]
+    for b in range(paths):
+        assert _rel(got[b], ref[b]) <= TOL, (a, b)
 
 
 def test_full_size_shift_by_T_shifts_frames(full):

@@ -62,3 +62,32 @@ def test_autotune_picks_a_valid_choice_and_caches_it(tmp_path):
     assert list(table.values()) == [list(choice)]
     other = JTFSPlan(**wl.params, batch=4)
     assert other.autotune(y, tgt, cache=str(cache)) == choice
+
+
+@pytest.mark.parametrize("name", ["tones8k_n8192", "chirps22k_b8_n65536"])
+def test_time_fft_engines_agree(name):
+    """Tuning choice 6: the in-place radix-16 / cluster time-axis FFT engine and the batched / four-step
+    kernels compute the same transforms (§3.2-§3.3) up to FP32 rounding, forward and gradient; the
+    four-step kernels with every small-FFT batching give one result."""
+    from paper_2602_11896_gb300 import JTFSPlan
+    wl = get_workload(name)
+    B = 2
+    plan = JTFSPlan(**wl.params, batch=B)
+    base = list(plan.tuning())
+    assert base[5] == 1
+    x = torch.tensor(np.stack([signals.harmonic_tones(wl.N, wl.sr, 5 + b) for b in range(B)]), device="cuda")
+    y = torch.tensor(np.stack([signals.white_noise(wl.N, 9 + b) for b in range(B)]), device="cuda")
+    res = {}
+    for eng in (1, 0):
+        plan.set_tuning(base[:5] + [eng])
+        assert plan.tuning()[5] == eng
+        phi = plan.forward(x)
+        loss, g = plan.loss_grad(y, phi.flip(0).contiguous())
+        res[eng] = (phi.clone(), loss.clone(), g.clone())
+    for a, b in zip(res[1], res[0]):
+        assert _rel(a, b) <= 2e-6, name
+    plan.set_tuning(base[:2] + [1024] + base[3:5] + [0])
+    l1, g1 = plan.loss_grad(y, res[0][0].flip(0).contiguous())
+    assert _rel(g1, res[0][2]) <= 1e-6
+    plan.set_tuning(base)
+    plan.check_status("engine comparison")

@@ -332,6 +332,19 @@ def test_selected_second_order_paths_equal_the_full_transform():
         assert torch.equal(blk, full["Phi2"][:, a])
 
 
+def test_second_order_frames_equal_the_full_transform():
+    """The frame-restricted second order (phi_T as its sum over the columns where the taps are not
+    negligible) equals the whole transform's frames, on a plan where that is a small part of the columns."""
+    p = O.Plan(N=2 ** 13, J=5, Q=4, Q2=2, J_fr=2, Q_fr=1, T=16, F=2)
+    x = torch.tensor(np.random.default_rng(11).standard_normal((2, p.N)))
+    full = O.jtfs(x, p, keep=True)["Phi2"]
+    frames = [0, 3, p.n_frames - 1]
+    for a in range(len(p.active)):
+        got = O.second_order_frames(x, p, a, frames)
+        assert got.shape == (2, 1 + 2 * p.K, p.R_out, len(frames))
+        assert (got - full[:, a][..., frames]).abs().max().item() <= 1e-12 * full[:, a].abs().max().item()
+
+
 # --------------------------------------------------------------------------- planted mistakes
 
 def test_pins_catch_dropped_kappa(monkeypatch):

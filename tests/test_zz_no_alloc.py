@@ -55,6 +55,32 @@ def test_forward_noalloc_matches_forward_on_two_calls():
         assert _rel(out, ref) <= TOL
 
 
+def _noalloc(lib, plan, x):
+    from paper_2602_11896_gb300 import _native
+    out = torch.full((plan.batch, plan.phi_size), float("nan"), device="cuda")
+    rc = lib.jtfs_forward_noalloc(plan._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, _native.error_string(rc)
+    return out
+
+
+def test_forward_noalloc_ignores_what_another_plan_left_in_the_scratch():
+    """A call of another plan (other N, batch and filterbank, on NaN input) fills the shared scratch with
+    garbage laid out differently; the next call must write every scratch byte it reads, so its Phi equals
+    jtfs_forward's bit for bit -- and so must the other plan's afterwards."""
+    from paper_2602_11896_gb300 import JTFSPlan, _native
+    lib = _native.load()
+    other = JTFSPlan(N=2 ** 12, J=5, Q=4, Q2=2, J_fr=2, Q_fr=1, T=32, F=2, batch=3)
+    plan = JTFSPlan(**PARAMS, batch=2)
+    assert other.workspace_bytes <= 32 << 20
+    poison = torch.full((3, 2 ** 12), float("nan"), device="cuda")
+    assert torch.isnan(_noalloc(lib, other, poison)).any()
+    x = torch.tensor(np.stack([signals.white_noise(PARAMS["N"], 23 + b) for b in range(2)]), device="cuda")
+    assert torch.equal(_noalloc(lib, plan, x), plan.forward(x))
+    xo = torch.tensor(np.stack([signals.white_noise(2 ** 12, 29 + b) for b in range(3)]), device="cuda")
+    assert torch.equal(_noalloc(lib, other, xo), other.forward(xo))
+
+
 def test_forward_noalloc_refuses_plans_beyond_its_scratch():
     from paper_2602_11896_gb300 import JTFSPlan, _native
     lib = _native.load()
