@@ -173,6 +173,12 @@ struct jtfs_batch_s {
   size_t ws_bytes = 0;
   int max_blocks_x = 1;
   bool on_device = false;
+  // Time-axis FFT stages of all groups merged (one launch per stage, one
+  // cluster launch per size 2^14 .. 2^16); empty with more than kMaxGroups
+  // groups, which then run one after another.
+  bool merged_ok = false;
+  jtfs::FftMerged merged[jtfs::FS_COUNT];
+  void* d_merged = nullptr;
 };
 
 namespace {
@@ -181,6 +187,7 @@ void destroy_batch(jtfs_batch_s* b) {
   if (!b) return;
   for (auto& g : b->groups) jtfs::release_plan(g.plan);
   if (b->d_clips) cudaFree(b->d_clips);
+  if (b->d_merged) cudaFree(b->d_merged);
   delete b;
 }
 
@@ -287,6 +294,31 @@ extern "C" int jtfs_batch_create(jtfs_batch_t* out, const int64_t* lengths, int 
           rc = JTFS_ERR_CUDA;
         b->on_device = rc == JTFS_OK;
       }
+      if (rc == JTFS_OK && b->on_device && b->groups.size() <= size_t(jtfs::kMaxGroups)) {
+        // Merged job and item tables of the time-axis FFT stages.
+        std::vector<const jtfs::Plan*> plans;
+        for (const auto& g : b->groups) plans.push_back(&g.plan);
+        std::vector<jtfs::Job> mj;
+        std::vector<int4> mi;
+        int j0[jtfs::FS_COUNT], i0[jtfs::FS_COUNT];
+        jtfs::merge_fft_stages(plans.data(), static_cast<int>(plans.size()), mj, mi, b->merged, j0, i0);
+        const size_t jb = mj.size() * sizeof(jtfs::Job), ib = mi.size() * sizeof(int4);
+        if (cudaMalloc(&b->d_merged, jtfs::align256(jb) + std::max<size_t>(ib, 16)) != cudaSuccess) {
+          rc = JTFS_ERR_NOMEM;
+        } else {
+          auto* at = static_cast<unsigned char*>(b->d_merged);
+          auto* dj = reinterpret_cast<jtfs::Job*>(at);
+          auto* di = reinterpret_cast<int4*>(at + jtfs::align256(jb));
+          if ((jb && cudaMemcpy(dj, mj.data(), jb, cudaMemcpyHostToDevice) != cudaSuccess) ||
+              (ib && cudaMemcpy(di, mi.data(), ib, cudaMemcpyHostToDevice) != cudaSuccess))
+            rc = JTFS_ERR_CUDA;
+          for (int st = 0; st < jtfs::FS_COUNT; ++st) {
+            b->merged[st].jobs = dj + j0[st];
+            b->merged[st].items = di + i0[st];
+          }
+          b->merged_ok = rc == JTFS_OK;
+        }
+      }
     }
   } catch (...) {
     rc = JTFS_ERR_NOMEM;
@@ -338,9 +370,49 @@ int gather_and_forward(jtfs_batch_t b, const float* x, void* ws, bool full, cuda
   jtfs::k_gather<<<dim3(std::min(b->max_blocks_x, 1024), count), jtfs::kThreadsB, 0, s>>>(
       b->d_clips, x, reinterpret_cast<float*>(base));
   if (launched() != JTFS_OK) return JTFS_ERR_CUDA;
+  if (b->merged_ok) {
+    const int n = static_cast<int>(b->groups.size());
+    const jtfs::Plan* plans[jtfs::kMaxGroups];
+    const float* x_g[jtfs::kMaxGroups];
+    float* phi_g[jtfs::kMaxGroups];
+    void* ws_g[jtfs::kMaxGroups];
+    for (int i = 0; i < n; ++i) {
+      const auto& g = b->groups[size_t(i)];
+      plans[i] = &g.plan;
+      x_g[i] = reinterpret_cast<const float*>(base + g.ypad_off);
+      phi_g[i] = reinterpret_cast<float*>(base + g.phi_off);
+      ws_g[i] = base + g.ws_off;
+    }
+    return jtfs::run_forward_multi(plans, x_g, phi_g, ws_g, n, b->merged, full, s);
+  }
   for (const auto& g : b->groups) {
     const int rc = jtfs::run_forward(g.plan, reinterpret_cast<const float*>(base + g.ypad_off),
                                      reinterpret_cast<float*>(base + g.phi_off), base + g.ws_off, full, s);
+    if (rc != JTFS_OK) return rc;
+  }
+  return JTFS_OK;
+}
+
+int backward_all(jtfs_batch_t b, void* ws, cudaStream_t s) {
+  auto* base = static_cast<unsigned char*>(ws);
+  if (b->merged_ok) {
+    const int n = static_cast<int>(b->groups.size());
+    const jtfs::Plan* plans[jtfs::kMaxGroups];
+    const float* dphi_g[jtfs::kMaxGroups];
+    float* dy_g[jtfs::kMaxGroups];
+    void* ws_g[jtfs::kMaxGroups];
+    for (int i = 0; i < n; ++i) {
+      const auto& g = b->groups[size_t(i)];
+      plans[i] = &g.plan;
+      dphi_g[i] = reinterpret_cast<const float*>(base + g.dphi_off);
+      dy_g[i] = reinterpret_cast<float*>(base + g.dy_off);
+      ws_g[i] = base + g.ws_off;
+    }
+    return jtfs::run_backward_multi(plans, dphi_g, dy_g, ws_g, n, b->merged, s);
+  }
+  for (const auto& g : b->groups) {
+    const int rc = jtfs::run_backward(g.plan, reinterpret_cast<const float*>(base + g.dphi_off),
+                                      reinterpret_cast<float*>(base + g.dy_off), base + g.ws_off, s);
     if (rc != JTFS_OK) return rc;
   }
   return JTFS_OK;
@@ -373,11 +445,8 @@ extern "C" int jtfs_batch_metamer_step(jtfs_batch_t batch, float* y, const float
   if (rc != JTFS_OK) return rc;
   jtfs::k_masked_loss<<<count, 512, 0, s>>>(batch->d_clips, phi_target, reinterpret_cast<float*>(base), loss);
   if (launched() != JTFS_OK) return JTFS_ERR_CUDA;
-  for (const auto& g : batch->groups) {
-    rc = jtfs::run_backward(g.plan, reinterpret_cast<const float*>(base + g.dphi_off),
-                            reinterpret_cast<float*>(base + g.dy_off), base + g.ws_off, s);
-    if (rc != JTFS_OK) return rc;
-  }
+  rc = backward_all(batch, workspace, s);
+  if (rc != JTFS_OK) return rc;
   jtfs::k_fold<<<dim3(std::min(batch->max_blocks_x, 1024), count), jtfs::kThreadsB, 0, s>>>(
       batch->d_clips, reinterpret_cast<float*>(base));
   if (launched() != JTFS_OK) return JTFS_ERR_CUDA;

@@ -1696,7 +1696,7 @@ int64_t forward_launches(const Plan& p, bool full) {
 }
 
 int64_t backward_launches(const Plan& p) {
-  int64_t n = 1 + fft_launches(p, p.L_ds1) + static_cast<int64_t>(p.L_u1inplace.size()) +
+  int64_t n = 1 + fft_launches(p, p.L_ds1) + (p.L_u1inplace.empty() ? 0 : 1) +
               2 * fft_launches(p, p.L_u1inplace) + (p.unpooled_t ? 1 : fft_launches(p, p.L_ds0)) + 1 + fft_launches(p, p.L_x);
   if (p.n_active > 0) n += 1 + freq2_launches(p) + fft_launches(p, p.L_y2inplace);
   return n;
@@ -1721,33 +1721,138 @@ size_t ct_smem(const Plan& p, int nbuf, int cols, FreqArgs& A) {
 
 // Forward stages.  `full` = false stops after what the adjoint needs
 // (Xhat, U1hat, S1, Y2) and skips writing Phi.
-int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, bool full, cudaStream_t s) {
-  // The band signals x * psi_n1 (decimated) stay in Zs for the adjoint's
-  // modulus derivative; U1h receives the FFT of their modulus.
-  JTFS_TRY((run_fft<false>(p, p.L_x, LdReal{x}, StC{w.Xh}, w.scr, s)));
-  JTFS_TRY((run_fft<true>(p, p.L_u1, LdBand{w.Xh, p.d_psi1, FiltD{}}, StC{w.Zs}, w.scr, s)));
-  JTFS_TRY((run_fft<false>(p, p.L_u1inplace, LdMod{w.Zs}, StC{w.U1h}, w.scr, s)));
-  if (full) {
-    if (p.unpooled_t)  // zeroth order = x
-      JTFS_TRY(copy_block(p, x, p.N, 0, phi, p.phi_size, 0, p.N, false, s));
-    else
-      JTFS_TRY((run_fft<true>(p, p.L_s0, LdBand{w.Xh, nullptr, p.h_phiT}, StR{phi}, w.scr, s)));
+// ---------------------------------------------------------------------------
+// Several plans run stage by stage (run_forward_multi in jtfs_internal.h);
+// a single plan is the case n = 1 without merged tables.
+// ---------------------------------------------------------------------------
+// One plan of a run, with its workspace buffers and inputs / outputs.
+struct Member {
+  const Plan* p;
+  Bufs w;
+  const float* x;
+  float* phi;
+  const float* dphi;
+  float* dx;
+};
+
+// Per-plan loaders / stores of a merged launch, chosen by the job's `pad`
+// (the kernels take them as __grid_constant__, so the table is indexed in
+// place).
+template <class F>
+struct GLd {
+  F f[kMaxGroups];
+  __device__ __forceinline__ float2 operator()(const Job& jb, int idx, int logn) const {
+    return f[jb.pad](jb, idx, logn);
   }
-  JTFS_TRY((run_fft<true>(p, p.L_s1, LdBand{w.U1h, nullptr, p.h_phiT}, StR{w.S1}, w.scr, s)));
-  const FreqArgs FA = freq_args(p, 1);
-  const FreqArgs FA2 = freq_args(p, 2);
-  if (full) {
-    if (p.unpooled_f || !launch_freq_fwd_ct(1, FA, p.lF, static_cast<unsigned>(p.tiles1.size()), freq_smem(p, 3), s,
-                                            p.d_tiles1, w.S1, nullptr, phi)) {
-      allow_big_smem<k_freq_fwd<1>>();
-      k_freq_fwd<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 3), s>>>(
-          FA, p.d_tiles1, w.S1, nullptr, phi);
-    }
+};
+template <class F>
+struct GSt {
+  F f[kMaxGroups];
+  __device__ __forceinline__ void operator()(const Job& jb, int idx, float2 v) const { f[jb.pad](jb, idx, v); }
+};
+
+// One time-axis FFT stage of every member: the merged launches of the FFT
+// engine when `merged` is given, else each plan's own launches.
+template <bool INV, class MkLd, class MkSt>
+int run_stage(const Member* m, int n, const FftMerged* merged, int stage, MkLd mkld, MkSt mkst, cudaStream_t s) {
+  using Ld = decltype(mkld(m[0]));
+  using St = decltype(mkst(m[0]));
+  if (!merged) {
+    for (int i = 0; i < n; ++i)
+      JTFS_TRY((run_fft<INV>(*m[i].p, stage_launches(*m[i].p, stage), mkld(m[i]), mkst(m[i]), m[i].w.scr, s)));
+    return JTFS_OK;
+  }
+  GLd<Ld> gl{};
+  GSt<St> gs{};
+  for (int i = 0; i < n; ++i) {
+    gl.f[i] = mkld(m[i]);
+    gs.f[i] = mkst(m[i]);
+  }
+  const FftMerged& fm = merged[stage];
+  if (fm.n_items > 0) {
+    allow_big_smem<k_tfft<INV, GLd<Ld>, GSt<St>>>();
+    k_tfft<INV, GLd<Ld>, GSt<St>><<<static_cast<unsigned>(fm.n_items), kTfThreads, kTfSmem, s>>>(gl, gs, fm.jobs,
+                                                                                               fm.items);
     JTFS_TRY(check_launch());
   }
-  if (p.n_active > 0) {
-    JTFS_TRY((run_fft<true>(p, p.L_y2, LdBand{w.U1h, p.d_psi2, FiltD{}}, StC{w.Y2}, w.scr, s)));
-    if (full) {
+  for (const FftLaunch& l : fm.cluster) {
+    allow_big_smem<k_tfft_cluster<INV, GLd<Ld>, GSt<St>>>();
+    const unsigned C = 1u << (l.logn - kTfLogP);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(static_cast<unsigned>(l.njobs) * C);
+    cfg.blockDim = dim3(kTfThreads);
+    cfg.dynamicSmemBytes = kTfSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_tfft_cluster<INV, GLd<Ld>, GSt<St>>, gl, gs, fm.jobs, l.job0, l.logn) !=
+        cudaSuccess)
+      return JTFS_ERR_CUDA;
+  }
+  // Sizes above 2^16 stay on each plan's four-step kernels.
+  for (int i = 0; i < n; ++i)
+    for (const FftLaunch& l : stage_launches(*m[i].p, stage))
+      if (l.logn > kTfLogP + 3) JTFS_TRY((run_fft_launch<INV>(*m[i].p, l, mkld(m[i]), mkst(m[i]), m[i].w.scr, s)));
+  return JTFS_OK;
+}
+
+// STAGE(inverse?, stage, loader, store): loader and store expressions in
+// terms of `g` (the member), `p` (its plan) and `w` (its buffers).
+#define STAGE(INV, ST, LD_EXPR, ST_EXPR)                                                                 \
+  JTFS_TRY((run_stage<INV>(                                                                            \
+      m, n, merged, ST,                                                                                \
+      [&](const Member& g) { const Plan& p = *g.p; const Bufs& w = g.w; (void)p; (void)w; return LD_EXPR; }, \
+      [&](const Member& g) { const Plan& p = *g.p; const Bufs& w = g.w; (void)p; (void)w; return ST_EXPR; }, s)))
+#define EACH for (int gi_ = 0; gi_ < n; ++gi_)
+#define PLAN                     \
+  const Plan& p = *m[gi_].p;     \
+  const Bufs& w = m[gi_].w;      \
+  (void)p;                       \
+  (void)w
+
+int forward_multi(const Member* m, int n, const FftMerged* merged, bool full, cudaStream_t s) {
+  // The band signals x * psi_n1 (decimated) stay in Zs for the adjoint's
+  // modulus derivative; U1h receives the FFT of their modulus.
+  STAGE(false, FS_X, LdReal{g.x}, StC{w.Xh});
+  STAGE(true, FS_U1, (LdBand{w.Xh, p.d_psi1, FiltD{}}), StC{w.Zs});
+  STAGE(false, FS_U1IP, LdMod{w.Zs}, StC{w.U1h});
+  if (full) {
+    if (m[0].p->unpooled_t) {  // zeroth order = x (batches refuse the unpooled flags)
+      EACH {
+        PLAN;
+        JTFS_TRY(copy_block(p, m[gi_].x, p.N, 0, m[gi_].phi, p.phi_size, 0, p.N, false, s));
+      }
+    } else {
+      STAGE(true, FS_S0, (LdBand{w.Xh, nullptr, p.h_phiT}), StR{g.phi});
+    }
+  }
+  STAGE(true, FS_S1, (LdBand{w.U1h, nullptr, p.h_phiT}), StR{w.S1});
+  if (full) {
+    EACH {
+      PLAN;
+      float* phi = m[gi_].phi;
+      const FreqArgs FA = freq_args(p, 1);
+      if (p.unpooled_f || !launch_freq_fwd_ct(1, FA, p.lF, static_cast<unsigned>(p.tiles1.size()), freq_smem(p, 3), s,
+                                              p.d_tiles1, w.S1, nullptr, phi)) {
+        allow_big_smem<k_freq_fwd<1>>();
+        k_freq_fwd<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 3), s>>>(
+            FA, p.d_tiles1, w.S1, nullptr, phi);
+      }
+      JTFS_TRY(check_launch());
+    }
+  }
+  STAGE(true, FS_Y2, (LdBand{w.U1h, p.d_psi2, FiltD{}}), StC{w.Y2});
+  if (full) {
+    EACH {
+      PLAN;
+      float* phi = m[gi_].phi;
+      if (p.n_active == 0) continue;
+      const FreqArgs FA2 = freq_args(p, 2);
       allow_big_smem<k_freq_fwd<2>>();
       prof_begin(p, JTFS_STAGE_FREQ2_FWD, s);
       FreqArgs FA2w = FA2, FA2n = FA2;
@@ -1775,7 +1880,7 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
       JTFS_TRY(check_launch());
       if (p.unpooled_t) {  // second-order blocks = V2 (no phi_T)
         JTFS_TRY(copy_block(p, w.V2, p.v2_tot, 0, phi, p.phi_size, p.phi2_base, p.v2_tot, false, s));
-        return JTFS_OK;
+        continue;
       }
       const PoolArgs PA = pool_args(p);
       const int fpt = p.n_frames >= 128 ? 16 : p.n_frames >= 64 ? 8 : p.n_frames >= 32 ? 4 : p.n_frames >= 16 ? 2 : 1;
@@ -1825,70 +1930,95 @@ int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, boo
 
 // Backward stages from dphi (device, [batch][phi_size]) to dx.  Requires
 // forward_stages(full or not) to have filled Zs, U1h, S1 and Y2.
-int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, cudaStream_t s) {
-  const FreqArgs FA = freq_args(p, 1);
-  const FreqArgs FA2 = freq_args(p, 2);
-  const GradArgs GA = grad_args(p);
-  if (p.n_active > 0) {
-    const PoolArgs PA = pool_args(p);
-    prof_begin(p, JTFS_STAGE_POOL_ADJ, s);
-    if (p.unpooled_t)  // dV2 = the second-order blocks of dPhi
-      JTFS_TRY(copy_block(p, dphi, p.phi_size, p.phi2_base, w.V2, p.v2_tot, 0, p.v2_tot, false, s));
-    if (!p.pool_tiles2.empty()) {
-      if (p.tune_pool_tc && pool_tc_supported(p))  // dense groups on the tensor cores
-        JTFS_TRY(pool_tc_adjoint(p, dphi, w.V2, s));
-      else
-        k_pool_adj2<<<static_cast<unsigned>(p.pool_tiles2.size()), kThreads, 0, s>>>(PA, dphi, w.V2,
-                                                                                     p.d_pool_tiles2);
+int backward_multi(const Member* m, int n, const FftMerged* merged, cudaStream_t s) {
+  EACH {
+    PLAN;
+    const float* dphi = m[gi_].dphi;
+    const FreqArgs FA = freq_args(p, 1);
+    const FreqArgs FA2 = freq_args(p, 2);
+    if (p.n_active > 0) {
+      const PoolArgs PA = pool_args(p);
+      prof_begin(p, JTFS_STAGE_POOL_ADJ, s);
+      if (p.unpooled_t)  // dV2 = the second-order blocks of dPhi
+        JTFS_TRY(copy_block(p, dphi, p.phi_size, p.phi2_base, w.V2, p.v2_tot, 0, p.v2_tot, false, s));
+      if (!p.pool_tiles2.empty()) {
+        if (p.tune_pool_tc && pool_tc_supported(p))  // dense groups on the tensor cores
+          JTFS_TRY(pool_tc_adjoint(p, dphi, w.V2, s));
+        else
+          k_pool_adj2<<<static_cast<unsigned>(p.pool_tiles2.size()), kThreads, 0, s>>>(PA, dphi, w.V2,
+                                                                                       p.d_pool_tiles2);
+      }
+      if (!p.pool_tiles.empty())
+        k_pool_adj<<<static_cast<unsigned>(p.pool_tiles.size()), kThreads, 0, s>>>(PA, dphi, w.V2, p.d_pool_tiles);
+      prof_end(p, JTFS_STAGE_POOL_ADJ, s);
+      JTFS_TRY(check_launch());
+      allow_big_smem<k_freq_adj<2>>();
+      prof_begin(p, JTFS_STAGE_FREQ2_ADJ, s);
+      FreqArgs FA2c = FA2;
+      const size_t smem_c = ct_smem(p, 5, p.freq_cols, FA2c);
+      const bool tc = p.tc_ok && p.tune_tc;
+      if (tc) {
+        prof_begin(p, JTFS_STAGE_FREQ2_ADJ_TC, s);
+        JTFS_TRY(tc_adjoint(p, w.Y2, w.V2, w.dY2, s));
+        prof_end(p, JTFS_STAGE_FREQ2_ADJ_TC, s);
+      }
+      const Tile* t2 = tc ? p.d_tiles2_fft : p.d_tiles2;
+      const unsigned n2 = static_cast<unsigned>(tc ? p.tiles2_fft.size() : p.tiles2.size());
+      if (n2 > 0 &&
+          (p.unpooled_f || !launch_freq_adj_ct(2, FA2c, p.lF, n2, smem_c, s, t2, nullptr, w.Y2, w.V2, nullptr, w.dY2)))
+        k_freq_adj<2><<<n2, kThreads, freq_smem(p, 5), s>>>(FA2, t2, nullptr, w.Y2, w.V2, nullptr, w.dY2);
+      prof_end(p, JTFS_STAGE_FREQ2_ADJ, s);
+      JTFS_TRY(check_launch());
     }
-    if (!p.pool_tiles.empty())
-      k_pool_adj<<<static_cast<unsigned>(p.pool_tiles.size()), kThreads, 0, s>>>(PA, dphi, w.V2, p.d_pool_tiles);
-    prof_end(p, JTFS_STAGE_POOL_ADJ, s);
-    JTFS_TRY(check_launch());
-    allow_big_smem<k_freq_adj<2>>();
-    prof_begin(p, JTFS_STAGE_FREQ2_ADJ, s);
-    FreqArgs FA2c = FA2;
-    const size_t smem_c = ct_smem(p, 5, p.freq_cols, FA2c);
-    const bool tc = p.tc_ok && p.tune_tc;
-    if (tc) {
-      prof_begin(p, JTFS_STAGE_FREQ2_ADJ_TC, s);
-      JTFS_TRY(tc_adjoint(p, w.Y2, w.V2, w.dY2, s));
-      prof_end(p, JTFS_STAGE_FREQ2_ADJ_TC, s);
-    }
-    const Tile* t2 = tc ? p.d_tiles2_fft : p.d_tiles2;
-    const unsigned n2 = static_cast<unsigned>(tc ? p.tiles2_fft.size() : p.tiles2.size());
-    if (n2 > 0 &&
-        (p.unpooled_f || !launch_freq_adj_ct(2, FA2c, p.lF, n2, smem_c, s, t2, nullptr, w.Y2, w.V2, nullptr, w.dY2)))
-      k_freq_adj<2><<<n2, kThreads, freq_smem(p, 5), s>>>(FA2, t2, nullptr, w.Y2, w.V2, nullptr, w.dY2);
-    prof_end(p, JTFS_STAGE_FREQ2_ADJ, s);
+    allow_big_smem<k_freq_adj<1>>();
+    if (p.unpooled_f || !launch_freq_adj_ct(1, FA, p.lF, static_cast<unsigned>(p.tiles1.size()), freq_smem(p, 5), s,
+                                            p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr))
+      k_freq_adj<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 5), s>>>(
+          FA, p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr);
     JTFS_TRY(check_launch());
   }
-  allow_big_smem<k_freq_adj<1>>();
-  if (p.unpooled_f || !launch_freq_adj_ct(1, FA, p.lF, static_cast<unsigned>(p.tiles1.size()), freq_smem(p, 5), s,
-                                          p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr))
-    k_freq_adj<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 5), s>>>(
-        FA, p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr);
-  JTFS_TRY(check_launch());
-  if (p.n_active > 0) JTFS_TRY((run_fft<false>(p, p.L_y2inplace, LdC{w.dY2}, StC{w.dY2}, w.scr, s)));
-  JTFS_TRY((run_fft<false>(p, p.L_ds1, LdReal{w.S1}, StC{w.dS1h}, w.scr, s)));
-  for (const FftLaunch& l : p.L_u1inplace) {
-    dim3 grid((1u << l.logn) / kThreads + 1, l.njobs);
-    k_dU1<<<grid, kThreads, 0, s>>>(GA, p.d_jobs + l.job0, w.dY2, w.dS1h, w.U1h);
-    JTFS_TRY(check_launch());
+  STAGE(false, FS_Y2IP, LdC{w.dY2}, StC{w.dY2});
+  STAGE(false, FS_DS1, LdReal{w.S1}, StC{w.dS1h});
+  EACH {
+    PLAN;
+    // Every level in one launch: the rows of U1 are consecutive jobs (blocks beyond a row's length return).
+    const GradArgs GA = grad_args(p);
+    int njobs = 0, maxlog = 0;
+    for (const FftLaunch& l : p.L_u1inplace) njobs += l.njobs, maxlog = std::max(maxlog, l.logn);
+    if (njobs > 0) {
+      const dim3 grid((1u << maxlog) / kThreads + 1, static_cast<unsigned>(njobs));
+      k_dU1<<<grid, kThreads, 0, s>>>(GA, p.d_jobs + p.L_u1inplace.front().job0, w.dY2, w.dS1h, w.U1h);
+      JTFS_TRY(check_launch());
+    }
   }
-  JTFS_TRY((run_fft<true>(p, p.L_u1inplace, LdC{w.U1h}, StC{w.U1h}, w.scr, s)));
-  JTFS_TRY((run_fft<false>(p, p.L_u1inplace, LdDz{w.U1h, w.Zs}, StC{w.Zs}, w.scr, s)));
-  if (!p.unpooled_t) JTFS_TRY((run_fft<false>(p, p.L_ds0, LdReal{dphi}, StC{w.dS0h}, w.scr, s)));
-  {
+  STAGE(true, FS_U1IP, LdC{w.U1h}, StC{w.U1h});
+  STAGE(false, FS_U1IP, (LdDz{w.U1h, w.Zs}), StC{w.Zs});
+  if (!m[0].p->unpooled_t) STAGE(false, FS_DS0, LdReal{g.dphi}, StC{w.dS0h});
+  EACH {
+    PLAN;
+    const GradArgs GA = grad_args(p);
     const int64_t total = int64_t(p.batch) * p.N;
     k_dX<<<static_cast<unsigned>((total + kThreads - 1) / kThreads), kThreads, 0, s>>>(
         GA, total, w.Zs, p.unpooled_t ? nullptr : w.dS0h, w.dXh);
     JTFS_TRY(check_launch());
   }
-  JTFS_TRY((run_fft<true>(p, p.L_x, LdC{w.dXh}, StR{dx}, w.scr, s)));
-  if (p.unpooled_t)  // the zeroth order is x: its gradient adds directly
-    JTFS_TRY(copy_block(p, dphi, p.phi_size, 0, dx, p.N, 0, p.N, true, s));
+  STAGE(true, FS_X, LdC{w.dXh}, StR{g.dx});
+  EACH {
+    PLAN;
+    if (p.unpooled_t)  // the zeroth order is x: its gradient adds directly
+      JTFS_TRY(copy_block(p, m[gi_].dphi, p.phi_size, 0, m[gi_].dx, p.N, 0, p.N, true, s));
+  }
   return JTFS_OK;
+}
+
+int forward_stages(const Plan& p, const float* x, float* phi, const Bufs& w, bool full, cudaStream_t s) {
+  const Member m{&p, w, x, phi, nullptr, nullptr};
+  return forward_multi(&m, 1, nullptr, full, s);
+}
+
+int backward_stages(const Plan& p, const float* dphi, float* dx, const Bufs& w, cudaStream_t s) {
+  const Member m{&p, w, nullptr, nullptr, dphi, dx};
+  return backward_multi(&m, 1, nullptr, s);
 }
 
 // Coloured initialisation (§2.3): y0 = ||x|| y~ / ||y~||,
@@ -1955,6 +2085,89 @@ int check_call(const Plan& p, void* ws) {
 bool misaligned(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15) != 0; }
 
 }  // namespace
+
+const std::vector<FftLaunch>& stage_launches(const Plan& p, int stage) {
+  switch (stage) {
+    case FS_X: return p.L_x;
+    case FS_U1: return p.L_u1;
+    case FS_U1IP: return p.L_u1inplace;
+    case FS_S0: return p.L_s0;
+    case FS_S1: return p.L_s1;
+    case FS_Y2: return p.L_y2;
+    case FS_Y2IP: return p.L_y2inplace;
+    case FS_DS1: return p.L_ds1;
+    default: return p.L_ds0;
+  }
+}
+
+void merge_fft_stages(const Plan* const* plans, int n, std::vector<Job>& jobs, std::vector<int4>& items,
+                      FftMerged (&out)[FS_COUNT], int (&job0)[FS_COUNT], int (&item0)[FS_COUNT]) {
+  jobs.clear();
+  items.clear();
+  for (int st = 0; st < FS_COUNT; ++st) {
+    FftMerged& fm = out[st];
+    fm.cluster.clear();
+    job0[st] = static_cast<int>(jobs.size());
+    item0[st] = static_cast<int>(items.size());
+    // Sizes up to 2^13: every plan's items, their jobs copied behind (pad = the plan).
+    for (int g = 0; g < n; ++g)
+      for (const FftLaunch& l : stage_launches(*plans[g], st)) {
+        if (l.logn > kTfLogP) continue;
+        const int base = static_cast<int>(jobs.size()) - job0[st];
+        for (int j = 0; j < l.njobs; ++j) {
+          Job jb = plans[g]->jobs[size_t(l.job0 + j)];
+          jb.pad = g;
+          jobs.push_back(jb);
+        }
+        for (int it = 0; it < l.n_items; ++it) {
+          int4 v = plans[g]->tf_items[size_t(l.item0 + it)];
+          v.x = base + (v.x - l.job0);   // relative to the stage's first job
+          items.push_back(v);
+        }
+      }
+    fm.n_items = static_cast<int>(items.size()) - item0[st];
+    // 2^14 .. 2^16: one cluster launch per size over every plan's jobs of that size.
+    for (int lg = kTfLogP + 1; lg <= kTfLogP + 3; ++lg) {
+      const int first = static_cast<int>(jobs.size()) - job0[st];
+      for (int g = 0; g < n; ++g)
+        for (const FftLaunch& l : stage_launches(*plans[g], st)) {
+          if (l.logn != lg) continue;
+          for (int j = 0; j < l.njobs; ++j) {
+            Job jb = plans[g]->jobs[size_t(l.job0 + j)];
+            jb.pad = g;
+            jobs.push_back(jb);
+          }
+        }
+      const int cnt = static_cast<int>(jobs.size()) - job0[st] - first;
+      if (cnt > 0) fm.cluster.push_back({lg, cnt, first, 0, 0});
+    }
+  }
+}
+
+namespace {
+std::vector<Member> members(const Plan* const* plans, const float* const* x, float* const* phi,
+                            const float* const* dphi, float* const* dx, void* const* ws, int n) {
+  std::vector<Member> m(static_cast<size_t>(n));
+  for (int i = 0; i < n; ++i)
+    m[size_t(i)] = {plans[i], bufs(*plans[i], ws[i]), x ? x[i] : nullptr, phi ? phi[i] : nullptr,
+                    dphi ? dphi[i] : nullptr, dx ? dx[i] : nullptr};
+  return m;
+}
+}  // namespace
+
+int run_forward_multi(const Plan* const* plans, const float* const* x, float* const* phi, void* const* ws, int n,
+                      const FftMerged* merged, bool full, cudaStream_t s) {
+  if (n < 1 || n > kMaxGroups) return JTFS_ERR_ARG;
+  const std::vector<Member> m = members(plans, x, phi, nullptr, nullptr, ws, n);
+  return forward_multi(m.data(), n, merged, full, s);
+}
+
+int run_backward_multi(const Plan* const* plans, const float* const* dphi, float* const* dx, void* const* ws, int n,
+                       const FftMerged* merged, cudaStream_t s) {
+  if (n < 1 || n > kMaxGroups) return JTFS_ERR_ARG;
+  const std::vector<Member> m = members(plans, nullptr, nullptr, dphi, dx, ws, n);
+  return backward_multi(m.data(), n, merged, s);
+}
 
 int run_forward(const Plan& p, const float* x, float* phi, void* ws, bool full, cudaStream_t s) {
   return forward_stages(p, x, phi, bufs(p, ws), full, s);

@@ -320,6 +320,29 @@ int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, c
 int run_forward(const Plan& p, const float* x, float* phi, void* ws, bool full, cudaStream_t s);
 int run_backward(const Plan& p, const float* dphi, float* dx, void* ws, cudaStream_t s);
 
+// Several plans run stage by stage (the groups of a ragged batch): each
+// time-axis FFT stage of all plans is one launch of the FFT engine (plus one
+// cluster launch per size 2^14 .. 2^16) over merged job tables, in which a
+// job's `pad` field names its plan; the other stages launch per plan.
+constexpr int kMaxGroups = 8;
+enum FftStage { FS_X, FS_U1, FS_U1IP, FS_S0, FS_S1, FS_Y2, FS_Y2IP, FS_DS1, FS_DS0, FS_COUNT };
+const std::vector<FftLaunch>& stage_launches(const Plan& p, int stage);
+struct FftMerged {
+  const Job* jobs = nullptr;          // device
+  const int4* items = nullptr;        // device: (first job, jobs, log2 n, 0) per CTA, sizes <= 2^13
+  int n_items = 0;
+  std::vector<FftLaunch> cluster;     // one per size 2^14 .. 2^16: (log2 n, jobs, first job)
+};
+// Host side of the merged tables of `n` plans (job / item arrays of every
+// stage concatenated); `jobs` / `items` receive the arrays to upload, and
+// `out[stage]` their ranges (pointers filled by the caller after upload).
+void merge_fft_stages(const Plan* const* plans, int n, std::vector<Job>& jobs, std::vector<int4>& items,
+                      FftMerged (&out)[FS_COUNT], int (&job0)[FS_COUNT], int (&item0)[FS_COUNT]);
+int run_forward_multi(const Plan* const* plans, const float* const* x, float* const* phi, void* const* ws,
+                      int n, const FftMerged* merged, bool full, cudaStream_t s);
+int run_backward_multi(const Plan* const* plans, const float* const* dphi, float* const* dx, void* const* ws,
+                       int n, const FftMerged* merged, cudaStream_t s);
+
 }  // namespace jtfs
 
 // Opaque handle of the C ABI.

@@ -276,18 +276,20 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
     for (int b = 0; b < B; ++b) js.push_back({int64_t(b) * N, int64_t(b) * N, -1, p.logN, b, 0});
     add(p.L_x, p.logN, js);
   }
-  for (int lev = 0; lev <= p.lT; ++lev) {
-    std::vector<Job> band, rows;
-    for (int b = 0; b < B; ++b)
-      for (int n1 = 0; n1 < p.N1; ++n1)
-        if (p.k1[n1] == lev) {
-          const int64_t o = int64_t(b) * p.u1_tot + p.u1_off[n1];
-          band.push_back({int64_t(b) * N, o, n1, p.logN, b, 0});
-          rows.push_back({o, o, n1, p.logN - lev, b, 0});
-        }
-    add(p.L_u1, p.logN - lev, band);
-    add(p.L_u1inplace, p.logN - lev, rows);
-  }
+  // Rows of U1 per level: all band jobs, then all row jobs, so that the row jobs of every level
+  // are consecutive (the adjoint's k_dU1 covers them in one launch).
+  for (int pass = 0; pass < 2; ++pass)
+    for (int lev = 0; lev <= p.lT; ++lev) {
+      std::vector<Job> js;
+      for (int b = 0; b < B; ++b)
+        for (int n1 = 0; n1 < p.N1; ++n1)
+          if (p.k1[n1] == lev) {
+            const int64_t o = int64_t(b) * p.u1_tot + p.u1_off[n1];
+            if (pass == 0) js.push_back({int64_t(b) * N, o, n1, p.logN, b, 0});
+            else js.push_back({o, o, n1, p.logN - lev, b, 0});
+          }
+      add(pass == 0 ? p.L_u1 : p.L_u1inplace, p.logN - lev, js);
+    }
   {
     std::vector<Job> s0, ds0, s1, ds1;
     for (int b = 0; b < B; ++b) {

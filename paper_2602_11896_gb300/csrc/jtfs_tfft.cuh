@@ -25,7 +25,8 @@
 //   reads are done.  Inputs are read before the first barrier and outputs
 //   written after it, so a stage may transform a buffer in place.
 // Loaders and stores are the functors of the four-step kernels (element idx
-// of the transform described by a job).
+// of the transform described by a job), passed as __grid_constant__ so that
+// the per-plan functor tables of a multi-plan run are indexed in place.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -132,7 +133,8 @@ __device__ void tf_fft(float2* s, int logn, int total) {
 // Transforms of up to kTfP points: item (job0, count, log2 n) per CTA.
 template <bool INV, class Ld, class St>
 __global__ void __launch_bounds__(kTfThreads, 2)
-k_tfft(Ld ld, St st, const Job* __restrict__ jobs, const int4* __restrict__ items) {
+k_tfft(const __grid_constant__ Ld ld, const __grid_constant__ St st, const Job* __restrict__ jobs,
+       const int4* __restrict__ items) {
   extern __shared__ float2 tf_sm[];
   __shared__ Job sj[kTfMaxJobs];
   const int4 it = items[blockIdx.x];
@@ -149,7 +151,8 @@ k_tfft(Ld ld, St st, const Job* __restrict__ jobs, const int4* __restrict__ item
 // One transform of n = C 2^13 points per cluster of C CTAs (C = 2, 4, 8).
 template <bool INV, class Ld, class St>
 __global__ void __launch_bounds__(kTfThreads, 2)
-k_tfft_cluster(Ld ld, St st, const Job* __restrict__ jobs, int job0, int logn) {
+k_tfft_cluster(const __grid_constant__ Ld ld, const __grid_constant__ St st, const Job* __restrict__ jobs, int job0,
+               int logn) {
   namespace cg = cooperative_groups;
   extern __shared__ float2 tf_sm[];
   cg::cluster_group cl = cg::this_cluster();
