@@ -87,19 +87,27 @@ __global__ void __launch_bounds__(kThreadsB) k_fold(const ClipD* __restrict__ cl
   }
 }
 
-// Set by k_masked_loss when a clip's loss is NaN or infinite (jtfs_status).
+// Set by k_masked_loss_sum when a clip's loss is NaN or infinite (jtfs_status).
 __device__ int g_batch_nonfinite;
 
 // Loss over the kept frames, dPhi = 2 (Phi - target) there and 0 on cropped
-// frames; one block per clip, fixed-order reduction.
-__global__ void __launch_bounds__(512) k_masked_loss(const ClipD* __restrict__ clips, const float* __restrict__ tgt,
-                                                    float* ws, float* __restrict__ loss) {
+// frames: kLossParts CTAs per clip each sum a fixed range of its entries in
+// double, then k_masked_loss_sum adds the parts of each clip in a fixed order
+// (deterministic).
+constexpr int kLossParts = 16;
+
+__global__ void __launch_bounds__(512) k_masked_loss_part(const ClipD* __restrict__ clips,
+                                                         const float* __restrict__ tgt, float* ws,
+                                                         double* __restrict__ part) {
   __shared__ double red[512];
-  const ClipD c = clips[blockIdx.x];
-  const int64_t total = static_cast<int64_t>(c.rows) * c.nf_full;
+  const ClipD c = clips[blockIdx.y];
+  const int lnf = __ffs(c.nf_full) - 1;   // N / T frames: a power of two
+  const int64_t total = static_cast<int64_t>(c.rows) << lnf;
+  const int64_t chunk = (total + kLossParts - 1) / kLossParts;
+  const int64_t lo = static_cast<int64_t>(blockIdx.x) * chunk, hi = min(total, lo + chunk);
   double acc = 0.0;
-  for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
-    const int r = static_cast<int>(i / c.nf_full), f = static_cast<int>(i % c.nf_full);
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const int r = static_cast<int>(i >> lnf), f = static_cast<int>(i & (c.nf_full - 1));
     float d = 0.f;
     if (f >= c.f0 && f < c.f0 + c.nf) {
       d = ws[c.phi + i] - tgt[c.po + static_cast<int64_t>(r) * c.nf + (f - c.f0)];
@@ -113,10 +121,16 @@ __global__ void __launch_bounds__(512) k_masked_loss(const ClipD* __restrict__ c
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    loss[blockIdx.x] = static_cast<float>(red[0]);
-    if (!isfinite(red[0])) atomicOr(&g_batch_nonfinite, 1);
-  }
+  if (threadIdx.x == 0) part[static_cast<int64_t>(blockIdx.y) * kLossParts + blockIdx.x] = red[0];
+}
+
+__global__ void k_masked_loss_sum(const double* __restrict__ part, float* __restrict__ loss, int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  double acc = 0.0;
+  for (int q = 0; q < kLossParts; ++q) acc += part[static_cast<int64_t>(b) * kLossParts + q];
+  loss[b] = static_cast<float>(acc);
+  if (!isfinite(acc)) atomicOr(&g_batch_nonfinite, 1);
 }
 
 // Cropped Phi, packed.
@@ -176,6 +190,7 @@ struct jtfs_batch_s {
   // Time-axis FFT stages of all groups merged (one launch per stage, one
   // cluster launch per size 2^14 .. 2^16); empty with more than kMaxGroups
   // groups, which then run one after another.
+  size_t lossp_off = 0;   // per-clip partial loss sums (kLossParts doubles per clip)
   bool merged_ok = false;
   jtfs::FftMerged merged[jtfs::FS_COUNT];
   void* d_merged = nullptr;
@@ -277,6 +292,8 @@ extern "C" int jtfs_batch_create(jtfs_batch_t* out, const int64_t* lengths, int 
         }
         b->max_blocks_x = std::max<int>(b->max_blocks_x, static_cast<int>((N + 255) / 256));
       }
+      b->lossp_off = off;
+      off = jtfs::align256(off + size_t(count) * jtfs::kLossParts * sizeof(double));
       b->ws_bytes = off;
       b->so.assign(count + 1, 0);
       b->po.assign(count + 1, 0);
@@ -443,7 +460,11 @@ extern "C" int jtfs_batch_metamer_step(jtfs_batch_t batch, float* y, const float
   const int count = static_cast<int>(batch->lengths.size());
   int rc = gather_and_forward(batch, y, workspace, true, s);
   if (rc != JTFS_OK) return rc;
-  jtfs::k_masked_loss<<<count, 512, 0, s>>>(batch->d_clips, phi_target, reinterpret_cast<float*>(base), loss);
+  jtfs::k_masked_loss_part<<<dim3(jtfs::kLossParts, count), 512, 0, s>>>(
+      batch->d_clips, phi_target, reinterpret_cast<float*>(base), reinterpret_cast<double*>(base + batch->lossp_off));
+  if (launched() != JTFS_OK) return JTFS_ERR_CUDA;
+  jtfs::k_masked_loss_sum<<<(count + 127) / 128, 128, 0, s>>>(reinterpret_cast<const double*>(base + batch->lossp_off),
+                                                               loss, count);
   if (launched() != JTFS_OK) return JTFS_ERR_CUDA;
   rc = backward_all(batch, workspace, s);
   if (rc != JTFS_OK) return rc;

@@ -428,6 +428,17 @@ int run_fft_launch(const Plan& p, const FftLaunch& l, const Ld& ld, const St& st
   return JTFS_OK;
 }
 
+// One launch description of 2^17 .. 2^20 points on the FFT engine (two passes through the scratch).
+template <bool INV, class Ld, class St>
+int run_tfft_big(const Plan& p, const FftLaunch& l, const Ld& ld, const St& st, float2* scr, cudaStream_t s) {
+  allow_big_smem<k_tfft_big1<INV, Ld>>();
+  allow_big_smem<k_tfft_big2<INV, St>>();
+  const unsigned grid = static_cast<unsigned>(l.njobs) << (l.logn - kTfLogP);
+  k_tfft_big1<INV, Ld><<<grid, kTfThreads, kTfSmem, s>>>(ld, p.d_jobs, l.job0, l.logn, scr);
+  k_tfft_big2<INV, St><<<grid, kTfThreads, kTfSmem, s>>>(st, p.d_jobs, l.job0, l.logn, scr);
+  return cudaGetLastError() == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA;
+}
+
 // Transforms of one stage on the time-axis FFT engine (jtfs_tfft.cuh): every
 // size up to 2^13 in one launch of k_tfft, each size 2^14 .. 2^16 in one
 // cluster launch, larger ones on the four-step kernels.
@@ -459,7 +470,8 @@ int run_tfft(const Plan& p, const std::vector<FftLaunch>& L, const Ld& ld, const
   for (const FftLaunch& l : L) {
     if (l.logn <= kTfLogP) continue;
     if (l.logn > kTfLogP + 3) {
-      const int rc = run_fft_launch<INV>(p, l, ld, st, scr, s);
+      const int rc = l.logn <= kTfLogP + 7 ? run_tfft_big<INV>(p, l, ld, st, scr, s)
+                                           : run_fft_launch<INV>(p, l, ld, st, scr, s);
       if (rc != JTFS_OK) return rc;
       continue;
     }
@@ -1794,10 +1806,10 @@ int run_stage(const Member* m, int n, const FftMerged* merged, int stage, MkLd m
         cudaSuccess)
       return JTFS_ERR_CUDA;
   }
-  // Sizes above 2^16 stay on each plan's four-step kernels.
+  // Sizes above 2^16: each plan's two-pass launches (they need its scratch).
   for (int i = 0; i < n; ++i)
     for (const FftLaunch& l : stage_launches(*m[i].p, stage))
-      if (l.logn > kTfLogP + 3) JTFS_TRY((run_fft_launch<INV>(*m[i].p, l, mkld(m[i]), mkst(m[i]), m[i].w.scr, s)));
+      if (l.logn > kTfLogP + 3) JTFS_TRY((run_tfft_big<INV>(*m[i].p, l, mkld(m[i]), mkst(m[i]), m[i].w.scr, s)));
   return JTFS_OK;
 }
 

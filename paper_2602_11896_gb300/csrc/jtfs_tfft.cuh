@@ -24,6 +24,10 @@
 //   memory); a second cluster barrier keeps every CTA's memory alive until all
 //   reads are done.  Inputs are read before the first barrier and outputs
 //   written after it, so a stage may transform a buffer in place.
+// * 2^17 .. 2^20 points: the same decimation over C = 16 .. 128 CTAs in two
+//   launches through a global scratch (k_tfft_big1: the sub-transforms and
+//   their twiddles; k_tfft_big2: the C-point transforms over them, in the same
+//   shared-memory engine), since clusters hold at most 8 (16) CTAs.
 // Loaders and stores are the functors of the four-step kernels (element idx
 // of the transform described by a job), passed as __grid_constant__ so that
 // the per-plan functor tables of a multi-plan run are indexed in place.
@@ -192,6 +196,52 @@ k_tfft_cluster(const __grid_constant__ Ld ld, const __grid_constant__ St st, con
     }
   }
   cl.sync();
+}
+
+// n = C 2^13 points with C = 16 .. 128 (2^17 .. 2^20), in two launches through
+// a global scratch of n points per job.
+// Pass 1, CTA (job, c): the 2^13-point transform X_c of x[c + C m], times the
+// twiddles W_n^(c k), into scratch [job][c][k].
+template <bool INV, class Ld>
+__global__ void __launch_bounds__(kTfThreads, 2)
+k_tfft_big1(const __grid_constant__ Ld ld, const Job* __restrict__ jobs, int job0, int logn,
+            float2* __restrict__ scr) {
+  extern __shared__ float2 tf_sm[];
+  const int lC = logn - kTfLogP;
+  const int jl = static_cast<int>(blockIdx.x >> lC), c = static_cast<int>(blockIdx.x & ((1u << lC) - 1));
+  const Job jb = jobs[job0 + jl];
+  for (int i = threadIdx.x; i < kTfP; i += kTfThreads) tf_sm[tf_pad(i)] = ld(jb, c + (i << lC), logn);
+  __syncthreads();
+  tf_fft<INV>(tf_sm, kTfLogP, kTfP);
+  float2* out = scr + (static_cast<int64_t>(jl) << logn) + (static_cast<int64_t>(c) << kTfLogP);
+  for (int k = threadIdx.x; k < kTfP; k += kTfThreads) {
+    const float2 v = tf_sm[tf_pad(k)];
+    out[k] = c == 0 ? v : cmul(v, tf_cis<INV>(ldexpf(static_cast<float>(2 * c * k), -logn)));
+  }
+}
+
+// Pass 2, CTA (job, block of K = 2^13 / C outputs k): the C-point transforms
+// over c of the twiddled X_c[k], X[k + 2^13 q] = sum_c W_C^(c q) u_c[k].
+template <bool INV, class St>
+__global__ void __launch_bounds__(kTfThreads, 2)
+k_tfft_big2(const __grid_constant__ St st, const Job* __restrict__ jobs, int job0, int logn,
+            const float2* __restrict__ scr) {
+  extern __shared__ float2 tf_sm[];
+  const int lC = logn - kTfLogP, lK = kTfLogP - lC;
+  const int jl = static_cast<int>(blockIdx.x >> lC), kb = static_cast<int>(blockIdx.x & ((1u << lC) - 1));
+  const Job jb = jobs[job0 + jl];
+  const int k0 = kb << lK;
+  const float2* in = scr + (static_cast<int64_t>(jl) << logn);
+  for (int i = threadIdx.x; i < kTfP; i += kTfThreads) {   // i = c K + j: u_c[k0 + j] -> element c of job j
+    const int c = i >> lK, j = i & ((1 << lK) - 1);
+    tf_sm[tf_pad((j << lC) + c)] = in[(static_cast<int64_t>(c) << kTfLogP) + k0 + j];
+  }
+  __syncthreads();
+  tf_fft<INV>(tf_sm, lC, kTfP);
+  for (int i = threadIdx.x; i < kTfP; i += kTfThreads) {   // i = q K + j
+    const int q = i >> lK, j = i & ((1 << lK) - 1);
+    st(jb, k0 + j + (q << kTfLogP), tf_sm[tf_pad((j << lC) + q)]);
+  }
 }
 
 }  // namespace
