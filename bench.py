@@ -45,7 +45,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one clip's launches of each stage (the tensor-core
 # frequential forward = 4 and adjoint = 5, both kernels of a stage summed), from the capture summarised in
 # profiles/top_kernels_chirps22k_b1_n65536.md; the traffic of a launch grows with the clips it processes.
-DRAM_BYTES_PER_CLIP = {4: 102.201856e6, 5: 213.601024e6}
+DRAM_BYTES_PER_CLIP = {4: (10.742016 + 83.440896 + 7.810816 + 0.003072) * 1e6,
+                       5: (155.725312 + 4.509440 + 52.681728 + 0.044032) * 1e6}
 
 
 def bf16_peak():

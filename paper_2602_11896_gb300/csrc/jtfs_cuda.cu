@@ -1903,11 +1903,17 @@ int forward_multi(const Member* m, int n, const FftMerged* merged, bool full, cu
       prof_begin(p, JTFS_STAGE_POOL_FWD, s);
       const int4* pt = p.d_pool_fwd_tiles[si];
       if (!p.pool_band_tiles.empty()) {
-        k_pool_fwd_band<<<static_cast<unsigned>(p.pool_band_tiles.size()), kThreads, 0, s>>>(PA, w.V2, phi,
-                                                                                            p.d_pool_band_tiles);
-        JTFS_TRY(check_launch());
+        // Banded groups: on the tensor cores where the widened sample range fits the circle.
+        const bool tcb = p.tune_pool_tc && !p.pool_tc_band_tiles.empty();
+        if (tcb) JTFS_TRY(pool_tc_band(p, w.V2, phi, s));
+        const auto& bt = tcb ? p.pool_band_rest : p.pool_band_tiles;
+        if (!bt.empty()) {
+          k_pool_fwd_band<<<static_cast<unsigned>(bt.size()), kThreads, 0, s>>>(
+              PA, w.V2, phi, tcb ? p.d_pool_band_rest : p.d_pool_band_tiles);
+          JTFS_TRY(check_launch());
+        }
       }
-      if (grid.x && p.tune_pool_tc && pool_tc_supported(p)) {
+      if (grid.x && p.tune_pool_tc && pool_tc_dense(p)) {
         // Tensor cores: 128 rows x all frames per CTA, partials into the same slots.
         JTFS_TRY(pool_tc_forward(p, w.V2, w.part, si, s));
       } else if (grid.x && p.n_frames >= 32) {
@@ -1954,7 +1960,7 @@ int backward_multi(const Member* m, int n, const FftMerged* merged, cudaStream_t
       if (p.unpooled_t)  // dV2 = the second-order blocks of dPhi
         JTFS_TRY(copy_block(p, dphi, p.phi_size, p.phi2_base, w.V2, p.v2_tot, 0, p.v2_tot, false, s));
       if (!p.pool_tiles2.empty()) {
-        if (p.tune_pool_tc && pool_tc_supported(p))  // dense groups on the tensor cores
+        if (p.tune_pool_tc && pool_tc_dense(p))  // dense groups on the tensor cores
           JTFS_TRY(pool_tc_adjoint(p, dphi, w.V2, s));
         else
           k_pool_adj2<<<static_cast<unsigned>(p.pool_tiles2.size()), kThreads, 0, s>>>(PA, dphi, w.V2,

@@ -184,6 +184,12 @@ struct Plan {
   // used; forward tiles of the banded levels: (clip, active n2, row tile, 32-frame block).
   std::vector<int> pool_w;
   std::vector<int4> pool_band_tiles;
+  // Banded groups whose widened sample range fits the circle (31 D + 2 W + 128 <= L): tiles of the
+  // tensor-core banded pooling (clip, group, even 64-row slot, 32-frame block), and the FMA tiles of
+  // the other banded groups.
+  std::vector<int4> pool_tc_band_tiles, pool_band_rest;
+  const int4* d_pool_tc_band_tiles = nullptr;
+  const int4* d_pool_band_rest = nullptr;
   // Frequential tables on the N_fr grid, one row of N_fr floats each:
   // rows [0, n_beta2): psi_beta; row n_beta2: phi_F; row n_beta2 + 1 + k:
   // phi_F periodised onto N_fr / 2^k bins (k = 0 .. log2 F).
@@ -290,7 +296,10 @@ void release_plan(Plan& p);
 // plan's frame count has a kernel (32, 64 or 128 frames), the forward
 // launch (partials in the slots of k_pool_reduce), and its expired-wait flag
 // (read and cleared).
-bool pool_tc_supported(const Plan& p);
+bool pool_tc_supported(const Plan& p);   // dense groups (32, 64, 128 frames) or banded tiles on tensor cores
+bool pool_tc_dense(const Plan& p);       // the dense kernels apply (32, 64 or 128 frames)
+// Banded groups on the tensor cores: 32 frames x 128 rows per CTA, Phi written directly.
+int pool_tc_band(const Plan& p, const float* V2, float* phi, cudaStream_t s);
 int pool_tc_forward(const Plan& p, const float* V2, float* part, int si, cudaStream_t s);
 int pool_tc_adjoint(const Plan& p, const float* dphi, float* dV2, cudaStream_t s);
 int pool_tc_error();

@@ -466,13 +466,21 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
       }
   }
   p.pool_band_tiles.clear();
+  p.pool_tc_band_tiles.clear();
+  p.pool_band_rest.clear();
   if (!p.unpooled_t) {
     const int rows = p.rows2;
     for (int b = 0; b < B; ++b)
       for (int a = 0; a < p.n_active; ++a) {
         if (!p.pool_w[a]) continue;
+        const int64_t L = N >> p.s2[a], D = int64_t(1) << (p.lT - p.s2[a]);
+        const bool tc = p.n_frames % 32 == 0 && 31 * D + 2 * int64_t(p.pool_w[a]) + 128 <= L;
         for (int rt = 0; rt < (rows + 63) / 64; ++rt)
-          for (int fb = 0; fb < (p.n_frames + 31) / 32; ++fb) p.pool_band_tiles.push_back(make_int4(b, a, rt, fb));
+          for (int fb = 0; fb < (p.n_frames + 31) / 32; ++fb) {
+            p.pool_band_tiles.push_back(make_int4(b, a, rt, fb));
+            if (!tc) p.pool_band_rest.push_back(make_int4(b, a, rt, fb));
+            else if ((rt & 1) == 0) p.pool_tc_band_tiles.push_back(make_int4(b, a, rt, fb));  // rows rt, rt + 1
+          }
       }
   }
   for (int si = 0; si < 3; ++si) {
@@ -577,6 +585,8 @@ int upload_plan(Plan& p) {
   const size_t o_s2 = put(p.s2.data(), p.s2.size() * sizeof(int));
   const size_t o_pw = put(p.pool_w.data(), p.pool_w.size() * sizeof(int));
   const size_t o_pbt = put(p.pool_band_tiles.data(), p.pool_band_tiles.size() * sizeof(int4));
+  const size_t o_ptcb = put(p.pool_tc_band_tiles.data(), p.pool_tc_band_tiles.size() * sizeof(int4));
+  const size_t o_pbr = put(p.pool_band_rest.data(), p.pool_band_rest.size() * sizeof(int4));
   const size_t o_n1m = put(n1max_act.data(), n1max_act.size() * sizeof(int));
   const size_t o_y2o = put(p.y2_off.data(), p.y2_off.size() * sizeof(int64_t));
   const size_t o_v2o = put(p.v2_off.data(), p.v2_off.size() * sizeof(int64_t));
@@ -626,6 +636,8 @@ int upload_plan(Plan& p) {
   p.d_s2 = reinterpret_cast<const int*>(at(o_s2));
   p.d_pool_w = reinterpret_cast<const int*>(at(o_pw));
   p.d_pool_band_tiles = reinterpret_cast<const int4*>(at(o_pbt));
+  p.d_pool_tc_band_tiles = reinterpret_cast<const int4*>(at(o_ptcb));
+  p.d_pool_band_rest = reinterpret_cast<const int4*>(at(o_pbr));
   p.d_n1max_act = reinterpret_cast<const int*>(at(o_n1m));
   p.d_y2_off = reinterpret_cast<const int64_t*>(at(o_y2o));
   p.d_v2_off = reinterpret_cast<const int64_t*>(at(o_v2o));

@@ -45,7 +45,7 @@ static_assert(kPtProd == 2 * kPtRows, "two producer threads per tile row");
 struct PtArgs {
   const float* V2;
   float* part;
-  const int4* tiles;      // (clip, active group, first 64-row slot, split)
+  const int4* tiles;      // (clip, active group, first 64-row slot, split) or, banded, (..., 32-frame block)
   const int* tile0;       // first partial slot of each (clip, group)
   const int* s2;
   const int64_t* v2_off;
@@ -53,6 +53,11 @@ struct PtArgs {
   const int64_t* tap_off;
   int64_t v2_tot;
   int logN, lT, n_frames, rows, n_active, split_len;
+  // Banded groups: reach of phi_T's taps per group, and Phi written directly.
+  const int* pool_w;
+  float* phi;
+  int64_t phi_size;
+  const int64_t* phi2_off;
 };
 
 struct PtCtl {
@@ -82,7 +87,12 @@ constexpr size_t pt_smem() {
   return sizeof(PtCtl) + 1024 + 2 * (2 * 16384 + 2 * size_t(F) * 128);
 }
 
-template <int F>
+// BAND: a group where phi_T's reach is short against the circle; the CTA
+// computes 32 frames f0 .. f0 + 31 of 128 rows from the samples within reach
+// only (t from f0 D - W to (f0 + 31) D + W, widened to whole 64-sample blocks;
+// the extra samples enter with their own exact taps), read circularly, and
+// writes Phi directly (no split, no reduction).
+template <int F, bool BAND = false>
 __global__ void __launch_bounds__(kPtThreads)
 k_pool_tc_fwd(const PtArgs A) {
   extern __shared__ uint8_t smem_raw[];
@@ -93,9 +103,18 @@ k_pool_tc_fwd(const PtArgs A) {
   const int4 tl = A.tiles[blockIdx.x];
   const int b = tl.x, a = tl.y, slot = tl.z, sp = tl.w;
   const int s = A.s2[a], lL = A.logN - s, L = 1 << lL, D = 1 << (A.lT - s);
-  const int tbeg = sp * A.split_len, tend = min(L, tbeg + A.split_len);
+  const int f0 = BAND ? sp * 32 : 0;   // first frame of the tile
+  int tbeg, tend;
+  if (BAND) {
+    const int W = A.pool_w[a];
+    tbeg = ((f0 * D - W) >> 6) << 6;                          // floor to a 64-sample block
+    tend = ((((f0 + 31) * D + W + 1) + 63) >> 6) << 6;
+  } else {
+    tbeg = sp * A.split_len;
+    tend = min(L, tbeg + A.split_len);
+  }
   const int nkb = (tend - tbeg + kPtK - 1) / kPtK;
-  const int nsplit = (L + A.split_len - 1) / A.split_len;
+  const int nsplit = BAND ? 1 : (L + A.split_len - 1) / A.split_len;
   const int r0 = slot * 64;
   volatile int* abort = &ctl->abort;
   if (tid == 0) {
@@ -129,6 +148,8 @@ k_pool_tc_fwd(const PtArgs A) {
         const int t = t0 + 32 * half + 4 * c;
         if (!rowok || t >= tend) {
           nxt[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else if (BAND) {   // whole 64-sample blocks, circular
+          nxt[c] = __ldg(reinterpret_cast<const float4*>(vrow + (t & (L - 1))));
         } else if (vec) {
           nxt[c] = __ldg(reinterpret_cast<const float4*>(vrow + t));
         } else {
@@ -166,7 +187,7 @@ k_pool_tc_fwd(const PtArgs A) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int t = t0 + 8 * ch + e;
-          v[e] = (f < A.n_frames && t < tend) ? __ldg(g + ((f * D - t) & (L - 1))) : 0.f;
+          v[e] = (f0 + f < A.n_frames && t < tend) ? __ldg(g + (((f0 + f) * D - t) & (L - 1))) : 0.f;
         }
         uint32_t hi[4], lo[4];
 #pragma unroll
@@ -208,9 +229,15 @@ k_pool_tc_fwd(const PtArgs A) {
       constexpr int FH = F / 2;
       const int q4 = warp & 3, fh = warp >> 2;
       const int r = r0 + 32 * q4 + lane;
-      const int64_t ba = static_cast<int64_t>(b) * A.n_active + a;
-      const int64_t t = A.tile0[ba] + static_cast<int64_t>(r >> 6) * nsplit + sp;
-      float4* out = reinterpret_cast<float4*>(A.part + (t * 64 + (r & 63)) * A.n_frames + fh * FH);
+      float4* out;
+      if (BAND) {
+        out = reinterpret_cast<float4*>(A.phi + static_cast<int64_t>(b) * A.phi_size + A.phi2_off[a] +
+                                        static_cast<int64_t>(r) * A.n_frames + f0 + fh * FH);
+      } else {
+        const int64_t ba = static_cast<int64_t>(b) * A.n_active + a;
+        const int64_t t = A.tile0[ba] + static_cast<int64_t>(r >> 6) * nsplit + sp;
+        out = reinterpret_cast<float4*>(A.part + (t * 64 + (r & 63)) * A.n_frames + fh * FH);
+      }
       const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(fh * FH);
       if (FH == 16) {
         uint32_t v[16];
@@ -441,11 +468,11 @@ cudaError_t pt_opt_in(size_t smem) {
   return cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
 }
 
-template <int F>
+template <int F, bool BAND = false>
 int launch_pt(const PtArgs& A, unsigned grid, cudaStream_t s) {
   constexpr size_t smem = pt_smem<F>();
-  if (pt_opt_in<k_pool_tc_fwd<F>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
-  k_pool_tc_fwd<F><<<grid, kPtThreads, smem, s>>>(A);
+  if (pt_opt_in<k_pool_tc_fwd<F, BAND>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
+  k_pool_tc_fwd<F, BAND><<<grid, kPtThreads, smem, s>>>(A);
   return cudaGetLastError() == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA;
 }
 
@@ -483,8 +510,30 @@ int pool_tc_adjoint(const Plan& p, const float* dphi, float* dV2, cudaStream_t s
   }
 }
 
-bool pool_tc_supported(const Plan& p) {
-  return p.n_frames == 32 || p.n_frames == 64 || p.n_frames == 128;
+bool pool_tc_dense(const Plan& p) { return p.n_frames == 32 || p.n_frames == 64 || p.n_frames == 128; }
+
+bool pool_tc_supported(const Plan& p) { return pool_tc_dense(p) || !p.pool_tc_band_tiles.empty(); }
+
+int pool_tc_band(const Plan& p, const float* V2, float* phi, cudaStream_t s) {
+  if (p.pool_tc_band_tiles.empty()) return JTFS_OK;
+  PtArgs A{};
+  A.V2 = V2;
+  A.tiles = p.d_pool_tc_band_tiles;
+  A.s2 = p.d_s2;
+  A.v2_off = p.d_v2_off;
+  A.taps = p.d_taps;
+  A.tap_off = p.d_tap_off;
+  A.v2_tot = p.v2_tot;
+  A.logN = p.logN;
+  A.lT = p.lT;
+  A.n_frames = p.n_frames;
+  A.rows = p.rows2;
+  A.n_active = p.n_active;
+  A.pool_w = p.d_pool_w;
+  A.phi = phi;
+  A.phi_size = p.phi_size;
+  A.phi2_off = p.d_phi2_off;
+  return launch_pt<32, true>(A, static_cast<unsigned>(p.pool_tc_band_tiles.size()), s);
 }
 
 int pool_tc_forward(const Plan& p, const float* V2, float* part, int si, cudaStream_t s) {
