@@ -474,7 +474,11 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
       for (int a = 0; a < p.n_active; ++a) {
         if (!p.pool_w[a]) continue;
         const int64_t L = N >> p.s2[a], D = int64_t(1) << (p.lT - p.s2[a]);
-        const bool tc = p.n_frames % 32 == 0 && 31 * D + 2 * int64_t(p.pool_w[a]) + 128 <= L;
+        // The widened range must fit the circle, and stay as short as a split of the dense path: the tensor
+        // cores' FP32 accumulation over tens of thousands of MMAs drifts (measured 3.7e-4 relative on a
+        // 2.2e5-sample window of the 2^20-sample plan), so long windows keep the FMA kernel.
+        const int64_t span = 31 * D + 2 * int64_t(p.pool_w[a]) + 128;
+        const bool tc = p.n_frames % 32 == 0 && span <= L && span <= 4096 + 128;
         for (int rt = 0; rt < (rows + 63) / 64; ++rt)
           for (int fb = 0; fb < (p.n_frames + 31) / 32; ++fb) {
             p.pool_band_tiles.push_back(make_int4(b, a, rt, fb));
