@@ -4,7 +4,8 @@ The oracle cannot evaluate the whole transform at 2^20 in test time, so:
 * the same filterbanks at reduced N (2^15 forward, 2^14 gradient) against the oracle, every Phi block;
 * at full size, in the launch configuration of the long-signal benchmark: S0, every first-order row and
   two sampled second-order paths of one clip against the oracle, every path of the finest second-order
-  level at two frames (the oracle evaluated at those frames only), and the shift-by-T property.
+  level at two frames (the oracle evaluated at those frames only), the adjoint on S0, the first order and
+  the coarsest second-order group, and the shift-by-T property.
 """
 
 import numpy as np
@@ -125,6 +126,41 @@ def test_full_size_finest_level_against_oracle(full):
     got = blk.reshape(paths, ref_plan.R_out, ref_plan.n_frames)[..., frames]
     for b in range(paths):
         assert _rel(got[b], ref[b]) <= TOL, (a, b)
+
+
+def test_full_size_gradient_on_sampled_paths(full):
+    """The adjoint at full size (4 x 2^20, the long benchmark's plan): J^T w for weights w on S0, every
+    first-order path and the coarsest second-order group of clip 0 (zero elsewhere), against the oracle's
+    autograd of the same linear functional of those outputs (FP64; the rest of the transform is not
+    evaluated).  Exercises the full-size first-layer adjoint (2^20-point transforms, k_dU1, k_dX) and one
+    second-order group's adjoint chain."""
+    plan, x, phi, _, _, _ = full
+    ref_plan = O.Plan(**WL.params)
+    s2 = [min(ref_plan.psi2[n2].j, ref_plan.lT) for n2 in ref_plan.active]
+    a = int(np.argmax(s2))
+    y = WL.inits()
+    yt = torch.tensor(y[:1], dtype=torch.float64, requires_grad=True)
+    out = O.jtfs(yt, ref_plan, active=[a])
+    nf = out["S0"][0].numel()
+    n_first = out["Phi1"][0].numel()
+    blk = out["Phi2_sel"][a][0].numel()
+    n2 = (plan.phi_size - nf - n_first) // len(ref_plan.active)
+    assert n2 == blk
+    off2 = nf + n_first + a * n2
+    rng = np.random.default_rng(77)
+    w_s0 = rng.standard_normal(nf)
+    w_1 = rng.standard_normal(n_first)
+    w_2 = rng.standard_normal(blk)
+    dphi = np.zeros((WL.batch, plan.phi_size), dtype=np.float32)
+    dphi[0, :nf] = w_s0
+    dphi[0, nf:nf + n_first] = w_1
+    dphi[0, off2:off2 + blk] = w_2
+    dx = plan.backward(torch.tensor(y, device="cuda"), torch.tensor(dphi, device="cuda"))[0].cpu().numpy()
+    f = ((out["S0"][0].reshape(-1) * torch.tensor(w_s0)).sum()
+         + (out["Phi1"][0].reshape(-1) * torch.tensor(w_1)).sum()
+         + (out["Phi2_sel"][a][0].reshape(-1) * torch.tensor(w_2)).sum())
+    f.backward()
+    assert _rel(dx, yt.grad[0].numpy()) <= TOL
 
 
 def test_full_size_shift_by_T_shifts_frames(full):
