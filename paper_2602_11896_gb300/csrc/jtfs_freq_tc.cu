@@ -152,6 +152,55 @@ __device__ __forceinline__ void load_a1(const TcArgs& A, const Tile& tl, int n1m
   }
 }
 
+// Y2 tile -> A1 in tensor memory: lane c (this warp's 32 lanes), column word n
+// holds (Re, Im) of Y2 row n as BF16 hi at a1 + n and lo at a1 + 32 KA + n (K
+// index 2n + (re, im), as in the shared-memory form).  Warp-collective: words
+// 4g .. 4g + 3 for g = part, part + nparts, ...; rows n >= n1max are zero.
+template <int KA>
+__device__ __forceinline__ void load_a1_tmem(const TcArgs& A, const Tile& tl, int n1m, int ks1, uint32_t a1, int c,
+                                             int part, int nparts) {
+  const int L2 = 1 << (A.logN - A.s2[tl.a]);
+  const float2* ysrc = A.Y2 + int64_t(tl.b) * A.y2_tot + A.y2_off[tl.a] + tl.t0 + c;
+  const bool colok = c < tl.ncols;
+  for (int g = part; g < 2 * ks1; g += nparts) {
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int n = 4 * g + e;
+      float2 v = make_float2(0.f, 0.f);
+      if (colok && n < n1m) v = ysrc[int64_t(n) * L2];
+      split2(v.x, v.y, hi[e], lo[e]);
+    }
+    tmem_st4(a1 + uint32_t(4 * g), hi);
+    tmem_st4(a1 + uint32_t(32 * KA + 4 * g), lo);
+  }
+}
+
+// GEMM1 of one chunk with A1 in tensor memory (hi at a1, lo at a1 + 32 KA).
+template <int KA, int S1>
+__device__ __forceinline__ bool issue_g1_ts(TcCtl* ctl, const TcChunk& c, int ks1, uint32_t a1, uint32_t sB1,
+                                            uint32_t d, int& c1, volatile int* abort) {
+  const uint32_t idesc = idesc_bf16_n(2 * c.rc);
+  const int na = (ks1 + 3) >> 2;
+  for (int a = 0; a < na; ++a) {
+    const int s = c1 % S1;
+    if (!tc_wait(smem_u32(&ctl->b1_full[s]), (c1 / S1) & 1, abort)) return false;
+    tc_fence_after();
+    const uint64_t bh = kdesc(sB1 + uint32_t(s) * 16384u), bl = bh + (8192u >> 4);
+    const int kn = min(4, ks1 - a * 4);
+    for (int kk = 0; kk < kn; ++kk) {
+      const uint64_t o = uint64_t(kk) * 2u;            // 32 bytes in 16-byte descriptor units
+      const uint32_t ah = a1 + uint32_t(32 * a + 8 * kk), al = ah + uint32_t(32 * KA);  // 8 words = 16 K
+      umma_bf16_ts(d, ah, bh + o, idesc, (a | kk) != 0);
+      umma_bf16_ts(d, al, bh + o, idesc, 1);
+      umma_bf16_ts(d, ah, bl + o, idesc, 1);
+    }
+    umma_commit(smem_u32(&ctl->b1_empty[s]));
+    ++c1;
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // Thread roles of both kernels: warps 0-15 are two epilogue groups of 8 warps
 // (group g takes the chunks i with i % 2 == g; inside a group warp w reads TMEM
@@ -468,31 +517,40 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
 
 // ---------------------------------------------------------------------------
 // Adjoint: dY2 of one tile of 128 columns, from Y2 (recomputed Z) and dV2.
-// Shared memory: A1 as forward, B1 ring S1 x 16 KB, B2' ring kS2 x 4 KB
-// (32 table rows, hi|lo packed), dV 2 x 16 KB (hi|lo packed), A3 NA3 x 32 KB
-// (dZ hi atom | lo atom; with NA3 = 2 one per group), B3 ring S3 x 16 KB (64 rows
-// (n, re/im) x 64 K, hi | lo).
-// TMEM (512 columns): D1 2 x 64 at 0, D2' 2 x 32 at 128, D3 <= 128 at 256.
+// The two data operands that are M x K tiles of the tile's columns, A1 (the Y2
+// tile, for GEMM1) and A3 (dZ of a chunk, for GEMM3), live in tensor memory:
+// an MMA at N = 64 reading a 4 KB A tile and a 2 KB B tile from shared memory
+// each time is bound by shared-memory bandwidth once the three GEMMs, the TMA
+// writes and the epilogue share it; from TMEM only B is read there, and the
+// epilogue writes dZ with tcgen05.st instead of shared-memory stores.
+// Shared memory: B1 ring S1 x 16 KB, B2' ring kS2 x 4 KB (32 table rows, hi|lo
+// packed), dV 2 x 16 KB (hi|lo packed), B3 ring S3 x 16 KB (64 rows (n, re/im)
+// x 64 K, hi | lo).
+// TMEM (512 columns): D1 2 x 64 at 0, D2' 2 x 32 at 128, then
+//   KA = 1: D3 (<= 64) at 192, A1 (32 hi + 32 lo) at 256, A3 NA3 x 64 at 320;
+//   KA = 2: A3 (one, 64) at 192, D3 (<= 128) at 256, A1 (64 hi + 64 lo) at 384.
 // ---------------------------------------------------------------------------
-template <int KA, int S1, int S3, int NA3>
+template <int S1, int S3>
 constexpr size_t tc_adj_smem() {
-  return sizeof(TcCtl) + 1024 + size_t(KA) * 32768 + size_t(S1) * 16384 + size_t(kS2) * 4096 + 2 * 16384 +
-         size_t(NA3) * 32768 + size_t(S3) * 16384;
+  return sizeof(TcCtl) + 1024 + size_t(S1) * 16384 + size_t(kS2) * 4096 + 2 * 16384 + size_t(S3) * 16384;
 }
+template <int KA> __host__ __device__ constexpr uint32_t adj_d3_col() { return KA == 1 ? 192u : 256u; }
+template <int KA> __host__ __device__ constexpr uint32_t adj_a1_col() { return KA == 1 ? 256u : 384u; }
+template <int KA> __host__ __device__ constexpr uint32_t adj_a3_col() { return KA == 1 ? 320u : 192u; }
 
 template <int KA, int S1, int S3, int NA3>
 __global__ void __launch_bounds__(kTcAdjThreads, 1)
 k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2t,
               const __grid_constant__ CUtensorMap tmB3, const TcArgs A) {
+  static_assert(NA3 >= 1 && NA3 <= (KA == 1 ? 2 : 1), "A3 buffers must fit the TMEM map");
   extern __shared__ uint8_t smem_raw[];
   TcCtl* ctl = reinterpret_cast<TcCtl*>(smem_raw);
   const uint32_t base = (smem_u32(smem_raw) + sizeof(TcCtl) + 1023u) & ~1023u;
-  const uint32_t sA1 = base;
-  const uint32_t sB1 = sA1 + uint32_t(KA) * 32768u;
+  const uint32_t sB1 = base;
   const uint32_t sB2 = sB1 + uint32_t(S1) * 16384u;
   const uint32_t sDV = sB2 + uint32_t(kS2) * 4096u;
-  const uint32_t sA3 = sDV + 2u * 16384u;
-  const uint32_t sB3 = sA3 + uint32_t(NA3) * 32768u;
+  const uint32_t sB3 = sDV + 2u * 16384u;
+  constexpr uint32_t kD3 = adj_d3_col<KA>(), kA1 = adj_a1_col<KA>(), kA3 = adj_a3_col<KA>();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Tile tl = A.tiles[blockIdx.x];
   const int n1m = A.n1max_act[tl.a];
@@ -558,7 +616,7 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
           if (!tc_wait(smem_u32(&ctl->d1_empty[j]), ((i >> 1) - 1) & 1, abort)) break;
           tc_fence_after();
         }
-        if (!issue_g1<KA, S1>(ctl, c, ks1, sA1, sB1, tmem + uint32_t(j) * 64u, c1, abort)) break;
+        if (!issue_g1_ts<KA, S1>(ctl, c, ks1, tmem + kA1, sB1, tmem + uint32_t(j) * 64u, c1, abort)) break;
         umma_commit(smem_u32(&ctl->d1_full[j]));
       }
     }
@@ -604,20 +662,21 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         const int ja = i % NA3;
         if (!tc_wait(smem_u32(&ctl->a2_full[ja]), (i / NA3) & 1, abort)) break;
         tc_fence_after();
-        const uint64_t ah = kdesc(sA3 + uint32_t(ja) * 32768u), al = ah + (16384u >> 4);
+        const uint32_t a3 = tmem + kA3 + uint32_t(ja) * 64u;  // dZ hi words 0..31, lo 32..63
         bool okb = true;
         for (int u = 0; u < nh; ++u) {
           const int s = c3 % S3;
           if (!tc_wait(smem_u32(&ctl->b3_full[s]), (c3 / S3) & 1, abort)) { okb = false; break; }
           tc_fence_after();
           const uint64_t bh = kdesc(sB3 + uint32_t(s) * 16384u), bl = bh + (8192u >> 4);
-          const uint32_t d = tmem + 256u + uint32_t(u) * 64u;
+          const uint32_t d = tmem + kD3 + uint32_t(u) * 64u;
           const uint32_t idesc = idesc_bf16_n(min(64, k1pad - 64 * u));
           for (int kk = 0; kk < (c.rc >> 3); ++kk) {  // K = 2 rc
             const uint64_t o = uint64_t(kk) * 2u;
-            umma_bf16(d, ah + o, bh + o, idesc, (i | kk) != 0);
-            umma_bf16(d, al + o, bh + o, idesc, 1);
-            umma_bf16(d, ah + o, bl + o, idesc, 1);
+            const uint32_t ah = a3 + uint32_t(8 * kk), al = ah + 32u;
+            umma_bf16_ts(d, ah, bh + o, idesc, (i | kk) != 0);
+            umma_bf16_ts(d, al, bh + o, idesc, 1);
+            umma_bf16_ts(d, ah, bl + o, idesc, 1);
           }
           umma_commit(smem_u32(&ctl->b3_empty[s]));
           ++c3;
@@ -655,9 +714,11 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         }
       }
     };
-    load_a1<KA>(A, tl, n1m, ks1, sA1, c, (warp >> 2) & 3, 4);
+    load_a1_tmem<KA>(A, tl, n1m, ks1, tmem + lane_off + kA1, c, (warp >> 2) & 3, 4);
+    tmem_st_wait();
     if (g == 0) load_dv(0);
     fence_proxy_async();
+    tc_fence_before();
     mbar_arrive(smem_u32(&ctl->a1_full));
     if (g == 0) mbar_arrive(smem_u32(&ctl->dv_full[0]));
     bool ok = true;
@@ -725,19 +786,24 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
       // last use would not: with NA3 = 1 its parity is the same after chunk i - 1 and after chunk i - 3.)
       const int ja = i % NA3, w = i - NA3;
       if (w >= 0 && !wait_warp(smem_u32(&ctl->a2_empty[w & 1]), (w >> 1) & 1, abort)) { ok = false; break; }
-      const uint32_t ah = sA3 + uint32_t(ja) * 32768u, al = ah + 16384u;
-      const int nck = ch.rc >> 3, ck0 = h * nck;
+      tc_fence_after();
+      // Row r = h rc / 2 + e of the chunk is word r of the A3 buffer: hi at + r, lo at + 32 + r.
+      const uint32_t a3 = tmem + lane_off + kA3 + uint32_t(ja) * 64u;
+      if (ch.rc == 32) {
+        uint32_t hi[16], lo[16];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        if (t < nck) {
-          uint32_t hi[4], lo[4];
+        for (int e = 0; e < 16; ++e) split2(z[2 * e], z[2 * e + 1], hi[e], lo[e]);
+        tmem_st16(a3 + uint32_t(16 * h), hi);
+        tmem_st16(a3 + 32u + uint32_t(16 * h), lo);
+      } else {
+        uint32_t hi[8], lo[8];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) split2(z[8 * t + 2 * e], z[8 * t + 2 * e + 1], hi[e], lo[e]);
-          st_shared_v4(ah + swz128(c, ck0 + t), hi);
-          st_shared_v4(al + swz128(c, ck0 + t), lo);
-        }
+        for (int e = 0; e < 8; ++e) split2(z[2 * e], z[2 * e + 1], hi[e], lo[e]);
+        tmem_st8(a3 + uint32_t(8 * h), hi);
+        tmem_st8(a3 + 32u + uint32_t(8 * h), lo);
       }
-      fence_proxy_async();
+      tmem_st_wait();
+      tc_fence_before();
       mbar_arrive(smem_u32(&ctl->a2_full[ja]));
     }
     if (g == 0 && ok && wait_warp(smem_u32(&ctl->d3_full), 0, abort)) {
@@ -747,7 +813,7 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
       const int ncol = k1pad >> 1;
       for (int b8 = 0; b8 < ncol; b8 += 8) {
         uint32_t r[8];
-        tmem_ld8_nowait(tmem + lane_off + 256u + uint32_t(h * ncol + b8), r);
+        tmem_ld8_nowait(tmem + lane_off + kD3 + uint32_t(h * ncol + b8), r);
         tmem_ld_wait();
         tmem_regs_ready(r);
         const int n0 = (h * ncol + b8) >> 1;
@@ -809,7 +875,7 @@ void split_bf16(double v, uint16_t& hi, uint16_t& lo) {
 }
 
 constexpr int kFwdS1[2] = {2, 6};  // n1max <= 32: two CTAs per SM, so a 2-stage table ring
-constexpr int kAdjS1[2] = {3, 3}, kAdjS3[2] = {2, 2}, kAdjNA3[2] = {2, 1};
+constexpr int kAdjS1[2] = {6, 6}, kAdjS3[2] = {4, 4}, kAdjNA3[2] = {2, 1};
 
 PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
@@ -1071,7 +1137,7 @@ int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, c
   A.dV2 = dV2;
   A.dY2 = dY2;
   if (!p.tc_tiles[0].empty()) {
-    constexpr size_t smem = tc_adj_smem<1, kAdjS1[0], kAdjS3[0], kAdjNA3[0]>();
+    constexpr size_t smem = tc_adj_smem<kAdjS1[0], kAdjS3[0]>();
     if (tc_opt_in<k_freq_tc_adj<1, kAdjS1[0], kAdjS3[0], kAdjNA3[0]>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
     A.tiles = p.d_tc_tiles[0];
     k_freq_tc_adj<1, kAdjS1[0], kAdjS3[0], kAdjNA3[0]>
@@ -1080,7 +1146,7 @@ int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, c
     if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
   }
   if (!p.tc_tiles[1].empty()) {
-    constexpr size_t smem = tc_adj_smem<2, kAdjS1[1], kAdjS3[1], kAdjNA3[1]>();
+    constexpr size_t smem = tc_adj_smem<kAdjS1[1], kAdjS3[1]>();
     if (tc_opt_in<k_freq_tc_adj<2, kAdjS1[1], kAdjS3[1], kAdjNA3[1]>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
     A.tiles = p.d_tc_tiles[1];
     k_freq_tc_adj<2, kAdjS1[1], kAdjS3[1], kAdjNA3[1]>
