@@ -449,12 +449,17 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
       }
       return true;
     };
+    // V2 of a filter is stored after this group's next chunk, not at once: GEMM2 of the filter's last chunk
+    // needs the |Z| this group has just written, and waiting for it here would leave the group idle for
+    // that GEMM's whole latency.  D2[beta & 1] is free again once stored, before GEMM2 of beta + 2 needs it.
+    int pend = -1;
+    bool eok = true;
     TcChunk nx = ld_chunk(A.chunks, g, nch);
     for (int i = g; i < nch; i += NG) {
       const TcChunk ch = nx;
       nx = ld_chunk(A.chunks, i + NG, nch);
       const int j = i & 1;
-      if (!wait_warp(smem_u32(&ctl->d1_full[j]), (i >> 1) & 1, abort)) break;
+      if (!wait_warp(smem_u32(&ctl->d1_full[j]), (i >> 1) & 1, abort)) { eok = false; break; }
       tc_fence_after();
       // D1 columns [h rc, h rc + rc): rc / 2 complex values, rows r = h rc / 2 + e.
       const uint32_t taddr = tmem + lane_off + uint32_t(j) * 64u + uint32_t(h * ch.rc);
@@ -477,7 +482,7 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
       tc_fence_before();
       mbar_arrive(smem_u32(&ctl->d1_empty[j]));
       // |Z| rows into this group's A2 (hi at K = r, lo at K = 32 + r) once GEMM2 of chunk i - 2 has read it.
-      if (i >= 2 && !wait_warp(smem_u32(&ctl->a2_empty[j]), ((i >> 1) - 1) & 1, abort)) break;
+      if (i >= 2 && !wait_warp(smem_u32(&ctl->a2_empty[j]), ((i >> 1) - 1) & 1, abort)) { eok = false; break; }
       const uint32_t a2 = sA2 + uint32_t(j) * 16384u;
       const int nck = ch.rc >> 4, ck0 = h * nck;
 #pragma unroll
@@ -492,8 +497,10 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
       }
       fence_proxy_async();
       mbar_arrive(smem_u32(&ctl->a2_full[j]));
-      if (ch.last && !store_v2(ch.beta)) break;
+      if (pend >= 0 && !store_v2(pend)) { eok = false; break; }
+      pend = ch.last ? ch.beta : -1;
     }
+    if (eok && pend >= 0) store_v2(pend);
   }
 
   // Teardown: no TMA copy or MMA of this CTA may be in flight when it exits.
@@ -524,15 +531,15 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
 // writes and the epilogue share it; from TMEM only B is read there, and the
 // epilogue writes dZ with tcgen05.st instead of shared-memory stores.
 // Shared memory: B1 ring S1 x 16 KB, B2' ring kS2 x 4 KB (32 table rows, hi|lo
-// packed), dV 2 x 16 KB (hi|lo packed), B3 ring S3 x 16 KB (64 rows (n, re/im)
-// x 64 K, hi | lo).
+// packed), dV 2 x 16 KB (hi|lo packed), B3 ring S3 x 16 KA KB (64 KA rows
+// (n, re/im) x 64 K, hi then lo; GEMM3 runs at N = 2 n1max).
 // TMEM (512 columns): D1 2 x 64 at 0, D2' 2 x 32 at 128, then
 //   KA = 1: D3 (<= 64) at 192, A1 (32 hi + 32 lo) at 256, A3 NA3 x 64 at 320;
 //   KA = 2: A3 (one, 64) at 192, D3 (<= 128) at 256, A1 (64 hi + 64 lo) at 384.
 // ---------------------------------------------------------------------------
-template <int S1, int S3>
+template <int KA, int S1, int S3>
 constexpr size_t tc_adj_smem() {
-  return sizeof(TcCtl) + 1024 + size_t(S1) * 16384 + size_t(kS2) * 4096 + 2 * 16384 + size_t(S3) * 16384;
+  return sizeof(TcCtl) + 1024 + size_t(S1) * 16384 + size_t(kS2) * 4096 + 2 * 16384 + size_t(S3) * 16384 * KA;
 }
 template <int KA> __host__ __device__ constexpr uint32_t adj_d3_col() { return KA == 1 ? 192u : 256u; }
 template <int KA> __host__ __device__ constexpr uint32_t adj_a1_col() { return KA == 1 ? 256u : 384u; }
@@ -549,14 +556,14 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
   const uint32_t sB1 = base;
   const uint32_t sB2 = sB1 + uint32_t(S1) * 16384u;
   const uint32_t sDV = sB2 + uint32_t(kS2) * 4096u;
-  const uint32_t sB3 = sDV + 2u * 16384u;
+  const uint32_t sB3 = sDV + 2u * 16384u;  // ring of S3 stages of 16 KB x KA
   constexpr uint32_t kD3 = adj_d3_col<KA>(), kA1 = adj_a1_col<KA>(), kA3 = adj_a3_col<KA>();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Tile tl = A.tiles[blockIdx.x];
   const int n1m = A.n1max_act[tl.a];
   const int ks1 = (2 * n1m + 15) >> 4;
   const int k1pad = 16 * ks1;               // GEMM3 N (columns (n, re/im) kept)
-  const int nh = (k1pad + 63) >> 6;         // GEMM3 N-halves of 64
+  constexpr uint32_t kB3 = 16384u * KA;     // B3 stage: 64 KA rows (n, re/im) x 64 K, hi then lo
   const int nch = A.n_chunks, RO = A.RO;
   const int nbeta = ld_chunk(A.chunks, nch - 1, nch).beta + 1;
   volatile int* abort = &ctl->abort;
@@ -580,16 +587,16 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         ++n2;
         return true;
       };
-      auto load_b3 = [&](const TcChunk& c) -> bool {
-        for (int u = 0; u < nh; ++u) {
-          const int s = n3 % S3;
-          if (n3 >= S3 && !tc_wait(smem_u32(&ctl->b3_empty[s]), ((n3 / S3) - 1) & 1, abort)) return false;
-          const uint32_t bar = smem_u32(&ctl->b3_full[s]);
-          mbar_expect_tx(bar, 16384u);
-          tma_load_2d(sB3 + uint32_t(s) * 16384u, &tmB3, bar, c.b1row, 64 * u);
-          tma_load_2d(sB3 + uint32_t(s) * 16384u + 8192u, &tmB3, bar, c.b1row, 128 + 64 * u);
-          ++n3;
+      auto load_b3 = [&](const TcChunk& c) -> bool {  // one stage: hi rows [0, 64 KA), then lo rows
+        const int s = n3 % S3;
+        if (n3 >= S3 && !tc_wait(smem_u32(&ctl->b3_empty[s]), ((n3 / S3) - 1) & 1, abort)) return false;
+        const uint32_t bar = smem_u32(&ctl->b3_full[s]), st = sB3 + uint32_t(s) * kB3;
+        mbar_expect_tx(bar, kB3);
+        for (int u = 0; u < KA; ++u) {
+          tma_load_2d(st + 8192u * u, &tmB3, bar, c.b1row, 64 * u);
+          tma_load_2d(st + 8192u * (KA + u), &tmB3, bar, c.b1row, 128 + 64 * u);
         }
+        ++n3;
         return true;
       };
       TcChunk cur = ld_chunk(A.chunks, 0, nch);
@@ -663,25 +670,22 @@ k_freq_tc_adj(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
         if (!tc_wait(smem_u32(&ctl->a2_full[ja]), (i / NA3) & 1, abort)) break;
         tc_fence_after();
         const uint32_t a3 = tmem + kA3 + uint32_t(ja) * 64u;  // dZ hi words 0..31, lo 32..63
-        bool okb = true;
-        for (int u = 0; u < nh; ++u) {
-          const int s = c3 % S3;
-          if (!tc_wait(smem_u32(&ctl->b3_full[s]), (c3 / S3) & 1, abort)) { okb = false; break; }
-          tc_fence_after();
-          const uint64_t bh = kdesc(sB3 + uint32_t(s) * 16384u), bl = bh + (8192u >> 4);
-          const uint32_t d = tmem + kD3 + uint32_t(u) * 64u;
-          const uint32_t idesc = idesc_bf16_n(min(64, k1pad - 64 * u));
-          for (int kk = 0; kk < (c.rc >> 3); ++kk) {  // K = 2 rc
-            const uint64_t o = uint64_t(kk) * 2u;
-            const uint32_t ah = a3 + uint32_t(8 * kk), al = ah + 32u;
-            umma_bf16_ts(d, ah, bh + o, idesc, (i | kk) != 0);
-            umma_bf16_ts(d, al, bh + o, idesc, 1);
-            umma_bf16_ts(d, ah, bl + o, idesc, 1);
-          }
-          umma_commit(smem_u32(&ctl->b3_empty[s]));
-          ++c3;
+        // N = k1pad (all (n, re/im) columns kept) in one MMA per term and K step.
+        const int s = c3 % S3;
+        if (!tc_wait(smem_u32(&ctl->b3_full[s]), (c3 / S3) & 1, abort)) break;
+        tc_fence_after();
+        const uint64_t bh = kdesc(sB3 + uint32_t(s) * kB3), bl = bh + ((8192u * KA) >> 4);
+        const uint32_t d = tmem + kD3;
+        const uint32_t idesc = idesc_bf16_n(k1pad);
+        for (int kk = 0; kk < (c.rc >> 3); ++kk) {  // K = 2 rc
+          const uint64_t o = uint64_t(kk) * 2u;
+          const uint32_t ah = a3 + uint32_t(8 * kk), al = ah + 32u;
+          umma_bf16_ts(d, ah, bh + o, idesc, (i | kk) != 0);
+          umma_bf16_ts(d, al, bh + o, idesc, 1);
+          umma_bf16_ts(d, ah, bl + o, idesc, 1);
         }
-        if (!okb) break;
+        umma_commit(smem_u32(&ctl->b3_empty[s]));
+        ++c3;
         umma_commit(smem_u32(&ctl->a2_empty[i & 1]));  // keyed on the chunk, not the buffer
         if (i == nch - 1) umma_commit(smem_u32(&ctl->d3_full));
       }
@@ -875,7 +879,7 @@ void split_bf16(double v, uint16_t& hi, uint16_t& lo) {
 }
 
 constexpr int kFwdS1[2] = {2, 6};  // n1max <= 32: two CTAs per SM, so a 2-stage table ring
-constexpr int kAdjS1[2] = {6, 6}, kAdjS3[2] = {4, 4}, kAdjNA3[2] = {2, 1};
+constexpr int kAdjS1[2] = {6, 6}, kAdjS3[2] = {4, 2}, kAdjNA3[2] = {2, 1};
 
 PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
@@ -1137,7 +1141,7 @@ int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, c
   A.dV2 = dV2;
   A.dY2 = dY2;
   if (!p.tc_tiles[0].empty()) {
-    constexpr size_t smem = tc_adj_smem<kAdjS1[0], kAdjS3[0]>();
+    constexpr size_t smem = tc_adj_smem<1, kAdjS1[0], kAdjS3[0]>();
     if (tc_opt_in<k_freq_tc_adj<1, kAdjS1[0], kAdjS3[0], kAdjNA3[0]>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
     A.tiles = p.d_tc_tiles[0];
     k_freq_tc_adj<1, kAdjS1[0], kAdjS3[0], kAdjNA3[0]>
@@ -1146,7 +1150,7 @@ int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, c
     if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
   }
   if (!p.tc_tiles[1].empty()) {
-    constexpr size_t smem = tc_adj_smem<kAdjS1[1], kAdjS3[1]>();
+    constexpr size_t smem = tc_adj_smem<2, kAdjS1[1], kAdjS3[1]>();
     if (tc_opt_in<k_freq_tc_adj<2, kAdjS1[1], kAdjS3[1], kAdjNA3[1]>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
     A.tiles = p.d_tc_tiles[1];
     k_freq_tc_adj<2, kAdjS1[1], kAdjS3[1], kAdjNA3[1]>
