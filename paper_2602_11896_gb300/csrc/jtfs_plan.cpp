@@ -247,16 +247,20 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
     const double c = 2.0 * M_PI * M_PI * sg * sg;
     const double amp = sg * std::sqrt(2.0 * M_PI);
     const int P = static_cast<int>(std::ceil(std::sqrt(60.0 / c) / double(N))) + 1;
+    // phi_T is even, so g_s[t] = g_s[L - t]: computed for t <= L / 2 and mirrored, which makes the table
+    // exactly symmetric (the pooling kernels read g_s[(t - f D) mod L] for g_s[(f D - t) mod L]).
     for (int s = 0; s <= p.lT; ++s) {
       const int64_t L = N >> s;
-      for (int64_t t = 0; t < L; ++t) {
+      for (int64_t t = 0; t <= L / 2; ++t) {
         const int64_t tau = t << s;
         double acc = 0.0;
         for (int q = -P; q <= P; ++q) {
           const double d = double(tau) - double(q) * double(N);
           acc += std::exp(-c * d * d);
         }
-        p.h_taps[p.tap_off[s] + t] = static_cast<float>(double(int64_t(1) << s) * amp * acc);
+        const float v = static_cast<float>(double(int64_t(1) << s) * amp * acc);
+        p.h_taps[p.tap_off[s] + t] = v;
+        p.h_taps[p.tap_off[s] + ((L - t) & (L - 1))] = v;
       }
     }
   }

@@ -180,14 +180,23 @@ k_pool_tc_fwd(const PtArgs A) {
         st_shared_v4(sA + swz128(rr, ch), hi);
         st_shared_v4(sAl + swz128(rr, ch), lo);
       }
-      // Taps: row f, samples t0 .. t0 + 63 of G[f][t] = g[(f D - t) mod L].
+      // Taps: row f, samples t0 .. t0 + 63 of G[f][t] = g[(f D - t) mod L] = g[(t - f D) mod L] (g is
+      // even).  With D a multiple of 8 the 8 samples of a chunk are 8 consecutive, 32-byte aligned taps.
       for (int q = tid; q < F * 8; q += kPtProd) {
         const int f = q >> 3, ch = q & 7;
+        const int tc = t0 + 8 * ch;
         float v[8];
+        if (f0 + f >= A.n_frames) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int t = t0 + 8 * ch + e;
-          v[e] = (f0 + f < A.n_frames && t < tend) ? __ldg(g + (((f0 + f) * D - t) & (L - 1))) : 0.f;
+          for (int e = 0; e < 8; ++e) v[e] = 0.f;
+        } else if (D >= 8 && tc + 8 <= tend) {
+          const float4* src = reinterpret_cast<const float4*>(g + ((tc - (f0 + f) * D) & (L - 1)));
+          const float4 x = __ldg(src), y = __ldg(src + 1);
+          v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+          v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = tc + e < tend ? __ldg(g + ((tc + e - (f0 + f) * D) & (L - 1))) : 0.f;
         }
         uint32_t hi[4], lo[4];
 #pragma unroll
@@ -352,17 +361,19 @@ k_pool_tc_adj(const PtArgs A, const float* __restrict__ dphi, int64_t phi_size, 
   if (warp < kPtWarpMma) {
     const float* g = A.taps + A.tap_off[s];
     // Tap tile of block j: row t (0..127) = sample tb0 + 128 j + t, K = frame f.
+    // Lanes run along the rows (samples), so each tap load of a warp reads 32 consecutive taps
+    // g[(t - f D) mod L] (= g[(f D - t) mod L], g is even).
     auto build_b = [&](int j) {
       const uint32_t tile = sB0 + uint32_t(j & 1) * kT;
       const int tj = tb0 + 128 * j;
       for (int q = tid; q < 128 * (F / 8); q += kPtProd) {
-        const int row = q / (F / 8), c = q % (F / 8);
+        const int row = q & 127, c = q >> 7;
         const int t = tj + row;
         float v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int f = 8 * c + e;
-          v[e] = (t < L && f < A.n_frames) ? __ldg(g + ((f * D - t) & (L - 1))) : 0.f;
+          v[e] = (t < L && f < A.n_frames) ? __ldg(g + ((t - f * D) & (L - 1))) : 0.f;
         }
         uint32_t hi[4], lo[4];
 #pragma unroll
