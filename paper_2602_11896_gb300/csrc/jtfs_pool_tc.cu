@@ -13,8 +13,8 @@
 // product is hi.hi + lo.hi + hi.lo (three MMAs into one FP32 accumulator).
 //
 // One CTA per (clip, group, 128 rows, time split), 288 threads: warps 0-7 turn
-// 64-sample blocks of V2 (two threads per row, 32 samples each, the next
-// block's loads in flight while the current one is converted) and of the taps
+// 64-sample blocks of V2 (a half-warp per row and load, 4 samples a thread, the
+// next block's loads in flight while the current one is converted) and of the taps
 // into BF16 hi/lo operand tiles (128-byte swizzle, two shared-memory stages)
 // and then read the accumulator (warp w: TMEM lanes 32 (w % 4) .. + 31, half
 // w / 4 of the frames); warp 8 lane 0 issues tcgen05.mma.
@@ -82,6 +82,16 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, const uint32_t (&v)[
                : "memory");
 }
 
+__device__ __forceinline__ float4 ld_shared_v4f(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_shared_v2(uint32_t addr, const uint32_t (&v)[2]) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(v[0]), "r"(v[1]) : "memory");
+}
+
 template <int F>
 constexpr size_t pt_smem() {
   return sizeof(PtCtl) + 1024 + 2 * (2 * 16384 + 2 * size_t(F) * 128);
@@ -93,7 +103,7 @@ constexpr size_t pt_smem() {
 // the extra samples enter with their own exact taps), read circularly, and
 // writes Phi directly (no split, no reduction).
 template <int F, bool BAND = false>
-__global__ void __launch_bounds__(kPtThreads)
+__global__ void __launch_bounds__(kPtThreads, 2)
 k_pool_tc_fwd(const PtArgs A) {
   extern __shared__ uint8_t smem_raw[];
   PtCtl* ctl = reinterpret_cast<PtCtl*>(smem_raw);
@@ -134,26 +144,30 @@ k_pool_tc_fwd(const PtArgs A) {
   bool issued = false;
 
   if (warp < kPtWarpMma) {
-    // Producer: thread pair per row r0 + tid / 2; thread tid % 2 takes samples 32 (tid % 2) .. + 31.
-    const int rr = tid >> 1, half = tid & 1;
-    const int r = r0 + rr;
-    const bool rowok = r < A.rows;
-    const float* vrow = A.V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a] + static_cast<int64_t>(rowok ? r : 0) * L;
+    // Producer: half-warps run along the samples, so each load instruction of a warp reads two rows' 256
+    // contiguous bytes.  Thread (warp w, lane l) takes samples 4 (l % 16) .. + 3 of the rows
+    // 2 (w + 8 i) + l / 16, i = 0 .. 7, of every 64-sample block.
+    const int c4 = lane & 15, sub = lane >> 4;
+    const float* vbase = A.V2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
     const float* g = A.taps + A.tap_off[s];
     const bool vec = L >= kPtK;  // whole 64-sample blocks inside the row: 16-byte loads
     float4 nxt[8];
+    const int rw = r0 + 2 * warp + sub;        // row of i = 0; row i is rw + 16 i
+    const float* vrow0 = vbase + static_cast<int64_t>(rw) * L;
     auto load_v = [&](int t0) {
+      const int t = t0 + 4 * c4;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int t = t0 + 32 * half + 4 * c;
-        if (!rowok || t >= tend) {
-          nxt[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = 0; i < 8; ++i) {
+        const int r = rw + 16 * i;
+        const float* vrow = vrow0 + static_cast<int64_t>(16 * i) * L;
+        if (r >= A.rows || t >= tend) {
+          nxt[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         } else if (BAND) {   // whole 64-sample blocks, circular
-          nxt[c] = __ldg(reinterpret_cast<const float4*>(vrow + (t & (L - 1))));
+          nxt[i] = __ldg(reinterpret_cast<const float4*>(vrow + (t & (L - 1))));
         } else if (vec) {
-          nxt[c] = __ldg(reinterpret_cast<const float4*>(vrow + t));
+          nxt[i] = __ldg(reinterpret_cast<const float4*>(vrow + t));
         } else {
-          nxt[c] = make_float4(vrow[t], t + 1 < tend ? vrow[t + 1] : 0.f, t + 2 < tend ? vrow[t + 2] : 0.f,
+          nxt[i] = make_float4(vrow[t], t + 1 < tend ? vrow[t + 1] : 0.f, t + 2 < tend ? vrow[t + 2] : 0.f,
                                t + 3 < tend ? vrow[t + 3] : 0.f);
         }
       }
@@ -169,16 +183,15 @@ k_pool_tc_fwd(const PtArgs A) {
       if (kb >= 2 && !pt_wait(smem_u32(&ctl->empty[st]), ((kb >> 1) - 1) & 1, abort)) break;
       const uint32_t sA = base + uint32_t(st) * kStage, sAl = sA + kA, sB = sA + 2 * kA, sBl = sB + kB;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {  // 8 samples per 16-byte chunk
-        const int ch = 4 * half + c;
-        const float4 p = cur[2 * c], q = cur[2 * c + 1];
-        uint32_t hi[4], lo[4];
+      for (int i = 0; i < 8; ++i) {  // 4 samples = the half of 16-byte chunk c4 / 2 selected by c4 % 2
+        const int rr = 2 * (warp + 8 * i) + sub;
+        const float4 p = cur[i];
+        uint32_t hi[2], lo[2];
         split2(p.x, p.y, hi[0], lo[0]);
         split2(p.z, p.w, hi[1], lo[1]);
-        split2(q.x, q.y, hi[2], lo[2]);
-        split2(q.z, q.w, hi[3], lo[3]);
-        st_shared_v4(sA + swz128(rr, ch), hi);
-        st_shared_v4(sAl + swz128(rr, ch), lo);
+        const uint32_t off = swz128(rr, c4 >> 1) + 8u * uint32_t(c4 & 1);
+        st_shared_v2(sA + off, hi);
+        st_shared_v2(sAl + off, lo);
       }
       // Taps: row f, samples t0 .. t0 + 63 of G[f][t] = g[(f D - t) mod L] = g[(t - f D) mod L] (g is
       // even).  With D a multiple of 8 the 8 samples of a chunk are 8 consecutive, 32-byte aligned taps.
@@ -307,7 +320,7 @@ template <int F>
 __host__ __device__ constexpr uint32_t pa_tile() { return F == 32 ? 16384u : uint32_t(F / 64) * 2u * 16384u; }  // 128 rows, hi + lo
 
 template <int F>
-constexpr size_t pa_smem() { return sizeof(PaCtl) + 1024 + 3 * size_t(pa_tile<F>()); }
+constexpr size_t pa_smem() { return sizeof(PaCtl) + 1024 + 3 * size_t(pa_tile<F>()) + (F == 32 ? 8 * 4608 : 0); }
 
 // Byte offsets of K-step kk (16 K) inside a hi + lo operand tile.
 template <int F>
@@ -408,9 +421,14 @@ k_pool_tc_adj(const PtArgs A, const float* __restrict__ dphi, int64_t phi_size, 
     build_b(0);
     if (nblk > 1) build_b(1);
     // Epilogue of block j: warp w stores rows 32 (w % 4) + lane, samples 64 (w / 4) .. + 63 of the block.
+    // For F = 32 each 32 x 32 piece goes through a padded per-warp shared-memory tile (rows of 36
+    // floats), so that the global stores run along the rows: 8 lanes x 16 bytes per row, 4 rows per
+    // store instruction, instead of one row per lane.
     const int q4 = warp & 3, hh = warp >> 2;
     const int r = r0 + 32 * q4 + lane;
     float* orow = dV2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a] + static_cast<int64_t>(r < A.rows ? r : 0) * L;
+    float* vbase = dV2 + static_cast<int64_t>(b) * A.v2_tot + A.v2_off[a];
+    const uint32_t stg = sB0 + 2 * kT + uint32_t(warp) * 4608u;
     for (int j = 0; j < nblk; ++j) {
       const int jb = j & 1;
       const bool ok = pt_wait(smem_u32(&ctl->d_full[jb]), (j >> 1) & 1, abort);
@@ -421,7 +439,33 @@ k_pool_tc_adj(const PtArgs A, const float* __restrict__ dphi, int64_t phi_size, 
       for (int h = 0; h < 2; ++h) {
         float v[32];
         tmem_ld32(tmem + (uint32_t(q4 * 32) << 16) + uint32_t(jb * 128 + 64 * hh + 32 * h), v);
-        if (r < A.rows) {
+        if (F == 32) {
+          const int tt = t + 32 * h;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const uint32_t w4[4] = {__float_as_uint(v[4 * e]), __float_as_uint(v[4 * e + 1]),
+                                    __float_as_uint(v[4 * e + 2]), __float_as_uint(v[4 * e + 3])};
+            st_shared_v4(stg + uint32_t(lane) * 144u + 16u * e, w4);
+          }
+          __syncwarp();
+          const int tl = tt + 4 * (lane & 7);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int rho = 4 * k + (lane >> 3), rg = r0 + 32 * q4 + rho;
+            const float4 x = ld_shared_v4f(stg + uint32_t(rho) * 144u + 16u * uint32_t(lane & 7));
+            if (rg < A.rows) {
+              float* o = vbase + static_cast<int64_t>(rg) * L + tl;
+              if (tl + 4 <= L) {
+                *reinterpret_cast<float4*>(o) = x;
+              } else {
+                if (tl < L) o[0] = x.x;
+                if (tl + 1 < L) o[1] = x.y;
+                if (tl + 2 < L) o[2] = x.z;
+              }
+            }
+          }
+          __syncwarp();
+        } else if (r < A.rows) {
           const int tt = t + 32 * h;
           if (tt + 32 <= L) {
             float4* o = reinterpret_cast<float4*>(orow + tt);
