@@ -129,32 +129,9 @@ __device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity, volatil
   return __all_sync(0xffffffffu, ok);
 }
 
-// Y2 tile -> A1 (BF16 hi in atoms [0, KA), lo in atoms [KA, 2 KA)), K index 2n + (re, im).
-// Chunks g = part, part + nparts, ... of the row of column c.
-template <int KA>
-__device__ __forceinline__ void load_a1(const TcArgs& A, const Tile& tl, int n1m, int ks1, uint32_t sA1, int c,
-                                        int part, int nparts) {
-  const int L2 = 1 << (A.logN - A.s2[tl.a]);
-  const float2* ysrc = A.Y2 + int64_t(tl.b) * A.y2_tot + A.y2_off[tl.a] + tl.t0 + c;
-  const bool colok = c < tl.ncols;
-  for (int g = part; g < 2 * ks1; g += nparts) {  // 16-byte chunk g holds n = 4g .. 4g + 3
-    uint32_t hi[4], lo[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int n = 4 * g + e;
-      float2 v = make_float2(0.f, 0.f);
-      if (colok && n < n1m) v = ysrc[int64_t(n) * L2];
-      split2(v.x, v.y, hi[e], lo[e]);
-    }
-    const uint32_t off = uint32_t(g >> 3) * 16384u + swz128(c, g & 7);
-    st_shared_v4(sA1 + off, hi);
-    st_shared_v4(sA1 + uint32_t(KA) * 16384u + off, lo);
-  }
-}
-
 // Y2 tile -> A1 in tensor memory: lane c (this warp's 32 lanes), column word n
 // holds (Re, Im) of Y2 row n as BF16 hi at a1 + n and lo at a1 + 32 KA + n (K
-// index 2n + (re, im), as in the shared-memory form).  Warp-collective: words
+// index 2n + (re, im)).  Warp-collective: words
 // 4g .. 4g + 3 for g = part, part + nparts, ...; rows n >= n1max are zero.
 template <int KA>
 __device__ __forceinline__ void load_a1_tmem(const TcArgs& A, const Tile& tl, int n1m, int ks1, uint32_t a1, int c,
@@ -242,33 +219,6 @@ __device__ __forceinline__ void init_barriers(TcCtl* ctl, int n_epi) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// GEMM1 of one chunk into D1 (TMEM column d): 3 passes per k-step; no fence
-// needed after the TMA waits (the mbarrier orders the async-proxy writes).
-template <int KA, int S1>
-__device__ __forceinline__ bool issue_g1(TcCtl* ctl, const TcChunk& c, int ks1, uint32_t sA1, uint32_t sB1,
-                                         uint32_t d, int& c1, volatile int* abort) {
-  const uint32_t idesc = idesc_bf16_n(2 * c.rc);
-  const int na = (ks1 + 3) >> 2;
-  const uint64_t ah0 = kdesc(sA1), al0 = kdesc(sA1 + uint32_t(KA) * 16384u);
-  for (int a = 0; a < na; ++a) {
-    const int s = c1 % S1;
-    if (!tc_wait(smem_u32(&ctl->b1_full[s]), (c1 / S1) & 1, abort)) return false;
-    tc_fence_after();
-    const uint64_t bh = kdesc(sB1 + uint32_t(s) * 16384u), bl = bh + (8192u >> 4);
-    const uint64_t ah = ah0 + uint64_t(a) * (16384u >> 4), al = al0 + uint64_t(a) * (16384u >> 4);
-    const int kn = min(4, ks1 - a * 4);
-    for (int kk = 0; kk < kn; ++kk) {
-      const uint64_t o = uint64_t(kk) * 2u;  // 32 bytes in 16-byte descriptor units
-      umma_bf16(d, ah + o, bh + o, idesc, (a | kk) != 0);
-      umma_bf16(d, al + o, bh + o, idesc, 1);
-      umma_bf16(d, ah + o, bl + o, idesc, 1);
-    }
-    umma_commit(smem_u32(&ctl->b1_empty[s]));
-    ++c1;
-  }
-  return true;
-}
-
 // TMA loads of one chunk's GEMM1 table rows (one stage per K atom used).
 template <int S1>
 __device__ __forceinline__ bool load_b1(TcCtl* ctl, const CUtensorMap* tm, const TcChunk& c, int ks1, int nr1,
@@ -298,10 +248,12 @@ __device__ __forceinline__ TcChunk ld_chunk(const TcChunk* p, int i, int n) {
 
 // ---------------------------------------------------------------------------
 // Forward: V2 of one tile of 128 columns.
-// Shared memory: A1 [KA atoms hi | KA atoms lo] (16 KB each), B1 ring
-// S1 x 16 KB (64 table rows hi | lo), B2 ring kS2 x 4 KB (R_out rows, hi|lo
-// packed in each 128-byte row), A2 2 x 16 KB (|Z| hi|lo packed, one per group).
-// TMEM: D1 2 x 64 columns at 0, D2 2 x 32 columns at 128.
+// Shared memory: B1 ring S1 x 16 KB (64 table rows hi | lo), B2 ring kS2 x 4 KB
+// (R_out rows, hi|lo packed in each 128-byte row), A2 2 x 16 KB (|Z| hi|lo
+// packed, one per group).
+// TMEM: D1 2 x 64 columns at 0, D2 2 x 32 columns at 128, A1 (the Y2 tile, as
+// in the adjoint: 32 KA hi + 32 KA lo columns) at 192 (KA = 1, 256 columns in
+// all, two CTAs per SM) or 256 (KA = 2, 512 columns).
 // ---------------------------------------------------------------------------
 // Forward threads with NG epilogue groups: 8 NG epilogue warps, then the TMA
 // warp and the two issuing warps.  NG = 1 runs two CTAs per SM (two
@@ -312,8 +264,10 @@ constexpr int kTcAdjThreads = 20 * 32;
 
 template <int KA, int S1>
 constexpr size_t tc_fwd_smem() {
-  return sizeof(TcCtl) + 1024 + size_t(KA) * 32768 + size_t(S1) * 16384 + size_t(kS2) * 4096 + 2 * 16384;
+  return sizeof(TcCtl) + 1024 + size_t(S1) * 16384 + size_t(kS2) * 4096 + 2 * 16384;
 }
+template <int KA> __host__ __device__ constexpr uint32_t fwd_a1_col() { return KA == 1 ? 192u : 256u; }
+template <int KA> __host__ __device__ constexpr uint32_t fwd_tmem_cols() { return KA == 1 ? 256u : 512u; }
 
 template <int KA, int S1, int NG>
 __global__ void __launch_bounds__(tc_fwd_threads<NG>(), NG == 1 ? 2 : 1)
@@ -322,8 +276,8 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
   extern __shared__ uint8_t smem_raw[];
   TcCtl* ctl = reinterpret_cast<TcCtl*>(smem_raw);
   const uint32_t base = (smem_u32(smem_raw) + sizeof(TcCtl) + 1023u) & ~1023u;
-  const uint32_t sA1 = base;
-  const uint32_t sB1 = sA1 + uint32_t(KA) * 32768u;
+  const uint32_t sB1 = base;
+  constexpr uint32_t kA1 = fwd_a1_col<KA>(), kCols = fwd_tmem_cols<KA>();
   const uint32_t sB2 = sB1 + uint32_t(S1) * 16384u;
   const uint32_t sA2 = sB2 + uint32_t(kS2) * 4096u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -333,7 +287,7 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
   const int nch = A.n_chunks, RO = A.RO;
   volatile int* abort = &ctl->abort;
   if (threadIdx.x == 0) init_barriers(ctl, kGrp * NG);
-  if (warp == wG1) tmem_alloc(smem_u32(&ctl->tmem), 256);
+  if (warp == wG1) tmem_alloc(smem_u32(&ctl->tmem), kCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -374,7 +328,7 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
           if (!tc_wait(smem_u32(&ctl->d1_empty[j]), ((i >> 1) - 1) & 1, abort)) break;
           tc_fence_after();
         }
-        if (!issue_g1<KA, S1>(ctl, c, ks1, sA1, sB1, tmem + uint32_t(j) * 64u, c1, abort)) break;
+        if (!issue_g1_ts<KA, S1>(ctl, c, ks1, tmem + kA1, sB1, tmem + uint32_t(j) * 64u, c1, abort)) break;
         umma_commit(smem_u32(&ctl->d1_full[j]));
       }
     }
@@ -414,8 +368,9 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
     const bool colok = c < tl.ncols;
     const int L2 = 1 << (A.logN - A.s2[tl.a]);
     float* vdst = A.V2 + int64_t(tl.b) * A.v2_tot + A.v2_off[tl.a] + tl.t0 + c;
-    load_a1<KA>(A, tl, n1m, ks1, sA1, c, (warp >> 2) & (2 * NG - 1), 2 * NG);
-    fence_proxy_async();
+    load_a1_tmem<KA>(A, tl, n1m, ks1, tmem + lane_off + kA1, c, (warp >> 2) & (2 * NG - 1), 2 * NG);
+    tmem_st_wait();
+    tc_fence_before();
     mbar_arrive(smem_u32(&ctl->a1_full));
     auto store_v2 = [&](int beta) -> bool {
       const int bj = beta & 1;
@@ -518,7 +473,7 @@ k_freq_tc_fwd(const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ 
   if (threadIdx.x == 0 && *abort) atomicExch(&g_tc_err, 1);
   if (warp == wG1) {
     __syncwarp();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, kCols);
   }
 }
 
@@ -878,7 +833,7 @@ void split_bf16(double v, uint16_t& hi, uint16_t& lo) {
   lo = bf16_rn(static_cast<float>(v - double(bf16_f(hi))));
 }
 
-constexpr int kFwdS1[2] = {2, 6};  // n1max <= 32: two CTAs per SM, so a 2-stage table ring
+constexpr int kFwdS1[2] = {4, 8};  // n1max <= 32: two CTAs per SM
 constexpr int kAdjS1[2] = {6, 6}, kAdjS3[2] = {4, 2}, kAdjNA3[2] = {2, 1};
 
 PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
