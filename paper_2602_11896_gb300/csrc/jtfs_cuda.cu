@@ -1677,6 +1677,47 @@ void prof_end(const Plan& p, int stage, cudaStream_t s) {
   }
 }
 
+// Fork / join of independent launches of one stage: branch k runs on the plan's auxiliary stream k,
+// which waits for the work already on the caller's stream; leaving the scope makes the caller's
+// stream wait for every branch used.  With stage events registered (jtfs_profile_stage) or without
+// auxiliary streams everything stays on the caller's stream, in order.
+class Fork {
+ public:
+  Fork(const Plan& p, cudaStream_t s) : p_(p), s_(s) {
+    bool prof = false;
+    for (const auto& e : p.prof_events) prof = prof || !e.empty();
+    on_ = p.aux[0] && p.aux_mu && !prof;
+    if (on_) {
+      lock_ = std::unique_lock<std::mutex>(*p.aux_mu);
+      on_ = cudaEventRecord(p.ev_fork, s) == cudaSuccess;
+    }
+  }
+  cudaStream_t branch(int k) {
+    if (!on_) return s_;
+    if (!(used_ & (1 << k))) {
+      if (cudaStreamWaitEvent(p_.aux[k], p_.ev_fork, 0) != cudaSuccess) return s_;
+      used_ |= 1 << k;
+    }
+    return p_.aux[k];
+  }
+  void join() {
+    for (int k = 0; k < 3; ++k)
+      if (used_ & (1 << k)) {
+        cudaEventRecord(p_.ev_join[k], p_.aux[k]);
+        cudaStreamWaitEvent(s_, p_.ev_join[k], 0);
+      }
+    used_ = 0;
+  }
+  ~Fork() { join(); }
+
+ private:
+  const Plan& p_;
+  cudaStream_t s_;
+  bool on_ = false;
+  int used_ = 0;
+  std::unique_lock<std::mutex> lock_;
+};
+
 int64_t fft_launches(const Plan& p, const std::vector<FftLaunch>& L) {
   int64_t n = 0;
   int end = -1;
@@ -1872,24 +1913,30 @@ int forward_multi(const Member* m, int n, const FftMerged* merged, bool full, cu
       FA2w.logW = ceil_log2(p.freq_cols_wide);
       const size_t smem_w = ct_smem(p, 3, p.freq_cols_wide, FA2w);
       const size_t smem_n = ct_smem(p, 3, p.freq_cols, FA2n);
-      // Groups with at most 64 rows n1 on the tensor cores, the others on the FFT kernels.
+      // Groups with at most 64 rows n1 on the tensor cores, the others on the FFT kernels; the three
+      // launches touch disjoint groups and run concurrently.
       const bool tc = p.tc_ok && p.tune_tc;
-      if (tc) {
-        prof_begin(p, JTFS_STAGE_FREQ2_FWD_TC, s);
-        JTFS_TRY(tc_forward(p, w.Y2, w.V2, s));
-        prof_end(p, JTFS_STAGE_FREQ2_FWD_TC, s);
+      {
+        Fork fk(p, s);
+        if (tc) {
+          prof_begin(p, JTFS_STAGE_FREQ2_FWD_TC, s);
+          JTFS_TRY(tc_forward(p, w.Y2, w.V2, s, tc_has_groups(p, 1) ? fk.branch(0) : s));
+          prof_end(p, JTFS_STAGE_FREQ2_FWD_TC, s);
+        }
+        const Tile* t2 = tc ? p.d_tiles2_fft : p.d_tiles2;
+        const Tile* t2w = tc ? p.d_tiles2w_fft : p.d_tiles2w;
+        const unsigned n2 = static_cast<unsigned>(tc ? p.tiles2_fft.size() : p.tiles2.size());
+        const unsigned n2w = static_cast<unsigned>(tc ? p.tiles2w_fft.size() : p.tiles2w.size());
+        if (n2 > 0) {
+          const cudaStream_t cs = fk.branch(1);
+          if (p.unpooled_f ||
+              (!(p.tune_wide && launch_freq_fwd_ct(2, FA2w, p.lF, n2w, smem_w, cs, t2w, nullptr, w.Y2, w.V2)) &&
+               !launch_freq_fwd_ct(2, FA2n, p.lF, n2, smem_n, cs, t2, nullptr, w.Y2, w.V2)))
+            k_freq_fwd<2><<<n2, kThreads, freq_smem(p, 3), cs>>>(FA2, t2, nullptr, w.Y2, w.V2);
+        }
+        JTFS_TRY(check_launch());
       }
-      const Tile* t2 = tc ? p.d_tiles2_fft : p.d_tiles2;
-      const Tile* t2w = tc ? p.d_tiles2w_fft : p.d_tiles2w;
-      const unsigned n2 = static_cast<unsigned>(tc ? p.tiles2_fft.size() : p.tiles2.size());
-      const unsigned n2w = static_cast<unsigned>(tc ? p.tiles2w_fft.size() : p.tiles2w.size());
-      if (n2 > 0 &&
-          (p.unpooled_f ||
-           (!(p.tune_wide && launch_freq_fwd_ct(2, FA2w, p.lF, n2w, smem_w, s, t2w, nullptr, w.Y2, w.V2)) &&
-            !launch_freq_fwd_ct(2, FA2n, p.lF, n2, smem_n, s, t2, nullptr, w.Y2, w.V2))))
-        k_freq_fwd<2><<<n2, kThreads, freq_smem(p, 3), s>>>(FA2, t2, nullptr, w.Y2, w.V2);
       prof_end(p, JTFS_STAGE_FREQ2_FWD, s);
-      JTFS_TRY(check_launch());
       if (p.unpooled_t) {  // second-order blocks = V2 (no phi_T)
         JTFS_TRY(copy_block(p, w.V2, p.v2_tot, 0, phi, p.phi_size, p.phi2_base, p.v2_tot, false, s));
         continue;
@@ -1971,29 +2018,45 @@ int backward_multi(const Member* m, int n, const FftMerged* merged, cudaStream_t
       prof_end(p, JTFS_STAGE_POOL_ADJ, s);
       JTFS_TRY(check_launch());
       allow_big_smem<k_freq_adj<2>>();
+      allow_big_smem<k_freq_adj<1>>();
       prof_begin(p, JTFS_STAGE_FREQ2_ADJ, s);
       FreqArgs FA2c = FA2;
       const size_t smem_c = ct_smem(p, 5, p.freq_cols, FA2c);
       const bool tc = p.tc_ok && p.tune_tc;
-      if (tc) {
-        prof_begin(p, JTFS_STAGE_FREQ2_ADJ_TC, s);
-        JTFS_TRY(tc_adjoint(p, w.Y2, w.V2, w.dY2, s));
-        prof_end(p, JTFS_STAGE_FREQ2_ADJ_TC, s);
+      {
+        // The tensor-core groups, the FFT groups and the first-order adjoint (which reads dphi and S1
+        // only) touch disjoint data and run concurrently.
+        Fork fk(p, s);
+        if (tc) {
+          prof_begin(p, JTFS_STAGE_FREQ2_ADJ_TC, s);
+          JTFS_TRY(tc_adjoint(p, w.Y2, w.V2, w.dY2, s, tc_has_groups(p, 1) ? fk.branch(0) : s));
+          prof_end(p, JTFS_STAGE_FREQ2_ADJ_TC, s);
+        }
+        const Tile* t2 = tc ? p.d_tiles2_fft : p.d_tiles2;
+        const unsigned n2 = static_cast<unsigned>(tc ? p.tiles2_fft.size() : p.tiles2.size());
+        if (n2 > 0) {
+          const cudaStream_t cs = fk.branch(1);
+          if (p.unpooled_f ||
+              !launch_freq_adj_ct(2, FA2c, p.lF, n2, smem_c, cs, t2, nullptr, w.Y2, w.V2, nullptr, w.dY2))
+            k_freq_adj<2><<<n2, kThreads, freq_smem(p, 5), cs>>>(FA2, t2, nullptr, w.Y2, w.V2, nullptr, w.dY2);
+        }
+        JTFS_TRY(check_launch());
+        prof_end(p, JTFS_STAGE_FREQ2_ADJ, s);
+        const cudaStream_t s1 = fk.branch(2);
+        if (p.unpooled_f || !launch_freq_adj_ct(1, FA, p.lF, static_cast<unsigned>(p.tiles1.size()),
+                                                freq_smem(p, 5), s1, p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr))
+          k_freq_adj<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 5), s1>>>(
+              FA, p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr);
+        JTFS_TRY(check_launch());
       }
-      const Tile* t2 = tc ? p.d_tiles2_fft : p.d_tiles2;
-      const unsigned n2 = static_cast<unsigned>(tc ? p.tiles2_fft.size() : p.tiles2.size());
-      if (n2 > 0 &&
-          (p.unpooled_f || !launch_freq_adj_ct(2, FA2c, p.lF, n2, smem_c, s, t2, nullptr, w.Y2, w.V2, nullptr, w.dY2)))
-        k_freq_adj<2><<<n2, kThreads, freq_smem(p, 5), s>>>(FA2, t2, nullptr, w.Y2, w.V2, nullptr, w.dY2);
-      prof_end(p, JTFS_STAGE_FREQ2_ADJ, s);
+    } else {
+      allow_big_smem<k_freq_adj<1>>();
+      if (p.unpooled_f || !launch_freq_adj_ct(1, FA, p.lF, static_cast<unsigned>(p.tiles1.size()), freq_smem(p, 5),
+                                              s, p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr))
+        k_freq_adj<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 5), s>>>(
+            FA, p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr);
       JTFS_TRY(check_launch());
     }
-    allow_big_smem<k_freq_adj<1>>();
-    if (p.unpooled_f || !launch_freq_adj_ct(1, FA, p.lF, static_cast<unsigned>(p.tiles1.size()), freq_smem(p, 5), s,
-                                            p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr))
-      k_freq_adj<1><<<static_cast<unsigned>(p.tiles1.size()), kThreads, freq_smem(p, 5), s>>>(
-          FA, p.d_tiles1, w.S1, nullptr, dphi, w.S1, nullptr);
-    JTFS_TRY(check_launch());
   }
   STAGE(false, FS_Y2IP, LdC{w.dY2}, StC{w.dY2});
   STAGE(false, FS_DS1, LdReal{w.S1}, StC{w.dS1h});

@@ -1064,7 +1064,9 @@ void tc_release(Plan& p) {
   p.d_tc = nullptr;
 }
 
-int tc_forward(const Plan& p, const float2* Y2, float* V2, cudaStream_t s) {
+bool tc_has_groups(const Plan& p, int which) { return p.tc_ok && p.tune_tc && !p.tc_tiles[which].empty(); }
+
+int tc_forward(const Plan& p, const float2* Y2, float* V2, cudaStream_t s, cudaStream_t s2) {
   if (!p.tc_ok || !p.tune_tc) return JTFS_OK;
   TcArgs A = tc_args(p);
   A.Y2 = Y2;
@@ -1082,14 +1084,14 @@ int tc_forward(const Plan& p, const float2* Y2, float* V2, cudaStream_t s) {
     constexpr size_t smem = tc_fwd_smem<2, kFwdS1[1]>();
     if (tc_opt_in<k_freq_tc_fwd<2, kFwdS1[1], 2>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
     A.tiles = p.d_tc_tiles[1];
-    k_freq_tc_fwd<2, kFwdS1[1], 2><<<static_cast<unsigned>(p.tc_tiles[1].size()), tc_fwd_threads<2>(), smem, s>>>(
+    k_freq_tc_fwd<2, kFwdS1[1], 2><<<static_cast<unsigned>(p.tc_tiles[1].size()), tc_fwd_threads<2>(), smem, s2>>>(
         p.tc_map[0], p.tc_map[1], A);
     if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
   }
   return JTFS_OK;
 }
 
-int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, cudaStream_t s) {
+int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, cudaStream_t s, cudaStream_t s2) {
   if (!p.tc_ok || !p.tune_tc) return JTFS_OK;
   TcArgs A = tc_args(p);
   A.Y2 = Y2;
@@ -1109,7 +1111,7 @@ int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, c
     if (tc_opt_in<k_freq_tc_adj<2, kAdjS1[1], kAdjS3[1], kAdjNA3[1]>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
     A.tiles = p.d_tc_tiles[1];
     k_freq_tc_adj<2, kAdjS1[1], kAdjS3[1], kAdjNA3[1]>
-        <<<static_cast<unsigned>(p.tc_tiles[1].size()), kTcAdjThreads, smem, s>>>(p.tc_map[0], p.tc_map[2],
+        <<<static_cast<unsigned>(p.tc_tiles[1].size()), kTcAdjThreads, smem, s2>>>(p.tc_map[0], p.tc_map[2],
                                                                                p.tc_map[3], A);
     if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
   }

@@ -4,6 +4,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -284,6 +286,16 @@ struct Plan {
   // Measurement hook (jtfs_profile_stage): events per stage and next index.
   mutable std::vector<void*> prof_events[6];
   mutable int prof_next[6] = {0, 0, 0, 0, 0, 0};
+
+  // The second-order frequential stage's launches are independent of one another (the two tensor-core
+  // kernels, the FFT kernels of the larger groups, the first-order adjoint): they run on auxiliary
+  // streams forked from and joined to the caller's stream by events, created with the plan on its
+  // device (null: the launches stay on the caller's stream).  The mutex orders the event records of
+  // host threads sharing the plan.
+  cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[3] = {nullptr, nullptr, nullptr};
+  std::shared_ptr<std::mutex> aux_mu;
 };
 
 // Host plan construction (jtfs_plan.cpp).  Returns 0 or a JTFS_ERR_* code.
@@ -320,8 +332,10 @@ int tc_upload(Plan& p);
 void tc_release(Plan& p);
 // Launch the second-order forward (V2 from Y2) / adjoint (dY2 from Y2, dV2)
 // on the tensor-core groups; no-ops when the plan has no such group.
-int tc_forward(const Plan& p, const float2* Y2, float* V2, cudaStream_t s);
-int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, cudaStream_t s);
+// The groups with n1max <= 32 run on s, those with 33..64 rows on s2.
+int tc_forward(const Plan& p, const float2* Y2, float* V2, cudaStream_t s, cudaStream_t s2);
+int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, cudaStream_t s, cudaStream_t s2);
+bool tc_has_groups(const Plan& p, int which);  // which = 0: n1max <= 32, 1: 33..64
 
 // Stages of one plan on a caller workspace (jtfs_cuda.cu).  run_forward with
 // full = false computes only what run_backward needs (phi may be NULL);

@@ -545,6 +545,18 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   return JTFS_OK;
 }
 
+void release_streams(Plan& p) {
+  for (int k = 0; k < 3; ++k) {
+    if (p.aux[k]) cudaStreamDestroy(p.aux[k]);
+    if (p.ev_join[k]) cudaEventDestroy(p.ev_join[k]);
+    p.aux[k] = nullptr;
+    p.ev_join[k] = nullptr;
+  }
+  if (p.ev_fork) cudaEventDestroy(p.ev_fork);
+  p.ev_fork = nullptr;
+  p.aux_mu.reset();
+}
+
 int upload_plan(Plan& p) {
   // Twiddles W^k = exp(-2 pi i k / TW) for the largest transform, in double.
   int64_t TW = std::max<int64_t>(p.N, p.N_fr);
@@ -657,6 +669,20 @@ int upload_plan(Plan& p) {
   p.d_cinit = reinterpret_cast<const float*>(at(o_cin));
   p.d_row_off = reinterpret_cast<const int*>(at(o_roff));
   p.on_device = true;
+  // Streams and events of the frequential stage's concurrent launches; without them the launches run
+  // in order on the caller's stream.
+  bool conc = true;
+  for (int k = 0; k < 3; ++k) {
+    conc = conc && cudaStreamCreateWithFlags(&p.aux[k], cudaStreamNonBlocking) == cudaSuccess;
+    conc = conc && cudaEventCreateWithFlags(&p.ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+  }
+  conc = conc && cudaEventCreateWithFlags(&p.ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  if (conc) {
+    p.aux_mu = std::make_shared<std::mutex>();
+  } else {
+    release_streams(p);
+    cudaGetLastError();
+  }
   return tc_upload(p);
 }
 
@@ -667,6 +693,7 @@ void release_plan(Plan& p) {
     if (p.device >= 0 && cur != p.device) cudaSetDevice(p.device);
     cudaFree(p.d_blob);
     tc_release(p);
+    release_streams(p);
     if (cur >= 0 && cur != p.device) cudaSetDevice(cur);
   }
   p.d_blob = nullptr;
