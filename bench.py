@@ -38,15 +38,12 @@ UNIT = "audio-samples/s"
 L2_FLUSH_BYTES = 256 << 20
 # FP32 ALU peak of a GB300 from unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per clip of one launch of the frequential kernels, keyed by profiling
-# stage (0 / 1: FFT forward / adjoint of the groups they keep, 4 / 5: tensor-core forward / adjoint),
-# from an ncu capture of the 1-clip case of this workload (traffic scales with the clips processed).
-# Valid for the kernel versions it was taken on; emptied when those kernels change.
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one clip's launches of each stage (the tensor-core
-# frequential forward = 4 and adjoint = 5, both kernels of a stage summed), from the capture summarised in
-# profiles/top_kernels_chirps22k_b1_n65536.md; the traffic of a launch grows with the clips it processes.
-DRAM_BYTES_PER_CLIP = {4: (10.742016 + 83.440896 + 7.810816 + 0.003072) * 1e6,
-                       5: (155.725312 + 4.509440 + 52.681728 + 0.044032) * 1e6}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one clip's launches of each profiling stage (the
+# tensor-core frequential forward = 4 and adjoint = 5, both kernels of a stage summed), from the capture
+# of the 1-clip case summarised in profiles/top_kernels_chirps22k_b1_n65536.md; the traffic of a launch
+# grows with the clips it processes.  Valid for the kernel versions it was taken on; emptied when those
+# kernels change.
+DRAM_BYTES_PER_CLIP = {5: (155.667968 + 4.582656 + 52.681728 + 0.054272) * 1e6}
 
 
 def bf16_peak():

@@ -1264,11 +1264,13 @@ struct GradArgs {
 // dU1hat[b][n1][m] = (1/L1) [ sum_{n2: n1 < n1max} lev_{psi_n2}(m) dZ2[n2][n1][m mod L2]
 //                             + lev_{phi_T}(m) dS1hat[n1][m mod N/T] ]
 __global__ void __launch_bounds__(kThreads)
-k_dU1(GradArgs A, const Job* __restrict__ jobs, const float2* __restrict__ dZ2,
+k_dU1(GradArgs A, const Job* __restrict__ jobs, const int2* __restrict__ blocks, const float2* __restrict__ dZ2,
       const float2* __restrict__ dS1h, float2* __restrict__ dU1h) {
-  const Job jb = jobs[blockIdx.y];
+  // blocks: (job, block in its row) per block of a 1-D grid; null: a 2-D grid of (block, job).
+  const int2 bk = blocks ? blocks[blockIdx.x] : make_int2(int(blockIdx.y), int(blockIdx.x));
+  const Job jb = jobs[bk.x];
   const int lL1 = jb.lslog, L1 = 1 << lL1;
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = bk.y * blockDim.x + threadIdx.x;
   if (m >= L1) return;
   const int n1 = jb.filt, b = jb.b;
   float2 acc = make_float2(0.f, 0.f);
@@ -2062,13 +2064,12 @@ int backward_multi(const Member* m, int n, const FftMerged* merged, cudaStream_t
   STAGE(false, FS_DS1, LdReal{w.S1}, StC{w.dS1h});
   EACH {
     PLAN;
-    // Every level in one launch: the rows of U1 are consecutive jobs (blocks beyond a row's length return).
+    // Every level in one launch: one block per kThreads samples of every U1 row (the block table).
+    static_assert(kDU1Block == kThreads, "block table built for kThreads-thread blocks");
     const GradArgs GA = grad_args(p);
-    int njobs = 0, maxlog = 0;
-    for (const FftLaunch& l : p.L_u1inplace) njobs += l.njobs, maxlog = std::max(maxlog, l.logn);
-    if (njobs > 0) {
-      const dim3 grid((1u << maxlog) / kThreads + 1, static_cast<unsigned>(njobs));
-      k_dU1<<<grid, kThreads, 0, s>>>(GA, p.d_jobs + p.L_u1inplace.front().job0, w.dY2, w.dS1h, w.U1h);
+    if (!p.du1_blocks.empty()) {
+      k_dU1<<<static_cast<unsigned>(p.du1_blocks.size()), kThreads, 0, s>>>(
+          GA, p.d_jobs + p.L_u1inplace.front().job0, p.d_du1_blocks, w.dY2, w.dS1h, w.U1h);
       JTFS_TRY(check_launch());
     }
   }
@@ -2126,7 +2127,7 @@ int coloured_init_stages(const Plan& p, const float* x, const float* w_noise, fl
   GA1.n_active = 0;  // no second-order term
   for (const FftLaunch& l : p.L_u1inplace) {
     dim3 grid((1u << l.logn) / kThreads + 1, l.njobs);
-    k_dU1<<<grid, kThreads, 0, s>>>(GA1, p.d_jobs + l.job0, nullptr, w.dS1h, w.U1h);
+    k_dU1<<<grid, kThreads, 0, s>>>(GA1, p.d_jobs + l.job0, nullptr, nullptr, w.dS1h, w.U1h);
     JTFS_TRY(check_launch());
   }
   JTFS_TRY((run_fft<true>(p, p.L_u1inplace, LdC{w.U1h}, StC{w.U1h}, w.scr, s)));

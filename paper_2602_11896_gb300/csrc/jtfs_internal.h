@@ -33,6 +33,8 @@ struct FiltD {
 // One FFT of a batched launch: where its input row and output row start
 // (element offsets into the launch's source / destination buffers), which
 // filter its loader applies and log2 of the source row length.
+constexpr int kDU1Block = 256;  // threads per block of the U1-row gradient gather (k_dU1)
+
 struct Job {
   int64_t src;
   int64_t dst;
@@ -250,6 +252,8 @@ struct Plan {
   mutable int tune_tfft = 1;
   std::vector<int4> tf_items;          // (first job, jobs, log2 n, 0) per CTA
   const int4* d_tf_items = nullptr;
+  std::vector<int2> du1_blocks;        // k_dU1: (U1 job - first U1 job, block of kDU1Block in its row)
+  const int2* d_du1_blocks = nullptr;
   const int* d_s2 = nullptr;          // per active index
   const int* d_pool_w = nullptr;      // per active index
   const int4* d_pool_band_tiles = nullptr;

@@ -344,6 +344,13 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
         p.tf_items.push_back(make_int4(l.job0 + j, std::min(per, l.njobs - j), l.logn, 0));
       l.n_items = static_cast<int>(p.tf_items.size()) - l.item0;
     }
+  // Blocks of the U1-row gradient gather (k_dU1): (job relative to the first U1 job, block in the row)
+  // for every row, so one launch covers every level without blocks past a row's end.
+  p.du1_blocks.clear();
+  for (const FftLaunch& l : p.L_u1inplace)
+    for (int j = 0; j < l.njobs; ++j)
+      for (int bx = 0; bx < std::max(1, (1 << l.logn) / kDU1Block); ++bx)
+        p.du1_blocks.push_back(make_int2(l.job0 + j - p.L_u1inplace.front().job0, bx));
 
   // Frequential tiles.
   p.freq_cols = std::max(2, std::min(kFreqCols, 2048 / p.N_fr));  // >= 2: kernels pair columns
@@ -585,6 +592,7 @@ int upload_plan(Plan& p) {
   const size_t o_taps = put(p.h_taps.data(), p.h_taps.size() * sizeof(float));
   const size_t o_jobs = put(p.jobs.data(), p.jobs.size() * sizeof(Job));
   const size_t o_tfi = put(p.tf_items.data(), p.tf_items.size() * sizeof(int4));
+  const size_t o_du1 = put(p.du1_blocks.data(), p.du1_blocks.size() * sizeof(int2));
   const size_t o_t1 = put(p.tiles1.data(), p.tiles1.size() * sizeof(Tile));
   const size_t o_t2 = put(p.tiles2.data(), p.tiles2.size() * sizeof(Tile));
   const size_t o_t2w = put(p.tiles2w.data(), p.tiles2w.size() * sizeof(Tile));
@@ -637,6 +645,7 @@ int upload_plan(Plan& p) {
   p.d_taps = reinterpret_cast<const float*>(at(o_taps));
   p.d_jobs = reinterpret_cast<const Job*>(at(o_jobs));
   p.d_tf_items = reinterpret_cast<const int4*>(at(o_tfi));
+  p.d_du1_blocks = reinterpret_cast<const int2*>(at(o_du1));
   p.d_tiles1 = reinterpret_cast<const Tile*>(at(o_t1));
   p.d_tiles2 = reinterpret_cast<const Tile*>(at(o_t2));
   p.d_tiles2w = reinterpret_cast<const Tile*>(at(o_t2w));
