@@ -2015,8 +2015,15 @@ int backward_multi(const Member* m, int n, const FftMerged* merged, cudaStream_t
           k_pool_adj2<<<static_cast<unsigned>(p.pool_tiles2.size()), kThreads, 0, s>>>(PA, dphi, w.V2,
                                                                                        p.d_pool_tiles2);
       }
-      if (!p.pool_tiles.empty())
-        k_pool_adj<<<static_cast<unsigned>(p.pool_tiles.size()), kThreads, 0, s>>>(PA, dphi, w.V2, p.d_pool_tiles);
+      if (!p.pool_tiles.empty()) {
+        // Banded groups: on the tensor cores where 64 frames cover a tile's reach, the rest on the FMA kernel.
+        const bool tcb = p.tune_pool_tc && !p.pool_tc_band_adj_tiles.empty();
+        if (tcb) JTFS_TRY(pool_tc_band_adjoint(p, dphi, w.V2, s));
+        const auto& bt = tcb ? p.pool_tiles_rest : p.pool_tiles;
+        if (!bt.empty())
+          k_pool_adj<<<static_cast<unsigned>(bt.size()), kThreads, 0, s>>>(PA, dphi, w.V2,
+                                                                          tcb ? p.d_pool_tiles_rest : p.d_pool_tiles);
+      }
       prof_end(p, JTFS_STAGE_POOL_ADJ, s);
       JTFS_TRY(check_launch());
       allow_big_smem<k_freq_adj<2>>();

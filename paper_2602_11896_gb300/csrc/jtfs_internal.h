@@ -33,7 +33,8 @@ struct FiltD {
 // One FFT of a batched launch: where its input row and output row start
 // (element offsets into the launch's source / destination buffers), which
 // filter its loader applies and log2 of the source row length.
-constexpr int kDU1Block = 256;  // threads per block of the U1-row gradient gather (k_dU1)
+constexpr int kDU1Block = 256;
+constexpr int kPoolBandAdjF = 64;  // frames per CTA of the banded tensor-core pooling adjoint  // threads per block of the U1-row gradient gather (k_dU1)
 
 struct Job {
   int64_t src;
@@ -192,6 +193,14 @@ struct Plan {
   // tensor-core banded pooling (clip, group, even 64-row slot, 32-frame block), and the FMA tiles of
   // the other banded groups.
   std::vector<int4> pool_tc_band_tiles, pool_band_rest;
+  bool pool_tc_band_long = false;      // some banded tensor-core window exceeds 4096 + 128 samples
+  // Banded adjoint on the tensor cores: samples per CTA of each active group (0: FMA kernel), its tiles
+  // (clip, group, even 64-row slot, first sample), and the FMA kernel's tiles of the other banded groups.
+  std::vector<int> pool_band_S;
+  std::vector<int4> pool_tc_band_adj_tiles, pool_tiles_rest;
+  const int* d_pool_band_S = nullptr;
+  const int4* d_pool_tc_band_adj_tiles = nullptr;
+  const int4* d_pool_tiles_rest = nullptr;
   const int4* d_pool_tc_band_tiles = nullptr;
   const int4* d_pool_band_rest = nullptr;
   // Frequential tables on the N_fr grid, one row of N_fr floats each:
@@ -314,6 +323,7 @@ void release_plan(Plan& p);
 // (read and cleared).
 bool pool_tc_supported(const Plan& p);   // dense groups (32, 64, 128 frames) or banded tiles on tensor cores
 bool pool_tc_dense(const Plan& p);       // the dense kernels apply (32, 64 or 128 frames)
+int pool_tc_band_adjoint(const Plan& p, const float* dphi, float* dV2, cudaStream_t s);
 // Banded groups on the tensor cores: 32 frames x 128 rows per CTA, Phi written directly.
 int pool_tc_band(const Plan& p, const float* V2, float* phi, cudaStream_t s);
 int pool_tc_forward(const Plan& p, const float* V2, float* part, int si, cudaStream_t s);

@@ -465,6 +465,38 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
         }
       }
   }
+  // Banded adjoint on the tensor cores: a CTA of 128 rows takes S samples and the kPoolBandAdjF frames from
+  // floor((t0 - W) / D), which hold every frame within reach when floor((S - 1 + 2 W) / D) + 2 <= that
+  // count; S is the largest multiple of 128 up to 1024 (and L) that satisfies it.
+  p.pool_band_S.assign(p.n_active, 0);
+  p.pool_tc_band_adj_tiles.clear();
+  p.pool_tiles_rest.clear();
+  if (!p.unpooled_t && p.n_frames >= kPoolBandAdjF) {
+    for (int a = 0; a < p.n_active; ++a) {
+      if (!p.pool_w[a]) continue;
+      const int64_t L = N >> p.s2[a], D = int64_t(1) << (p.lT - p.s2[a]), W = p.pool_w[a];
+      for (int64_t S = std::min<int64_t>(1024, L) / 128 * 128; S >= 128; S -= 128)
+        if ((S - 1 + 2 * W) / D + 2 <= kPoolBandAdjF) {
+          p.pool_band_S[a] = static_cast<int>(S);
+          break;
+        }
+    }
+  }
+  if (!p.unpooled_t) {
+    for (int b = 0; b < B; ++b)
+      for (int a = 0; a < p.n_active; ++a) {
+        if (!p.pool_w[a]) continue;
+        const int L = static_cast<int>(N >> p.s2[a]), S = p.pool_band_S[a];
+        for (int rt = 0; rt < (p.rows2 + 63) / 64; ++rt) {
+          if (S) {
+            if ((rt & 1) == 0)
+              for (int t0 = 0; t0 < L; t0 += S) p.pool_tc_band_adj_tiles.push_back(make_int4(b, a, rt, t0));
+          } else {
+            for (int tt = 0; tt < (L + 63) / 64; ++tt) p.pool_tiles_rest.push_back(make_int4(b, a, rt, tt));
+          }
+        }
+      }
+  }
   // Tensor-core adjoint pooling of the dense groups: 128 rows x 1024 samples per CTA.
   p.pool_tc_adj_tiles.clear();
   if (!p.unpooled_t) {
@@ -478,6 +510,7 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
   }
   p.pool_band_tiles.clear();
   p.pool_tc_band_tiles.clear();
+  p.pool_tc_band_long = false;
   p.pool_band_rest.clear();
   if (!p.unpooled_t) {
     const int rows = p.rows2;
@@ -485,11 +518,11 @@ int build_plan(Plan& p, int64_t N, int J, int Q, int Q2, int J_fr, int Q_fr,
       for (int a = 0; a < p.n_active; ++a) {
         if (!p.pool_w[a]) continue;
         const int64_t L = N >> p.s2[a], D = int64_t(1) << (p.lT - p.s2[a]);
-        // The widened range must fit the circle, and stay as short as a split of the dense path: the tensor
-        // cores' FP32 accumulation over tens of thousands of MMAs drifts (measured 3.7e-4 relative on a
-        // 2.2e5-sample window of the 2^20-sample plan), so long windows keep the FMA kernel.
+        // The widened range must fit the circle (long windows are summed in sub-windows of 4096 samples
+        // inside the kernel, so the FP32 accumulation stays as short as a split of the dense path).
         const int64_t span = 31 * D + 2 * int64_t(p.pool_w[a]) + 128;
-        const bool tc = p.n_frames % 32 == 0 && span <= L && span <= 4096 + 128;
+        const bool tc = p.n_frames % 32 == 0 && span <= L;
+        if (tc && span > 4096 + 128) p.pool_tc_band_long = true;
         for (int rt = 0; rt < (rows + 63) / 64; ++rt)
           for (int fb = 0; fb < (p.n_frames + 31) / 32; ++fb) {
             p.pool_band_tiles.push_back(make_int4(b, a, rt, fb));
@@ -614,6 +647,9 @@ int upload_plan(Plan& p) {
   const size_t o_pw = put(p.pool_w.data(), p.pool_w.size() * sizeof(int));
   const size_t o_pbt = put(p.pool_band_tiles.data(), p.pool_band_tiles.size() * sizeof(int4));
   const size_t o_ptcb = put(p.pool_tc_band_tiles.data(), p.pool_tc_band_tiles.size() * sizeof(int4));
+  const size_t o_pbS = put(p.pool_band_S.data(), p.pool_band_S.size() * sizeof(int));
+  const size_t o_pbat = put(p.pool_tc_band_adj_tiles.data(), p.pool_tc_band_adj_tiles.size() * sizeof(int4));
+  const size_t o_ptr = put(p.pool_tiles_rest.data(), p.pool_tiles_rest.size() * sizeof(int4));
   const size_t o_pbr = put(p.pool_band_rest.data(), p.pool_band_rest.size() * sizeof(int4));
   const size_t o_n1m = put(n1max_act.data(), n1max_act.size() * sizeof(int));
   const size_t o_y2o = put(p.y2_off.data(), p.y2_off.size() * sizeof(int64_t));
@@ -666,6 +702,9 @@ int upload_plan(Plan& p) {
   p.d_pool_w = reinterpret_cast<const int*>(at(o_pw));
   p.d_pool_band_tiles = reinterpret_cast<const int4*>(at(o_pbt));
   p.d_pool_tc_band_tiles = reinterpret_cast<const int4*>(at(o_ptcb));
+  p.d_pool_band_S = reinterpret_cast<const int*>(at(o_pbS));
+  p.d_pool_tc_band_adj_tiles = reinterpret_cast<const int4*>(at(o_pbat));
+  p.d_pool_tiles_rest = reinterpret_cast<const int4*>(at(o_ptr));
   p.d_pool_band_rest = reinterpret_cast<const int4*>(at(o_pbr));
   p.d_n1max_act = reinterpret_cast<const int*>(at(o_n1m));
   p.d_y2_off = reinterpret_cast<const int64_t*>(at(o_y2o));

@@ -55,16 +55,23 @@ struct PtArgs {
   int logN, lT, n_frames, rows, n_active, split_len;
   // Banded groups: reach of phi_T's taps per group, and Phi written directly.
   const int* pool_w;
+  const int* band_S;      // banded adjoint: samples per CTA of each active group
   float* phi;
   int64_t phi_size;
   const int64_t* phi2_off;
 };
 
 struct PtCtl {
-  unsigned long long full[2], empty[2], done;
+  unsigned long long full[2], empty[2], done, sub_full[2], sub_empty[2];
   uint32_t tmem;
   int abort;
 };
+
+// Banded windows are accumulated in sub-windows of kPtSubK blocks (4096 samples), alternating between two
+// TMEM accumulators; the producer warps add each finished sub-window into FP32 registers.  One FP32
+// accumulator taking tens of thousands of MMAs drifts (3.7e-4 relative on a 2.2e5-sample window); sums of
+// at most 4096 samples stay within the dense path's bound.
+constexpr int kPtSubK = 64;
 
 __device__ __forceinline__ bool pt_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
   const uint32_t polls = c_wait_polls;
@@ -82,6 +89,14 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, const uint32_t (&v)[
                : "memory");
 }
 
+__device__ __forceinline__ float ld_shared_f32(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_shared_f32(uint32_t addr, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
 __device__ __forceinline__ float4 ld_shared_v4f(uint32_t addr) {
   float4 v;
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr)
@@ -92,17 +107,20 @@ __device__ __forceinline__ void st_shared_v2(uint32_t addr, const uint32_t (&v)[
   asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(v[0]), "r"(v[1]) : "memory");
 }
 
-template <int F>
+// Banded tiles with long windows (SUBW) add the producers' running sums of finished sub-windows: 16 floats
+// per producer thread.
+template <int F, bool SUBW = false>
 constexpr size_t pt_smem() {
-  return sizeof(PtCtl) + 1024 + 2 * (2 * 16384 + 2 * size_t(F) * 128);
+  return sizeof(PtCtl) + 1024 + 2 * (2 * 16384 + 2 * size_t(F) * 128) + (SUBW ? size_t(kPtProd) * 16 * 4 : 0);
 }
 
 // BAND: a group where phi_T's reach is short against the circle; the CTA
 // computes 32 frames f0 .. f0 + 31 of 128 rows from the samples within reach
 // only (t from f0 D - W to (f0 + 31) D + W, widened to whole 64-sample blocks;
 // the extra samples enter with their own exact taps), read circularly, and
-// writes Phi directly (no split, no reduction).
-template <int F, bool BAND = false>
+// writes Phi directly (no split, no reduction); windows longer than kPtSubK
+// blocks are summed sub-window by sub-window.
+template <int F, bool BAND = false, bool SUBW = false>
 __global__ void __launch_bounds__(kPtThreads, 2)
 k_pool_tc_fwd(const PtArgs A) {
   extern __shared__ uint8_t smem_raw[];
@@ -124,6 +142,9 @@ k_pool_tc_fwd(const PtArgs A) {
     tend = min(L, tbeg + A.split_len);
   }
   const int nkb = (tend - tbeg + kPtK - 1) / kPtK;
+  // Banded: blocks per sub-window (a window of up to kPtSubK + 2 blocks stays one sub-window; without
+  // SUBW every window is one, which the host allows only when none is longer).
+  const int subk = SUBW && nkb > kPtSubK + 2 ? kPtSubK : max(nkb, 1);
   const int nsplit = BAND ? 1 : (L + A.split_len - 1) / A.split_len;
   const int r0 = slot * 64;
   volatile int* abort = &ctl->abort;
@@ -133,15 +154,37 @@ k_pool_tc_fwd(const PtArgs A) {
       mbar_init(smem_u32(&ctl->empty[i]), 1);
     }
     mbar_init(smem_u32(&ctl->done), 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&ctl->sub_full[i]), 1);
+      mbar_init(smem_u32(&ctl->sub_empty[i]), kPtProd);
+    }
     ctl->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == kPtWarpMma) tmem_alloc(smem_u32(&ctl->tmem), F < 32 ? 32 : F);
+  constexpr uint32_t kCols = SUBW ? 2 * F : (F < 32 ? 32 : F);
+  if (warp == kPtWarpMma) tmem_alloc(smem_u32(&ctl->tmem), kCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = ctl->tmem;
   bool issued = false;
+  // Banded: warp w's share of the finished sub-windows (rows 32 (w % 4) + lane, frames w / 4 * F / 2 ..),
+  // summed in this thread's shared-memory slots (element e at word e * kPtProd + tid).
+  constexpr int FH = F / 2;
+  static_assert(!SUBW || (BAND && FH == 16), "sub-windows are for banded tiles of 32 frames");
+  const uint32_t racc = base + 2u * kStage + uint32_t(tid) * 4u;
+  int q_read = 0;  // sub-windows already added into racc
+  auto add_sub = [&](int q) {  // warp-collective: sub-window q's accumulator into racc
+    uint32_t v[16];
+    tmem_ld16_nowait(tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t((q & 1) * F + (warp >> 2) * FH), v);
+    tmem_ld_wait();
+    tmem_regs_ready(v);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const uint32_t a4 = racc + uint32_t(e * kPtProd * 4);
+      st_shared_f32(a4, (q == 0 ? 0.f : ld_shared_f32(a4)) + __uint_as_float(v[e]));
+    }
+  };
 
   if (warp < kPtWarpMma) {
     // Producer: half-warps run along the samples, so each load instruction of a warp reads two rows' 256
@@ -176,6 +219,17 @@ k_pool_tc_fwd(const PtArgs A) {
     for (int kb = 0; kb < nkb; ++kb) {
       const int st = kb & 1;
       const int t0 = tbeg + kb * kPtK;
+      if (SUBW && kb % subk == 2 && kb > subk) {
+        // Sub-window q - 1 is complete once its MMAs are (at most two blocks behind this producer).
+        const int q = kb / subk - 1;
+        const bool okw = __all_sync(0xffffffffu, pt_wait(smem_u32(&ctl->sub_full[q & 1]), (q >> 1) & 1, abort));
+        if (!okw) break;
+        tc_fence_after();
+        add_sub(q);
+        q_read = q + 1;
+        tc_fence_before();
+        mbar_arrive(smem_u32(&ctl->sub_empty[q & 1]));
+      }
       float4 cur[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) cur[c] = nxt[c];
@@ -225,19 +279,25 @@ k_pool_tc_fwd(const PtArgs A) {
     const uint32_t idesc = idesc_bf16_n(F);
     for (int kb = 0; kb < nkb; ++kb) {
       const int st = kb & 1;
+      const int q = SUBW ? kb / subk : 0;
+      const bool first = SUBW ? kb % subk == 0 : kb == 0;
+      // Accumulator q & 1 last held sub-window q - 2: the producers have read it.
+      if (SUBW && first && q >= 2 && !pt_wait(smem_u32(&ctl->sub_empty[q & 1]), ((q - 2) >> 1) & 1, abort)) break;
       if (!pt_wait(smem_u32(&ctl->full[st]), (kb >> 1) & 1, abort)) break;
       tc_fence_after();
       const uint32_t sA = base + uint32_t(st) * kStage;
       const uint64_t ah = sdesc(sA, 16, 1024), al = sdesc(sA + kA, 16, 1024);
       const uint64_t bh = sdesc(sA + 2 * kA, 16, 1024), bl = sdesc(sA + 2 * kA + kB, 16, 1024);
+      const uint32_t d = tmem + uint32_t((q & 1) * F);
 #pragma unroll
       for (int kk = 0; kk < kPtK / 16; ++kk) {
         const uint64_t o = uint64_t(kk) * 2u;  // 32 bytes in 16-byte descriptor units
-        umma_bf16(tmem, ah + o, bh + o, idesc, (kb | kk) != 0);
-        umma_bf16(tmem, al + o, bh + o, idesc, 1);
-        umma_bf16(tmem, ah + o, bl + o, idesc, 1);
+        umma_bf16(d, ah + o, bh + o, idesc, !(first && kk == 0));
+        umma_bf16(d, al + o, bh + o, idesc, 1);
+        umma_bf16(d, ah + o, bl + o, idesc, 1);
       }
       umma_commit(smem_u32(&ctl->empty[st]));
+      if (SUBW && (kb % subk == subk - 1 || kb == nkb - 1)) umma_commit(smem_u32(&ctl->sub_full[q & 1]));
     }
     umma_commit(smem_u32(&ctl->done));  // completes once every issued MMA has completed
   }
@@ -248,7 +308,6 @@ k_pool_tc_fwd(const PtArgs A) {
     tc_fence_after();
     if (all) {
       // Warp w: rows 32 (w % 4) + lane of the tile (its TMEM lanes), frames [w / 4 * F / 2, + F / 2).
-      constexpr int FH = F / 2;
       const int q4 = warp & 3, fh = warp >> 2;
       const int r = r0 + 32 * q4 + lane;
       float4* out;
@@ -261,7 +320,19 @@ k_pool_tc_fwd(const PtArgs A) {
         out = reinterpret_cast<float4*>(A.part + (t * 64 + (r & 63)) * A.n_frames + fh * FH);
       }
       const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(fh * FH);
-      if (FH == 16) {
+      if (SUBW && subk < nkb) {
+        // Every MMA has completed (done): add the sub-windows not yet read.
+        const int nsub = (nkb + subk - 1) / subk;
+        for (int q = q_read; q < nsub; ++q) add_sub(q);
+        if (r < A.rows) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            out[e] = make_float4(ld_shared_f32(racc + uint32_t((4 * e) * kPtProd * 4)),
+                                 ld_shared_f32(racc + uint32_t((4 * e + 1) * kPtProd * 4)),
+                                 ld_shared_f32(racc + uint32_t((4 * e + 2) * kPtProd * 4)),
+                                 ld_shared_f32(racc + uint32_t((4 * e + 3) * kPtProd * 4)));
+        }
+      } else if (FH == 16) {
         uint32_t v[16];
         tmem_ld16_nowait(taddr, v);
         tmem_ld_wait();
@@ -295,7 +366,7 @@ k_pool_tc_fwd(const PtArgs A) {
   if (tid == 0 && *abort) atomicExch(&g_pt_err, 1);
   if (warp == kPtWarpMma) {
     __syncwarp();
-    tmem_dealloc(tmem, F < 32 ? 32 : F);
+    tmem_dealloc(tmem, kCols);
   }
 }
 
@@ -319,8 +390,13 @@ struct PaCtl {
 template <int F>
 __host__ __device__ constexpr uint32_t pa_tile() { return F == 32 ? 16384u : uint32_t(F / 64) * 2u * 16384u; }  // 128 rows, hi + lo
 
-template <int F>
-constexpr size_t pa_smem() { return sizeof(PaCtl) + 1024 + 3 * size_t(pa_tile<F>()) + (F == 32 ? 8 * 4608 : 0); }
+// Tiles that store dV2 through the per-warp transposing tile (8 warps x 32 rows x 36 floats).
+template <int F, bool BAND>
+__host__ __device__ constexpr bool pa_staged() { return F == 32 || BAND; }
+template <int F, bool BAND = false>
+constexpr size_t pa_smem() {
+  return sizeof(PaCtl) + 1024 + 3 * size_t(pa_tile<F>()) + (pa_staged<F, BAND>() ? 8 * 4608 : 0);
+}
 
 // Byte offsets of K-step kk (16 K) inside a hi + lo operand tile.
 template <int F>
@@ -338,7 +414,11 @@ __device__ __forceinline__ uint32_t pa_chunk(uint32_t tile, int row, int c, bool
   return tile + (lo ? uint32_t(F / 64) * 16384u : 0u) + uint32_t(c >> 3) * 16384u + swz128(row, c & 7);
 }
 
-template <int F>
+// BAND: a group where phi_T's reach is short against the circle; the CTA covers band_S[a] samples from
+// t0 (tile.w) and only the F frames fa .. fa + F - 1 (mod n_frames), fa = floor((t0 - W) / D), that
+// can reach them (band_S is chosen so that every frame within reach is among them; the others enter
+// with their exact taps).
+template <int F, bool BAND = false>
 __global__ void __launch_bounds__(kPtThreads)
 k_pool_tc_adj(const PtArgs A, const float* __restrict__ dphi, int64_t phi_size, const int64_t* __restrict__ phi2_off,
               float* __restrict__ dV2) {
@@ -348,10 +428,12 @@ k_pool_tc_adj(const PtArgs A, const float* __restrict__ dphi, int64_t phi_size, 
   const uint32_t base = (smem_u32(smem_raw) + sizeof(PaCtl) + 1023u) & ~1023u;
   const uint32_t sA = base, sB0 = base + kT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
-  const int4 tl = A.tiles[blockIdx.x];  // (clip, active group, first 64-row slot, block of kPtTb samples)
-  const int b = tl.x, a = tl.y, r0 = tl.z * 64, tb0 = tl.w * kPtTb;
+  const int4 tl = A.tiles[blockIdx.x];  // (clip, active group, first 64-row slot, block of kPtTb samples or t0)
+  const int b = tl.x, a = tl.y, r0 = tl.z * 64, tb0 = BAND ? tl.w : tl.w * kPtTb;
   const int s = A.s2[a], L = 1 << (A.logN - s), D = 1 << (A.lT - s);
-  const int nblk = (min(L - tb0, kPtTb) + 127) / 128;
+  const int nblk = (min(L - tb0, BAND ? A.band_S[a] : kPtTb) + 127) / 128;
+  // First frame of the K range: 0, or for banded tiles floor((t0 - W) / D) (t0 - W may be negative).
+  const int fa = BAND ? -((A.pool_w[a] - tb0 + D - 1) >> (A.lT - s)) : 0;
   volatile int* abort = &ctl->abort;
   if (tid == 0) {
     mbar_init(smem_u32(&ctl->a_full), kPtProd);
@@ -385,8 +467,8 @@ k_pool_tc_adj(const PtArgs A, const float* __restrict__ dphi, int64_t phi_size, 
         float v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const int f = 8 * c + e;
-          v[e] = (t < L && f < A.n_frames) ? __ldg(g + ((t - f * D) & (L - 1))) : 0.f;
+          const int f = fa + 8 * c + e;
+          v[e] = (t < L && 8 * c + e < A.n_frames) ? __ldg(g + ((t - f * D) & (L - 1))) : 0.f;
         }
         uint32_t hi[4], lo[4];
 #pragma unroll
@@ -403,7 +485,14 @@ k_pool_tc_adj(const PtArgs A, const float* __restrict__ dphi, int64_t phi_size, 
       const int row = q / (F / 8), c = q % (F / 8);
       const int r = r0 + row;
       float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
-      if (r < A.rows) {
+      if (r < A.rows && BAND) {  // frames fa + 8 c .. + 7, taken mod n_frames
+        const float* src = dp + static_cast<int64_t>(r) * A.n_frames;
+        const int m = A.n_frames - 1, f = fa + 8 * c;
+        x = make_float4(__ldg(src + (f & m)), __ldg(src + ((f + 1) & m)), __ldg(src + ((f + 2) & m)),
+                        __ldg(src + ((f + 3) & m)));
+        y = make_float4(__ldg(src + ((f + 4) & m)), __ldg(src + ((f + 5) & m)), __ldg(src + ((f + 6) & m)),
+                        __ldg(src + ((f + 7) & m)));
+      } else if (r < A.rows) {
         const float4* src = reinterpret_cast<const float4*>(dp + static_cast<int64_t>(r) * A.n_frames + 8 * c);
         x = __ldg(src);
         y = __ldg(src + 1);
@@ -439,7 +528,7 @@ k_pool_tc_adj(const PtArgs A, const float* __restrict__ dphi, int64_t phi_size, 
       for (int h = 0; h < 2; ++h) {
         float v[32];
         tmem_ld32(tmem + (uint32_t(q4 * 32) << 16) + uint32_t(jb * 128 + 64 * hh + 32 * h), v);
-        if (F == 32) {
+        if (pa_staged<F, BAND>()) {
           const int tt = t + 32 * h;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
@@ -523,20 +612,20 @@ cudaError_t pt_opt_in(size_t smem) {
   return cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
 }
 
-template <int F, bool BAND = false>
+template <int F, bool BAND = false, bool SUBW = false>
 int launch_pt(const PtArgs& A, unsigned grid, cudaStream_t s) {
-  constexpr size_t smem = pt_smem<F>();
-  if (pt_opt_in<k_pool_tc_fwd<F, BAND>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
-  k_pool_tc_fwd<F, BAND><<<grid, kPtThreads, smem, s>>>(A);
+  constexpr size_t smem = pt_smem<F, SUBW>();
+  if (pt_opt_in<k_pool_tc_fwd<F, BAND, SUBW>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
+  k_pool_tc_fwd<F, BAND, SUBW><<<grid, kPtThreads, smem, s>>>(A);
   return cudaGetLastError() == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA;
 }
 
-template <int F>
+template <int F, bool BAND = false>
 int launch_pa(const PtArgs& A, const float* dphi, int64_t phi_size, const int64_t* phi2_off, float* dV2,
               unsigned grid, cudaStream_t s) {
-  constexpr size_t smem = pa_smem<F>();
-  if (pt_opt_in<k_pool_tc_adj<F>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
-  k_pool_tc_adj<F><<<grid, kPtThreads, smem, s>>>(A, dphi, phi_size, phi2_off, dV2);
+  constexpr size_t smem = pa_smem<F, BAND>();
+  if (pt_opt_in<k_pool_tc_adj<F, BAND>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
+  k_pool_tc_adj<F, BAND><<<grid, kPtThreads, smem, s>>>(A, dphi, phi_size, phi2_off, dV2);
   return cudaGetLastError() == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA;
 }
 
@@ -565,6 +654,26 @@ int pool_tc_adjoint(const Plan& p, const float* dphi, float* dV2, cudaStream_t s
   }
 }
 
+int pool_tc_band_adjoint(const Plan& p, const float* dphi, float* dV2, cudaStream_t s) {
+  if (p.pool_tc_band_adj_tiles.empty()) return JTFS_OK;
+  PtArgs A{};
+  A.tiles = p.d_pool_tc_band_adj_tiles;
+  A.s2 = p.d_s2;
+  A.v2_off = p.d_v2_off;
+  A.taps = p.d_taps;
+  A.tap_off = p.d_tap_off;
+  A.v2_tot = p.v2_tot;
+  A.logN = p.logN;
+  A.lT = p.lT;
+  A.n_frames = p.n_frames;
+  A.rows = p.rows2;
+  A.n_active = p.n_active;
+  A.pool_w = p.d_pool_w;
+  A.band_S = p.d_pool_band_S;
+  return launch_pa<kPoolBandAdjF, true>(A, dphi, p.phi_size, p.d_phi2_off, dV2,
+                                     static_cast<unsigned>(p.pool_tc_band_adj_tiles.size()), s);
+}
+
 bool pool_tc_dense(const Plan& p) { return p.n_frames == 32 || p.n_frames == 64 || p.n_frames == 128; }
 
 bool pool_tc_supported(const Plan& p) { return pool_tc_dense(p) || !p.pool_tc_band_tiles.empty(); }
@@ -588,7 +697,8 @@ int pool_tc_band(const Plan& p, const float* V2, float* phi, cudaStream_t s) {
   A.phi = phi;
   A.phi_size = p.phi_size;
   A.phi2_off = p.d_phi2_off;
-  return launch_pt<32, true>(A, static_cast<unsigned>(p.pool_tc_band_tiles.size()), s);
+  const unsigned grid = static_cast<unsigned>(p.pool_tc_band_tiles.size());
+  return p.pool_tc_band_long ? launch_pt<32, true, true>(A, grid, s) : launch_pt<32, true, false>(A, grid, s);
 }
 
 int pool_tc_forward(const Plan& p, const float* V2, float* part, int si, cudaStream_t s) {
