@@ -24,7 +24,13 @@
  *   at least jtfs_workspace_bytes(plan) bytes (256-byte aligned).  Its content
  *   on entry is ignored; calls sharing one workspace must not overlap in time.
  * - A plan is immutable after creation and may be shared by several streams
- *   provided each uses its own workspace.
+ *   provided each uses its own workspace.  Besides its tables it owns three
+ *   CUDA streams and four events, created with it on its device: a call forks
+ *   the independent launches of the second-order frequential stage onto those
+ *   streams and joins them back to the caller's stream before the next stage
+ *   (which keeps every call asynchronous and capturable in a CUDA graph); with
+ *   stage events registered (jtfs_profile_stage) the launches stay in order on
+ *   the caller's stream.
  * - Device-side errors: a kernel cannot return a code, so the two failures
  *   only a running kernel sees -- a non-finite loss (JTFS_ERR_NONFINITE) and a
  *   tensor-core barrier wait that ran out (JTFS_ERR_TIMEOUT) -- set a status
