@@ -1738,22 +1738,24 @@ int64_t fft_launches(const Plan& p, const std::vector<FftLaunch>& L) {
 
 // Launches of the second-order frequential stage (forward or adjoint): the
 // tensor-core kernels of the groups they handle plus one FFT-kernel launch.
-int64_t freq2_launches(const Plan& p) {
+int64_t freq2_launches(const Plan& p, bool fwd) {
   if (!(p.tc_ok && p.tune_tc)) return 1;
-  return int64_t(!p.tc_tiles[0].empty()) + int64_t(!p.tc_tiles[1].empty()) + int64_t(!p.tiles2_fft.empty());
+  int64_t n = 0;
+  for (int k = 0; k < (fwd ? 5 : 2); ++k) n += int64_t(!p.tc_tiles[k].empty());
+  return n + int64_t(!(fwd ? p.tiles2_fft_f : p.tiles2_fft).empty());
 }
 
 int64_t forward_launches(const Plan& p, bool full) {
   int64_t n = fft_launches(p, p.L_x) + fft_launches(p, p.L_u1) + fft_launches(p, p.L_u1inplace) + fft_launches(p, p.L_s1);
   if (full) n += (p.unpooled_t ? 1 : fft_launches(p, p.L_s0)) + 1;
-  if (p.n_active > 0) n += fft_launches(p, p.L_y2) + (full ? (p.unpooled_t ? 1 : 2) + freq2_launches(p) : 0);
+  if (p.n_active > 0) n += fft_launches(p, p.L_y2) + (full ? (p.unpooled_t ? 1 : 2) + freq2_launches(p, true) : 0);
   return n;
 }
 
 int64_t backward_launches(const Plan& p) {
   int64_t n = 1 + fft_launches(p, p.L_ds1) + (p.L_u1inplace.empty() ? 0 : 1) +
               2 * fft_launches(p, p.L_u1inplace) + (p.unpooled_t ? 1 : fft_launches(p, p.L_ds0)) + 1 + fft_launches(p, p.L_x);
-  if (p.n_active > 0) n += 1 + freq2_launches(p) + fft_launches(p, p.L_y2inplace);
+  if (p.n_active > 0) n += 1 + freq2_launches(p, false) + fft_launches(p, p.L_y2inplace);
   return n;
 }
 
@@ -1922,13 +1924,15 @@ int forward_multi(const Member* m, int n, const FftMerged* merged, bool full, cu
         Fork fk(p, s);
         if (tc) {
           prof_begin(p, JTFS_STAGE_FREQ2_FWD_TC, s);
-          JTFS_TRY(tc_forward(p, w.Y2, w.V2, s, tc_has_groups(p, 1) ? fk.branch(0) : s));
+          bool more = false;
+          for (int k = 1; k < 5; ++k) more = more || tc_has_groups(p, k);
+          JTFS_TRY(tc_forward(p, w.Y2, w.V2, s, more ? fk.branch(0) : s));
           prof_end(p, JTFS_STAGE_FREQ2_FWD_TC, s);
         }
-        const Tile* t2 = tc ? p.d_tiles2_fft : p.d_tiles2;
-        const Tile* t2w = tc ? p.d_tiles2w_fft : p.d_tiles2w;
-        const unsigned n2 = static_cast<unsigned>(tc ? p.tiles2_fft.size() : p.tiles2.size());
-        const unsigned n2w = static_cast<unsigned>(tc ? p.tiles2w_fft.size() : p.tiles2w.size());
+        const Tile* t2 = tc ? p.d_tiles2_fft_f : p.d_tiles2;
+        const Tile* t2w = tc ? p.d_tiles2w_fft_f : p.d_tiles2w;
+        const unsigned n2 = static_cast<unsigned>(tc ? p.tiles2_fft_f.size() : p.tiles2.size());
+        const unsigned n2w = static_cast<unsigned>(tc ? p.tiles2w_fft_f.size() : p.tiles2w.size());
         if (n2 > 0) {
           const cudaStream_t cs = fk.branch(1);
           if (p.unpooled_f ||

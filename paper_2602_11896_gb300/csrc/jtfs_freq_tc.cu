@@ -72,7 +72,7 @@ struct TcArgs {
 };
 
 struct TcCtl {
-  unsigned long long b1_full[8], b1_empty[8], b2_full[4], b2_empty[4], b3_full[8], b3_empty[8];
+  unsigned long long b1_full[16], b1_empty[16], b2_full[4], b2_empty[4], b3_full[8], b3_empty[8];
   unsigned long long a1_full, d1_full[2], d1_empty[2], a2_full[2], a2_empty[2], d2_full[2], d2_empty[2];
   unsigned long long dv_full[2], dv_empty[2], d3_full, drain[3];
   uint32_t tmem;
@@ -192,9 +192,11 @@ constexpr int kEpiAll = 2 * kGrp;         // epilogue threads
 constexpr int kWarpTma = 16, kWarpG1 = 17, kWarpG2 = 18, kWarpG3 = 19;
 
 __device__ __forceinline__ void init_barriers(TcCtl* ctl, int n_epi) {
-  for (int s = 0; s < 8; ++s) {
+  for (int s = 0; s < 16; ++s) {
     mbar_init(smem_u32(&ctl->b1_full[s]), 1);
     mbar_init(smem_u32(&ctl->b1_empty[s]), 1);
+  }
+  for (int s = 0; s < 8; ++s) {
     mbar_init(smem_u32(&ctl->b3_full[s]), 1);
     mbar_init(smem_u32(&ctl->b3_empty[s]), 1);
   }
@@ -252,8 +254,8 @@ __device__ __forceinline__ TcChunk ld_chunk(const TcChunk* p, int i, int n) {
 // (R_out rows, hi|lo packed in each 128-byte row), A2 2 x 16 KB (|Z| hi|lo
 // packed, one per group).
 // TMEM: D1 2 x 64 columns at 0, D2 2 x 32 columns at 128, A1 (the Y2 tile, as
-// in the adjoint: 32 KA hi + 32 KA lo columns) at 192 (KA = 1, 256 columns in
-// all, two CTAs per SM) or 256 (KA = 2, 512 columns).
+// in the adjoint: 32 KA hi + 32 KA lo columns) at 192: 256 columns in all for
+// KA = 1 (two CTAs per SM), 512 for KA = 2 .. 5 (n1max up to 160).
 // ---------------------------------------------------------------------------
 // Forward threads with NG epilogue groups: 8 NG epilogue warps, then the TMA
 // warp and the two issuing warps.  NG = 1 runs two CTAs per SM (two
@@ -266,7 +268,7 @@ template <int KA, int S1>
 constexpr size_t tc_fwd_smem() {
   return sizeof(TcCtl) + 1024 + size_t(S1) * 16384 + size_t(kS2) * 4096 + 2 * 16384;
 }
-template <int KA> __host__ __device__ constexpr uint32_t fwd_a1_col() { return KA == 1 ? 192u : 256u; }
+template <int KA> __host__ __device__ constexpr uint32_t fwd_a1_col() { return 192u; }
 template <int KA> __host__ __device__ constexpr uint32_t fwd_tmem_cols() { return KA == 1 ? 256u : 512u; }
 
 template <int KA, int S1, int NG>
@@ -834,6 +836,9 @@ void split_bf16(double v, uint16_t& hi, uint16_t& lo) {
 }
 
 constexpr int kFwdS1[2] = {4, 8};  // n1max <= 32: two CTAs per SM
+constexpr int kFwdS1Wide[4] = {8, 9, 8, 10};  // table ring stages for KA = 2 .. 5 (>= 2 chunks of KA atoms)
+constexpr int kTcMaxKA = 5;
+constexpr int kTcWideMinTiles = 148;  // tiles (one per SM) a group with KA >= 3 needs to take the tensor cores
 constexpr int kAdjS1[2] = {6, 6}, kAdjS3[2] = {4, 2}, kAdjNA3[2] = {2, 1};
 
 PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
@@ -890,26 +895,31 @@ cudaError_t tc_opt_in(size_t smem) {
 void tc_build(Plan& p) {
   p.tc_ok = false;
   p.tc_chunks.clear();
-  p.tc_tiles[0].clear();
-  p.tc_tiles[1].clear();
+  for (auto& t : p.tc_tiles) t.clear();
   p.tc_b1.clear();
   p.tc_b2.clear();
   p.tc_b2t.clear();
   p.tc_b3.clear();
-  p.tiles2_fft = p.tiles2;
-  p.tiles2w_fft = p.tiles2w;
+  p.tiles2_fft = p.tiles2_fft_f = p.tiles2;
+  p.tiles2w_fft = p.tiles2w_fft_f = p.tiles2w;
   const int RO = p.R_out, NF = p.N_fr;
   if (p.n_active == 0 || (RO != 16 && RO != 32) || NF < 64 || NF > 1024) return;
   if (p.unpooled_f) return;  // the GEMM tables include the phi_F averaging
+  // K atoms of A1 per group: the forward takes n1max <= 160 (KA <= 5), the adjoint n1max <= 64 (KA <= 2:
+  // its D3 of 2 n1max TMEM columns and the rest leave no room for more).
   std::vector<int> ka(p.n_active, 0);
-  bool any = false;
+  int ka_max = 0;
   for (int a = 0; a < p.n_active; ++a) {
     const int n1 = p.n1max[p.active[a]];
     const int64_t L2 = p.N >> p.s2[a];
-    ka[a] = L2 < kTcM ? 0 : n1 <= 32 ? 1 : n1 <= 64 ? 2 : 0;
-    any = any || ka[a] > 0;
+    ka[a] = L2 < kTcM || n1 > 32 * kTcMaxKA ? 0 : (n1 + 31) / 32;
+    // A wide group runs 3-5x the MMAs per tile of a KA = 1 group; with fewer tiles than SMs its few long
+    // CTAs are slower than the FFT kernels' many short ones (measured on the 8 x 2^16 chirp plan).
+    if (ka[a] >= 3 && int64_t(p.batch) * L2 < int64_t(kTcWideMinTiles) * kTcM) ka[a] = 0;
+    ka_max = std::max(ka_max, ka[a]);
   }
-  if (!any) return;
+  if (!ka_max) return;
+  auto ka_adj = [&](int a) { return ka[a] <= 2 ? ka[a] : 0; };
 
   // Chunks of up to 32 rows per filter, in filter order.
   std::vector<int> rowP(p.lF + 2, 0);
@@ -944,13 +954,15 @@ void tc_build(Plan& p) {
       hi[size_t(b) * NF + t] = si / NF;
     }
   }
-  // GEMM1 table B1 [(beta, r, re/im)][(n, re/im)], n < 64: [Zr, Zi] = Yr [Hr, Hi] + Yi [-Hi, Hr].
-  p.tc_b1.assign(size_t(2) * nr1 * 128, 0);
+  // GEMM1 table B1 [(beta, r, re/im)][(n, re/im)], n < W1 / 2: [Zr, Zi] = Yr [Hr, Hi] + Yi [-Hi, Hr].
+  const int W1 = 64 * std::max(2, ka_max);
+  p.tc_w1 = W1;
+  p.tc_b1.assign(size_t(2) * nr1 * W1, 0);
   p.tc_b3.assign(size_t(256) * nr1, 0);
   for (int b = 0; b < p.n_beta2; ++b) {
     const int k = p.beta_k[b], R = NF >> k;
     for (int r = 0; r < R; ++r)
-      for (int n = 0; n < 64; ++n) {
+      for (int n = 0; n < W1 / 2; ++n) {
         const int t = (((r << k) - n) % NF + NF) % NF;
         const double vr = hr[size_t(b) * NF + t], vi = hi[size_t(b) * NF + t];
         const int row = 2 * (rowB[b] + r);
@@ -960,10 +972,12 @@ void tc_build(Plan& p) {
             uint16_t h16, l16;
             split_bf16(v[x][y], h16, l16);
             const int rr = row + x, cc = 2 * n + y;
-            p.tc_b1[size_t(rr) * 128 + cc] = h16;
-            p.tc_b1[size_t(nr1 + rr) * 128 + cc] = l16;
-            p.tc_b3[size_t(cc) * nr1 + rr] = h16;          // transposed: rows (n, y), columns (r, x)
-            p.tc_b3[size_t(128 + cc) * nr1 + rr] = l16;
+            p.tc_b1[size_t(rr) * W1 + cc] = h16;
+            p.tc_b1[size_t(nr1 + rr) * W1 + cc] = l16;
+            if (n < 64) {
+              p.tc_b3[size_t(cc) * nr1 + rr] = h16;          // transposed: rows (n, y), columns (r, x)
+              p.tc_b3[size_t(128 + cc) * nr1 + rr] = l16;
+            }
           }
       }
   }
@@ -995,10 +1009,16 @@ void tc_build(Plan& p) {
   // Tiles of 128 columns for the tensor-core groups; the FFT kernels keep the others.
   p.tiles2_fft.clear();
   p.tiles2w_fft.clear();
-  for (const Tile& t : p.tiles2)
-    if (!ka[t.a]) p.tiles2_fft.push_back(t);
-  for (const Tile& t : p.tiles2w)
-    if (!ka[t.a]) p.tiles2w_fft.push_back(t);
+  p.tiles2_fft_f.clear();
+  p.tiles2w_fft_f.clear();
+  for (const Tile& t : p.tiles2) {
+    if (!ka_adj(t.a)) p.tiles2_fft.push_back(t);
+    if (!ka[t.a]) p.tiles2_fft_f.push_back(t);
+  }
+  for (const Tile& t : p.tiles2w) {
+    if (!ka_adj(t.a)) p.tiles2w_fft.push_back(t);
+    if (!ka[t.a]) p.tiles2w_fft_f.push_back(t);
+  }
   for (int b = 0; b < p.batch; ++b)
     for (int a = 0; a < p.n_active; ++a) {
       if (!ka[a]) continue;
@@ -1024,10 +1044,12 @@ int tc_upload(Plan& p) {
   const size_t o_b2t = put(p.tc_b2t.data(), p.tc_b2t.size() * 2);
   const size_t o_b3 = put(p.tc_b3.data(), p.tc_b3.size() * 2);
   const size_t o_ch = put(p.tc_chunks.data(), p.tc_chunks.size() * sizeof(TcChunk));
-  const size_t o_t0 = put(p.tc_tiles[0].data(), p.tc_tiles[0].size() * sizeof(Tile));
-  const size_t o_t1 = put(p.tc_tiles[1].data(), p.tc_tiles[1].size() * sizeof(Tile));
+  size_t o_t[5];
+  for (int k = 0; k < 5; ++k) o_t[k] = put(p.tc_tiles[k].data(), p.tc_tiles[k].size() * sizeof(Tile));
   const size_t o_f = put(p.tiles2_fft.data(), p.tiles2_fft.size() * sizeof(Tile));
   const size_t o_fw = put(p.tiles2w_fft.data(), p.tiles2w_fft.size() * sizeof(Tile));
+  const size_t o_ff = put(p.tiles2_fft_f.data(), p.tiles2_fft_f.size() * sizeof(Tile));
+  const size_t o_ffw = put(p.tiles2w_fft_f.data(), p.tiles2w_fft_f.size() * sizeof(Tile));
   void* blob = nullptr;
   if (cudaMalloc(&blob, total) != cudaSuccess) return JTFS_ERR_NOMEM;
   std::vector<unsigned char> host(total, 0);
@@ -1040,11 +1062,12 @@ int tc_upload(Plan& p) {
   unsigned char* at = static_cast<unsigned char*>(blob);
   p.d_tc = blob;
   p.d_tc_chunks = reinterpret_cast<const TcChunk*>(at + o_ch);
-  p.d_tc_tiles[0] = reinterpret_cast<const Tile*>(at + o_t0);
-  p.d_tc_tiles[1] = reinterpret_cast<const Tile*>(at + o_t1);
+  for (int k = 0; k < 5; ++k) p.d_tc_tiles[k] = reinterpret_cast<const Tile*>(at + o_t[k]);
   p.d_tiles2_fft = reinterpret_cast<const Tile*>(at + o_f);
   p.d_tiles2w_fft = reinterpret_cast<const Tile*>(at + o_fw);
-  const bool ok = make_map(&p.tc_map[0], at + o_b1, 128, uint64_t(2) * p.tc_nr1, 64) &&
+  p.d_tiles2_fft_f = reinterpret_cast<const Tile*>(at + o_ff);
+  p.d_tiles2w_fft_f = reinterpret_cast<const Tile*>(at + o_ffw);
+  const bool ok = make_map(&p.tc_map[0], at + o_b1, uint64_t(p.tc_w1), uint64_t(2) * p.tc_nr1, 64) &&
                   make_map(&p.tc_map[1], at + o_b2, p.tc_kp2, uint64_t(p.lF + 1) * p.R_out, p.R_out) &&
                   make_map(&p.tc_map[2], at + o_b2t, 64, p.tc_np2, 32) &&
                   make_map(&p.tc_map[3], at + o_b3, p.tc_nr1, 256, 64);
@@ -1053,8 +1076,8 @@ int tc_upload(Plan& p) {
     cudaFree(blob);
     p.d_tc = nullptr;
     p.tc_ok = false;
-    p.tiles2_fft = p.tiles2;
-    p.tiles2w_fft = p.tiles2w;
+    p.tiles2_fft = p.tiles2_fft_f = p.tiles2;
+    p.tiles2w_fft = p.tiles2w_fft_f = p.tiles2w;
   }
   return JTFS_OK;
 }
@@ -1065,6 +1088,20 @@ void tc_release(Plan& p) {
 }
 
 bool tc_has_groups(const Plan& p, int which) { return p.tc_ok && p.tune_tc && !p.tc_tiles[which].empty(); }
+
+// Forward tiles of the groups with KA > 1 (one CTA per SM, two epilogue groups, 512 TMEM columns).
+template <int KA>
+int launch_fwd_wide(const Plan& p, TcArgs A, cudaStream_t s) {
+  if (p.tc_tiles[KA - 1].empty()) return JTFS_OK;
+  constexpr int S1 = kFwdS1Wide[KA - 2];
+  constexpr size_t smem = tc_fwd_smem<KA, S1>();
+  static_assert(smem + 1024 <= 227 * 1024 && S1 <= 16 && fwd_a1_col<KA>() + 64 * KA <= 512, "forward budget");
+  if (tc_opt_in<k_freq_tc_fwd<KA, S1, 2>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
+  A.tiles = p.d_tc_tiles[KA - 1];
+  k_freq_tc_fwd<KA, S1, 2><<<static_cast<unsigned>(p.tc_tiles[KA - 1].size()), tc_fwd_threads<2>(), smem, s>>>(
+      p.tc_map[0], p.tc_map[1], A);
+  return cudaGetLastError() == cudaSuccess ? JTFS_OK : JTFS_ERR_CUDA;
+}
 
 int tc_forward(const Plan& p, const float2* Y2, float* V2, cudaStream_t s, cudaStream_t s2) {
   if (!p.tc_ok || !p.tune_tc) return JTFS_OK;
@@ -1080,15 +1117,13 @@ int tc_forward(const Plan& p, const float2* Y2, float* V2, cudaStream_t s, cudaS
         p.tc_map[0], p.tc_map[1], A);
     if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
   }
-  if (!p.tc_tiles[1].empty()) {
-    constexpr size_t smem = tc_fwd_smem<2, kFwdS1[1]>();
-    if (tc_opt_in<k_freq_tc_fwd<2, kFwdS1[1], 2>>(smem) != cudaSuccess) return JTFS_ERR_CUDA;
-    A.tiles = p.d_tc_tiles[1];
-    k_freq_tc_fwd<2, kFwdS1[1], 2><<<static_cast<unsigned>(p.tc_tiles[1].size()), tc_fwd_threads<2>(), smem, s2>>>(
-        p.tc_map[0], p.tc_map[1], A);
-    if (cudaGetLastError() != cudaSuccess) return JTFS_ERR_CUDA;
-  }
-  return JTFS_OK;
+  // The wider groups, one after another on s2.
+  int rc = JTFS_OK;
+  if (rc == JTFS_OK) rc = launch_fwd_wide<2>(p, A, s2);
+  if (rc == JTFS_OK) rc = launch_fwd_wide<3>(p, A, s2);
+  if (rc == JTFS_OK) rc = launch_fwd_wide<4>(p, A, s2);
+  if (rc == JTFS_OK) rc = launch_fwd_wide<5>(p, A, s2);
+  return rc;
 }
 
 int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, cudaStream_t s, cudaStream_t s2) {
@@ -1159,10 +1194,12 @@ extern "C" int64_t jtfs_tc_table(jtfs_plan_t plan, int which, float* out, int64_
     std::memcpy(&v, &u, 4);
     return v;
   };
-  if (which == 0) {
-    const int64_t total = int64_t(p.tc_nr1) * 128;
-    for (int64_t i = 0; out && i < std::min(n, total); ++i)
-      out[i] = f(p.tc_b1[size_t(i)]) + f(p.tc_b1[size_t(total + i)]);
+  if (which == 0) {  // the first 128 columns (n < 64) of each row of the GEMM1 table
+    const int64_t total = int64_t(p.tc_nr1) * 128, W1 = p.tc_w1, half = int64_t(p.tc_nr1) * W1;
+    for (int64_t i = 0; out && i < std::min(n, total); ++i) {
+      const int64_t o = (i / 128) * W1 + i % 128;
+      out[i] = f(p.tc_b1[size_t(o)]) + f(p.tc_b1[size_t(half + o)]);
+    }
     return total;
   }
   const int RO = p.R_out, NF = p.N_fr;

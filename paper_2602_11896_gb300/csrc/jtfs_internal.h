@@ -286,14 +286,20 @@ struct Plan {
   int tc_nr1 = 0, tc_kp2 = 0, tc_np2 = 0;
   std::vector<uint16_t> tc_b1, tc_b2, tc_b2t, tc_b3;
   std::vector<TcChunk> tc_chunks;
-  std::vector<Tile> tc_tiles[2];
-  std::vector<Tile> tiles2_fft, tiles2w_fft;
+  // Tiles of the tensor-core groups by K atoms of A1 (KA = 1 .. 5: n1max <= 32, 64, 96, 128, 160); the
+  // adjoint takes KA <= 2. The FFT kernels keep the other groups: of the adjoint (tiles2_fft, wide
+  // tiles2w_fft) and of the forward (the _f lists).
+  std::vector<Tile> tc_tiles[5];
+  std::vector<Tile> tiles2_fft, tiles2w_fft, tiles2_fft_f, tiles2w_fft_f;
+  int tc_w1 = 128;                     // columns (n, re/im) of the GEMM1 table
   mutable int tune_tc = 1;
   void* d_tc = nullptr;
   const TcChunk* d_tc_chunks = nullptr;
-  const Tile* d_tc_tiles[2] = {nullptr, nullptr};
+  const Tile* d_tc_tiles[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   const Tile* d_tiles2_fft = nullptr;
   const Tile* d_tiles2w_fft = nullptr;
+  const Tile* d_tiles2_fft_f = nullptr;
+  const Tile* d_tiles2w_fft_f = nullptr;
   CUtensorMap tc_map[4];  // GEMM1 table, forward pooling, adjoint pooling, GEMM1 transposed
 
   // Measurement hook (jtfs_profile_stage): events per stage and next index.
@@ -349,7 +355,7 @@ void tc_release(Plan& p);
 // The groups with n1max <= 32 run on s, those with 33..64 rows on s2.
 int tc_forward(const Plan& p, const float2* Y2, float* V2, cudaStream_t s, cudaStream_t s2);
 int tc_adjoint(const Plan& p, const float2* Y2, const float* dV2, float2* dY2, cudaStream_t s, cudaStream_t s2);
-bool tc_has_groups(const Plan& p, int which);  // which = 0: n1max <= 32, 1: 33..64
+bool tc_has_groups(const Plan& p, int which);  // which = KA - 1: n1max <= 32, 33..64, .., 129..160
 
 // Stages of one plan on a caller workspace (jtfs_cuda.cu).  run_forward with
 // full = false computes only what run_backward needs (phi may be NULL);
