@@ -43,8 +43,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # of the 1-clip case summarised in profiles/top_kernels_chirps22k_b1_n65536.md; the traffic of a launch
 # grows with the clips it processes.  Valid for the kernel versions it was taken on; emptied when those
 # kernels change.
-DRAM_BYTES_PER_CLIP = {4: (10.637824 + 83.553792 + 7.814400 + 0.016896) * 1e6,
-                       5: (155.667968 + 4.582656 + 52.681728 + 0.054272) * 1e6}
+DRAM_BYTES_PER_CLIP = {4: (10.712064 + 83.598592 + 7.814400 + 0.015616) * 1e6,
+                       5: (155.660800 + 4.626432 + 52.681216 + 0.058880) * 1e6}
 
 
 def bf16_peak():
