@@ -5,7 +5,7 @@ The oracle cannot evaluate the whole transform at 2^20 in test time, so:
 * at full size, in the launch configuration of the long-signal benchmark: S0, every first-order row and
   two sampled second-order paths of one clip against the oracle, every path of the finest second-order
   level at two frames (the oracle evaluated at those frames only), the adjoint on S0, the first order and
-  the coarsest second-order group, and the shift-by-T property.
+  three second-order groups (coarsest, middle, level 11), and the shift-by-T property.
 """
 
 import numpy as np
@@ -130,35 +130,39 @@ def test_full_size_finest_level_against_oracle(full):
 
 def test_full_size_gradient_on_sampled_paths(full):
     """The adjoint at full size (4 x 2^20, the long benchmark's plan): J^T w for weights w on S0, every
-    first-order path and the coarsest second-order group of clip 0 (zero elsewhere), against the oracle's
+    first-order path and three second-order groups of clip 0 (zero elsewhere), against the oracle's
     autograd of the same linear functional of those outputs (FP64; the rest of the transform is not
-    evaluated).  Exercises the full-size first-layer adjoint (2^20-point transforms, k_dU1, k_dX) and one
-    second-order group's adjoint chain."""
+    evaluated).  Exercises the full-size first-layer adjoint (2^20-point transforms, k_dU1, k_dX) and the
+    second-order adjoint chain of a coarsest group (banded phi_T adjoint on the FMA kernel), a middle one
+    and one of the level-11 groups (banded phi_T adjoint on the tensor cores: 1024 and 128 samples per
+    CTA, D = 64 and 4)."""
     plan, x, phi, _, _, _ = full
     ref_plan = O.Plan(**WL.params)
     s2 = [min(ref_plan.psi2[n2].j, ref_plan.lT) for n2 in ref_plan.active]
-    a = int(np.argmax(s2))
+    order = np.argsort(s2, kind="stable")
+    sample = [int(order[-1]), int(order[len(order) // 2]), int(order[-5])]
     y = WL.inits()
     yt = torch.tensor(y[:1], dtype=torch.float64, requires_grad=True)
-    out = O.jtfs(yt, ref_plan, active=[a])
+    out = O.jtfs(yt, ref_plan, active=sample)
     nf = out["S0"][0].numel()
     n_first = out["Phi1"][0].numel()
-    blk = out["Phi2_sel"][a][0].numel()
     n2 = (plan.phi_size - nf - n_first) // len(ref_plan.active)
-    assert n2 == blk
-    off2 = nf + n_first + a * n2
     rng = np.random.default_rng(77)
     w_s0 = rng.standard_normal(nf)
     w_1 = rng.standard_normal(n_first)
-    w_2 = rng.standard_normal(blk)
     dphi = np.zeros((WL.batch, plan.phi_size), dtype=np.float32)
     dphi[0, :nf] = w_s0
     dphi[0, nf:nf + n_first] = w_1
-    dphi[0, off2:off2 + blk] = w_2
-    dx = plan.backward(torch.tensor(y, device="cuda"), torch.tensor(dphi, device="cuda"))[0].cpu().numpy()
     f = ((out["S0"][0].reshape(-1) * torch.tensor(w_s0)).sum()
-         + (out["Phi1"][0].reshape(-1) * torch.tensor(w_1)).sum()
-         + (out["Phi2_sel"][a][0].reshape(-1) * torch.tensor(w_2)).sum())
+         + (out["Phi1"][0].reshape(-1) * torch.tensor(w_1)).sum())
+    for a in sample:
+        blk = out["Phi2_sel"][a][0].numel()
+        assert n2 == blk
+        w_2 = rng.standard_normal(blk)
+        off2 = nf + n_first + a * n2
+        dphi[0, off2:off2 + blk] = w_2
+        f = f + (out["Phi2_sel"][a][0].reshape(-1) * torch.tensor(w_2)).sum()
+    dx = plan.backward(torch.tensor(y, device="cuda"), torch.tensor(dphi, device="cuda"))[0].cpu().numpy()
     f.backward()
     assert _rel(dx, yt.grad[0].numpy()) <= TOL
 
