@@ -171,6 +171,25 @@ int jtfs_plan_filters(jtfs_plan_t plan, int which, double* xi, double* sigma,
                       int32_t* j, int count);
 
 /*
+ * jtfs_plan_schedule copies one of the plan's work tables, for inspection
+ * and tests (the paper has no counterpart: these are this library's launch
+ * schedules), as int64 into out[0 .. min(n, size)) (host memory) and returns
+ * the table's size in values (call with out = NULL, n = 0 to size it):
+ *   which = 0: the gradient gather onto the U1 rows, per block of 256
+ *              samples: (row, block in the row, log2 of the row's length);
+ *   which = 1: the banded phi_T adjoint on the tensor cores, per CTA:
+ *              (clip, active group, first of its 128 rows, first sample);
+ *   which = 2: per active second-order group: (level s2, rows, n1max,
+ *              reach W of the banded phi_T average or 0 when dense, samples
+ *              per CTA of its tensor-core banded adjoint or 0, K atoms of its
+ *              tensor-core frequential forward or 0 for the FFT kernels, the
+ *              same for the adjoint).
+ * Works on host-only plans.  Errors: JTFS_ERR_ARG (NULL plan, bad which,
+ * n < 0, out NULL with n > 0).
+ */
+int64_t jtfs_plan_schedule(jtfs_plan_t plan, int which, int64_t* out, int64_t n);
+
+/*
  * Forward transform, Eqs. (1)-(5) with the multirate schedule of §3.2-§3.5:
  *   x   [batch][N] float32 (device), real audio clips.
  *   phi [batch][phi_size] float32 (device), output, layout as above.

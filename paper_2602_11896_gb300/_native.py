@@ -26,6 +26,7 @@ SIGNATURES = {
     "jtfs_plan_info": (c_int, [c_void_p, POINTER(c_int64), c_int]),
     "jtfs_plan_filters": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_double),
                                   POINTER(c_int32), c_int]),
+    "jtfs_plan_schedule": (c_int64, [c_void_p, c_int, POINTER(c_int64), c_int64]),
     "jtfs_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "jtfs_coloured_init": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "jtfs_init_gains": (c_int64, [c_void_p, POINTER(c_float), c_int64]),

@@ -824,6 +824,38 @@ extern "C" int jtfs_plan_info(jtfs_plan_t plan, int64_t* info, int count) {
   return 19;
 }
 
+extern "C" int64_t jtfs_plan_schedule(jtfs_plan_t plan, int which, int64_t* out, int64_t n) {
+  if (!plan || n < 0 || (n > 0 && !out)) return JTFS_ERR_ARG;
+  const jtfs::Plan& p = plan->p;
+  std::vector<int64_t> v;
+  switch (which) {
+    case 0:  // U1-row gradient gather: (row, block, log2 row length) per block
+      for (const int2& e : p.du1_blocks)
+        v.insert(v.end(), {e.x, e.y, p.jobs[size_t(p.L_u1inplace.front().job0 + e.x)].lslog});
+      break;
+    case 1:  // banded phi_T adjoint on the tensor cores: (clip, group, first row, first sample) per CTA
+      for (const int4& t : p.pool_tc_band_adj_tiles) v.insert(v.end(), {t.x, t.y, int64_t(t.z) * 64, t.w});
+      break;
+    case 2:  // per active group: s2, rows, n1max, reach W (0: dense pooling), band samples per CTA (0: FMA),
+             // forward tensor-core K atoms (0: FFT kernels), adjoint tensor-core K atoms (0: FFT kernels)
+      for (int a = 0; a < p.n_active; ++a) {
+        int kf = 0, kb = 0;
+        for (int k = 0; k < 5; ++k)
+          for (const jtfs::Tile& t : p.tc_tiles[k])
+            if (t.a == a) kf = k + 1;
+        for (int k = 0; k < 2; ++k)
+          for (const jtfs::Tile& t : p.tc_tiles[k])
+            if (t.a == a) kb = k + 1;
+        v.insert(v.end(), {p.s2[a], p.rows2, p.n1max[p.active[a]], p.pool_w[a], p.pool_band_S[a], kf, kb});
+      }
+      break;
+    default:
+      return JTFS_ERR_ARG;
+  }
+  for (int64_t i = 0; i < n && i < int64_t(v.size()); ++i) out[i] = v[size_t(i)];
+  return static_cast<int64_t>(v.size());
+}
+
 extern "C" int jtfs_plan_filters(jtfs_plan_t plan, int which, double* xi, double* sigma,
                                  int32_t* j, int count) {
   if (!plan) return JTFS_ERR_ARG;

@@ -95,6 +95,16 @@ class JTFSPlan:
         out["offset"] = np.array(off[:], dtype=np.int64)
         return out
 
+    def schedule(self, which: int) -> np.ndarray:
+        """One of the plan's work tables (see jtfs_plan_schedule): which = 0 U1-row gradient blocks
+        [n][row, block, log2 length]; 1 banded phi_T adjoint CTAs [n][clip, group, first row, first sample];
+        2 per active group [n_active][s2, rows, n1max, W, band samples per CTA, forward KA, adjoint KA]."""
+        n = int(self._lib.jtfs_plan_schedule(self._h, which, None, 0))
+        _native.check(0 if n >= 0 else n, "jtfs_plan_schedule")
+        buf = (c_int64 * max(n, 1))()
+        self._lib.jtfs_plan_schedule(self._h, which, buf, n)
+        return np.array(buf[:n], dtype=np.int64).reshape(-1, (3, 4, 7)[which])
+
     # -- tuning -----------------------------------------------------------
     def tuning(self) -> Tuple[int, int, int, int, int, int]:
         """(wide forward tiles, pooling split, small-FFT points per CTA, tensor-core frequential path,
