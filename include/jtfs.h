@@ -17,9 +17,10 @@
  *   row-major; pointers to float data must be 16-byte aligned.  The library
  *   never frees or retains them beyond the call.
  * - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
- *   stream).  Every compute call only enqueues work on that stream and returns
- *   without synchronising; errors that only a finished kernel can reveal are
- *   not reported by the call.
+ *   stream).  Every compute call only enqueues work, ordered on that stream
+ *   (some of it on the plan's own streams, forked from and joined back to it,
+ *   see below), and returns without synchronising; errors that only a
+ *   finished kernel can reveal are not reported by the call.
  * - Workspace: compute calls need a caller-allocated device scratch buffer of
  *   at least jtfs_workspace_bytes(plan) bytes (256-byte aligned).  Its content
  *   on entry is ignored; calls sharing one workspace must not overlap in time.
